@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Throughput of rpCholesky-QR (Garrison & Ipsen, arXiv 2406.11751, Algorithm alg_2) on GB300.
+
+One step = one full rpcholqr_factor call (sample + Householder R_s + fused preconditioning/Gram
+pass + Cholesky + second pass + R recovery) on an m x n FP64 matrix resident in HBM.
+
+Default workload: m = 2^20, n = 128, s = 3n = 384, A = U diag(sigma) V^T with sigma log-spaced
+from 1 to 1e-8 (kappa = 1e8), U, V Haar.  A (1.07 GB) is larger than L2, so consecutive steps do
+not reuse cached inputs.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only "reference" this project has: the paper
+ships no code) on the host cores, on a bounded row sample of the same workload.
+Under torchrun (N > 1) every rank factors its own matrix (independent problems, weak scaling,
+no collective on the data path); rank 0 prints the aggregate over max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TS-QR matrices/s & effective TFLOP/s at ||Q^T Q - I||_2 <= 1e-13; % of roofline"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--m", type=int, default=1 << 20)
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--s", type=int, default=None, help="sampled rows (default 3n)")
+    ap.add_argument("--kappa", type=float, default=1e8)
+    ap.add_argument("--seed", type=int, default=20240617)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample-rows", type=int, default=1 << 17)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def alg_flops(m, n, s):
+    """3mn^2 (two row-solve passes + Gram) + 2sn^2 (sketch QR) + 2n^3/3 (Cholesky + R product)."""
+    return 3.0 * m * n * n + 2.0 * s * n * n + 2.0 * n ** 3 / 3.0
+
+
+# ---- clocks sampled during the timed region --------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---- distributed helpers (torchrun) -----------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if ws > 1 else None
+
+
+def max_over_ranks(value, dist, device=None):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ---- metrics on the device (after timing) -----------------------------------------------------------
+def gpu_metrics(A, Q, R):
+    """||Q^T Q - I||_2 (4096-row blocks, FP64) and ||A - QR||_2 / ||A||_2."""
+    import torch
+    m, n = Q.shape
+    blk = 4096
+    full = (m // blk) * blk
+    G = torch.zeros((n, n), dtype=torch.float64, device=Q.device)
+    if full:
+        parts = torch.bmm(Q[:full].view(-1, blk, n).transpose(1, 2), Q[:full].view(-1, blk, n))
+        while parts.shape[0] > 1:
+            h = parts.shape[0] // 2
+            rest = parts[2 * h:]
+            parts = torch.cat([parts[:h] + parts[h:2 * h], rest], 0)
+        G += parts[0]
+    if full < m:
+        G += Q[full:].T @ Q[full:]
+    E = G - torch.eye(n, dtype=torch.float64, device=Q.device)
+    orth = float(torch.linalg.eigvalsh(0.5 * (E + E.T)).abs().max())
+    D = A - Q @ R
+    nd = float(torch.linalg.eigvalsh(D.T @ D).abs().max().sqrt())
+    na = float(torch.linalg.eigvalsh(A.T @ A).abs().max().sqrt())
+    return orth, nd / na
+
+
+def traffic_from_profiles(kernel_tag, src_file):
+    """DRAM bytes per launch from profiles/traffic.txt when the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(src_file, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("kernel") == kernel_tag and f.get("src_sha") == sha:
+            try:
+                return float(f["dram_bytes_per_launch"])
+            except (KeyError, ValueError):
+                return None
+    return None
+
+
+# ---- the oracle on the host cores --------------------------------------------------------------------
+def oracle_sample_time(m, n, s, kappa, seed, rows, reps):
+    import inputs
+    import oracle
+    oracle.build()
+    rows = min(rows, m)
+    A = inputs.usv(rows, n, kappa, seed)
+    times = []
+    for r in range(reps):
+        t0 = time.perf_counter()
+        o = oracle.rpcholqr(A, min(s, rows), 1 + r)
+        times.append(time.perf_counter() - t0)
+        if o["status"] != 0:
+            raise RuntimeError(f"oracle status {o['status']}")
+    return times, rows, oracle.num_threads()
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    m, n = args.m, args.n
+    s = args.s or 3 * n
+    times, rows, cores = oracle_sample_time(m, n, s, args.kappa, args.seed, args.cpu_sample_rows,
+                                            args.warmup + args.steps)
+    timed = times[args.warmup:]
+    per_step = sum(timed) / len(timed)
+    scale = m / rows
+    value = 1.0 / (per_step * scale)
+    sample = (f"oracle rpCholesky-QR on the first {rows} of {m} rows (same n, s, kappa), "
+              f"time x{scale:g} for the full m; {len(timed)} timed steps after {args.warmup} warm-up")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "matrices/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_step * scale * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"rpCholesky-QR m={m} n={n} s={s} kappa={args.kappa:g}", "m": m, "n": n,
+                   "s": s, "kappa": args.kappa},
+        "effective_tflops": alg_flops(m, n, s) * value / 1e12,
+        "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---- our CUDA path -------------------------------------------------------------------------------------
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import inputs
+    import paper_2406_11751_gb300 as rq
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = init_dist(ws, "nccl")
+    rq.build()
+    m, n = args.m, args.n
+    s = args.s or 3 * n
+    K, W = args.steps, args.warmup
+
+    A = inputs.usv_torch(m, n, args.kappa, args.seed + rank, dev)
+    Q = torch.empty_like(A)
+    R = torch.empty((n, n), dtype=torch.float64, device=dev)
+    info = torch.empty(2, dtype=torch.int32, device=dev)
+    plan = rq.rpcholqr_plan_create(local, m, n, s)
+    stream = torch.cuda.current_stream(dev)
+    fp64_peak = rq.rpcholqr_probe_fp64_mma(local, 4096)
+
+    for w in range(W):
+        rq.rpcholqr_factor(plan, A, s, 1 + w, Q=Q, R=R, info=info, stream=stream)
+    torch.cuda.synchronize(dev)
+    st = info.cpu().tolist()
+    if st[0] != 0:
+        raise RuntimeError(f"warm-up status {rq.rpcholqr_status_string(st[0])}")
+
+    rq.rpcholqr_plan_collect_timing(plan)          # reset counters
+    rq.rpcholqr_plan_enable_timing(plan, K)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(dist)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for k in range(K):
+            rq.rpcholqr_factor(plan, A, s, 1 + k, Q=Q, R=R, info=info, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+    t_ms = e0.elapsed_time(e1)
+    phases, calls, launches = rq.rpcholqr_plan_collect_timing(plan)
+    rq.rpcholqr_plan_enable_timing(plan, 0)
+    t_ms_max = max_over_ranks(t_ms, dist, dev)
+    st = info.cpu().tolist()
+    orth, res = gpu_metrics(A, Q, R)
+
+    # end to end through the host-buffer C-ABI call (H2D of A, D2H of Q, R, info inside the region)
+    Ah = A.cpu().pin_memory()
+    Qh = torch.empty((m, n), dtype=torch.float64).pin_memory()
+    Rh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    rq.rpcholqr_factor_host(plan, Ah, s, 1, Q=Qh, R=Rh, stream=stream)   # allocates staging
+    barrier(dist)
+    t0 = time.perf_counter()
+    for k in range(args.e2e_steps):
+        _, _, st_h, _ = rq.rpcholqr_factor_host(plan, Ah, s, 1 + k, Q=Qh, R=Rh, stream=stream)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    barrier(dist)
+
+    if rank != 0:
+        plan.close()
+        return 0
+
+    N = ws
+    value = N * K / (t_ms_max / 1e3)
+    flops = alg_flops(m, n, s)
+    pass1_ms = phases["pass1"] / max(calls, 1)
+    pass1_flops = 2.0 * m * n * n      # algorithmic: m rows x (n^2 solve + n^2 Gram) flops
+    pass1_bytes = 16.0 * m * n         # read A, write A1
+    achieved = pass1_flops / (pass1_ms / 1e3) / 1e12
+    peak = fp64_peak / 1e12
+    src = os.path.join(ROOT, "paper_2406_11751_gb300", "csrc", "rowpass.cu")
+    traffic = traffic_from_profiles(f"k_rowpass<{n if n % 16 == 0 else (n + 15) // 16 * 16},true>", src)
+
+    cpu = None
+    if not args.no_cpu_baseline and N == 1:
+        times, rows, cores = oracle_sample_time(m, n, s, args.kappa, args.seed, args.cpu_sample_rows, 3)
+        per = min(times) * (m / rows)
+        cpu = {"value": 1.0 / per, "unit": "matrices/s", "cores": cores, "kind": "oracle",
+               "sample": f"oracle on the first {rows} of {m} rows (numpy-generated, same n, s, kappa), "
+                         f"best of 3, time x{m / rows:g}"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": N, "steps": K, "warmup": W,
+        "ms_per_step": t_ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (A = U diag(sigma) V^T, Haar U/V from torch, sigma log-spaced)",
+        "config": {"workload": f"rpCholesky-QR FP64 m={m} n={n} s={s} kappa={args.kappa:g}", "m": m,
+                   "n": n, "s": s, "kappa": args.kappa, "mode": "fp64",
+                   "l2": f"inputs larger than L2 (A = {8 * m * n / 1e9:.2f} GB > 129 MB), no flush"},
+        "effective_tflops": flops * value / 1e12,
+        "orth": orth, "residual": res, "gate_orth_le_1e-13": bool(orth <= 1e-13), "status": st[0],
+        "phases_ms_per_step": {k: v / max(calls, 1) for k, v in phases.items()},
+        "roofline": {"kernel": "k_rowpass<NP,SYRK=true> (pass 1: A1 = A Rs^-1 + Gram)", "bound": "tensor",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": traffic, "algorithmic_flops": pass1_flops,
+                     "algorithmic_bytes": pass1_bytes, "ms_per_launch": pass1_ms,
+                     "peak_source": "FP64 mma.sync m16n8k16 probe measured in this run "
+                                    "(MEASURED_PEAKS.json has no FP64 figure)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": N * args.e2e_steps / e2e_s, "unit": "matrices/s",
+                "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * m * n + 8 * n * n + 8},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+    plan.close()
+    return 0
+
+
+def main():
+    args = parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

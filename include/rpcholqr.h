@@ -1,0 +1,181 @@
+/*
+ * rpcholqr.h -- C ABI of the GB300 (sm_103a) implementation of rpCholesky-QR
+ * (J. E. Garrison and I. C. F. Ipsen, "A randomized preconditioned Cholesky-QR algorithm",
+ * arXiv 2406.11751).
+ *
+ * The library computes the thin QR factorisation A = Q R of a tall-skinny A (m x n, m >> n,
+ * rank n; the problem statement of Section 1 and Section 2.1) with Algorithm alg_2
+ * ("rpCholesky-QR", Section 4):
+ *
+ *   sample        A_s = S A            s rows of A drawn uniformly, independently and with
+ *                                      replacement, scaled by sqrt(m/s) (Remark r_exp, Section 5;
+ *                                      the smoothing transform F is not applied)
+ *   factor        A_s = Q_s R_s        Householder QR of the s x n sample, R_s kept
+ *   precondition  A_1 = A R_s^{-1}     m independent row solves (row-wise view of Section 2.1)
+ *   Gram          G_1 = A_1^T A_1      fused with the preconditioning pass
+ *   Cholesky      G_1 = R_1^T R_1      (the paper's R_2)
+ *   solve         Q   = A_1 R_1^{-1}   second streaming pass, in place over A_1
+ *   recover       R   = R_1 R_s
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are ROW-MAJOR FP64 (double) with a leading dimension (elements between the starts of
+ *     consecutive rows) >= the number of columns.  n x n triangular factors are dense row-major n x n
+ *     arrays with leading dimension n; the strictly lower part is written as 0.
+ *   - "device" pointers must be CUDA device (or managed) memory of the plan's device; "host" pointers
+ *     are ordinary host memory.  The caller owns every buffer it passes; the library never frees them.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*, NULL = legacy default
+ *     stream) unless stated otherwise.  The return value reports argument and launch errors only.
+ *     Numerical outcomes are written to a device int32 pair info[2] = {status, pivot}: status is an
+ *     rpcholqr_status, pivot the failing Cholesky pivot (0-based) for RPCHOLQR_ERR_NOT_SPD, else -1.
+ *     Once a step writes a non-zero status, every later step of the same call returns at once and
+ *     leaves its outputs unwritten.
+ *   - Sampling is deterministic: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) keyed by
+ *     (seed, stream_id), counter block k = (k, 0, 0, 0); sample j takes word j mod 4 of block j/4 and
+ *     maps it to the row floor(word * m / 2^64).  Results are bit-reproducible for a fixed plan, shape
+ *     and seed on one GPU model.
+ *   - No entry point falls back to the host: every arithmetic step runs in this library's kernels.
+ */
+#ifndef RPCHOLQR_H
+#define RPCHOLQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RPCHOLQR_OK = 0,
+    RPCHOLQR_ERR_ARG = 1,             /* invalid argument (shape, pointer, leading dimension)     */
+    RPCHOLQR_ERR_NONFINITE = 2,       /* A holds a NaN or an infinity                             */
+    RPCHOLQR_ERR_SINGULAR_SKETCH = 3, /* a diagonal of R_s is 0, subnormal or non-finite: the
+                                         sample has rank < n (Lemma l_31 and Theorem t_prob need
+                                         rank(A_s) = n)                                           */
+    RPCHOLQR_ERR_NOT_SPD = 4,         /* Cholesky of G_1 met a pivot that is not > 0 (Theorem
+                                         t_perturb2 assumes kappa(A_1)^2 gamma_2 < 1)             */
+    RPCHOLQR_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up                       */
+    RPCHOLQR_ERR_CUDA = 6,            /* a CUDA runtime call failed                               */
+    RPCHOLQR_ERR_NOMEM = 7,           /* workspace allocation failed                              */
+    RPCHOLQR_ERR_UNSUPPORTED = 8      /* the requested mode or shape is not built                 */
+} rpcholqr_status;
+
+typedef enum {
+    RPCHOLQR_FP64 = 0 /* every step in FP64 (FP64 tensor-core mma.sync m16n8k16 + DFMA)          */
+} rpcholqr_mode;
+
+/* Largest n a plan accepts. */
+#define RPCHOLQR_MAX_N 128
+
+typedef struct rpcholqr_plan_s* rpcholqr_plan;
+
+/* Create a plan for matrices up to max_m x max_n sampled with up to max_s rows, on `device`.
+ * The plan owns its device workspace (sample, R_s, fragment tables, per-CTA Gram partials),
+ * allocated here with cudaMalloc; *plan receives the handle.
+ * Requires 1 <= max_n <= RPCHOLQR_MAX_N, max_s >= max_n, max_m >= max_s.
+ * Errors: RPCHOLQR_ERR_ARG, RPCHOLQR_ERR_UNSUPPORTED (mode), RPCHOLQR_ERR_NOMEM, RPCHOLQR_ERR_CUDA. */
+rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_mode mode,
+                                     int64_t max_m, int32_t max_n, int32_t max_s);
+
+/* Free the plan and its workspace (synchronises the plan's device first).  NULL is accepted. */
+rpcholqr_status rpcholqr_plan_destroy(rpcholqr_plan plan);
+
+/* Bytes of device workspace a plan with these limits allocates (host-only query). */
+rpcholqr_status rpcholqr_workspace_size(int64_t max_m, int32_t max_n, int32_t max_s,
+                                        size_t* bytes);
+
+/* rpCholesky-QR of A (Algorithm alg_2, Section 4).
+ *   A    device, m x n row-major, lda >= n; read only.
+ *   s    number of sampled rows, n <= s <= m (the paper's c; s = 3n is its recommendation).
+ *   seed Philox key word 0 (key word 1 = stream_id = 0).
+ *   Q    device, m x n row-major, ldq >= n; must not overlap A.  Holds A_1 between the passes.
+ *   R    device, n x n row-major upper triangular (strict lower part set to 0).
+ *   info device int32[2], see above; written by every call.
+ * Requires 1 <= n <= plan max_n, s <= plan max_s, m <= plan max_m, m >= s >= n.
+ * On a non-zero info status the contents of Q and R are unspecified. */
+rpcholqr_status rpcholqr_factor(rpcholqr_plan plan, const double* A, int64_t m, int32_t n,
+                                int64_t lda, int32_t s, uint64_t seed, double* Q, int64_t ldq,
+                                double* R, int32_t* info, void* stream);
+
+/* End-to-end variant of rpcholqr_factor on HOST buffers: copies A (host, m x n, lda) to a device
+ * staging buffer the plan allocates on first use, factors it, copies Q (host, ldq) and R (host)
+ * back, and returns only after the copies completed.  info_host (int32[2], host) receives the
+ * numerical status.  Staging buffers are kept for later calls and freed with the plan. */
+rpcholqr_status rpcholqr_factor_host(rpcholqr_plan plan, const double* A, int64_t m, int32_t n,
+                                     int64_t lda, int32_t s, uint64_t seed, double* Q, int64_t ldq,
+                                     double* R, int32_t* info_host, void* stream);
+
+/* ---- individual steps (the same kernels rpcholqr_factor launches), for testing and composition ---- */
+
+/* Sampling matrix S of Section 4: idx[j] (device int64[s]) = 0-based row of sample j. */
+rpcholqr_status rpcholqr_sample_indices(uint64_t seed, uint64_t stream_id, int64_t m, int32_t s,
+                                        int64_t* idx, void* stream);
+
+/* Sample + Householder QR (steps 'sample' and 'factor'): Rs (device, n x n) receives R_s with a
+ * positive diagonal (rows negated where Householder produced a negative diagonal).  info as above
+ * (RPCHOLQR_ERR_NONFINITE for a non-finite sampled entry, RPCHOLQR_ERR_SINGULAR_SKETCH). */
+rpcholqr_status rpcholqr_sketch_r(rpcholqr_plan plan, const double* A, int64_t m, int32_t n,
+                                  int64_t lda, int32_t s, uint64_t seed, double* Rs, int32_t* info,
+                                  void* stream);
+
+/* Fused preconditioning pass (steps 'precondition' and 'Gram'): A1 = A Rs^{-1} (device, m x n,
+ * ld1; may not overlap A) and G = A1^T A1 (device, n x n, full symmetric).  Rs: device n x n upper
+ * triangular with a non-zero diagonal.  Sets RPCHOLQR_ERR_NONFINITE if A holds a NaN/Inf. */
+rpcholqr_status rpcholqr_precondition_gram(rpcholqr_plan plan, const double* A, int64_t m,
+                                           int32_t n, int64_t lda, const double* Rs, double* A1,
+                                           int64_t ld1, double* G, int32_t* info, void* stream);
+
+/* Cholesky (step 'Cholesky'): G = R1^T R1 for device n x n symmetric G; R1 device n x n upper.
+ * RPCHOLQR_ERR_NOT_SPD with the pivot index when a pivot is not > 0. */
+rpcholqr_status rpcholqr_cholesky(rpcholqr_plan plan, const double* G, int32_t n, double* R1,
+                                  int32_t* info, void* stream);
+
+/* Row-wise triangular solve (step 'solve'): Y = X T^{-1}, T device n x n upper triangular with a
+ * non-zero diagonal, X and Y device m x n (ldx, ldy); X == Y (same ld) solves in place, any other
+ * overlap is an error of the caller.  m <= plan max_m, n <= plan max_n. */
+rpcholqr_status rpcholqr_solve_rows(rpcholqr_plan plan, const double* X, int64_t m, int32_t n,
+                                    int64_t ldx, const double* T, double* Y, int64_t ldy,
+                                    int32_t* info, void* stream);
+
+/* R = R1 Rs for device n x n upper-triangular R1, Rs (step 'recover'); R device n x n. */
+rpcholqr_status rpcholqr_triu_mul(const double* R1, const double* Rs, int32_t n, double* R,
+                                  void* stream);
+
+/* FP64 tensor-pipe throughput probe: runs `iters` chains of dependent m16n8k16 FP64 mma on every
+ * SM and writes the sustained FLOP/s to *flops_per_s (host).  Synchronous.  Used to report the
+ * FP64 roofline denominator measured on the running GPU. */
+rpcholqr_status rpcholqr_probe_fp64_mma(int device, int32_t iters, double* flops_per_s);
+
+/* ---- per-phase timing (CUDA events on the call's stream) ----
+ * Phases of one rpcholqr_factor call, in launch order. */
+enum {
+    RPCHOLQR_PHASE_SAMPLE = 0,    /* Philox indices + gather/scale of the s rows           */
+    RPCHOLQR_PHASE_SKETCH_QR,     /* Householder QR of the sample                           */
+    RPCHOLQR_PHASE_PREP_RS,       /* fragment tables of R_s                                 */
+    RPCHOLQR_PHASE_PASS1,         /* fused A1 = A R_s^{-1} and per-CTA Gram partials        */
+    RPCHOLQR_PHASE_GRAM_REDUCE,   /* fixed-order sum of the Gram partials                   */
+    RPCHOLQR_PHASE_CHOLESKY,      /* G1 = R1^T R1                                           */
+    RPCHOLQR_PHASE_PREP_R1,       /* fragment tables of R1                                  */
+    RPCHOLQR_PHASE_PASS2,         /* Q = A1 R1^{-1} in place                                */
+    RPCHOLQR_PHASE_RECOVER_R,     /* R = R1 R_s                                             */
+    RPCHOLQR_NUM_PHASES
+};
+
+/* Enable (max_calls > 0) or disable (0) event timing of the next rpcholqr_factor calls on this
+ * plan: events are recorded on the call's stream around every phase for up to max_calls calls
+ * (later calls are not timed).  Creating the events happens here, not in rpcholqr_factor. */
+rpcholqr_status rpcholqr_plan_enable_timing(rpcholqr_plan plan, int32_t max_calls);
+
+/* Wait for the recorded events and report, summed over the timed calls since the last collect:
+ * ms_per_phase[RPCHOLQR_NUM_PHASES] (host), *calls (host) = number of timed calls, and *launches
+ * (host) = kernels this plan launched since the last collect (timed or not).  Resets the counts. */
+rpcholqr_status rpcholqr_plan_collect_timing(rpcholqr_plan plan, float* ms_per_phase, int32_t* calls,
+                                             int64_t* launches);
+
+/* Human-readable name of a status code (static string). */
+const char* rpcholqr_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPCHOLQR_H */

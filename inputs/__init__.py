@@ -11,6 +11,9 @@ Recipes (all FP64, row-major m x n):
   diagonal (Haar-distributed, the first n columns of the Haar matrix in Section 5.3, Eq. (5.2)),
   ``V`` the same for an n x n N(0,1) matrix, and ``sigma_i = kappa^{-(i-1)/(n-1)}`` (log-spaced
   from 1 to 1/kappa, the reading of ``gallery('randsvd', n, kappa)`` used throughout Section 5).
+* ``usv_torch(m, n, kappa, seed, device)`` -- the same recipe drawn with torch's generator on the
+  given device and orthonormalised with ``torch.linalg.qr`` (fast at m = 2^20 and above; its bits
+  differ from ``usv``'s, so parity tests use ``usv`` and timing runs may use this one).
 * ``coherent_diag(m, n, seed)`` -- the maximally coherent ``[D; 0]`` with D diagonal, the
   worst-coherence shape of Eq. (5.1) with a diagonal top block.  Without the smoothing transform
   an unsmoothed uniform sample misses some of the first n rows, so column j of the sample can be
@@ -24,7 +27,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["usv", "usv_factors", "coherent_diag", "batch_manifest", "log_sigmas"]
+__all__ = ["usv", "usv_factors", "usv_torch", "coherent_diag", "batch_manifest", "log_sigmas"]
 
 
 def log_sigmas(n: int, kappa: float) -> np.ndarray:
@@ -58,6 +61,25 @@ def usv(m: int, n: int, kappa: float, seed: int, return_factors: bool = False):
     if return_factors:
         return a, (u, s, v)
     return a
+
+
+def usv_torch(m: int, n: int, kappa: float, seed: int, device="cuda"):
+    """A = U diag(sigma) V^T drawn with torch on `device` (float64, row-major)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+
+    def haar(rows, cols):
+        x = torch.randn((rows, cols), generator=g, dtype=torch.float64, device=device)
+        q, r = torch.linalg.qr(x, mode="reduced")
+        d = torch.sign(torch.diagonal(r))
+        d[d == 0] = 1.0
+        return q * d[None, :]
+
+    u = haar(m, n)
+    v = haar(n, n)
+    s = torch.from_numpy(log_sigmas(n, kappa)).to(device)
+    return ((u * s[None, :]) @ v.T).contiguous()
 
 
 def coherent_diag(m: int, n: int, seed: int) -> np.ndarray:

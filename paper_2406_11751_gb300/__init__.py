@@ -1,0 +1,307 @@
+"""rpCholesky-QR on GB300 (sm_103a): thin Python binding over ``librpcholqr.so``.
+
+Garrison & Ipsen, "A randomized preconditioned Cholesky-QR algorithm" (arXiv 2406.11751),
+Algorithm alg_2 (Section 4).  Every arithmetic step runs in the library's CUDA kernels; this module
+only marshals torch tensors (device memory, streams) into the C ABI of ``include/rpcholqr.h`` and
+keeps the same function names.  There is no CPU fallback: if the library is missing or a tensor is
+not on a CUDA device the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB_PATH, build  # noqa: F401  (re-exported for __graft_entry__)
+
+__all__ = [
+    "RpcholqrError", "Plan", "STATUS", "load_library", "rpcholqr_plan_create", "rpcholqr_plan_destroy",
+    "rpcholqr_workspace_size", "rpcholqr_factor", "rpcholqr_factor_host", "rpcholqr_sample_indices",
+    "rpcholqr_sketch_r", "rpcholqr_precondition_gram", "rpcholqr_cholesky", "rpcholqr_solve_rows",
+    "rpcholqr_triu_mul", "rpcholqr_probe_fp64_mma", "rpcholqr_status_string", "EXPORTED_SYMBOLS",
+    "rpcholqr_plan_enable_timing", "rpcholqr_plan_collect_timing", "PHASES",
+]
+
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NONFINITE", 3: "ERR_SINGULAR_SKETCH", 4: "ERR_NOT_SPD",
+          5: "ERR_TIMEOUT", 6: "ERR_CUDA", 7: "ERR_NOMEM", 8: "ERR_UNSUPPORTED"}
+OK, ERR_ARG, ERR_NONFINITE, ERR_SINGULAR_SKETCH, ERR_NOT_SPD = 0, 1, 2, 3, 4
+FP64 = 0
+MAX_N = 128
+
+EXPORTED_SYMBOLS = (
+    "rpcholqr_plan_create", "rpcholqr_plan_destroy", "rpcholqr_workspace_size", "rpcholqr_factor",
+    "rpcholqr_factor_host", "rpcholqr_sample_indices", "rpcholqr_sketch_r",
+    "rpcholqr_precondition_gram", "rpcholqr_cholesky", "rpcholqr_solve_rows", "rpcholqr_triu_mul",
+    "rpcholqr_probe_fp64_mma", "rpcholqr_status_string", "rpcholqr_plan_enable_timing",
+    "rpcholqr_plan_collect_timing",
+)
+PHASES = ("sample", "sketch_qr", "prep_rs", "pass1", "gram_reduce", "cholesky", "prep_r1", "pass2",
+          "recover_r")
+
+
+class RpcholqrError(RuntimeError):
+    """A host-side (argument / launch / allocation) error returned by the C ABI."""
+
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn} failed: {STATUS.get(code, code)}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library():
+    """Load librpcholqr.so (no automatic build: a missing library is an error)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           f"`python -m paper_2406_11751_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, U64, D = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                           ctypes.c_double)
+    st = ctypes.c_int
+    sig = {
+        "rpcholqr_plan_create": [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, I64, I32, I32],
+        "rpcholqr_plan_destroy": [P],
+        "rpcholqr_workspace_size": [I64, I32, I32, ctypes.POINTER(ctypes.c_size_t)],
+        "rpcholqr_factor": [P, P, I64, I32, I64, I32, U64, P, I64, P, P, P],
+        "rpcholqr_factor_host": [P, P, I64, I32, I64, I32, U64, P, I64, P, P, P],
+        "rpcholqr_sample_indices": [U64, U64, I64, I32, P, P],
+        "rpcholqr_sketch_r": [P, P, I64, I32, I64, I32, U64, P, P, P],
+        "rpcholqr_precondition_gram": [P, P, I64, I32, I64, P, P, I64, P, P, P],
+        "rpcholqr_cholesky": [P, P, I32, P, P, P],
+        "rpcholqr_solve_rows": [P, P, I64, I32, I64, P, P, I64, P, P],
+        "rpcholqr_triu_mul": [P, P, I32, P, P],
+        "rpcholqr_probe_fp64_mma": [ctypes.c_int, I32, ctypes.POINTER(D)],
+        "rpcholqr_plan_enable_timing": [P, I32],
+        "rpcholqr_plan_collect_timing": [P, P, ctypes.POINTER(I32), ctypes.POINTER(I64)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = st
+    lib.rpcholqr_status_string.argtypes = [ctypes.c_int]
+    lib.rpcholqr_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(fn: str, code: int):
+    if code != 0:
+        raise RpcholqrError(fn, code)
+
+
+def rpcholqr_status_string(code: int) -> str:
+    return load_library().rpcholqr_status_string(int(code)).decode()
+
+
+# ---- tensor helpers -----------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _mat(x, name, dtype=None):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dim() != 2 or x.stride(1) != 1:
+        raise ValueError(f"{name} must be a 2-D row-major tensor with unit column stride")
+    if x.dtype != (dtype or torch.float64):
+        raise TypeError(f"{name} must be {dtype or torch.float64}")
+    return x
+
+
+def _stream(stream, device):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """Owner of a C plan handle (device workspace for matrices up to max_m x max_n, max_s samples)."""
+
+    def __init__(self, handle, device, max_m, max_n, max_s):
+        self.handle = handle
+        self.device = device
+        self.max_m, self.max_n, self.max_s = max_m, max_n, max_s
+
+    def close(self):
+        if self.handle:
+            load_library().rpcholqr_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rpcholqr_plan_create(device: int, max_m: int, max_n: int, max_s: int, mode: int = FP64) -> Plan:
+    h = ctypes.c_void_p()
+    _check("rpcholqr_plan_create",
+           load_library().rpcholqr_plan_create(ctypes.byref(h), device, mode, max_m, max_n, max_s))
+    return Plan(h, device, max_m, max_n, max_s)
+
+
+def rpcholqr_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def rpcholqr_workspace_size(max_m: int, max_n: int, max_s: int) -> int:
+    b = ctypes.c_size_t()
+    _check("rpcholqr_workspace_size",
+           load_library().rpcholqr_workspace_size(max_m, max_n, max_s, ctypes.byref(b)))
+    return int(b.value)
+
+
+def _info(info, device):
+    torch = _torch()
+    if info is None:
+        info = torch.empty(2, dtype=torch.int32, device=device)
+    return info
+
+
+def rpcholqr_factor(plan: Plan, A, s: int, seed: int, Q=None, R=None, info=None, stream=None):
+    """(Q, R, info) of rpCholesky-QR; info is a device int32[2] {status, pivot} (not synchronised)."""
+    torch = _torch()
+    _mat(A, "A")
+    m, n = A.shape
+    if Q is None:
+        Q = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64, device=A.device)
+    _mat(Q, "Q")
+    _mat(R, "R")
+    info = _info(info, A.device)
+    _check("rpcholqr_factor", load_library().rpcholqr_factor(
+        plan.handle, _ptr(A), m, n, A.stride(0), s, seed, _ptr(Q), Q.stride(0), _ptr(R), _ptr(info),
+        _stream(stream, A.device)))
+    return Q, R, info
+
+
+def rpcholqr_factor_host(plan: Plan, A, s: int, seed: int, Q=None, R=None, stream=None):
+    """Host-buffer variant: A, Q, R are CPU float64 tensors (pinned for full copy speed).
+    Returns (Q, R, status, pivot) after the device work and the copies finished."""
+    torch = _torch()
+    if A.is_cuda or A.dtype != torch.float64 or A.dim() != 2 or A.stride(1) != 1:
+        raise TypeError("A must be a row-major float64 CPU tensor")
+    m, n = A.shape
+    if Q is None:
+        Q = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    info = (ctypes.c_int32 * 2)()
+    dev = torch.device("cuda", plan.device)
+    _check("rpcholqr_factor_host", load_library().rpcholqr_factor_host(
+        plan.handle, _ptr(A), m, n, A.stride(0), s, seed, _ptr(Q), Q.stride(0), _ptr(R),
+        ctypes.cast(info, ctypes.c_void_p), _stream(stream, dev)))
+    return Q, R, int(info[0]), int(info[1])
+
+
+def rpcholqr_sample_indices(seed: int, m: int, s: int, stream_id: int = 0, idx=None, device=None,
+                            stream=None):
+    torch = _torch()
+    if idx is None:
+        idx = torch.empty(s, dtype=torch.int64, device=device if device is not None else "cuda")
+    _check("rpcholqr_sample_indices", load_library().rpcholqr_sample_indices(
+        seed, stream_id, m, s, _ptr(idx), _stream(stream, idx.device)))
+    return idx
+
+
+def rpcholqr_sketch_r(plan: Plan, A, s: int, seed: int, Rs=None, info=None, stream=None):
+    torch = _torch()
+    _mat(A, "A")
+    m, n = A.shape
+    if Rs is None:
+        Rs = torch.empty((n, n), dtype=torch.float64, device=A.device)
+    info = _info(info, A.device)
+    _check("rpcholqr_sketch_r", load_library().rpcholqr_sketch_r(
+        plan.handle, _ptr(A), m, n, A.stride(0), s, seed, _ptr(Rs), _ptr(info),
+        _stream(stream, A.device)))
+    return Rs, info
+
+
+def rpcholqr_precondition_gram(plan: Plan, A, Rs, A1=None, G=None, info=None, stream=None):
+    torch = _torch()
+    _mat(A, "A")
+    m, n = A.shape
+    Rs = _mat(Rs.contiguous(), "Rs")
+    if A1 is None:
+        A1 = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    if G is None:
+        G = torch.empty((n, n), dtype=torch.float64, device=A.device)
+    info = _info(info, A.device)
+    _check("rpcholqr_precondition_gram", load_library().rpcholqr_precondition_gram(
+        plan.handle, _ptr(A), m, n, A.stride(0), _ptr(Rs), _ptr(A1), A1.stride(0), _ptr(G),
+        _ptr(info), _stream(stream, A.device)))
+    return A1, G, info
+
+
+def rpcholqr_cholesky(plan: Plan, G, R1=None, info=None, stream=None):
+    torch = _torch()
+    G = _mat(G.contiguous(), "G")
+    n = G.shape[0]
+    if R1 is None:
+        R1 = torch.empty((n, n), dtype=torch.float64, device=G.device)
+    info = _info(info, G.device)
+    _check("rpcholqr_cholesky", load_library().rpcholqr_cholesky(
+        plan.handle, _ptr(G), n, _ptr(R1), _ptr(info), _stream(stream, G.device)))
+    return R1, info
+
+
+def rpcholqr_solve_rows(plan: Plan, X, T, Y=None, info=None, stream=None):
+    torch = _torch()
+    _mat(X, "X")
+    m, n = X.shape
+    T = _mat(T.contiguous(), "T")
+    if Y is None:
+        Y = torch.empty((m, n), dtype=torch.float64, device=X.device)
+    info = _info(info, X.device)
+    _check("rpcholqr_solve_rows", load_library().rpcholqr_solve_rows(
+        plan.handle, _ptr(X), m, n, X.stride(0), _ptr(T), _ptr(Y), Y.stride(0), _ptr(info),
+        _stream(stream, X.device)))
+    return Y, info
+
+
+def rpcholqr_triu_mul(R1, Rs, R=None, stream=None):
+    torch = _torch()
+    R1 = _mat(R1.contiguous(), "R1")
+    Rs = _mat(Rs.contiguous(), "Rs")
+    n = R1.shape[0]
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64, device=R1.device)
+    _check("rpcholqr_triu_mul", load_library().rpcholqr_triu_mul(
+        _ptr(R1), _ptr(Rs), n, _ptr(R), _stream(stream, R1.device)))
+    return R
+
+
+def rpcholqr_probe_fp64_mma(device: int = 0, iters: int = 2048) -> float:
+    """Measured FP64 mma.sync m16n8k16 throughput of the device, FLOP/s."""
+    out = ctypes.c_double()
+    _check("rpcholqr_probe_fp64_mma",
+           load_library().rpcholqr_probe_fp64_mma(device, iters, ctypes.byref(out)))
+    return float(out.value)
+
+
+def rpcholqr_plan_enable_timing(plan: Plan, max_calls: int):
+    """Record CUDA events around every phase of the next ``max_calls`` factor calls (0 disables)."""
+    _check("rpcholqr_plan_enable_timing",
+           load_library().rpcholqr_plan_enable_timing(plan.handle, max_calls))
+
+
+def rpcholqr_plan_collect_timing(plan: Plan):
+    """({phase: summed ms}, timed calls, kernel launches since the last collect)."""
+    ms = (ctypes.c_float * len(PHASES))()
+    calls = ctypes.c_int32()
+    launches = ctypes.c_int64()
+    _check("rpcholqr_plan_collect_timing", load_library().rpcholqr_plan_collect_timing(
+        plan.handle, ctypes.cast(ms, ctypes.c_void_p), ctypes.byref(calls), ctypes.byref(launches)))
+    return dict(zip(PHASES, [float(x) for x in ms])), int(calls.value), int(launches.value)

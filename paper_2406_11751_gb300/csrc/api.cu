@@ -1,0 +1,475 @@
+// C ABI of the library (declared in include/rpcholqr.h): plans, the full rpCholesky-QR call,
+// the individual steps, and the FP64 tensor-pipe probe.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace rpq {
+// sample.cu
+void launch_sample_indices(uint64_t seed, uint64_t stream_id, int64_t m, int32_t s, int64_t* idx,
+                           cudaStream_t st);
+void launch_sample_gather(const double* A, int64_t m, int32_t n, int64_t lda, int32_t s, uint64_t seed,
+                          uint64_t stream_id, double scale, double* As, int64_t lds, int32_t np,
+                          int64_t* idx_out, int32_t* info, cudaStream_t st);
+// smallfactor.cu
+cudaError_t launch_householder(double* W, int64_t lds, int s, int n, int np, double* Rs,
+                               double* Rs_user, int32_t* info, cudaStream_t st);
+size_t householder_smem_bytes(int s);
+cudaError_t launch_cholesky(const double* G, int64_t ldg, int n, int np, double* R, double* R_user,
+                            int32_t* info, cudaStream_t st);
+void launch_triu_mul(const double* R1, int64_t ld1, const double* Rs, int64_t lds, int n, double* R,
+                     int64_t ldr, const int32_t* info, cudaStream_t st);
+// rowpass.cu
+void launch_prep_tri(const double* T, int64_t ldt, int n, int np, double* frag, double* diag,
+                     const int32_t* info, cudaStream_t st);
+cudaError_t launch_rowpass(bool syrk, int np, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                           int64_t m, int n, const double* frag, const double* diag, double* gpart,
+                           int32_t* info, int grid, cudaStream_t st);
+void launch_gram_reduce(const double* gpart, int nparts, int np, int n, double* G, int64_t ldg,
+                        const int32_t* info, cudaStream_t st);
+// probe.cu
+cudaError_t run_fp64_mma_probe(int iters, double* flops_per_s);
+}  // namespace rpq
+
+using namespace rpq;
+
+struct rpcholqr_plan_s {
+    int device = 0;
+    rpcholqr_mode mode = RPCHOLQR_FP64;
+    int64_t max_m = 0;
+    int32_t max_n = 0, max_s = 0, np = 0;
+    int grid = 0;  // CTAs of the row passes (one per SM)
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    double* As = nullptr;       // max_s x np, column-major
+    double* Rs = nullptr;       // np x np
+    double* R1 = nullptr;       // np x np
+    double* G = nullptr;        // np x np
+    double* frag_s = nullptr;   // np*np
+    double* diag_s = nullptr;   // np/8*64
+    double* frag_1 = nullptr;
+    double* diag_1 = nullptr;
+    double* gpart = nullptr;    // grid x np x np
+    int32_t* info_ws = nullptr; // 2 ints (for step calls without a caller info)
+    // staging for rpcholqr_factor_host
+    double* hA = nullptr;
+    double* hQ = nullptr;
+    double* hR = nullptr;
+    int32_t* hinfo = nullptr;
+    size_t staged_elems = 0;
+    // phase timing
+    int32_t timing_slots = 0;
+    int32_t timed_calls = 0;
+    cudaEvent_t* events = nullptr;  // timing_slots x (RPCHOLQR_NUM_PHASES + 1)
+    int64_t launches = 0;
+};
+
+namespace {
+
+struct WsLayout {
+    size_t As, Rs, R1, G, frag_s, diag_s, frag_1, diag_1, gpart, info, total;
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+WsLayout ws_layout(int32_t max_n, int32_t max_s, int grid) {
+    const size_t np = static_cast<size_t>(pad16(max_n));
+    WsLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    L.As = take(sizeof(double) * static_cast<size_t>(max_s) * np);
+    L.Rs = take(sizeof(double) * np * np);
+    L.R1 = take(sizeof(double) * np * np);
+    L.G = take(sizeof(double) * np * np);
+    L.frag_s = take(sizeof(double) * np * np);
+    L.diag_s = take(sizeof(double) * (np / 8) * 64);
+    L.frag_1 = take(sizeof(double) * np * np);
+    L.diag_1 = take(sizeof(double) * (np / 8) * 64);
+    L.gpart = take(sizeof(double) * static_cast<size_t>(grid) * np * np);
+    L.info = take(sizeof(int32_t) * 2);
+    L.total = off;
+    return L;
+}
+
+int default_grid(int device) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0)
+        sms = 152;
+    return sms;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+rpcholqr_status check_launch() {
+    return cudaGetLastError() == cudaSuccess ? RPCHOLQR_OK : RPCHOLQR_ERR_CUDA;
+}
+
+rpcholqr_status reset_info(int32_t* info, cudaStream_t st) {
+    if (cudaMemsetAsync(info, 0, sizeof(int32_t), st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    if (cudaMemsetAsync(info + 1, 0xFF, sizeof(int32_t), st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    return RPCHOLQR_OK;
+}
+
+bool shape_ok(const rpcholqr_plan_s* p, int64_t m, int32_t n, int32_t s) {
+    return n >= 1 && n <= p->max_n && s >= n && s <= p->max_s && m >= s && m <= p->max_m;
+}
+
+// Records the start of `phase` (or the end of the call for phase == RPCHOLQR_NUM_PHASES) when
+// the plan times this call.
+struct PhaseMarks {
+    rpcholqr_plan_s* p;
+    cudaStream_t st;
+    int slot;
+    PhaseMarks(rpcholqr_plan_s* plan, cudaStream_t stream) : p(plan), st(stream), slot(-1) {
+        if (p->events && p->timed_calls < p->timing_slots) slot = p->timed_calls++;
+    }
+    void mark(int phase) const {
+        if (slot >= 0) cudaEventRecord(p->events[slot * (RPCHOLQR_NUM_PHASES + 1) + phase], st);
+    }
+};
+
+void free_events(rpcholqr_plan_s* p) {
+    if (!p->events) return;
+    for (int i = 0; i < p->timing_slots * (RPCHOLQR_NUM_PHASES + 1); ++i) cudaEventDestroy(p->events[i]);
+    delete[] p->events;
+    p->events = nullptr;
+    p->timing_slots = 0;
+    p->timed_calls = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rpcholqr_status_string(int status) {
+    switch (status) {
+        case RPCHOLQR_OK: return "RPCHOLQR_OK";
+        case RPCHOLQR_ERR_ARG: return "RPCHOLQR_ERR_ARG";
+        case RPCHOLQR_ERR_NONFINITE: return "RPCHOLQR_ERR_NONFINITE";
+        case RPCHOLQR_ERR_SINGULAR_SKETCH: return "RPCHOLQR_ERR_SINGULAR_SKETCH";
+        case RPCHOLQR_ERR_NOT_SPD: return "RPCHOLQR_ERR_NOT_SPD";
+        case RPCHOLQR_ERR_TIMEOUT: return "RPCHOLQR_ERR_TIMEOUT";
+        case RPCHOLQR_ERR_CUDA: return "RPCHOLQR_ERR_CUDA";
+        case RPCHOLQR_ERR_NOMEM: return "RPCHOLQR_ERR_NOMEM";
+        case RPCHOLQR_ERR_UNSUPPORTED: return "RPCHOLQR_ERR_UNSUPPORTED";
+        default: return "RPCHOLQR_UNKNOWN_STATUS";
+    }
+}
+
+rpcholqr_status rpcholqr_workspace_size(int64_t max_m, int32_t max_n, int32_t max_s, size_t* bytes) {
+    if (!bytes || max_n < 1 || max_n > RPCHOLQR_MAX_N || max_s < max_n || max_m < max_s)
+        return RPCHOLQR_ERR_ARG;
+    *bytes = ws_layout(max_n, max_s, 152).total;
+    return RPCHOLQR_OK;
+}
+
+rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_mode mode,
+                                     int64_t max_m, int32_t max_n, int32_t max_s) {
+    if (!plan) return RPCHOLQR_ERR_ARG;
+    *plan = nullptr;
+    if (max_n < 1 || max_n > RPCHOLQR_MAX_N || max_s < max_n || max_m < max_s) return RPCHOLQR_ERR_ARG;
+    if (mode != RPCHOLQR_FP64) return RPCHOLQR_ERR_UNSUPPORTED;
+    if (householder_smem_bytes(max_s) > 200 * 1024) return RPCHOLQR_ERR_UNSUPPORTED;
+    DeviceGuard guard(device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    auto* p = new (std::nothrow) rpcholqr_plan_s();
+    if (!p) return RPCHOLQR_ERR_NOMEM;
+    p->device = device;
+    p->mode = mode;
+    p->max_m = max_m;
+    p->max_n = max_n;
+    p->max_s = max_s;
+    p->np = pad16(max_n);
+    p->grid = default_grid(device);
+    const WsLayout L = ws_layout(max_n, max_s, p->grid);
+    if (cudaMalloc(&p->ws, L.total) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return RPCHOLQR_ERR_NOMEM;
+    }
+    p->ws_bytes = L.total;
+    char* b = static_cast<char*>(p->ws);
+    p->As = reinterpret_cast<double*>(b + L.As);
+    p->Rs = reinterpret_cast<double*>(b + L.Rs);
+    p->R1 = reinterpret_cast<double*>(b + L.R1);
+    p->G = reinterpret_cast<double*>(b + L.G);
+    p->frag_s = reinterpret_cast<double*>(b + L.frag_s);
+    p->diag_s = reinterpret_cast<double*>(b + L.diag_s);
+    p->frag_1 = reinterpret_cast<double*>(b + L.frag_1);
+    p->diag_1 = reinterpret_cast<double*>(b + L.diag_1);
+    p->gpart = reinterpret_cast<double*>(b + L.gpart);
+    p->info_ws = reinterpret_cast<int32_t*>(b + L.info);
+    *plan = p;
+    return RPCHOLQR_OK;
+}
+
+rpcholqr_status rpcholqr_plan_destroy(rpcholqr_plan plan) {
+    if (!plan) return RPCHOLQR_OK;
+    DeviceGuard guard(plan->device);
+    cudaDeviceSynchronize();
+    cudaFree(plan->ws);
+    cudaFree(plan->hA);
+    cudaFree(plan->hQ);
+    cudaFree(plan->hR);
+    cudaFree(plan->hinfo);
+    free_events(plan);
+    delete plan;
+    return RPCHOLQR_OK;
+}
+
+rpcholqr_status rpcholqr_sample_indices(uint64_t seed, uint64_t stream_id, int64_t m, int32_t s,
+                                        int64_t* idx, void* stream) {
+    if (!idx || m < 1 || s < 1) return RPCHOLQR_ERR_ARG;
+    launch_sample_indices(seed, stream_id, m, s, idx, static_cast<cudaStream_t>(stream));
+    return check_launch();
+}
+
+static rpcholqr_status sketch_internal(rpcholqr_plan p, const double* A, int64_t m, int32_t n,
+                                       int64_t lda, int32_t s, uint64_t seed, uint64_t stream_id,
+                                       double* Rs_user, int32_t* info, cudaStream_t st,
+                                       const PhaseMarks* pm) {
+    const int np = pad16(n);
+    const double scale = std::sqrt(static_cast<double>(m) / static_cast<double>(s));
+    if (pm) pm->mark(RPCHOLQR_PHASE_SAMPLE);
+    launch_sample_gather(A, m, n, lda, s, seed, stream_id, scale, p->As, s, np, nullptr, info, st);
+    ++p->launches;
+    if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
+    if (pm) pm->mark(RPCHOLQR_PHASE_SKETCH_QR);
+    if (launch_householder(p->As, s, s, n, np, p->Rs, Rs_user, info, st) != cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    ++p->launches;
+    return RPCHOLQR_OK;
+}
+
+static rpcholqr_status precondition_internal(rpcholqr_plan p, const double* A, int64_t m, int32_t n,
+                                             int64_t lda, const double* Rs, int64_t ldrs, double* A1,
+                                             int64_t ld1, double* G_user, int32_t* info,
+                                             cudaStream_t st, const PhaseMarks* pm) {
+    const int np = pad16(n);
+    if (pm) pm->mark(RPCHOLQR_PHASE_PREP_RS);
+    launch_prep_tri(Rs, ldrs, n, np, p->frag_s, p->diag_s, info, st);
+    ++p->launches;
+    if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
+    const int64_t panels = (m + 127) / 128;
+    const int grid = static_cast<int>(panels < p->grid ? panels : p->grid);
+    if (pm) pm->mark(RPCHOLQR_PHASE_PASS1);
+    if (launch_rowpass(true, np, A, lda, A1, ld1, m, n, p->frag_s, p->diag_s, p->gpart, info, grid, st) !=
+        cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    ++p->launches;
+    if (pm) pm->mark(RPCHOLQR_PHASE_GRAM_REDUCE);
+    launch_gram_reduce(p->gpart, grid, np, n, G_user ? G_user : p->G, G_user ? n : np, info, st);
+    ++p->launches;
+    return check_launch();
+}
+
+static rpcholqr_status solve_internal(rpcholqr_plan p, const double* X, int64_t m, int32_t n,
+                                      int64_t ldx, const double* T, int64_t ldt, double* Y, int64_t ldy,
+                                      int32_t* info, cudaStream_t st, const PhaseMarks* pm) {
+    const int np = pad16(n);
+    if (pm) pm->mark(RPCHOLQR_PHASE_PREP_R1);
+    launch_prep_tri(T, ldt, n, np, p->frag_1, p->diag_1, info, st);
+    ++p->launches;
+    if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
+    const int64_t panels = (m + 127) / 128;
+    const int grid = static_cast<int>(panels < p->grid ? panels : p->grid);
+    if (pm) pm->mark(RPCHOLQR_PHASE_PASS2);
+    if (launch_rowpass(false, np, X, ldx, Y, ldy, m, n, p->frag_1, p->diag_1, nullptr, info, grid, st) !=
+        cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    ++p->launches;
+    return RPCHOLQR_OK;
+}
+
+rpcholqr_status rpcholqr_factor(rpcholqr_plan p, const double* A, int64_t m, int32_t n, int64_t lda,
+                                int32_t s, uint64_t seed, double* Q, int64_t ldq, double* R,
+                                int32_t* info, void* stream) {
+    if (!p || !A || !Q || !R || !info) return RPCHOLQR_ERR_ARG;
+    if (!shape_ok(p, m, n, s) || lda < n || ldq < n) return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int np = pad16(n);
+    const PhaseMarks pm(p, st);
+    rpcholqr_status rc = reset_info(info, st);
+    if (rc != RPCHOLQR_OK) return rc;
+    if ((rc = sketch_internal(p, A, m, n, lda, s, seed, 0, nullptr, info, st, &pm)) != RPCHOLQR_OK) return rc;
+    if ((rc = precondition_internal(p, A, m, n, lda, p->Rs, np, Q, ldq, nullptr, info, st, &pm)) !=
+        RPCHOLQR_OK)
+        return rc;
+    pm.mark(RPCHOLQR_PHASE_CHOLESKY);
+    if (launch_cholesky(p->G, np, n, np, p->R1, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    ++p->launches;
+    if ((rc = solve_internal(p, Q, m, n, ldq, p->R1, np, Q, ldq, info, st, &pm)) != RPCHOLQR_OK) return rc;
+    pm.mark(RPCHOLQR_PHASE_RECOVER_R);
+    launch_triu_mul(p->R1, np, p->Rs, np, n, R, n, info, st);
+    ++p->launches;
+    pm.mark(RPCHOLQR_NUM_PHASES);
+    return check_launch();
+}
+
+rpcholqr_status rpcholqr_plan_enable_timing(rpcholqr_plan p, int32_t max_calls) {
+    if (!p || max_calls < 0) return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    free_events(p);
+    if (max_calls == 0) return RPCHOLQR_OK;
+    const int total = max_calls * (RPCHOLQR_NUM_PHASES + 1);
+    p->events = new (std::nothrow) cudaEvent_t[total];
+    if (!p->events) return RPCHOLQR_ERR_NOMEM;
+    for (int i = 0; i < total; ++i) {
+        if (cudaEventCreate(&p->events[i]) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(p->events[j]);
+            delete[] p->events;
+            p->events = nullptr;
+            return RPCHOLQR_ERR_CUDA;
+        }
+    }
+    p->timing_slots = max_calls;
+    p->timed_calls = 0;
+    return RPCHOLQR_OK;
+}
+
+rpcholqr_status rpcholqr_plan_collect_timing(rpcholqr_plan p, float* ms_per_phase, int32_t* calls,
+                                             int64_t* launches) {
+    if (!p) return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    if (ms_per_phase)
+        for (int ph = 0; ph < RPCHOLQR_NUM_PHASES; ++ph) ms_per_phase[ph] = 0.f;
+    const int n = p->events ? p->timed_calls : 0;
+    for (int c = 0; c < n; ++c) {
+        cudaEvent_t* ev = p->events + c * (RPCHOLQR_NUM_PHASES + 1);
+        if (cudaEventSynchronize(ev[RPCHOLQR_NUM_PHASES]) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+        for (int ph = 0; ph < RPCHOLQR_NUM_PHASES; ++ph) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+            if (ms_per_phase) ms_per_phase[ph] += ms;
+        }
+    }
+    if (calls) *calls = n;
+    if (launches) *launches = p->launches;
+    p->timed_calls = 0;
+    p->launches = 0;
+    return RPCHOLQR_OK;
+}
+
+rpcholqr_status rpcholqr_factor_host(rpcholqr_plan p, const double* A, int64_t m, int32_t n, int64_t lda,
+                                     int32_t s, uint64_t seed, double* Q, int64_t ldq, double* R,
+                                     int32_t* info_host, void* stream) {
+    if (!p || !A || !Q || !R || !info_host) return RPCHOLQR_ERR_ARG;
+    if (!shape_ok(p, m, n, s) || lda < n || ldq < n) return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t elems = static_cast<size_t>(m) * static_cast<size_t>(n);
+    if (elems > p->staged_elems || !p->hR) {
+        cudaFree(p->hA); cudaFree(p->hQ); cudaFree(p->hR); cudaFree(p->hinfo);
+        p->hA = p->hQ = p->hR = nullptr; p->hinfo = nullptr; p->staged_elems = 0;
+        const size_t nn = static_cast<size_t>(p->max_n) * p->max_n;
+        if (cudaMalloc(&p->hA, elems * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&p->hQ, elems * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&p->hR, nn * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&p->hinfo, 2 * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return RPCHOLQR_ERR_NOMEM;
+        }
+        p->staged_elems = elems;
+    }
+    const size_t row_bytes = static_cast<size_t>(n) * sizeof(double);
+    if (cudaMemcpy2DAsync(p->hA, row_bytes, A, static_cast<size_t>(lda) * sizeof(double), row_bytes,
+                          static_cast<size_t>(m), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    rpcholqr_status rc = rpcholqr_factor(p, p->hA, m, n, n, s, seed, p->hQ, n, p->hR, p->hinfo, stream);
+    if (rc != RPCHOLQR_OK) return rc;
+    if (cudaMemcpy2DAsync(Q, static_cast<size_t>(ldq) * sizeof(double), p->hQ, row_bytes, row_bytes,
+                          static_cast<size_t>(m), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(R, p->hR, static_cast<size_t>(n) * n * sizeof(double), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaMemcpyAsync(info_host, p->hinfo, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? RPCHOLQR_OK : RPCHOLQR_ERR_CUDA;
+}
+
+rpcholqr_status rpcholqr_sketch_r(rpcholqr_plan p, const double* A, int64_t m, int32_t n, int64_t lda,
+                                  int32_t s, uint64_t seed, double* Rs, int32_t* info, void* stream) {
+    if (!p || !A || !Rs || !info) return RPCHOLQR_ERR_ARG;
+    if (!shape_ok(p, m, n, s) || lda < n) return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rpcholqr_status rc = reset_info(info, st);
+    if (rc != RPCHOLQR_OK) return rc;
+    return sketch_internal(p, A, m, n, lda, s, seed, 0, Rs, info, st, nullptr);
+}
+
+rpcholqr_status rpcholqr_precondition_gram(rpcholqr_plan p, const double* A, int64_t m, int32_t n,
+                                           int64_t lda, const double* Rs, double* A1, int64_t ld1,
+                                           double* G, int32_t* info, void* stream) {
+    if (!p || !A || !Rs || !A1 || !G || !info) return RPCHOLQR_ERR_ARG;
+    if (n < 1 || n > p->max_n || m < 1 || m > p->max_m || lda < n || ld1 < n) return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rpcholqr_status rc = reset_info(info, st);
+    if (rc != RPCHOLQR_OK) return rc;
+    return precondition_internal(p, A, m, n, lda, Rs, n, A1, ld1, G, info, st, nullptr);
+}
+
+rpcholqr_status rpcholqr_cholesky(rpcholqr_plan p, const double* G, int32_t n, double* R1,
+                                  int32_t* info, void* stream) {
+    if (!p || !G || !R1 || !info || n < 1 || n > p->max_n) return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rpcholqr_status rc = reset_info(info, st);
+    if (rc != RPCHOLQR_OK) return rc;
+    const int np = pad16(n);
+    return launch_cholesky(G, n, n, np, p->R1, R1, info, st) == cudaSuccess ? RPCHOLQR_OK
+                                                                             : RPCHOLQR_ERR_CUDA;
+}
+
+rpcholqr_status rpcholqr_solve_rows(rpcholqr_plan p, const double* X, int64_t m, int32_t n, int64_t ldx,
+                                    const double* T, double* Y, int64_t ldy, int32_t* info,
+                                    void* stream) {
+    if (!p || !X || !T || !Y || !info) return RPCHOLQR_ERR_ARG;
+    if (n < 1 || n > p->max_n || m < 1 || m > p->max_m || ldx < n || ldy < n) return RPCHOLQR_ERR_ARG;
+    if (X == Y && ldx != ldy) return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rpcholqr_status rc = reset_info(info, st);
+    if (rc != RPCHOLQR_OK) return rc;
+    return solve_internal(p, X, m, n, ldx, T, n, Y, ldy, info, st, nullptr);
+}
+
+rpcholqr_status rpcholqr_triu_mul(const double* R1, const double* Rs, int32_t n, double* R, void* stream) {
+    if (!R1 || !Rs || !R || n < 1) return RPCHOLQR_ERR_ARG;
+    launch_triu_mul(R1, n, Rs, n, n, R, n, nullptr, static_cast<cudaStream_t>(stream));
+    return check_launch();
+}
+
+rpcholqr_status rpcholqr_probe_fp64_mma(int device, int32_t iters, double* flops_per_s) {
+    if (!flops_per_s || iters < 1) return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    return run_fp64_mma_probe(iters, flops_per_s) == cudaSuccess ? RPCHOLQR_OK : RPCHOLQR_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,50 @@
+// Device-side building blocks shared by the rpCholesky-QR kernels (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rpcholqr.h"
+
+namespace rpq {
+
+// Every matrix dimension is padded to a multiple of this (the k extent of mma m16n8k16).
+constexpr int kPad = 16;
+constexpr int kMaxNP = RPCHOLQR_MAX_N;  // padded n handled by the row-pass kernels
+
+__host__ __device__ constexpr int pad16(int n) { return (n + kPad - 1) / kPad * kPad; }
+
+// ---- status word: info[0] = status, info[1] = pivot ---------------------------------------------
+__device__ __forceinline__ int load_status(const int32_t* info) {
+    return *reinterpret_cast<const volatile int32_t*>(info);
+}
+// First error wins.
+__device__ __forceinline__ void set_status(int32_t* info, int status, int pivot = -1) {
+    if (atomicCAS(info, 0, status) == 0 && pivot >= 0) info[1] = pivot;
+}
+
+// ---- FP64 tensor-core mma: D(16x8) += A(16x16) * B(16x8), all FP64 ------------------------------
+// Fragment layouts (g = lane/4, t = lane%4):
+//   A: a[i] = A[g + 8*(i&1)][t + 4*(i>>1)]      i = 0..7
+//   B: b[i] = B[t + 4*i][g]                     i = 0..3
+//   C: c[i] = C[g + 8*(i>>1)][2*t + (i&1)]      i = 0..3
+__device__ __forceinline__ void mma_f64_16816(double (&d)[4], const double (&a)[8],
+                                              const double (&b)[4]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, "
+        "{%4,%5,%6,%7,%8,%9,%10,%11}, {%12,%13,%14,%15}, {%0,%1,%2,%3};\n"
+        : "+d"(d[0]), "+d"(d[1]), "+d"(d[2]), "+d"(d[3])
+        : "d"(a[0]), "d"(a[1]), "d"(a[2]), "d"(a[3]), "d"(a[4]), "d"(a[5]), "d"(a[6]), "d"(a[7]),
+          "d"(b[0]), "d"(b[1]), "d"(b[2]), "d"(b[3]));
+}
+
+// ---- cp.async (Ampere+ LDGSTS), 8-byte granules with zero fill ----------------------------------
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src, bool valid) {
+    unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    int src_size = valid ? 8 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem_src),
+                 "r"(src_size));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+}  // namespace rpq
