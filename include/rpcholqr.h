@@ -146,6 +146,23 @@ rpcholqr_status rpcholqr_triu_mul(const double* R1, const double* Rs, int32_t n,
  * FP64 roofline denominator measured on the running GPU. */
 rpcholqr_status rpcholqr_probe_fp64_mma(int device, int32_t iters, double* flops_per_s);
 
+/* Allocation-free variant of rpcholqr_precondition_gram (same arguments without the plan, same
+ * results on the same GPU).  The paper has no counterpart: this exists for callers that may not
+ * allocate device memory once running -- code living inside a framework whose allocator owns the
+ * device memory, or services that reserve memory at start-up and forbid cudaMalloc/cudaFree later
+ * (both synchronise the device and can fail under pressure).  Such callers cannot create a plan.
+ * Scratch comes from one fixed __device__ array of about 5.3 MB inside the library, which every
+ * GPU that loads the library holds until the process exits; it fits n <= 64 (larger n returns
+ * RPCHOLQR_ERR_UNSUPPORTED; any m is accepted).  The call allocates nothing and calls no
+ * allocating library routine.  Runs on the current device.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current, so make that first
+ * call before any stream capture.  Every call shares the array and leaves its contents behind:
+ * calls whose kernels overlap on the GPU (other streams, other threads) race on it and must be
+ * serialised by the caller. */
+rpcholqr_status rpcholqr_precondition_gram_noalloc(const double* A, int64_t m, int32_t n, int64_t lda,
+                                                   const double* Rs, double* A1, int64_t ld1,
+                                                   double* G, int32_t* info, void* stream);
+
 /* ---- per-phase timing (CUDA events on the call's stream) ----
  * Phases of one rpcholqr_factor call, in launch order. */
 enum {

@@ -305,3 +305,24 @@ def rpcholqr_plan_collect_timing(plan: Plan):
     _check("rpcholqr_plan_collect_timing", load_library().rpcholqr_plan_collect_timing(
         plan.handle, ctypes.cast(ms, ctypes.c_void_p), ctypes.byref(calls), ctypes.byref(launches)))
     return dict(zip(PHASES, [float(x) for x in ms])), int(calls.value), int(launches.value)
+
+
+def rpcholqr_precondition_gram_noalloc(A, Rs, A1, G, info, stream=None):
+    """Plan-free, allocation-free fused pass (n <= 64): every output buffer is the caller's.
+
+    For callers that may not allocate device memory while running; the library's fixed device
+    scratch array is used instead (see include/rpcholqr.h).  Calls must not overlap on the GPU."""
+    lib = load_library()
+    f = lib.rpcholqr_precondition_gram_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    _mat(A, "A")
+    m, n = A.shape
+    Rs = _mat(Rs.contiguous(), "Rs")
+    _mat(A1, "A1")
+    _mat(G, "G")
+    _check("rpcholqr_precondition_gram_noalloc", f(
+        _ptr(A), m, n, A.stride(0), _ptr(Rs), _ptr(A1), A1.stride(0), _ptr(G), _ptr(info),
+        _stream(stream, A.device)))
+    return A1, G, info
