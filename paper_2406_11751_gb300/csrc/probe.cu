@@ -10,7 +10,7 @@ __global__ void __launch_bounds__(256) k_probe_fp64_mma(double* out, int iters, 
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) c[j][q] = threadIdx.x * 1e-3 + q;
+        for (int q = 0; q < 4; ++q) c[j][q] = threadIdx.x * 1e-3 + q + 0.25 * j;  // distinct chains
     double a[8], b[4];
 #pragma unroll
     for (int q = 0; q < 8; ++q) a[q] = seed + q * 1e-9;
