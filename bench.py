@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--inputs", choices=["gpu", "cpu"], default="gpu",
                     help="draw A with torch on the GPU (fast) or with the numpy recipe on the host")
     ap.add_argument("--no-metrics", action="store_true", help="skip the orthogonality/residual check")
+    ap.add_argument("--mode", choices=["fp64", "split"], default="fp64",
+                    help="fp64: every step in FP64; split: Ozaki-split BF16 tensor-core products")
     return ap.parse_args()
 
 
@@ -253,7 +255,7 @@ def run_ours(args, ws, rank, local):
     Q = torch.empty_like(A)
     R = torch.empty((n, n), dtype=torch.float64, device=dev)
     info = torch.empty(2, dtype=torch.int32, device=dev)
-    plan = rq.rpcholqr_plan_create(local, m, n, s)
+    plan = rq.rpcholqr_plan_create(local, m, n, s, mode=rq.SPLIT64 if args.mode == "split" else rq.FP64)
     stream = torch.cuda.current_stream(dev)
     fp64_peak = rq.rpcholqr_probe_fp64_mma(local, 4096)
 
@@ -327,8 +329,8 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": N, "steps": K, "warmup": W,
         "ms_per_step": t_ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (A = U diag(sigma) V^T, Haar U/V from torch, sigma log-spaced)",
-        "config": {"workload": f"rpCholesky-QR FP64 m={m} n={n} s={s} kappa={args.kappa:g}", "m": m,
-                   "n": n, "s": s, "kappa": args.kappa, "mode": "fp64",
+        "config": {"workload": f"rpCholesky-QR {args.mode.upper()} m={m} n={n} s={s} kappa={args.kappa:g}", "m": m,
+                   "n": n, "s": s, "kappa": args.kappa, "mode": args.mode,
                    "l2": f"inputs larger than L2 (A = {8 * m * n / 1e9:.2f} GB > 129 MB), no flush"},
         "effective_tflops": flops * value / 1e12,
         "orth": orth, "residual": res, "gate_orth_le_1e-13": None if orth is None else bool(orth <= 1e-13), "status": st[0],

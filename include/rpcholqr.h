@@ -61,7 +61,13 @@ typedef enum {
 } rpcholqr_status;
 
 typedef enum {
-    RPCHOLQR_FP64 = 0 /* every step in FP64 (FP64 tensor-core mma.sync m16n8k16 + DFMA)          */
+    RPCHOLQR_FP64 = 0,   /* every step in FP64 (FP64 tensor-core mma.sync m16n8k16 + DFMA)        */
+    RPCHOLQR_SPLIT64 = 1 /* FP64-accurate split precision: sketch QR, Cholesky and the diagonal
+                            blocks of the row solves in FP64; the Gram matrix, the off-diagonal
+                            block update of the row solve (n > 64) and Q = A1 R1^{-1} (explicit
+                            inverse of the well-conditioned R1) as Ozaki-split BF16 tensor-core
+                            (tcgen05) products with exact FP32 group sums and int64 combination.
+                            Needs an extra max_m x n FP64 plan buffer for A1.                      */
 } rpcholqr_mode;
 
 /* Largest n a plan accepts. */
@@ -140,6 +146,21 @@ rpcholqr_status rpcholqr_solve_rows(rpcholqr_plan plan, const double* X, int64_t
 /* R = R1 Rs for device n x n upper-triangular R1, Rs (step 'recover'); R device n x n. */
 rpcholqr_status rpcholqr_triu_mul(const double* R1, const double* Rs, int32_t n, double* R,
                                   void* stream);
+
+/* Split-precision FP64 product C = X Y on the BF16 tensor cores (the kernel SPLIT64 uses):
+ * X device m x K (ldx), Y device K x N (ldy), C device m x N (ldc), K, N <= plan max_n; each entry
+ * carries an absolute error below ~2^-53 * 2^(Ex+Ey) (Ex, Ey: power-of-two bounds of row i of X and
+ * column j of Y).  The plan must be a SPLIT64 plan.  info as above (RPCHOLQR_ERR_TIMEOUT if a bounded
+ * tensor-core wait gave up). */
+rpcholqr_status rpcholqr_ozaki_gemm(rpcholqr_plan plan, const double* X, int64_t m, int32_t K, int64_t ldx,
+                                    const double* Y, int32_t N, int64_t ldy, double* C, int64_t ldc,
+                                    int32_t* info, void* stream);
+
+/* Split-precision Gram matrix G = X^T X (device n x n, full) of X (device m x n, ldx), the kernel
+ * SPLIT64 uses for G1; error per entry below ~2^-53 * 2^(Ep+Eq) * rows (Ep: power-of-two bound of
+ * column p).  SPLIT64 plan, m <= plan max_m. */
+rpcholqr_status rpcholqr_ozaki_gram(rpcholqr_plan plan, const double* X, int64_t m, int32_t n, int64_t ldx,
+                                    double* G, int32_t* info, void* stream);
 
 /* FP64 tensor-pipe throughput probe: runs `iters` chains of dependent m16n8k16 FP64 mma on every
  * SM and writes the sustained FLOP/s to *flops_per_s (host).  Synchronous.  Used to report the

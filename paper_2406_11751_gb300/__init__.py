@@ -18,13 +18,15 @@ __all__ = [
     "rpcholqr_workspace_size", "rpcholqr_factor", "rpcholqr_factor_host", "rpcholqr_sample_indices",
     "rpcholqr_sketch_r", "rpcholqr_precondition_gram", "rpcholqr_cholesky", "rpcholqr_solve_rows",
     "rpcholqr_triu_mul", "rpcholqr_probe_fp64_mma", "rpcholqr_status_string", "EXPORTED_SYMBOLS",
-    "rpcholqr_plan_enable_timing", "rpcholqr_plan_collect_timing", "PHASES",
+    "rpcholqr_plan_enable_timing", "rpcholqr_plan_collect_timing", "PHASES", "rpcholqr_ozaki_gemm",
+    "rpcholqr_ozaki_gram", "SPLIT64",
 ]
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NONFINITE", 3: "ERR_SINGULAR_SKETCH", 4: "ERR_NOT_SPD",
           5: "ERR_TIMEOUT", 6: "ERR_CUDA", 7: "ERR_NOMEM", 8: "ERR_UNSUPPORTED"}
 OK, ERR_ARG, ERR_NONFINITE, ERR_SINGULAR_SKETCH, ERR_NOT_SPD = 0, 1, 2, 3, 4
 FP64 = 0
+SPLIT64 = 1
 MAX_N = 128
 
 EXPORTED_SYMBOLS = (
@@ -32,7 +34,7 @@ EXPORTED_SYMBOLS = (
     "rpcholqr_factor_host", "rpcholqr_sample_indices", "rpcholqr_sketch_r",
     "rpcholqr_precondition_gram", "rpcholqr_cholesky", "rpcholqr_solve_rows", "rpcholqr_triu_mul",
     "rpcholqr_probe_fp64_mma", "rpcholqr_status_string", "rpcholqr_plan_enable_timing",
-    "rpcholqr_plan_collect_timing",
+    "rpcholqr_plan_collect_timing", "rpcholqr_ozaki_gemm", "rpcholqr_ozaki_gram",
 )
 PHASES = ("sample", "sketch_qr", "prep_rs", "pass1", "gram_reduce", "cholesky", "prep_r1", "pass2",
           "recover_r")
@@ -76,6 +78,8 @@ def load_library():
         "rpcholqr_probe_fp64_mma": [ctypes.c_int, I32, ctypes.POINTER(D)],
         "rpcholqr_plan_enable_timing": [P, I32],
         "rpcholqr_plan_collect_timing": [P, P, ctypes.POINTER(I32), ctypes.POINTER(I64)],
+        "rpcholqr_ozaki_gemm": [P, P, I64, I32, I64, P, I32, I64, P, I64, P, P],
+        "rpcholqr_ozaki_gram": [P, P, I64, I32, I64, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -281,6 +285,35 @@ def rpcholqr_triu_mul(R1, Rs, R=None, stream=None):
     _check("rpcholqr_triu_mul", load_library().rpcholqr_triu_mul(
         _ptr(R1), _ptr(Rs), n, _ptr(R), _stream(stream, R1.device)))
     return R
+
+
+def rpcholqr_ozaki_gemm(plan: Plan, X, Y, C=None, info=None, stream=None):
+    """C = X Y as a split-precision (FP64-accurate) BF16 tensor-core product (SPLIT64 plan)."""
+    torch = _torch()
+    _mat(X, "X")
+    _mat(Y, "Y")
+    m, K = X.shape
+    N = Y.shape[1]
+    if C is None:
+        C = torch.empty((m, N), dtype=torch.float64, device=X.device)
+    info = _info(info, X.device)
+    _check("rpcholqr_ozaki_gemm", load_library().rpcholqr_ozaki_gemm(
+        plan.handle, _ptr(X), m, K, X.stride(0), _ptr(Y), N, Y.stride(0), _ptr(C), C.stride(0),
+        _ptr(info), _stream(stream, X.device)))
+    return C, info
+
+
+def rpcholqr_ozaki_gram(plan: Plan, X, G=None, info=None, stream=None):
+    """G = X^T X as a split-precision BF16 tensor-core product (SPLIT64 plan)."""
+    torch = _torch()
+    _mat(X, "X")
+    m, n = X.shape
+    if G is None:
+        G = torch.empty((n, n), dtype=torch.float64, device=X.device)
+    info = _info(info, X.device)
+    _check("rpcholqr_ozaki_gram", load_library().rpcholqr_ozaki_gram(
+        plan.handle, _ptr(X), m, n, X.stride(0), _ptr(G), _ptr(info), _stream(stream, X.device)))
+    return G, info
 
 
 def rpcholqr_probe_fp64_mma(device: int = 0, iters: int = 2048) -> float:

@@ -30,8 +30,28 @@ cudaError_t launch_rowpass(bool syrk, int np, const double* X, int64_t ldx, doub
                            int32_t* info, int grid, cudaStream_t st);
 void launch_gram_reduce(const double* gpart, int nparts, int np, int n, double* G, int64_t ldg,
                         const int32_t* info, cudaStream_t st);
+cudaError_t launch_rowpass_ex(bool syrk, int np, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                              int64_t m, int n, const double* frag, const double* diag, double* gpart,
+                              int32_t* info, int grid, cudaStream_t st, bool check_finite);
 // probe.cu
 cudaError_t run_fp64_mma_probe(int iters, double* flops_per_s);
+// smallfactor.cu
+void launch_triu_inv(const double* T, int64_t ldt, int n, int np, double* W, const int32_t* info,
+                     cudaStream_t st);
+// ozaki.cu
+size_t ozaki_yblocks_bytes(int K, int N);
+int32_t ozaki_no_exp();
+void launch_ozaki_slice_cols(const double* Y, int64_t ldy, int K, int N, uint8_t* blocks, int32_t* yexp,
+                             const int32_t* info, cudaStream_t st);
+cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int32_t* xexp, int K,
+                              const uint8_t* yblocks, const int32_t* yexp, int N, const double* B,
+                              int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, int grid,
+                              cudaStream_t st);
+int ozaki_gram_halves(int np);
+cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
+                              int nranges, double* gpart, int32_t* info, cudaStream_t st);
+void launch_row_exp(const double* X, int64_t ldx, int64_t m, int K, int32_t* rowexp, cudaStream_t st);
+void launch_col_exp(const double* X, int64_t ldx, int64_t m, int n, int32_t* colexp, cudaStream_t st);
 }  // namespace rpq
 
 using namespace rpq;
@@ -65,6 +85,14 @@ struct rpcholqr_plan_s {
     int32_t timed_calls = 0;
     cudaEvent_t* events = nullptr;  // timing_slots x (RPCHOLQR_NUM_PHASES + 1)
     int64_t launches = 0;
+    // SPLIT64 buffers (separate allocation)
+    void* split_ws = nullptr;
+    double* A1 = nullptr;       // max_m x np
+    int32_t* xexp = nullptr;    // max_m
+    int32_t* colexp = nullptr;  // np
+    int32_t* yexp = nullptr;    // np
+    uint8_t* yblocks = nullptr; // Ozaki column slices (K, N <= np)
+    double* W = nullptr;        // np x np
 };
 
 namespace {
@@ -183,7 +211,7 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
     if (!plan) return RPCHOLQR_ERR_ARG;
     *plan = nullptr;
     if (max_n < 1 || max_n > RPCHOLQR_MAX_N || max_s < max_n || max_m < max_s) return RPCHOLQR_ERR_ARG;
-    if (mode != RPCHOLQR_FP64) return RPCHOLQR_ERR_UNSUPPORTED;
+    if (mode != RPCHOLQR_FP64 && mode != RPCHOLQR_SPLIT64) return RPCHOLQR_ERR_UNSUPPORTED;
     if (householder_smem_bytes(max_s) > 200 * 1024) return RPCHOLQR_ERR_UNSUPPORTED;
     DeviceGuard guard(device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
@@ -214,6 +242,31 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
     p->diag_1 = reinterpret_cast<double*>(b + L.diag_1);
     p->gpart = reinterpret_cast<double*>(b + L.gpart);
     p->info_ws = reinterpret_cast<int32_t*>(b + L.info);
+    if (mode == RPCHOLQR_SPLIT64) {
+        const size_t np = static_cast<size_t>(p->np);
+        size_t off = 0;
+        auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+        const size_t oA1 = take(sizeof(double) * static_cast<size_t>(max_m) * np);
+        const size_t oX = take(sizeof(int32_t) * static_cast<size_t>(max_m));
+        const size_t oC = take(sizeof(int32_t) * np);
+        const size_t oY = take(sizeof(int32_t) * np);
+        const size_t oB = take(ozaki_yblocks_bytes(p->np, p->np));
+        const size_t oW = take(sizeof(double) * np * np);
+        if (cudaMalloc(&p->split_ws, off) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(p->ws);
+            delete p;
+            return RPCHOLQR_ERR_NOMEM;
+        }
+        char* c = static_cast<char*>(p->split_ws);
+        p->A1 = reinterpret_cast<double*>(c + oA1);
+        p->xexp = reinterpret_cast<int32_t*>(c + oX);
+        p->colexp = reinterpret_cast<int32_t*>(c + oC);
+        p->yexp = reinterpret_cast<int32_t*>(c + oY);
+        p->yblocks = reinterpret_cast<uint8_t*>(c + oB);
+        p->W = reinterpret_cast<double*>(c + oW);
+        p->ws_bytes += off;
+    }
     *plan = p;
     return RPCHOLQR_OK;
 }
@@ -227,6 +280,7 @@ rpcholqr_status rpcholqr_plan_destroy(rpcholqr_plan plan) {
     cudaFree(plan->hQ);
     cudaFree(plan->hR);
     cudaFree(plan->hinfo);
+    cudaFree(plan->split_ws);
     free_events(plan);
     delete plan;
     return RPCHOLQR_OK;
@@ -296,6 +350,102 @@ static rpcholqr_status solve_internal(rpcholqr_plan p, const double* X, int64_t 
     return RPCHOLQR_OK;
 }
 
+// C = X Y (sub = false) or C = B - X Y (sub = true) on the tensor cores; X row bounds computed here.
+static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const double* X, int64_t m, int K,
+                                           int64_t ldx, const double* Y, int N, int64_t ldy, const double* B,
+                                           int64_t ldb, double* C, int64_t ldc, int32_t* info, cudaStream_t st) {
+    launch_row_exp(X, ldx, m, K, p->xexp, st);
+    launch_ozaki_slice_cols(Y, ldy, K, N, p->yblocks, p->yexp, info, st);
+    p->launches += 2;
+    if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
+    const int64_t tiles = ((m + 127) / 128) * ((N + 63) / 64);
+    const int grid = static_cast<int>(tiles < p->grid ? tiles : p->grid);
+    if (launch_ozaki_gemm(sub, X, ldx, p->xexp, K, p->yblocks, p->yexp, N, B, ldb, C, ldc, m, info, grid, st) !=
+        cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    ++p->launches;
+    return RPCHOLQR_OK;
+}
+
+// G (n x n, ld ldg) = X^T X on the tensor cores: column bounds, per-range partials, fixed-order sum.
+static rpcholqr_status ozaki_gram_internal(rpcholqr_plan p, const double* X, int64_t m, int n, int64_t ldx,
+                                           double* G, int64_t ldg, int32_t* info, cudaStream_t st) {
+    const int np = pad16(n);
+    launch_col_exp(X, ldx, m, n, p->colexp, st);
+    p->launches += 2;
+    const int nh = ozaki_gram_halves(np);
+    int nranges = p->grid / nh;
+    if (nranges < 1) nranges = 1;
+    const int64_t max_ranges = (m + 31) / 32;
+    if (nranges > max_ranges) nranges = static_cast<int>(max_ranges);
+    if (launch_ozaki_gram(X, ldx, m, n, np, p->colexp, nranges, p->gpart, info, st) != cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    ++p->launches;
+    launch_gram_reduce(p->gpart, nranges, np, n, G, ldg, info, st);
+    ++p->launches;
+    return check_launch();
+}
+
+// SPLIT64 factorisation: see rpcholqr_mode.  A1 lives in the plan's buffer, Q receives only Q.
+static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m, int32_t n, int64_t lda,
+                                    int32_t s, uint64_t seed, double* Q, int64_t ldq, double* R,
+                                    int32_t* info, cudaStream_t st, const PhaseMarks& pm) {
+    const int np = pad16(n);
+    rpcholqr_status rc = sketch_internal(p, A, m, n, lda, s, seed, 0, nullptr, info, st, &pm);
+    if (rc != RPCHOLQR_OK) return rc;
+    double* A1 = p->A1;
+    const int64_t ld1 = np;
+    const int64_t panels = (m + 127) / 128;
+    const int grid = static_cast<int>(panels < p->grid ? panels : p->grid);
+    pm.mark(RPCHOLQR_PHASE_PREP_RS);
+    if (n <= 64) {
+        launch_prep_tri(p->Rs, np, n, np, p->frag_s, p->diag_s, info, st);
+        ++p->launches;
+        pm.mark(RPCHOLQR_PHASE_PASS1);
+        if (launch_rowpass_ex(false, np, A, lda, A1, ld1, m, n, p->frag_s, p->diag_s, nullptr, info, grid, st,
+                              true) != cudaSuccess)
+            return RPCHOLQR_ERR_CUDA;
+        ++p->launches;
+    } else {
+        const int n2 = n - 64;
+        launch_prep_tri(p->Rs, np, 64, 64, p->frag_s, p->diag_s, info, st);
+        launch_prep_tri(p->Rs + 64 * np + 64, np, n2, pad16(n2), p->frag_1, p->diag_1, info, st);
+        p->launches += 2;
+        pm.mark(RPCHOLQR_PHASE_PASS1);
+        // A1[:, :64] = A[:, :64] R11^{-1}
+        if (launch_rowpass_ex(false, 64, A, lda, A1, ld1, m, 64, p->frag_s, p->diag_s, nullptr, info, grid, st,
+                              true) != cudaSuccess)
+            return RPCHOLQR_ERR_CUDA;
+        ++p->launches;
+        // A1[:, 64:] = A[:, 64:] - A1[:, :64] R12   (tensor cores)
+        if ((rc = ozaki_gemm_internal(p, true, A1, m, 64, ld1, p->Rs + 64, n2, np, A + 64, lda, A1 + 64, ld1,
+                                      info, st)) != RPCHOLQR_OK)
+            return rc;
+        // A1[:, 64:] = A1[:, 64:] R22^{-1}
+        if (launch_rowpass_ex(false, pad16(n2), A1 + 64, ld1, A1 + 64, ld1, m, n2, p->frag_1, p->diag_1, nullptr,
+                              info, grid, st, true) != cudaSuccess)
+            return RPCHOLQR_ERR_CUDA;
+        ++p->launches;
+    }
+    pm.mark(RPCHOLQR_PHASE_GRAM_REDUCE);
+    if ((rc = ozaki_gram_internal(p, A1, m, n, ld1, p->G, np, info, st)) != RPCHOLQR_OK) return rc;
+    pm.mark(RPCHOLQR_PHASE_CHOLESKY);
+    if (launch_cholesky(p->G, np, n, np, p->R1, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    ++p->launches;
+    pm.mark(RPCHOLQR_PHASE_PREP_R1);
+    launch_triu_inv(p->R1, np, n, np, p->W, info, st);
+    ++p->launches;
+    pm.mark(RPCHOLQR_PHASE_PASS2);
+    if ((rc = ozaki_gemm_internal(p, false, A1, m, n, ld1, p->W, n, np, nullptr, 0, Q, ldq, info, st)) !=
+        RPCHOLQR_OK)
+        return rc;
+    pm.mark(RPCHOLQR_PHASE_RECOVER_R);
+    launch_triu_mul(p->R1, np, p->Rs, np, n, R, n, info, st);
+    ++p->launches;
+    pm.mark(RPCHOLQR_NUM_PHASES);
+    return check_launch();
+}
+
 rpcholqr_status rpcholqr_factor(rpcholqr_plan p, const double* A, int64_t m, int32_t n, int64_t lda,
                                 int32_t s, uint64_t seed, double* Q, int64_t ldq, double* R,
                                 int32_t* info, void* stream) {
@@ -308,6 +458,7 @@ rpcholqr_status rpcholqr_factor(rpcholqr_plan p, const double* A, int64_t m, int
     const PhaseMarks pm(p, st);
     rpcholqr_status rc = reset_info(info, st);
     if (rc != RPCHOLQR_OK) return rc;
+    if (p->mode == RPCHOLQR_SPLIT64) return factor_split(p, A, m, n, lda, s, seed, Q, ldq, R, info, st, pm);
     if ((rc = sketch_internal(p, A, m, n, lda, s, seed, 0, nullptr, info, st, &pm)) != RPCHOLQR_OK) return rc;
     if ((rc = precondition_internal(p, A, m, n, lda, p->Rs, np, Q, ldq, nullptr, info, st, &pm)) !=
         RPCHOLQR_OK)
@@ -463,6 +614,32 @@ rpcholqr_status rpcholqr_triu_mul(const double* R1, const double* Rs, int32_t n,
     if (!R1 || !Rs || !R || n < 1) return RPCHOLQR_ERR_ARG;
     launch_triu_mul(R1, n, Rs, n, n, R, n, nullptr, static_cast<cudaStream_t>(stream));
     return check_launch();
+}
+
+rpcholqr_status rpcholqr_ozaki_gemm(rpcholqr_plan p, const double* X, int64_t m, int32_t K, int64_t ldx,
+                                    const double* Y, int32_t N, int64_t ldy, double* C, int64_t ldc,
+                                    int32_t* info, void* stream) {
+    if (!p || !X || !Y || !C || !info || p->mode != RPCHOLQR_SPLIT64) return RPCHOLQR_ERR_ARG;
+    if (m < 1 || m > p->max_m || K < 1 || K > p->np || N < 1 || N > p->np || ldx < K || ldy < N || ldc < N)
+        return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rpcholqr_status rc = reset_info(info, st);
+    if (rc != RPCHOLQR_OK) return rc;
+    return ozaki_gemm_internal(p, false, X, m, K, ldx, Y, N, ldy, nullptr, 0, C, ldc, info, st);
+}
+
+rpcholqr_status rpcholqr_ozaki_gram(rpcholqr_plan p, const double* X, int64_t m, int32_t n, int64_t ldx,
+                                    double* G, int32_t* info, void* stream) {
+    if (!p || !X || !G || !info || p->mode != RPCHOLQR_SPLIT64) return RPCHOLQR_ERR_ARG;
+    if (m < 1 || m > p->max_m || n < 1 || n > p->max_n || ldx < n) return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rpcholqr_status rc = reset_info(info, st);
+    if (rc != RPCHOLQR_OK) return rc;
+    return ozaki_gram_internal(p, X, m, n, ldx, G, n, info, st);
 }
 
 rpcholqr_status rpcholqr_probe_fp64_mma(int device, int32_t iters, double* flops_per_s) {

@@ -1,0 +1,624 @@
+// Split-precision (Ozaki-style) FP64 products on the GB300 BF16 tensor cores (tcgen05).
+//
+// Used by the SPLIT64 mode for the well-conditioned products of Algorithm alg_2 (Section 4):
+//   Gram          G_1 = A_1^T A_1               (k_ozaki_gram)
+//   solve         Q   = A_1 R_1^{-1}            (k_ozaki_gemm with the explicit R_1^{-1}; kappa(R_1) =
+//                                                kappa(A_1) is small, Lemma l_31)
+//   precondition  the off-diagonal block update A[:,J] - A_1[:,<J] R_s[<J,J] of the blocked row solve
+//                                               (k_ozaki_gemm, subtract form; the diagonal blocks stay
+//                                                FP64 substitution)
+//
+// Splitting (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix multiplication by using
+// fast routines of matrix multiplication and its applications", Numer. Algorithms 2012, restated): every
+// FP64 value x of a row (or column) with the shared power-of-two bound 2^E > max|x| is cut into eight
+// 7-bit signed integer slices, x = 2^E sum_{a=1..8} s_a 2^{-7a} + O(2^{E-56}), |s_a| <= 127 (exact in
+// BF16).  A product of two such operands is sum_{a,b} 2^{-7(a+b)} S_a S_b; the 36 slice pairs with
+// a + b <= 9 are kept (the dropped ones are below 2^-53 of the scale).  Pairs with the same d = a + b
+// share one FP32 accumulator in tensor memory: with K <= 128 every partial sum is an integer below
+// 8 * 127^2 * 128 < 2^24, so the FP32 accumulation is exact.  The eight accumulators (d = 2..9) are
+// combined exactly in int64, I = sum_{d<=6} M_d 2^{7(6-d)} + rint(sum_{d>6} M_d 2^{7(6-d)}), and the
+// result is 2^{E_x + E_y - 42} I.
+//
+// Tile: M = 128 output rows (TMEM lanes) x N = 64 output columns; 8 groups x 64 columns = the 512 TMEM
+// columns of the SM.  K is staged 32 at a time in shared memory (core-matrix K-major layout, no
+// swizzle), two stages in flight: while the tensor core works on one stage the CTA slices the next.
+// One thread issues the 72 tcgen05.mma of a stage and commits them to the stage's mbarrier.  Every
+// mbarrier wait is bounded; on timeout the kernel records RPCHOLQR_ERR_TIMEOUT, waits (bounded) for
+// its own MMAs, frees its tensor memory and returns.
+#include <climits>
+
+#include "common.cuh"
+
+namespace rpq {
+namespace oz {
+
+constexpr int kSlices = 8;
+constexpr int kGroups = 8;                 // d = 2..9
+constexpr int kTileM = 128;
+constexpr int kTileN = 64;
+constexpr int kKW = 32;                    // K per stage
+constexpr int kThreads = 256;            // 8 warps: 2 producers per tile row, 2 drain warps per TMEM lane quarter
+constexpr int kSBO = (kKW * 2 / 16) * 128; // 512 B between 8-row core-matrix groups
+constexpr int kLBO = 128;                  // 128 B between K-adjacent core matrices
+constexpr int kASlice = kTileM * kKW * 2;  // 8 KB
+constexpr int kBSlice = kTileN * kKW * 2;  // 4 KB
+constexpr int kAStage = kSlices * kASlice; // 64 KB
+constexpr int kBStage = kSlices * kBSlice; // 32 KB
+constexpr int kTmemCols = 512;
+constexpr long kSpinLimit = 1L << 24;
+constexpr int kNoExp = INT_MIN / 2;        // "row/column is all zero" marker (below any real exponent)
+// BF16 x BF16 -> FP32, A and B K-major, M = 128, N = 64
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
+                            ((uint32_t)(kTileM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// byte offset of (row r, K byte kb) inside one slice of a stage (8-row x 16-byte core matrices)
+__device__ __forceinline__ uint32_t core_off(int r, int kb) {
+    return (r >> 3) * kSBO + (kb >> 4) * kLBO + (r & 7) * 16 + (kb & 15);
+}
+// tcgen05 shared-memory matrix descriptor: start, LBO, SBO (>>4), version 1 at bit 46, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    return static_cast<uint64_t>((addr >> 4) & 0x3FFF) | (static_cast<uint64_t>(kLBO >> 4) << 16) |
+           (static_cast<uint64_t>(kSBO >> 4) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+        smem_u32(bar)));
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (long it = 0; it < kSpinLimit && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity));
+    }
+    return done != 0;
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(addr));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t addr, float (&v)[4]) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// Exponent bound: |v| < 2^e for a normal v (e = unbiased exponent + 1); kNoExp for 0/subnormal.
+__device__ __forceinline__ int exp_bound(double v) {
+    const int ex = static_cast<int>((__double_as_longlong(v) >> 52) & 0x7FF);
+    return ex == 0 ? kNoExp : ex - 1022;
+}
+
+// 56-bit fixed-point magnitude F = floor(|x| 2^{56-E}) of x relative to the bound 2^E > |x|, split in
+// two 28-bit halves (hi: slices 1..4, lo: slices 5..8).  0 for zero, subnormal, non-finite or unknown E.
+__device__ __forceinline__ void fixed56(double x, int E, uint32_t& fhi, uint32_t& flo) {
+    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+    const int ex = static_cast<int>((bits >> 52) & 0x7FF);
+    unsigned long long F = 0;
+    if (ex != 0 && ex != 0x7FF && E > kNoExp) {
+        const unsigned long long mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+        const int sh = ex - 1019 - E;          // F = mant 2^sh, < 2^56 when |x| < 2^E
+        if (sh > 3) F = (1ull << 56) - 1;      // |x| >= 2^E: not a valid bound; saturate
+        else if (sh >= 0) F = mant << sh;
+        else if (sh > -64) F = mant >> (-sh);
+    }
+    fhi = static_cast<uint32_t>(F >> 28);
+    flo = static_cast<uint32_t>(F) & 0x0FFFFFFFu;
+}
+
+// Two 7-bit fields (bits pos..pos+6 of u0 and u1) as a packed BF16 pair (u0 in the low half): each
+// field v becomes the float 2^23 + v minus 2^23, whose upper 16 bits are the exact BF16 of v.
+__device__ __forceinline__ uint32_t bf16x2_field(uint32_t u0, uint32_t u1, int pos) {
+    const float f0 = __uint_as_float(0x4B000000u | ((u0 >> pos) & 0x7Fu)) - 8388608.0f;
+    const float f1 = __uint_as_float(0x4B000000u | ((u1 >> pos) & 0x7Fu)) - 8388608.0f;
+    return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+}
+
+// Slice the 8 values x[0..7] (consecutive K) and store slice a of all eight as one 16-byte core-matrix
+// row at dst + a * slice_bytes (x[i] in BF16 lane i).  Every slice carries the sign of its value.
+__device__ __forceinline__ void slice_store8(const double (&x)[8], int E, uint8_t* dst, int slice_bytes) {
+    uint32_t fh[8], fl[8], smask[4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) fixed56(x[i], E, fh[i], fl[i]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        smask[j] = ((__double_as_longlong(x[2 * j]) < 0) ? 0x8000u : 0u) |
+                   ((__double_as_longlong(x[2 * j + 1]) < 0) ? 0x80000000u : 0u);
+#pragma unroll
+    for (int a = 0; a < kSlices; ++a) {
+        const int pos = 21 - 7 * (a & 3);
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            w[j] = (a < 4 ? bf16x2_field(fh[2 * j], fh[2 * j + 1], pos) : bf16x2_field(fl[2 * j], fl[2 * j + 1], pos)) |
+                   smask[j];
+        *reinterpret_cast<uint4*>(dst + a * slice_bytes) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Exact combination of the eight group sums M_d (d = 2..9) of one output element:
+//   I = sum_{d=2..6} M_d 2^{7(6-d)}  (units of 2^-42 of the operand scale, |I| < 2^50),
+//   L = sum_{d=7..9} M_d 2^{7(9-d)}  (units of 2^-63, |L| < 2^39).
+__device__ __forceinline__ void combine_groups(const float (&m)[kGroups], long long& I, long long& L) {
+    I = (static_cast<long long>(__float2int_rn(m[0])) << 28) +
+        (static_cast<long long>(__float2int_rn(m[1])) << 21) +
+        (static_cast<long long>(__float2int_rn(m[2])) << 14) +
+        (static_cast<long long>(__float2int_rn(m[3])) << 7) + static_cast<long long>(__float2int_rn(m[4]));
+    L = (static_cast<long long>(__float2int_rn(m[5])) << 14) +
+        (static_cast<long long>(__float2int_rn(m[6])) << 7) + static_cast<long long>(__float2int_rn(m[7]));
+}
+// the value in units of 2^-53 (rounded), for a single-window product: |result| < 2^61
+__device__ __forceinline__ long long combine_units53(const float (&m)[kGroups]) {
+    long long I, L;
+    combine_groups(m, I, L);
+    return (I << 11) + ((L + 512) >> 10);
+}
+// the value in units of 2^-49 (rounded), accumulated across windows
+__device__ __forceinline__ long long combine_units49(const float (&m)[kGroups]) {
+    long long I, L;
+    combine_groups(m, I, L);
+    return (I << 7) + ((L + (1ll << 13)) >> 14);
+}
+
+// I * 2^e: I converted to FP64 (rounded to nearest above 2^53), exponent added in the bit pattern
+// when the result stays normal (the usual case), ldexp otherwise.
+__device__ __forceinline__ double scale_pow2(long long I, int e) {
+    if (I == 0) return 0.0;
+    const double v = static_cast<double>(I);
+    const long long bits = __double_as_longlong(v);
+    const int ex = static_cast<int>((bits >> 52) & 0x7FF);
+    if (ex + e > 0 && ex + e < 0x7FF) return __longlong_as_double(bits + (static_cast<long long>(e) << 52));
+    return ldexp(v, e);
+}
+
+// Issue the 72 MMAs of one stage: all pairs (a, b), a + b <= 9, for the two K=16 steps.
+// first_window: the stage starts an exactness window (the first MMA into each accumulator clears it).
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, uint32_t b_base,
+                                           uint32_t b_slice_bytes, bool first_window) {
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+        for (int d = 2; d <= 9; ++d) {
+            const int alo = d - 8 > 1 ? d - 8 : 1, ahi = d - 1 < 8 ? d - 1 : 8;
+#pragma unroll
+            for (int a = alo; a <= ahi; ++a) {
+                const int b = d - a;
+                const uint64_t ad = sdesc(a_base + (a - 1) * kASlice + kk * 256);   // K step = 2 core matrices
+                const uint64_t bd = sdesc(b_base + (b - 1) * b_slice_bytes + kk * 256);
+                const uint32_t acc = (first_window && kk == 0 && a == alo) ? 0u : 1u;
+                mma_bf16(tmem + (d - 2) * kTileN, ad, bd, acc);
+            }
+        }
+    }
+}
+
+struct TmemState {
+    uint32_t base;
+};
+
+// ---- column slices of a small K x N matrix Y (the B operand of k_ozaki_gemm) ----------------------
+// yexp[q] = exponent bound of column q over its K rows; blocks[(tn*nkw + kw)*8 + b] (4 KB each) hold
+// slice b of columns 64tn..64tn+63 and rows 32kw..32kw+31 in the core-matrix K-major layout.
+// Y rows >= K and columns >= N read as 0.  One CTA per (tn, kw), 256 threads: (column, 8-row chunk).
+__global__ void __launch_bounds__(256) k_ozaki_slice_cols(const double* __restrict__ Y, int64_t ldy, int K,
+                                                          int N, uint8_t* __restrict__ blocks,
+                                                          int32_t* __restrict__ yexp, const int32_t* info) {
+    if (info && load_status(info) != 0) return;
+    const int tn = blockIdx.x, kw = blockIdx.y, nkw = gridDim.y;
+    const int q = threadIdx.x & 63, c = threadIdx.x >> 6;   // 64 columns x 4 chunks of 8 rows
+    const int col = tn * kTileN + q;
+    int E = kNoExp;
+    if (col < N)
+        for (int k = 0; k < K; ++k) {
+            const int e = exp_bound(Y[static_cast<int64_t>(k) * ldy + col]);
+            E = e > E ? e : E;
+        }
+    if (kw == 0 && c == 0 && col < N) yexp[col] = E;
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int k = kw * kKW + 8 * c + i;
+        x[i] = (col < N && k < K) ? Y[static_cast<int64_t>(k) * ldy + col] : 0.0;
+    }
+    uint8_t* blk = blocks + static_cast<size_t>((tn * nkw + kw) * kSlices) * kBSlice;
+    slice_store8(x, E, blk + core_off(q, 16 * c), kBSlice);
+}
+
+// ---- C = X Y (SUB = false) or C = B - X Y (SUB = true) ------------------------------------------------
+// X: m x K FP64 (ldx) with row exponent bounds xexp[m] (max over the K columns used);
+// Y: pre-sliced by k_ozaki_slice_cols (K x N, column bounds yexp[N]);
+// B, C: m x N FP64 (ldb, ldc); C may equal B.  Persistent grid over 128-row x 64-column tiles.
+template <bool SUB>
+__global__ void __launch_bounds__(kThreads, 1)
+k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int K,
+             const uint8_t* __restrict__ yblocks, const int32_t* __restrict__ yexp, int N,
+             const double* B, int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t tslot;
+    if (load_status(info) != 0) return;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    uint8_t* stA[2] = {sm, sm + kAStage};
+    uint8_t* stB[2] = {sm + 2 * kAStage, sm + 2 * kAStage + kBStage};
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tslot)), "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tslot;
+
+    const int nkw = (K + kKW - 1) / kKW;
+    const int ntn = (N + kTileN - 1) / kTileN;
+    const int64_t ntm = (m + kTileM - 1) / kTileM;
+    const int64_t ntiles = ntm * ntn;
+    uint32_t phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    bool timed_out = false;
+    int step = 0;
+
+    for (int64_t tile = blockIdx.x; tile < ntiles && !timed_out; tile += gridDim.x) {
+        const int64_t tm = tile / ntn;
+        const int tn = static_cast<int>(tile - tm * ntn);
+        const int64_t row0 = tm * kTileM;
+        const int lr = tid & (kTileM - 1);  // tile row: producer row and drain row (TMEM lane)
+        const int chalf = tid >> 7;         // producer K chunks 2*chalf, 2*chalf+1; drain columns 32*chalf..
+        const int64_t myrow = row0 + lr;
+        const int E = myrow < m ? xexp[myrow] : kNoExp;
+        for (int kw = 0; kw < nkw; ++kw, ++step) {
+            const int s = step & 1;
+            if (pending[s]) {
+                const bool ok = mbar_wait(&mbar[s], phase[s]);
+                if (__syncthreads_or(!ok)) { timed_out = true; break; }
+                phase[s] ^= 1u;
+                pending[s] = false;
+            }
+            // B slices: one contiguous 32 KB block, 16-byte cp.async granules
+            const uint8_t* src = yblocks + static_cast<size_t>((tn * nkw + kw) * kSlices) * kBSlice;
+            for (int e = tid; e < kBStage / 16; e += kThreads) {
+                const unsigned dst = smem_u32(stB[s] + 16 * e);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 16 * e));
+            }
+            asm volatile("cp.async.commit_group;\n");
+            // A slices: this thread's row, two chunks of 8 K values
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                const int c = 2 * chalf + cc;
+                double x[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int k = kw * kKW + 8 * c + i;
+                    x[i] = (myrow < m && k < K) ? X[myrow * ldx + k] : 0.0;
+                }
+                slice_store8(x, E, stA[s] + core_off(lr, 16 * c), kASlice);
+            }
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            fence_async_smem();
+            tc_before_sync();
+            __syncthreads();
+            tc_after_sync();
+            if (tid == 0) {
+                issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), kBSlice, kw == 0);
+                mma_commit(&mbar[s]);
+            }
+            pending[s] = true;
+        }
+        if (timed_out) break;
+        // all MMAs of the tile done
+        for (int s = 0; s < 2 && !timed_out; ++s)
+            if (pending[s]) {
+                const bool ok = mbar_wait(&mbar[s], phase[s]);
+                if (__syncthreads_or(!ok)) { timed_out = true; break; }
+                phase[s] ^= 1u;
+                pending[s] = false;
+            }
+        if (timed_out) break;
+        tc_after_sync();
+        // drain: lane = output row; this warp's 32 columns in chunks of 8
+#pragma unroll 1
+        for (int c0 = 32 * chalf; c0 < 32 * chalf + 32; c0 += 8) {
+            float mg[kGroups][8];
+#pragma unroll
+            for (int g = 0; g < kGroups; ++g)
+                tmem_ld8(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + g * kTileN + c0, mg[g]);
+            tmem_wait_ld();
+            if (myrow < m) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int col = tn * kTileN + c0 + j;
+                    if (col < N) {
+                        float grp[kGroups];
+#pragma unroll
+                        for (int g = 0; g < kGroups; ++g) grp[g] = mg[g][j];
+                        const long long I = combine_units53(grp);
+                        const int ey = yexp[col];
+                        const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(I, E + ey - 53) : 0.0;
+                        if (SUB) C[myrow * ldc + col] = B[myrow * ldb + col] - v;
+                        else C[myrow * ldc + col] = v;
+                    }
+                }
+            }
+        }
+        tc_before_sync();
+        __syncthreads();
+    }
+
+    if (timed_out) {
+        if (tid == 0) set_status(info, RPCHOLQR_ERR_TIMEOUT);
+        for (int s = 0; s < 2; ++s)
+            if (pending[s]) mbar_wait(&mbar[s], phase[s]);
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// ---- Gram partials G_rr = X_rr^T X_rr (upper and lower) -------------------------------------------------
+// X: m x n FP64 (ldx), column exponent bounds colexp[n] over all m rows.  Grid = nhalf x nranges CTAs;
+// CTA (h, rr) accumulates columns 64h..64h+63 of the Gram matrix of rows [rr*rows_per, ...) and writes
+// gpart[rr][p][q] (np x np, p < np, q in its 64 columns).  Exactness windows of 128 rows are drained
+// into int64 accumulators in units of 2^-49 of the scale 2^(Ep+Eq) (one output row per thread, 64
+// columns); every 64 windows (8192 rows, |sum| < 2^63 even for maximal slices) the accumulators are
+// added into the CTA's own FP64 partial and cleared.
+__global__ void __launch_bounds__(kThreads, 1)
+k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np,
+             const int32_t* __restrict__ colexp, int64_t rows_per, double* __restrict__ gpart,
+             int32_t* info) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t tslot;
+    if (load_status(info) != 0) return;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int nhalf = (np + kTileN - 1) / kTileN;
+    const int h = blockIdx.x % nhalf;
+    const int64_t rr = blockIdx.x / nhalf;
+    const int64_t r0 = rr * rows_per;
+    const int64_t r1 = (r0 + rows_per < m) ? r0 + rows_per : m;
+    uint8_t* stA[2] = {sm, sm + kAStage};
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tslot)), "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tslot;
+
+    const int p = tid & 127;                // producer column of X and drain output row (TMEM lane)
+    const int chalf = tid >> 7;             // producer row chunks 2*chalf.., drain columns 32*chalf..
+    const int Ep = p < n ? colexp[p] : kNoExp;
+    constexpr int kCols = kTileN / 2;       // output columns drained by this thread
+    long long acc[kCols];
+#pragma unroll
+    for (int j = 0; j < kCols; ++j) acc[j] = 0;
+    uint32_t phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    bool timed_out = false;
+    const int64_t nstages = r1 > r0 ? (r1 - r0 + kKW - 1) / kKW : 0;
+    const uint32_t b_off = static_cast<uint32_t>(h * kTileN / 8) * kSBO;   // B = A slices, rows 64h..
+
+    for (int64_t st = 0; st < nstages && !timed_out; ++st) {
+        const int s = static_cast<int>(st & 1);
+        if (pending[s]) {
+            const bool ok = mbar_wait(&mbar[s], phase[s]);
+            if (__syncthreads_or(!ok)) { timed_out = true; break; }
+            phase[s] ^= 1u;
+            pending[s] = false;
+        }
+        const int64_t k0 = r0 + st * kKW;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c = 2 * chalf + cc;
+            double x[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int64_t row = k0 + 8 * c + i;
+                x[i] = (row < r1 && p < n) ? X[row * ldx + p] : 0.0;
+            }
+            slice_store8(x, Ep, stA[s] + core_off(p, 16 * c), kASlice);
+        }
+        fence_async_smem();
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+        const bool first_window = (st & 3) == 0;
+        if (tid == 0) {
+            issue_stage(tmem, smem_u32(stA[s]), smem_u32(stA[s]) + b_off, kASlice, first_window);
+            mma_commit(&mbar[s]);
+        }
+        pending[s] = true;
+        const bool flush = ((st & 255) == 255) || st == nstages - 1;   // every 64 windows and at the end
+        if ((st & 3) == 3 || st == nstages - 1) {
+            // end of an exactness window: wait for every MMA, drain into the int64 accumulators
+            for (int q = 0; q < 2 && !timed_out; ++q)
+                if (pending[q]) {
+                    const bool ok = mbar_wait(&mbar[q], phase[q]);
+                    if (__syncthreads_or(!ok)) { timed_out = true; break; }
+                    phase[q] ^= 1u;
+                    pending[q] = false;
+                }
+            if (timed_out) break;
+            tc_after_sync();
+#pragma unroll
+            for (int c0 = 0; c0 < kCols; c0 += 8) {
+                float mg[kGroups][8];
+#pragma unroll
+                for (int g = 0; g < kGroups; ++g)
+                    tmem_ld8(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + g * kTileN + kCols * chalf + c0,
+                             mg[g]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float grp[kGroups];
+#pragma unroll
+                    for (int g = 0; g < kGroups; ++g) grp[g] = mg[g][j];
+                    acc[c0 + j] += combine_units49(grp);
+                }
+            }
+            if (flush && p < np) {
+                double* out = gpart + static_cast<size_t>(rr) * np * np + static_cast<size_t>(p) * np;
+#pragma unroll
+                for (int j = 0; j < kCols; ++j) {
+                    const int q = h * kTileN + kCols * chalf + j;
+                    if (q < np) {
+                        const int Eq = q < n ? colexp[q] : kNoExp;
+                        const double v = (Ep > kNoExp && Eq > kNoExp) ? scale_pow2(acc[j], Ep + Eq - 49) : 0.0;
+                        out[q] = (st < 256 ? 0.0 : out[q]) + v;   // first flush initialises the slot
+                    }
+                    acc[j] = 0;
+                }
+            }
+            tc_before_sync();
+            __syncthreads();
+        }
+    }
+
+    if (timed_out) {
+        if (tid == 0) set_status(info, RPCHOLQR_ERR_TIMEOUT);
+        for (int s = 0; s < 2; ++s)
+            if (pending[s]) mbar_wait(&mbar[s], phase[s]);
+    } else if (nstages == 0 && p < np) {
+        double* out = gpart + static_cast<size_t>(rr) * np * np + static_cast<size_t>(p) * np;
+        for (int j = 0; j < kCols; ++j) {
+            const int q = h * kTileN + kCols * chalf + j;
+            if (q < np) out[q] = 0.0;
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// rowexp[i] = exponent bound of row i of X (m x K, ldx); kNoExp for an all-zero row.
+__global__ void k_row_exp(const double* __restrict__ X, int64_t ldx, int64_t m, int K, int32_t* __restrict__ rowexp) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int E = kNoExp;
+    for (int k = 0; k < K; ++k) {
+        const int e = exp_bound(X[i * ldx + k]);
+        E = e > E ? e : E;
+    }
+    rowexp[i] = E;
+}
+
+// colexp[c] = max over rows of the exponent bounds (atomicMax; colexp must start at kNoExp).
+__global__ void k_col_exp(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int32_t* colexp) {
+    const int c = threadIdx.x;
+    if (c >= n) return;
+    int E = kNoExp;
+    for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+        const int e = exp_bound(X[i * ldx + c]);
+        E = e > E ? e : E;
+    }
+    if (E > kNoExp) atomicMax(&colexp[c], E);
+}
+
+__global__ void k_fill_i32(int32_t* p, int n, int32_t v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+}  // namespace oz
+
+// ---- host launchers ----------------------------------------------------------------------------------
+size_t ozaki_yblocks_bytes(int K, int N) {
+    const int nkw = (K + oz::kKW - 1) / oz::kKW, ntn = (N + oz::kTileN - 1) / oz::kTileN;
+    return static_cast<size_t>(nkw) * ntn * oz::kSlices * oz::kBSlice;
+}
+
+void launch_ozaki_slice_cols(const double* Y, int64_t ldy, int K, int N, uint8_t* blocks, int32_t* yexp,
+                             const int32_t* info, cudaStream_t st) {
+    dim3 grid((N + oz::kTileN - 1) / oz::kTileN, (K + oz::kKW - 1) / oz::kKW);
+    oz::k_ozaki_slice_cols<<<grid, 256, 0, st>>>(Y, ldy, K, N, blocks, yexp, info);
+}
+
+cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int32_t* xexp, int K,
+                              const uint8_t* yblocks, const int32_t* yexp, int N, const double* B,
+                              int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, int grid,
+                              cudaStream_t st) {
+    const int smem = 2 * (oz::kAStage + oz::kBStage);
+    cudaError_t err;
+    if (sub) {
+        err = cudaFuncSetAttribute(oz::k_ozaki_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (err != cudaSuccess) return err;
+        oz::k_ozaki_gemm<true><<<grid, oz::kThreads, smem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb,
+                                                                 C, ldc, m, info);
+    } else {
+        err = cudaFuncSetAttribute(oz::k_ozaki_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (err != cudaSuccess) return err;
+        oz::k_ozaki_gemm<false><<<grid, oz::kThreads, smem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B,
+                                                                  ldb, C, ldc, m, info);
+    }
+    return cudaGetLastError();
+}
+
+int32_t ozaki_no_exp() { return oz::kNoExp; }
+
+void launch_row_exp(const double* X, int64_t ldx, int64_t m, int K, int32_t* rowexp, cudaStream_t st) {
+    oz::k_row_exp<<<static_cast<unsigned>((m + 255) / 256), 256, 0, st>>>(X, ldx, m, K, rowexp);
+}
+
+void launch_col_exp(const double* X, int64_t ldx, int64_t m, int n, int32_t* colexp, cudaStream_t st) {
+    oz::k_fill_i32<<<(n + 127) / 128, 128, 0, st>>>(colexp, n, oz::kNoExp);
+    const int64_t blocks = m < 1024 ? m : 1024;
+    oz::k_col_exp<<<static_cast<unsigned>(blocks), (n + 31) / 32 * 32, 0, st>>>(X, ldx, m, n, colexp);
+}
+
+int ozaki_gram_halves(int np) { return (np + oz::kTileN - 1) / oz::kTileN; }
+
+cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
+                              int nranges, double* gpart, int32_t* info, cudaStream_t st) {
+    const int smem = 2 * oz::kAStage;
+    cudaError_t err = cudaFuncSetAttribute(oz::k_ozaki_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err != cudaSuccess) return err;
+    const int nh = ozaki_gram_halves(np);
+    int64_t rows_per = (m + nranges - 1) / nranges;
+    rows_per = (rows_per + oz::kKW - 1) / oz::kKW * oz::kKW;
+    oz::k_ozaki_gram<<<nh * nranges, oz::kThreads, smem, st>>>(X, ldx, m, n, np, colexp, rows_per, gpart, info);
+    return cudaGetLastError();
+}
+
+}  // namespace rpq

@@ -5,10 +5,10 @@
 //
 // Both are m independent row solves x_i^T = T^{-T} b_i^T (the row-wise view of Section 2.1).
 //
-// GB300 design.  FP64 on this part is slow (about 1 TFLOP/s DFMA) except for the FP64 tensor-core
-// mma.sync m16n8k16, which reaches about 4.2 TFLOP/s but only with >= 16 independent dependent-chains
-// in flight per SM (each m16n8k16 takes ~2.4 us to retire).  HBM is ~20x faster than the FP64 work
-// needs, so the kernels are organised for FP64 mma throughput, not for bandwidth:
+// GB300 design.  FP64 on this part runs at about 1.05 TFLOP/s whether it is issued as DFMA or as the
+// FP64 tensor-core mma.sync m16n8k16 (measured); HBM is ~100x faster than this FP64 work needs, so the
+// kernels are organised to keep the FP64 pipe busy, not for bandwidth.  mma.sync m16n8k16 carries 2048
+// FMAs per instruction, so the issue slots stay free for address math and shared-memory traffic:
 //   * a CTA (4 warps) owns a 128-row panel staged in shared memory with cp.async; the row stride
 //     NP+4 doubles keeps every fragment load at the minimum two wavefronts;
 //   * the solve is blocked by 8 columns, left-looking: block J of a 16-row tile is
@@ -73,7 +73,7 @@ template <int NP, bool SYRK>
 __global__ void __launch_bounds__(128, 1)
 k_rowpass(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m, int n,
           const double* __restrict__ frag, const double* __restrict__ diag,
-          double* __restrict__ gpart, int32_t* info) {
+          double* __restrict__ gpart, int32_t* info, bool check_finite) {
     constexpr int S = NP + 4;    // shared-memory row stride in doubles
     constexpr int ROWS = 128;    // panel rows: 4 warps x 32
     constexpr int NB = NP / 8;   // 8-column blocks
@@ -123,7 +123,7 @@ k_rowpass(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m, int n
                     const int c = 8 * J + 2 * t + (i & 1);
                     acc[mt][i] = panel[r * S + c];
                     acc2[mt][i] = 0.0;
-                    if constexpr (SYRK) bad |= !isfinite(acc[mt][i]);
+                    if (check_finite) bad |= !isfinite(acc[mt][i]);
                 }
             const int nk = (8 * J + 15) / 16;
             for (int kc = 0; kc < nk; ++kc) {
@@ -210,8 +210,8 @@ k_rowpass(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m, int n
                 }
             }
         }
-        if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(info, RPCHOLQR_ERR_NONFINITE);
     }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(info, RPCHOLQR_ERR_NONFINITE);
 }
 
 // G[p][q] = G[q][p] = sum over CTAs b = 0..nparts-1 (in this order) of part_b[p][q], q >= p.
@@ -240,23 +240,23 @@ size_t rowpass_smem_bytes(int np) { return static_cast<size_t>(128) * (np + 4) *
 template <int NP, bool SYRK>
 static cudaError_t launch_rowpass_t(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
                                     int n, const double* frag, const double* diag, double* gpart,
-                                    int32_t* info, int grid, cudaStream_t st) {
+                                    int32_t* info, int grid, cudaStream_t st, bool check) {
     const size_t smem = rowpass_smem_bytes(NP);
     cudaError_t err = cudaFuncSetAttribute(k_rowpass<NP, SYRK>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
-    k_rowpass<NP, SYRK><<<grid, 128, smem, st>>>(X, ldx, Y, ldy, m, n, frag, diag, gpart, info);
+    k_rowpass<NP, SYRK><<<grid, 128, smem, st>>>(X, ldx, Y, ldy, m, n, frag, diag, gpart, info, check);
     return cudaGetLastError();
 }
 
 template <bool SYRK>
 static cudaError_t launch_rowpass_np(int np, const double* X, int64_t ldx, double* Y, int64_t ldy,
                                      int64_t m, int n, const double* frag, const double* diag,
-                                     double* gpart, int32_t* info, int grid, cudaStream_t st) {
+                                     double* gpart, int32_t* info, int grid, cudaStream_t st, bool check) {
     switch (np) {
 #define RPQ_CASE(V) \
-    case V: return launch_rowpass_t<V, SYRK>(X, ldx, Y, ldy, m, n, frag, diag, gpart, info, grid, st);
+    case V: return launch_rowpass_t<V, SYRK>(X, ldx, Y, ldy, m, n, frag, diag, gpart, info, grid, st, check);
         RPQ_CASE(16) RPQ_CASE(32) RPQ_CASE(48) RPQ_CASE(64) RPQ_CASE(80) RPQ_CASE(96) RPQ_CASE(112)
         RPQ_CASE(128)
 #undef RPQ_CASE
@@ -264,11 +264,21 @@ static cudaError_t launch_rowpass_np(int np, const double* X, int64_t ldx, doubl
     }
 }
 
+// check_finite: set NONFINITE when an input entry is NaN/Inf.
+cudaError_t launch_rowpass_ex(bool syrk, int np, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                              int64_t m, int n, const double* frag, const double* diag, double* gpart,
+                              int32_t* info, int grid, cudaStream_t st, bool check_finite) {
+    return syrk ? launch_rowpass_np<true>(np, X, ldx, Y, ldy, m, n, frag, diag, gpart, info, grid, st,
+                                          check_finite)
+                : launch_rowpass_np<false>(np, X, ldx, Y, ldy, m, n, frag, diag, gpart, info, grid, st,
+                                           check_finite);
+}
+
+// The fused Gram pass checks its input for NaN/Inf, the plain solve does not.
 cudaError_t launch_rowpass(bool syrk, int np, const double* X, int64_t ldx, double* Y, int64_t ldy,
                            int64_t m, int n, const double* frag, const double* diag, double* gpart,
                            int32_t* info, int grid, cudaStream_t st) {
-    return syrk ? launch_rowpass_np<true>(np, X, ldx, Y, ldy, m, n, frag, diag, gpart, info, grid, st)
-                : launch_rowpass_np<false>(np, X, ldx, Y, ldy, m, n, frag, diag, gpart, info, grid, st);
+    return launch_rowpass_ex(syrk, np, X, ldx, Y, ldy, m, n, frag, diag, gpart, info, grid, st, syrk);
 }
 
 void launch_gram_reduce(const double* gpart, int nparts, int np, int n, double* G, int64_t ldg,

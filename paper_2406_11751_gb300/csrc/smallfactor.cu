@@ -148,6 +148,26 @@ __global__ void k_triu_mul(const double* __restrict__ R1, int64_t ld1, const dou
     }
 }
 
+// W = T^{-1} for upper-triangular T (n x n, ld ldt), by back substitution, one column per thread:
+//   W[j][j] = 1/T[j][j],  W[i][j] = -(sum_{k=i+1..j} T[i][k] W[k][j]) / T[i][i]  (i < j).
+// W: np x np row-major (ld np), padded with the identity.
+__global__ void __launch_bounds__(256) k_triu_inv(const double* __restrict__ T, int64_t ldt, int n, int np,
+                                                  double* __restrict__ W, const int32_t* info) {
+    if (info && load_status(info) != 0) return;
+    for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
+        const int r = e / np, c = e - r * np;
+        if (r >= n || c >= n || r > c) W[e] = (r == c) ? 1.0 : 0.0;
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        W[j * np + j] = 1.0 / T[static_cast<int64_t>(j) * ldt + j];
+        for (int i = j - 1; i >= 0; --i) {
+            double acc = 0.0;
+            for (int k = i + 1; k <= j; ++k) acc += T[static_cast<int64_t>(i) * ldt + k] * W[k * np + j];
+            W[i * np + j] = -acc / T[static_cast<int64_t>(i) * ldt + i];
+        }
+    }
+}
+
 // ---- host launchers ------------------------------------------------------------------------------
 size_t householder_smem_bytes(int s) { return (static_cast<size_t>(s) + 40) * sizeof(double); }
 
@@ -177,4 +197,11 @@ void launch_triu_mul(const double* R1, int64_t ld1, const double* Rs, int64_t ld
     k_triu_mul<<<n, threads, 0, st>>>(R1, ld1, Rs, lds, n, R, ldr, info);
 }
 
+}  // namespace rpq
+
+namespace rpq {
+void launch_triu_inv(const double* T, int64_t ldt, int n, int np, double* W, const int32_t* info,
+                     cudaStream_t st) {
+    k_triu_inv<<<1, 128, 0, st>>>(T, ldt, n, np, W, info);
+}
 }  // namespace rpq
