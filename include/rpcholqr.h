@@ -162,6 +162,17 @@ rpcholqr_status rpcholqr_ozaki_gemm(rpcholqr_plan plan, const double* X, int64_t
 rpcholqr_status rpcholqr_ozaki_gram(rpcholqr_plan plan, const double* X, int64_t m, int32_t n, int64_t ldx,
                                     double* G, int32_t* info, void* stream);
 
+/* Basic Cholesky-QR (Algorithm alg_0, Section 2.1): G = A^T A, G = R^T R, Q = A R^{-1}, all in FP64
+ * with the same kernels as rpcholqr_factor (preconditioner = identity).  Arguments as for
+ * rpcholqr_factor without s/seed.  Breaks down (RPCHOLQR_ERR_NOT_SPD) when kappa(A)^2 u >~ 1. */
+rpcholqr_status rpcholqr_cholqr(rpcholqr_plan plan, const double* A, int64_t m, int32_t n, int64_t lda,
+                                double* Q, int64_t ldq, double* R, int32_t* info, void* stream);
+
+/* Cholesky-QR2 (Yamamoto et al., the comparison method of Section 5.3): Cholesky-QR of A, then of the
+ * first Q; R = R_b R_a.  The breakdown reference for numerically singular inputs. */
+rpcholqr_status rpcholqr_cholqr2(rpcholqr_plan plan, const double* A, int64_t m, int32_t n, int64_t lda,
+                                 double* Q, int64_t ldq, double* R, int32_t* info, void* stream);
+
 /* FP64 tensor-pipe throughput probe: runs `iters` chains of dependent m16n8k16 FP64 mma on every
  * SM and writes the sustained FLOP/s to *flops_per_s (host).  Synchronous.  Used to report the
  * FP64 roofline denominator measured on the running GPU. */

@@ -19,7 +19,7 @@ __all__ = [
     "rpcholqr_sketch_r", "rpcholqr_precondition_gram", "rpcholqr_cholesky", "rpcholqr_solve_rows",
     "rpcholqr_triu_mul", "rpcholqr_probe_fp64_mma", "rpcholqr_status_string", "EXPORTED_SYMBOLS",
     "rpcholqr_plan_enable_timing", "rpcholqr_plan_collect_timing", "PHASES", "rpcholqr_ozaki_gemm",
-    "rpcholqr_ozaki_gram", "SPLIT64",
+    "rpcholqr_ozaki_gram", "SPLIT64", "rpcholqr_cholqr", "rpcholqr_cholqr2",
 ]
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NONFINITE", 3: "ERR_SINGULAR_SKETCH", 4: "ERR_NOT_SPD",
@@ -34,7 +34,8 @@ EXPORTED_SYMBOLS = (
     "rpcholqr_factor_host", "rpcholqr_sample_indices", "rpcholqr_sketch_r",
     "rpcholqr_precondition_gram", "rpcholqr_cholesky", "rpcholqr_solve_rows", "rpcholqr_triu_mul",
     "rpcholqr_probe_fp64_mma", "rpcholqr_status_string", "rpcholqr_plan_enable_timing",
-    "rpcholqr_plan_collect_timing", "rpcholqr_ozaki_gemm", "rpcholqr_ozaki_gram",
+    "rpcholqr_plan_collect_timing", "rpcholqr_ozaki_gemm", "rpcholqr_ozaki_gram", "rpcholqr_cholqr",
+    "rpcholqr_cholqr2",
 )
 PHASES = ("sample", "sketch_qr", "prep_rs", "pass1", "gram_reduce", "cholesky", "prep_r1", "pass2",
           "recover_r")
@@ -80,6 +81,8 @@ def load_library():
         "rpcholqr_plan_collect_timing": [P, P, ctypes.POINTER(I32), ctypes.POINTER(I64)],
         "rpcholqr_ozaki_gemm": [P, P, I64, I32, I64, P, I32, I64, P, I64, P, P],
         "rpcholqr_ozaki_gram": [P, P, I64, I32, I64, P, P, P],
+        "rpcholqr_cholqr": [P, P, I64, I32, I64, P, I64, P, P, P],
+        "rpcholqr_cholqr2": [P, P, I64, I32, I64, P, I64, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -285,6 +288,31 @@ def rpcholqr_triu_mul(R1, Rs, R=None, stream=None):
     _check("rpcholqr_triu_mul", load_library().rpcholqr_triu_mul(
         _ptr(R1), _ptr(Rs), n, _ptr(R), _stream(stream, R1.device)))
     return R
+
+
+def _cholqr_call(name, plan, A, Q, R, info, stream):
+    torch = _torch()
+    _mat(A, "A")
+    m, n = A.shape
+    if Q is None:
+        Q = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64, device=A.device)
+    info = _info(info, A.device)
+    _check(name, getattr(load_library(), name)(
+        plan.handle, _ptr(A), m, n, A.stride(0), _ptr(Q), Q.stride(0), _ptr(R), _ptr(info),
+        _stream(stream, A.device)))
+    return Q, R, info
+
+
+def rpcholqr_cholqr(plan: Plan, A, Q=None, R=None, info=None, stream=None):
+    """Basic Cholesky-QR (Algorithm alg_0) on the GPU; (Q, R, info)."""
+    return _cholqr_call("rpcholqr_cholqr", plan, A, Q, R, info, stream)
+
+
+def rpcholqr_cholqr2(plan: Plan, A, Q=None, R=None, info=None, stream=None):
+    """Cholesky-QR2 on the GPU (the paper's comparison method); (Q, R, info)."""
+    return _cholqr_call("rpcholqr_cholqr2", plan, A, Q, R, info, stream)
 
 
 def rpcholqr_ozaki_gemm(plan: Plan, X, Y, C=None, info=None, stream=None):

@@ -17,7 +17,7 @@ void launch_sample_gather(const double* A, int64_t m, int32_t n, int64_t lda, in
 // smallfactor.cu
 cudaError_t launch_householder(double* W, int64_t lds, int s, int n, int np, double* Rs,
                                double* Rs_user, int32_t* info, cudaStream_t st);
-size_t householder_smem_bytes(int s);
+size_t householder_smem_bytes(int s, int n);
 cudaError_t launch_cholesky(const double* G, int64_t ldg, int n, int np, double* R, double* R_user,
                             int32_t* info, cudaStream_t st);
 void launch_triu_mul(const double* R1, int64_t ld1, const double* Rs, int64_t lds, int n, double* R,
@@ -108,7 +108,7 @@ WsLayout ws_layout(int32_t max_n, int32_t max_s, int grid) {
     WsLayout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
-    L.As = take(sizeof(double) * static_cast<size_t>(max_s) * np);
+    L.As = take(sizeof(double) * static_cast<size_t>(max_s) * np);   // sample, s x np column-major
     L.Rs = take(sizeof(double) * np * np);
     L.R1 = take(sizeof(double) * np * np);
     L.G = take(sizeof(double) * np * np);
@@ -212,7 +212,7 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
     *plan = nullptr;
     if (max_n < 1 || max_n > RPCHOLQR_MAX_N || max_s < max_n || max_m < max_s) return RPCHOLQR_ERR_ARG;
     if (mode != RPCHOLQR_FP64 && mode != RPCHOLQR_SPLIT64) return RPCHOLQR_ERR_UNSUPPORTED;
-    if (householder_smem_bytes(max_s) > 200 * 1024) return RPCHOLQR_ERR_UNSUPPORTED;
+    if (householder_smem_bytes(max_s, max_n) > 200 * 1024) return RPCHOLQR_ERR_UNSUPPORTED;
     DeviceGuard guard(device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
     auto* p = new (std::nothrow) rpcholqr_plan_s();
@@ -300,11 +300,12 @@ static rpcholqr_status sketch_internal(rpcholqr_plan p, const double* A, int64_t
     const int np = pad16(n);
     const double scale = std::sqrt(static_cast<double>(m) / static_cast<double>(s));
     if (pm) pm->mark(RPCHOLQR_PHASE_SAMPLE);
-    launch_sample_gather(A, m, n, lda, s, seed, stream_id, scale, p->As, s, np, nullptr, info, st);
+    const int64_t lds = s;
+    launch_sample_gather(A, m, n, lda, s, seed, stream_id, scale, p->As, lds, np, nullptr, info, st);
     ++p->launches;
     if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
     if (pm) pm->mark(RPCHOLQR_PHASE_SKETCH_QR);
-    if (launch_householder(p->As, s, s, n, np, p->Rs, Rs_user, info, st) != cudaSuccess)
+    if (launch_householder(p->As, lds, s, n, np, p->Rs, Rs_user, info, st) != cudaSuccess)
         return RPCHOLQR_ERR_CUDA;
     ++p->launches;
     return RPCHOLQR_OK;
@@ -640,6 +641,61 @@ rpcholqr_status rpcholqr_ozaki_gram(rpcholqr_plan p, const double* X, int64_t m,
     rpcholqr_status rc = reset_info(info, st);
     if (rc != RPCHOLQR_OK) return rc;
     return ozaki_gram_internal(p, X, m, n, ldx, G, n, info, st);
+}
+
+// One Cholesky-QR step in FP64: Q = X R^{-1} with R = chol(X^T X) written to R_out (np x np, ld np).
+static rpcholqr_status cholqr_step(rpcholqr_plan p, const double* X, int64_t m, int32_t n, int64_t ldx,
+                                   double* Q, int64_t ldq, double* R_out, int32_t* info, cudaStream_t st) {
+    const int np = pad16(n);
+    launch_prep_tri(nullptr, 0, 0, np, p->frag_s, p->diag_s, info, st);   // identity preconditioner
+    const int64_t panels = (m + 127) / 128;
+    const int grid = static_cast<int>(panels < p->grid ? panels : p->grid);
+    if (launch_rowpass(true, np, X, ldx, Q, ldq, m, n, p->frag_s, p->diag_s, p->gpart, info, grid, st) !=
+        cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    launch_gram_reduce(p->gpart, grid, np, n, p->G, np, info, st);
+    if (launch_cholesky(p->G, np, n, np, R_out, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    p->launches += 4;
+    return solve_internal(p, Q, m, n, ldq, R_out, np, Q, ldq, info, st, nullptr);
+}
+
+static rpcholqr_status cholqr_args(rpcholqr_plan p, const double* A, int64_t m, int32_t n, int64_t lda,
+                                   const double* Q, int64_t ldq, const double* R, const int32_t* info) {
+    if (!p || !A || !Q || !R || !info) return RPCHOLQR_ERR_ARG;
+    if (n < 1 || n > p->max_n || m < n || m > p->max_m || lda < n || ldq < n) return RPCHOLQR_ERR_ARG;
+    return RPCHOLQR_OK;
+}
+
+rpcholqr_status rpcholqr_cholqr(rpcholqr_plan p, const double* A, int64_t m, int32_t n, int64_t lda,
+                                double* Q, int64_t ldq, double* R, int32_t* info, void* stream) {
+    rpcholqr_status rc = cholqr_args(p, A, m, n, lda, Q, ldq, R, info);
+    if (rc != RPCHOLQR_OK) return rc;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = reset_info(info, st)) != RPCHOLQR_OK) return rc;
+    if ((rc = cholqr_step(p, A, m, n, lda, Q, ldq, p->R1, info, st)) != RPCHOLQR_OK) return rc;
+    const size_t np = static_cast<size_t>(pad16(n));
+    if (cudaMemcpy2DAsync(R, sizeof(double) * n, p->R1, sizeof(double) * np, sizeof(double) * n,
+                          static_cast<size_t>(n), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    return RPCHOLQR_OK;
+}
+
+rpcholqr_status rpcholqr_cholqr2(rpcholqr_plan p, const double* A, int64_t m, int32_t n, int64_t lda,
+                                 double* Q, int64_t ldq, double* R, int32_t* info, void* stream) {
+    rpcholqr_status rc = cholqr_args(p, A, m, n, lda, Q, ldq, R, info);
+    if (rc != RPCHOLQR_OK) return rc;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = reset_info(info, st)) != RPCHOLQR_OK) return rc;
+    if ((rc = cholqr_step(p, A, m, n, lda, Q, ldq, p->Rs, info, st)) != RPCHOLQR_OK) return rc;   // R_a
+    if ((rc = cholqr_step(p, Q, m, n, ldq, Q, ldq, p->R1, info, st)) != RPCHOLQR_OK) return rc;   // R_b
+    const int np = pad16(n);
+    launch_triu_mul(p->R1, np, p->Rs, np, n, R, n, info, st);
+    ++p->launches;
+    return check_launch();
 }
 
 rpcholqr_status rpcholqr_probe_fp64_mma(int device, int32_t iters, double* flops_per_s) {

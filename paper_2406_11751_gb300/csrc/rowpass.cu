@@ -9,7 +9,8 @@
 // FP64 tensor-core mma.sync m16n8k16 (measured); HBM is ~100x faster than this FP64 work needs, so the
 // kernels are organised to keep the FP64 pipe busy, not for bandwidth.  mma.sync m16n8k16 carries 2048
 // FMAs per instruction, so the issue slots stay free for address math and shared-memory traffic:
-//   * a CTA (4 warps) owns a 128-row panel staged in shared memory with cp.async; the row stride
+//   * a CTA (4 warps, or 8 when NP <= 64) owns a 32-rows-per-warp panel staged in shared memory with
+//     cp.async; the row stride
 //     NP+4 doubles keeps every fragment load at the minimum two wavefronts;
 //   * the solve is blocked by 8 columns, left-looking: block J of a 16-row tile is
 //       acc = X[:, J] - A1[:, <J] T[<J, J]          (mma m16n8k16, FP64, B = -T chunks)
@@ -69,16 +70,20 @@ __global__ void k_prep_tri(const double* __restrict__ T, int64_t ldt, int n, int
     }
 }
 
+// Warps per CTA: 8 when the 256-row panel fits shared memory (NP <= 64), else 4 (128-row panel).
+__host__ __device__ constexpr int rowpass_warps(int np) { return np <= 64 ? 8 : 4; }
+
 template <int NP, bool SYRK>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(rowpass_warps(NP) * 32, 1)
 k_rowpass(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m, int n,
           const double* __restrict__ frag, const double* __restrict__ diag,
           double* __restrict__ gpart, int32_t* info, bool check_finite) {
     constexpr int S = NP + 4;    // shared-memory row stride in doubles
-    constexpr int ROWS = 128;    // panel rows: 4 warps x 32
-    constexpr int NB = NP / 8;   // 8-column blocks
+    constexpr int WARPS = rowpass_warps(NP);
+    constexpr int ROWS = 32 * WARPS;   // panel rows: 32 per warp
+    constexpr int NB = NP / 8;         // 8-column blocks
     constexpr int NT = upper_tiles(NP);
-    constexpr int TPW = (NT + 3) / 4;
+    constexpr int TPW = (NT + WARPS - 1) / WARPS;
     extern __shared__ double panel[];
 
     if (load_status(info) != 0) return;
@@ -92,7 +97,7 @@ k_rowpass(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m, int n
 #pragma unroll
         for (int q = 0; q < TPW; ++q) {
             gacc[q][0] = gacc[q][1] = gacc[q][2] = gacc[q][3] = 0.0;
-            const int tt = warp + 4 * q;
+            const int tt = warp + WARPS * q;
             if (tt < NT) tile_coords(NP, tt, tI[q], tJ[q]);
             else { tI[q] = 0; tJ[q] = 0; }
         }
@@ -179,7 +184,7 @@ k_rowpass(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m, int n
         if constexpr (SYRK) {
 #pragma unroll
             for (int q = 0; q < TPW; ++q) {
-                if (warp + 4 * q < NT) {
+                if (warp + WARPS * q < NT) {
                     const int I = tI[q], Jt = tJ[q];
 #pragma unroll 2
                     for (int kc = 0; kc < ROWS / 16; ++kc) {
@@ -201,7 +206,7 @@ k_rowpass(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m, int n
         double* out = gpart + static_cast<size_t>(blockIdx.x) * NP * NP;
 #pragma unroll
         for (int q = 0; q < TPW; ++q) {
-            if (warp + 4 * q < NT) {
+            if (warp + WARPS * q < NT) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int pr = 16 * tI[q] + g + 8 * (i >> 1);
@@ -235,7 +240,9 @@ void launch_prep_tri(const double* T, int64_t ldt, int n, int np, double* frag, 
     k_prep_tri<<<(total + 255) / 256, 256, 0, st>>>(T, ldt, n, np, frag, diag, info);
 }
 
-size_t rowpass_smem_bytes(int np) { return static_cast<size_t>(128) * (np + 4) * sizeof(double); }
+size_t rowpass_smem_bytes(int np) {
+    return static_cast<size_t>(32 * rowpass_warps(np)) * (np + 4) * sizeof(double);
+}
 
 template <int NP, bool SYRK>
 static cudaError_t launch_rowpass_t(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
@@ -246,7 +253,8 @@ static cudaError_t launch_rowpass_t(const double* X, int64_t ldx, double* Y, int
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
-    k_rowpass<NP, SYRK><<<grid, 128, smem, st>>>(X, ldx, Y, ldy, m, n, frag, diag, gpart, info, check);
+    k_rowpass<NP, SYRK><<<grid, 32 * rowpass_warps(NP), smem, st>>>(X, ldx, Y, ldy, m, n, frag, diag, gpart, info,
+                                                                    check);
     return cudaGetLastError();
 }
 

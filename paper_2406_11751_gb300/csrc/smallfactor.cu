@@ -1,5 +1,5 @@
 // The small dense steps of Algorithm alg_2 (Section 4):
-//   'factor'   A_s = Q_s R_s   -- Householder QR of the s x n sample, one CTA;
+//   'factor'   A_s = Q_s R_s   -- Householder QR of the s x n sample on a 16-CTA cluster;
 //   'Cholesky' G_1 = R_1^T R_1 -- n x n upper Cholesky, one CTA;
 //   'recover'  R = R_1 R_s     -- product of upper-triangular factors, one CTA per row.
 #include <cfloat>
@@ -7,8 +7,6 @@
 #include "common.cuh"
 
 namespace rpq {
-
-constexpr int kQrThreads = 1024;
 
 // Block-wide sum of one double per thread (every thread gets the result).
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -24,23 +22,51 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;
 }
 
-// Householder QR of W (s x n, column-major, ld lds; overwritten).  Reflector for column j:
-// beta = -sign(alpha) ||x||, v = x / (alpha - beta) with v_j = 1, tau = (beta - alpha) / beta;
-// a column with nothing below the diagonal is left as is (tau = 0).  On exit Rs (np x np,
-// row-major, ld np) holds R_s with each row negated where its diagonal was negative, padded with
-// the identity; Rs_user (optional, n x n, ld n) receives the same n x n block.  A diagonal that is
-// 0, subnormal or not finite sets SINGULAR_SKETCH.
-__global__ void __launch_bounds__(kQrThreads)
-k_householder(double* __restrict__ W, int64_t lds, int s, int n, int np, double* __restrict__ Rs,
-              double* __restrict__ Rs_user, int32_t* info) {
+// Householder QR of the sample on one thread-block cluster.  FP64 on GB300 retires one warp-wide
+// DFMA per 64 cycles per SM sub-partition, so a single CTA would run this O(s n^2) step at 1/152 of
+// the GPU; instead kClusterQr CTAs (one per SM) share the columns round-robin and advance one
+// column per hardware cluster barrier:
+//   every CTA: read column j (rows j..s-1), form the reflector (beta = -sign(alpha)||x||,
+//              v = x / (alpha - beta) with v_j = 1, tau = (beta - alpha) / beta; no reflection when
+//              nothing is below the diagonal) -- identical in every CTA;
+//   every CTA: apply it to its own columns k > j;
+//   cluster barrier (release/acquire orders the global-memory column updates).
+// The diagonal betas are kept in shared memory (column j is still being read by the other CTAs
+// while it is reflected) and CTA 0 assembles R_s at the end: each row negated where its diagonal is
+// negative, padded with the identity; a diagonal that is 0, subnormal or not finite sets
+// SINGULAR_SKETCH.  W: s x n column-major (ld lds), overwritten.
+constexpr int kClusterQr = 16;
+constexpr int kClusterQrThreads = 256;
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;\n" : "=r"(r));
+    return r;
+}
+
+__global__ void __launch_bounds__(kClusterQrThreads)
+k_hh_cluster(double* __restrict__ W, int64_t lds, int s, int n, int np, double* __restrict__ Rs,
+             double* __restrict__ Rs_user, const int32_t* info_in, int32_t* info) {
     extern __shared__ double qsm[];
-    double* v = qsm;            // s
-    double* red = qsm + s;      // 32
-    if (load_status(info) != 0) return;
+    double* v = qsm;                 // s
+    double* betas = qsm + s;         // n
+    double* red = betas + n;         // 32
+    // every CTA of the cluster sees the same status, so all take the same number of barriers
+    if (load_status(info_in) != 0) return;
+    const unsigned rank = cluster_rank(), csize = cluster_size();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
 
     for (int j = 0; j < n; ++j) {
-        double* colj = W + static_cast<int64_t>(j) * lds;
+        const double* colj = W + static_cast<int64_t>(j) * lds;
         double part = 0.0;
         for (int i = j + 1 + tid; i < s; i += blockDim.x) part += colj[i] * colj[i];
         const double sigma = block_sum(part, red);
@@ -55,10 +81,12 @@ k_householder(double* __restrict__ W, int64_t lds, int s, int n, int np, double*
             inv = 1.0 / (alpha - beta);
         }
         for (int i = j + tid; i < s; i += blockDim.x) v[i] = (i == j) ? 1.0 : colj[i] * inv;
+        if (tid == 0) betas[j] = beta;
         __syncthreads();
-        if (tid == 0) colj[j] = beta;
         if (tau != 0.0) {
-            for (int k = j + 1 + warp; k < n; k += nwarps) {
+            // this CTA's columns k > j: k = rank (mod csize); one warp per column
+            const int k0 = j + 1 + static_cast<int>((rank + csize - static_cast<unsigned>((j + 1) % csize)) % csize);
+            for (int k = k0 + warp * static_cast<int>(csize); k < n; k += nwarps * static_cast<int>(csize)) {
                 double* colk = W + static_cast<int64_t>(k) * lds;
                 double w = 0.0;
                 for (int i = j + lane; i < s; i += 32) w += v[i] * colk[i];
@@ -69,16 +97,18 @@ k_householder(double* __restrict__ W, int64_t lds, int s, int n, int np, double*
             }
         }
         __syncthreads();
+        cluster_sync_all();
     }
 
+    if (rank != 0) return;
     bool singular = false;
     for (int e = tid; e < np * np; e += blockDim.x) {
         const int r = e / np, c = e - r * np;
         double val;
         if (r < n && c < n) {
-            const double d = W[static_cast<int64_t>(r) * lds + r];
+            const double d = betas[r];
             const double sg = d < 0.0 ? -1.0 : 1.0;
-            val = (c >= r) ? sg * W[static_cast<int64_t>(c) * lds + r] : 0.0;
+            val = c > r ? sg * W[static_cast<int64_t>(c) * lds + r] : (c == r ? fabs(d) : 0.0);
             if (c == r && (!isfinite(d) || fabs(d) < DBL_MIN)) singular = true;
             if (Rs_user) Rs_user[r * n + c] = val;
         } else {
@@ -169,16 +199,41 @@ __global__ void __launch_bounds__(256) k_triu_inv(const double* __restrict__ T, 
 }
 
 // ---- host launchers ------------------------------------------------------------------------------
-size_t householder_smem_bytes(int s) { return (static_cast<size_t>(s) + 40) * sizeof(double); }
+size_t householder_smem_bytes(int s, int n) { return (static_cast<size_t>(s) + n + 40) * sizeof(double); }
 
+// W: s x n column-major (ld lds).  One cluster of kClusterQr CTAs (16 needs the non-portable cluster
+// size; 8 is used where the device refuses 16).
 cudaError_t launch_householder(double* W, int64_t lds, int s, int n, int np, double* Rs,
                                double* Rs_user, int32_t* info, cudaStream_t st) {
-    const size_t smem = householder_smem_bytes(s);
-    cudaError_t err = cudaFuncSetAttribute(k_householder, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = householder_smem_bytes(s, n);
+    cudaError_t err = cudaFuncSetAttribute(k_hh_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
-    k_householder<<<1, kQrThreads, smem, st>>>(W, lds, s, n, np, Rs, Rs_user, info);
-    return cudaGetLastError();
+    err = cudaFuncSetAttribute(k_hh_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (err != cudaSuccess) return err;
+    for (int csize : {kClusterQr, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(csize, 1, 1);
+        cfg.blockDim = dim3(kClusterQrThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = csize;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, k_hh_cluster, &cfg) != cudaSuccess || clusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        err = cudaLaunchKernelEx(&cfg, k_hh_cluster, W, lds, s, n, np, Rs, Rs_user,
+                                 static_cast<const int32_t*>(info), info);
+        return err == cudaSuccess ? cudaGetLastError() : err;
+    }
+    return cudaErrorInvalidConfiguration;
 }
 
 cudaError_t launch_cholesky(const double* G, int64_t ldg, int n, int np, double* R, double* R_user,

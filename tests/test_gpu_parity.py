@@ -284,3 +284,35 @@ def test_factor_full_size_against_oracle(lib, oracle_mod):
         _check_against_oracle(lib, oracle_mod, plan, A, s, 1, kappa, fast_metrics=True)
     finally:
         plan.close()
+
+
+# ---- Cholesky-QR / Cholesky-QR2 (the comparison method of Section 5.3) -------------------------------
+@pytest.mark.parametrize("m,n,kappa", [(10007, 50, 1e2), (20000, 128, 1e6), (3000, 7, 1e4)])
+def test_cholqr2_matches_oracle(lib, oracle_mod, plan, m, n, kappa):
+    # Cholesky-QR's factors depend on the rounding of A^T A (kappa(A)^2 u), so R is gated against the
+    # oracle's own floor (every sum reversed) as well as the absolute 1e-12.
+    A = inputs.usv(m, n, kappa, 900 + n)
+    Q, R, info = lib.rpcholqr_cholqr2(plan, cu(A))
+    assert status(info) == (0, -1)
+    o = oracle_mod.cholqr2(A)
+    o_rev = oracle_mod.cholqr2(A, variant=1)
+    assert o["status"] == 0
+    floor = nrm2(o["R"] - o_rev["R"])
+    assert nrm2(host(R) - o["R"]) <= max(1e-12 * nrm2(o["R"]), 10 * floor)
+    assert oracle_mod.orth_error(host(Q)) <= 10 * oracle_mod.orth_error(o["Q"]) + 1e-15
+    Q1, R1, info1 = lib.rpcholqr_cholqr(plan, cu(A))
+    o1 = oracle_mod.cholqr(A)
+    floor1 = nrm2(o1["R"] - oracle_mod.cholqr(A, variant=1)["R"])
+    assert status(info1) == (0, -1)
+    assert nrm2(host(R1) - o1["R"]) <= max(1e-12 * nrm2(o1["R"]), 10 * floor1)
+
+
+def test_cholqr2_breaks_down_where_rpcholqr_succeeds(lib, oracle_mod, plan):
+    # kappa = 1e16: the Gram matrix is not numerically SPD (Section 1, Existing work)
+    A = inputs.usv(20000, 64, 1e16, 33)
+    _, _, info = lib.rpcholqr_cholqr2(plan, cu(A))
+    assert status(info)[0] == lib.ERR_NOT_SPD
+    assert oracle_mod.cholqr2(A)["status"] == oracle_mod.ERR_NOT_SPD
+    Q, R, info = lib.rpcholqr_factor(plan, cu(A), 192, 1)
+    assert status(info) == (0, -1)
+    assert oracle_mod.orth_error(host(Q)) <= 1e-13
