@@ -49,8 +49,11 @@ def parse_args():
     ap.add_argument("--inputs", choices=["gpu", "cpu"], default="gpu",
                     help="draw A with torch on the GPU (fast) or with the numpy recipe on the host")
     ap.add_argument("--no-metrics", action="store_true", help="skip the orthogonality/residual check")
-    ap.add_argument("--mode", choices=["fp64", "split"], default="fp64",
-                    help="fp64: every step in FP64; split: Ozaki-split BF16 tensor-core products")
+    ap.add_argument("--mode", choices=["fp64", "split"], default="split",
+                    help="split (default): FP64-accurate Ozaki-split BF16 tensor-core products for the "
+                         "well-conditioned steps; fp64: every step in FP64")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="do not also time the other mode (reported as 'other_mode')")
     return ap.parse_args()
 
 
@@ -60,6 +63,17 @@ def alg_flops(m, n, s):
 
 
 # ---- clocks sampled during the timed region --------------------------------------------------------
+class _NoClock:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+    def summary(self):
+        return None
+
+
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -255,34 +269,43 @@ def run_ours(args, ws, rank, local):
     Q = torch.empty_like(A)
     R = torch.empty((n, n), dtype=torch.float64, device=dev)
     info = torch.empty(2, dtype=torch.int32, device=dev)
-    plan = rq.rpcholqr_plan_create(local, m, n, s, mode=rq.SPLIT64 if args.mode == "split" else rq.FP64)
     stream = torch.cuda.current_stream(dev)
     fp64_peak = rq.rpcholqr_probe_fp64_mma(local, 4096)
 
-    for w in range(W):
-        rq.rpcholqr_factor(plan, A, s, 1 + w, Q=Q, R=R, info=info, stream=stream)
-    torch.cuda.synchronize(dev)
-    st = info.cpu().tolist()
-    if st[0] != 0:
-        raise RuntimeError(f"warm-up status {rq.rpcholqr_status_string(st[0])}")
+    def timed(mode, clocks):
+        """W warm-up + K timed factor calls on a fresh plan of `mode`: (ms, phases, calls, launches, plan)."""
+        plan = rq.rpcholqr_plan_create(local, m, n, s, mode=rq.SPLIT64 if mode == "split" else rq.FP64)
+        for w in range(W):
+            rq.rpcholqr_factor(plan, A, s, 1 + w, Q=Q, R=R, info=info, stream=stream)
+        torch.cuda.synchronize(dev)
+        st0 = info.cpu().tolist()
+        if st0[0] != 0:
+            raise RuntimeError(f"{mode} warm-up status {rq.rpcholqr_status_string(st0[0])}")
+        rq.rpcholqr_plan_collect_timing(plan)          # reset counters
+        rq.rpcholqr_plan_enable_timing(plan, K)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with (ClockSampler(local) if clocks else _NoClock()) as clk:
+            barrier(dist)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for k in range(K):
+                rq.rpcholqr_factor(plan, A, s, 1 + k, Q=Q, R=R, info=info, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            barrier(dist)
+        ph, calls, launches = rq.rpcholqr_plan_collect_timing(plan)
+        rq.rpcholqr_plan_enable_timing(plan, 0)
+        return max_over_ranks(e0.elapsed_time(e1), dist, dev), ph, calls, launches, plan, clk
 
-    rq.rpcholqr_plan_collect_timing(plan)          # reset counters
-    rq.rpcholqr_plan_enable_timing(plan, K)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier(dist)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for k in range(K):
-            rq.rpcholqr_factor(plan, A, s, 1 + k, Q=Q, R=R, info=info, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        barrier(dist)
-    t_ms = e0.elapsed_time(e1)
-    phases, calls, launches = rq.rpcholqr_plan_collect_timing(plan)
-    rq.rpcholqr_plan_enable_timing(plan, 0)
-    t_ms_max = max_over_ranks(t_ms, dist, dev)
+    other = None
+    if not args.no_compare:
+        omode = "fp64" if args.mode == "split" else "split"
+        o_ms, o_ph, o_calls, _, o_plan, _ = timed(omode, False)
+        o_plan.close()
+        other = {"mode": omode, "value": ws * K / (o_ms / 1e3), "ms_per_step": o_ms / K,
+                 "phases_ms_per_step": {k: v / max(o_calls, 1) for k, v in o_ph.items()}}
+    t_ms_max, phases, calls, launches, plan, clk = timed(args.mode, True)
     st = info.cpu().tolist()
     orth, res = (None, None) if args.no_metrics else gpu_metrics(A, Q, R)
 
@@ -309,13 +332,29 @@ def run_ours(args, ws, rank, local):
     N = ws
     value = N * K / (t_ms_max / 1e3)
     flops = alg_flops(m, n, s)
-    pass1_ms = phases["pass1"] / max(calls, 1)
-    pass1_flops = 2.0 * m * n * n      # algorithmic: m rows x (n^2 solve + n^2 Gram) flops
-    pass1_bytes = 16.0 * m * n         # read A, write A1
-    achieved = pass1_flops / (pass1_ms / 1e3) / 1e12
-    peak = fp64_peak / 1e12
+    np_ = (n + 15) // 16 * 16
     src = os.path.join(ROOT, "paper_2406_11751_gb300", "csrc", "rowpass.cu")
-    traffic = traffic_from_profiles(f"k_rowpass<{n if n % 16 == 0 else (n + 15) // 16 * 16},true>", src)
+    c = max(calls, 1)
+    if args.mode == "fp64":
+        # dominant kernel: fused pass 1 (row solve by R_s + Gram partials), FP64 pipe
+        kname = "k_rowpass<%d,true> (FP64 pass 1: A1 = A Rs^-1 + Gram partials)" % np_
+        launches_per_call = 1
+        k_ms = phases["pass1"] / c
+        k_flops = 2.0 * m * n * n                       # m rows x (n^2 solve + n^2 Gram)
+        k_bytes = 16.0 * m * n                          # read A, write A1
+        traffic = traffic_from_profiles(f"k_rowpass<{np_},true>", src)
+    else:
+        # dominant kernel: the FP64 block row solves of pass 1 (<= 64 columns each)
+        n1 = min(n, 64)
+        n2 = n - n1
+        kname = "k_rowpass<%d,false> (SPLIT64 pass 1: FP64 block row solves by R_s)" % min(np_, 64)
+        launches_per_call = 2 if n2 > 0 else 1
+        k_ms = (phases["pass1"] + phases["pass1_solve2"]) / c / launches_per_call
+        k_flops = m * (n1 * n1 + n2 * n2) / launches_per_call
+        k_bytes = 16.0 * m * (n1 + n2) / launches_per_call
+        traffic = traffic_from_profiles(f"k_rowpass<{min(np_, 64)},false>", src)
+    achieved = k_flops / (k_ms / 1e3) / 1e12
+    peak = fp64_peak / 1e12
 
     cpu = None
     if not args.no_cpu_baseline and N == 1:
@@ -328,19 +367,24 @@ def run_ours(args, ws, rank, local):
     out = {
         "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": N, "steps": K, "warmup": W,
         "ms_per_step": t_ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (A = U diag(sigma) V^T, Haar U/V from torch, sigma log-spaced)",
+        "dtype": "f64" if args.mode == "fp64" else "f64+bf16",
+        "data": "synthetic (A = U diag(sigma) V^T, Haar U/V from torch, sigma log-spaced)",
         "config": {"workload": f"rpCholesky-QR {args.mode.upper()} m={m} n={n} s={s} kappa={args.kappa:g}", "m": m,
                    "n": n, "s": s, "kappa": args.kappa, "mode": args.mode,
                    "l2": f"inputs larger than L2 (A = {8 * m * n / 1e9:.2f} GB > 129 MB), no flush"},
         "effective_tflops": flops * value / 1e12,
         "orth": orth, "residual": res, "gate_orth_le_1e-13": None if orth is None else bool(orth <= 1e-13), "status": st[0],
         "phases_ms_per_step": {k: v / max(calls, 1) for k, v in phases.items()},
-        "roofline": {"kernel": "k_rowpass<NP,SYRK=true> (pass 1: A1 = A Rs^-1 + Gram)", "bound": "tensor",
+        "roofline": {"kernel": kname, "bound": "alu",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": traffic, "algorithmic_flops": pass1_flops,
-                     "algorithmic_bytes": pass1_bytes, "ms_per_launch": pass1_ms,
-                     "peak_source": "FP64 mma.sync m16n8k16 probe measured in this run "
-                                    "(MEASURED_PEAKS.json has no FP64 figure)"},
+                     "traffic": traffic, "algorithmic_flops": k_flops,
+                     "algorithmic_bytes": k_bytes, "ms_per_launch": k_ms,
+                     "launches_per_step": launches_per_call,
+                     "peak_source": "FP64 pipe (DFMA and FP64 mma.sync share it): in-run mma.sync "
+                                    "m16n8k16 probe; MEASURED_PEAKS.json has no FP64 figure "
+                                    "(unit count x clock: 152 SM x 4 x 32 lanes / 64 cycles x 2 flop "
+                                    "x 2.07 GHz = 1.26 TFLOP/s)"},
+        "other_mode": other,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

@@ -201,11 +201,15 @@ enum {
     RPCHOLQR_PHASE_SAMPLE = 0,    /* Philox indices + gather/scale of the s rows           */
     RPCHOLQR_PHASE_SKETCH_QR,     /* Householder QR of the sample                           */
     RPCHOLQR_PHASE_PREP_RS,       /* fragment tables of R_s                                 */
-    RPCHOLQR_PHASE_PASS1,         /* fused A1 = A R_s^{-1} and per-CTA Gram partials        */
-    RPCHOLQR_PHASE_GRAM_REDUCE,   /* fixed-order sum of the Gram partials                   */
+    RPCHOLQR_PHASE_PASS1,         /* FP64: fused A1 = A R_s^{-1} + Gram partials;
+                                     SPLIT64: row solve of the first (<= 64-column) block       */
+    RPCHOLQR_PHASE_PASS1_UPDATE,  /* SPLIT64, n > 64: tensor-core off-diagonal block update     */
+    RPCHOLQR_PHASE_PASS1_SOLVE2,  /* SPLIT64, n > 64: row solve of the second block            */
+    RPCHOLQR_PHASE_GRAM_REDUCE,   /* FP64: fixed-order sum of the Gram partials;
+                                     SPLIT64: tensor-core Gram matrix and its sum              */
     RPCHOLQR_PHASE_CHOLESKY,      /* G1 = R1^T R1                                           */
-    RPCHOLQR_PHASE_PREP_R1,       /* fragment tables of R1                                  */
-    RPCHOLQR_PHASE_PASS2,         /* Q = A1 R1^{-1} in place                                */
+    RPCHOLQR_PHASE_PREP_R1,       /* FP64: fragment tables of R1; SPLIT64: R1^{-1}          */
+    RPCHOLQR_PHASE_PASS2,         /* Q = A1 R1^{-1} (FP64: in place; SPLIT64: tensor cores) */
     RPCHOLQR_PHASE_RECOVER_R,     /* R = R1 R_s                                             */
     RPCHOLQR_NUM_PHASES
 };

@@ -37,8 +37,8 @@ EXPORTED_SYMBOLS = (
     "rpcholqr_plan_collect_timing", "rpcholqr_ozaki_gemm", "rpcholqr_ozaki_gram", "rpcholqr_cholqr",
     "rpcholqr_cholqr2",
 )
-PHASES = ("sample", "sketch_qr", "prep_rs", "pass1", "gram_reduce", "cholesky", "prep_r1", "pass2",
-          "recover_r")
+PHASES = ("sample", "sketch_qr", "prep_rs", "pass1", "pass1_update", "pass1_solve2", "gram_reduce",
+          "cholesky", "prep_r1", "pass2", "recover_r")
 
 
 class RpcholqrError(RuntimeError):

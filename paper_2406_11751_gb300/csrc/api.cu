@@ -32,7 +32,9 @@ void launch_gram_reduce(const double* gpart, int nparts, int np, int n, double* 
                         const int32_t* info, cudaStream_t st);
 cudaError_t launch_rowpass_ex(bool syrk, int np, const double* X, int64_t ldx, double* Y, int64_t ldy,
                               int64_t m, int n, const double* frag, const double* diag, double* gpart,
-                              int32_t* info, int grid, cudaStream_t st, bool check_finite);
+                              int32_t* info, int grid, cudaStream_t st, bool check_finite, int32_t* rowexp,
+                              int rowexp_mode, int32_t* colexp);
+void launch_fill_noexp(int32_t* p, int n, cudaStream_t st);
 // probe.cu
 cudaError_t run_fp64_mma_probe(int iters, double* flops_per_s);
 // smallfactor.cu
@@ -327,7 +329,11 @@ static rpcholqr_status precondition_internal(rpcholqr_plan p, const double* A, i
         cudaSuccess)
         return RPCHOLQR_ERR_CUDA;
     ++p->launches;
-    if (pm) pm->mark(RPCHOLQR_PHASE_GRAM_REDUCE);
+    if (pm) {
+        pm->mark(RPCHOLQR_PHASE_PASS1_UPDATE);
+        pm->mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
+        pm->mark(RPCHOLQR_PHASE_GRAM_REDUCE);
+    }
     launch_gram_reduce(p->gpart, grid, np, n, G_user ? G_user : p->G, G_user ? n : np, info, st);
     ++p->launches;
     return check_launch();
@@ -352,12 +358,17 @@ static rpcholqr_status solve_internal(rpcholqr_plan p, const double* X, int64_t 
 }
 
 // C = X Y (sub = false) or C = B - X Y (sub = true) on the tensor cores; X row bounds computed here.
+// xexp_ready: p->xexp already holds the row bounds of X (written by the row pass that produced X).
 static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const double* X, int64_t m, int K,
                                            int64_t ldx, const double* Y, int N, int64_t ldy, const double* B,
-                                           int64_t ldb, double* C, int64_t ldc, int32_t* info, cudaStream_t st) {
-    launch_row_exp(X, ldx, m, K, p->xexp, st);
+                                           int64_t ldb, double* C, int64_t ldc, int32_t* info, cudaStream_t st,
+                                           bool xexp_ready = false) {
+    if (!xexp_ready) {
+        launch_row_exp(X, ldx, m, K, p->xexp, st);
+        ++p->launches;
+    }
     launch_ozaki_slice_cols(Y, ldy, K, N, p->yblocks, p->yexp, info, st);
-    p->launches += 2;
+    ++p->launches;
     if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
     const int64_t tiles = ((m + 127) / 128) * ((N + 63) / 64);
     const int grid = static_cast<int>(tiles < p->grid ? tiles : p->grid);
@@ -369,11 +380,15 @@ static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const doub
 }
 
 // G (n x n, ld ldg) = X^T X on the tensor cores: column bounds, per-range partials, fixed-order sum.
+// colexp_ready: p->colexp already holds the column bounds of X.
 static rpcholqr_status ozaki_gram_internal(rpcholqr_plan p, const double* X, int64_t m, int n, int64_t ldx,
-                                           double* G, int64_t ldg, int32_t* info, cudaStream_t st) {
+                                           double* G, int64_t ldg, int32_t* info, cudaStream_t st,
+                                           bool colexp_ready = false) {
     const int np = pad16(n);
-    launch_col_exp(X, ldx, m, n, p->colexp, st);
-    p->launches += 2;
+    if (!colexp_ready) {
+        launch_col_exp(X, ldx, m, n, p->colexp, st);
+        p->launches += 2;
+    }
     const int nh = ozaki_gram_halves(np);
     int nranges = p->grid / nh;
     if (nranges < 1) nranges = 1;
@@ -399,14 +414,18 @@ static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m,
     const int64_t panels = (m + 127) / 128;
     const int grid = static_cast<int>(panels < p->grid ? panels : p->grid);
     pm.mark(RPCHOLQR_PHASE_PREP_RS);
+    launch_fill_noexp(p->colexp, n, st);   // column bounds of A1, atomically max-merged by the row passes
+    ++p->launches;
     if (n <= 64) {
         launch_prep_tri(p->Rs, np, n, np, p->frag_s, p->diag_s, info, st);
         ++p->launches;
         pm.mark(RPCHOLQR_PHASE_PASS1);
         if (launch_rowpass_ex(false, np, A, lda, A1, ld1, m, n, p->frag_s, p->diag_s, nullptr, info, grid, st,
-                              true) != cudaSuccess)
+                              true, p->xexp, 1, p->colexp) != cudaSuccess)
             return RPCHOLQR_ERR_CUDA;
         ++p->launches;
+        pm.mark(RPCHOLQR_PHASE_PASS1_UPDATE);
+        pm.mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
     } else {
         const int n2 = n - 64;
         launch_prep_tri(p->Rs, np, 64, 64, p->frag_s, p->diag_s, info, st);
@@ -415,21 +434,23 @@ static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m,
         pm.mark(RPCHOLQR_PHASE_PASS1);
         // A1[:, :64] = A[:, :64] R11^{-1}
         if (launch_rowpass_ex(false, 64, A, lda, A1, ld1, m, 64, p->frag_s, p->diag_s, nullptr, info, grid, st,
-                              true) != cudaSuccess)
+                              true, p->xexp, 1, p->colexp) != cudaSuccess)
             return RPCHOLQR_ERR_CUDA;
         ++p->launches;
+        pm.mark(RPCHOLQR_PHASE_PASS1_UPDATE);
         // A1[:, 64:] = A[:, 64:] - A1[:, :64] R12   (tensor cores)
         if ((rc = ozaki_gemm_internal(p, true, A1, m, 64, ld1, p->Rs + 64, n2, np, A + 64, lda, A1 + 64, ld1,
-                                      info, st)) != RPCHOLQR_OK)
+                                      info, st, true)) != RPCHOLQR_OK)
             return rc;
+        pm.mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
         // A1[:, 64:] = A1[:, 64:] R22^{-1}
         if (launch_rowpass_ex(false, pad16(n2), A1 + 64, ld1, A1 + 64, ld1, m, n2, p->frag_1, p->diag_1, nullptr,
-                              info, grid, st, true) != cudaSuccess)
+                              info, grid, st, true, p->xexp, 2, p->colexp + 64) != cudaSuccess)
             return RPCHOLQR_ERR_CUDA;
         ++p->launches;
     }
     pm.mark(RPCHOLQR_PHASE_GRAM_REDUCE);
-    if ((rc = ozaki_gram_internal(p, A1, m, n, ld1, p->G, np, info, st)) != RPCHOLQR_OK) return rc;
+    if ((rc = ozaki_gram_internal(p, A1, m, n, ld1, p->G, np, info, st, true)) != RPCHOLQR_OK) return rc;
     pm.mark(RPCHOLQR_PHASE_CHOLESKY);
     if (launch_cholesky(p->G, np, n, np, p->R1, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
     ++p->launches;
@@ -437,7 +458,7 @@ static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m,
     launch_triu_inv(p->R1, np, n, np, p->W, info, st);
     ++p->launches;
     pm.mark(RPCHOLQR_PHASE_PASS2);
-    if ((rc = ozaki_gemm_internal(p, false, A1, m, n, ld1, p->W, n, np, nullptr, 0, Q, ldq, info, st)) !=
+    if ((rc = ozaki_gemm_internal(p, false, A1, m, n, ld1, p->W, n, np, nullptr, 0, Q, ldq, info, st, true)) !=
         RPCHOLQR_OK)
         return rc;
     pm.mark(RPCHOLQR_PHASE_RECOVER_R);

@@ -1,5 +1,6 @@
 // Device-side building blocks shared by the rpCholesky-QR kernels (sm_103a).
 #pragma once
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -12,6 +13,14 @@ constexpr int kPad = 16;
 constexpr int kMaxNP = RPCHOLQR_MAX_N;  // padded n handled by the row-pass kernels
 
 __host__ __device__ constexpr int pad16(int n) { return (n + kPad - 1) / kPad * kPad; }
+
+// ---- power-of-two bounds used by the split-precision products ------------------------------------
+// exp_bound(v): |v| < 2^e for a normal v (e = unbiased exponent + 1); kNoExp for 0 or subnormal.
+constexpr int kNoExp = INT_MIN / 2;
+__device__ __forceinline__ int exp_bound(double v) {
+    const int ex = static_cast<int>((__double_as_longlong(v) >> 52) & 0x7FF);
+    return ex == 0 ? kNoExp : ex - 1022;
+}
 
 // ---- status word: info[0] = status, info[1] = pivot ---------------------------------------------
 __device__ __forceinline__ int load_status(const int32_t* info) {

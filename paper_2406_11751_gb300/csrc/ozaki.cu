@@ -46,7 +46,6 @@ constexpr int kAStage = kSlices * kASlice; // 64 KB
 constexpr int kBStage = kSlices * kBSlice; // 32 KB
 constexpr int kTmemCols = 512;
 constexpr long kSpinLimit = 1L << 24;
-constexpr int kNoExp = INT_MIN / 2;        // "row/column is all zero" marker (below any real exponent)
 // BF16 x BF16 -> FP32, A and B K-major, M = 128, N = 64
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
                             ((uint32_t)(kTileM >> 4) << 24);
@@ -106,12 +105,6 @@ __device__ __forceinline__ void tmem_ld4(uint32_t addr, float (&v)[4]) {
     for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
-
-// Exponent bound: |v| < 2^e for a normal v (e = unbiased exponent + 1); kNoExp for 0/subnormal.
-__device__ __forceinline__ int exp_bound(double v) {
-    const int ex = static_cast<int>((__double_as_longlong(v) >> 52) & 0x7FF);
-    return ex == 0 ? kNoExp : ex - 1022;
-}
 
 // 56-bit fixed-point magnitude F = floor(|x| 2^{56-E}) of x relative to the bound 2^E > |x|, split in
 // two 28-bit halves (hi: slices 1..4, lo: slices 5..8).  0 for zero, subnormal, non-finite or unknown E.
@@ -349,6 +342,14 @@ k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int
         // drain: lane = output row; this warp's 32 columns in chunks of 8
 #pragma unroll 1
         for (int c0 = 32 * chalf; c0 < 32 * chalf + 32; c0 += 8) {
+            double bv[8];
+            if (SUB) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int col = tn * kTileN + c0 + j;
+                    bv[j] = (myrow < m && col < N) ? B[myrow * ldb + col] : 0.0;
+                }
+            }
             float mg[kGroups][8];
 #pragma unroll
             for (int g = 0; g < kGroups; ++g)
@@ -365,7 +366,7 @@ k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int
                         const long long I = combine_units53(grp);
                         const int ey = yexp[col];
                         const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(I, E + ey - 53) : 0.0;
-                        if (SUB) C[myrow * ldc + col] = B[myrow * ldb + col] - v;
+                        if (SUB) C[myrow * ldc + col] = bv[j] - v;
                         else C[myrow * ldc + col] = v;
                     }
                 }
@@ -595,19 +596,23 @@ cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int3
     return cudaGetLastError();
 }
 
-int32_t ozaki_no_exp() { return oz::kNoExp; }
+int32_t ozaki_no_exp() { return kNoExp; }
 
 void launch_row_exp(const double* X, int64_t ldx, int64_t m, int K, int32_t* rowexp, cudaStream_t st) {
     oz::k_row_exp<<<static_cast<unsigned>((m + 255) / 256), 256, 0, st>>>(X, ldx, m, K, rowexp);
 }
 
 void launch_col_exp(const double* X, int64_t ldx, int64_t m, int n, int32_t* colexp, cudaStream_t st) {
-    oz::k_fill_i32<<<(n + 127) / 128, 128, 0, st>>>(colexp, n, oz::kNoExp);
+    oz::k_fill_i32<<<(n + 127) / 128, 128, 0, st>>>(colexp, n, kNoExp);
     const int64_t blocks = m < 1024 ? m : 1024;
     oz::k_col_exp<<<static_cast<unsigned>(blocks), (n + 31) / 32 * 32, 0, st>>>(X, ldx, m, n, colexp);
 }
 
 int ozaki_gram_halves(int np) { return (np + oz::kTileN - 1) / oz::kTileN; }
+
+void launch_fill_noexp(int32_t* p, int n, cudaStream_t st) {
+    oz::k_fill_i32<<<(n + 127) / 128, 128, 0, st>>>(p, n, kNoExp);
+}
 
 cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
                               int nranges, double* gpart, int32_t* info, cudaStream_t st) {

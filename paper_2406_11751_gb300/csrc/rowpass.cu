@@ -77,7 +77,8 @@ template <int NP, bool SYRK>
 __global__ void __launch_bounds__(rowpass_warps(NP) * 32, 1)
 k_rowpass(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m, int n,
           const double* __restrict__ frag, const double* __restrict__ diag,
-          double* __restrict__ gpart, int32_t* info, bool check_finite) {
+          double* __restrict__ gpart, int32_t* info, bool check_finite, int32_t* rowexp, int rowexp_mode,
+          int32_t* colexp) {
     constexpr int S = NP + 4;    // shared-memory row stride in doubles
     constexpr int WARPS = rowpass_warps(NP);
     constexpr int ROWS = 32 * WARPS;   // panel rows: 32 per warp
@@ -103,6 +104,7 @@ k_rowpass(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m, int n
         }
     }
     bool bad = false;
+    int col_e = kNoExp;   // column threadIdx.x: exponent bound over the rows this CTA solved
 
     for (int64_t p = blockIdx.x; p < npanels; p += gridDim.x) {
         const int64_t row0 = p * ROWS;
@@ -180,6 +182,29 @@ k_rowpass(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m, int n
             const int64_t gr = row0 + r;
             if (gr < m && c < n) Y[gr * ldy + c] = panel[r * S + c];
         }
+        // power-of-two bounds of the solved rows (one thread per row) and columns, for the
+        // split-precision products that read A1 next
+        if (rowexp) {
+            const int r = threadIdx.x;          // ROWS == blockDim.x
+            const int64_t gr = row0 + r;
+            if (gr < m) {
+                int e = kNoExp;
+                for (int c = 0; c < n; ++c) {
+                    const int ec = exp_bound(panel[r * S + c]);
+                    e = ec > e ? ec : e;
+                }
+                if (rowexp_mode == 2 && rowexp[gr] > e) e = rowexp[gr];
+                rowexp[gr] = e;
+            }
+        }
+        if (colexp && threadIdx.x < n) {
+            const int c = threadIdx.x;
+            const int64_t rows = (m - row0) < ROWS ? (m - row0) : ROWS;
+            for (int r = 0; r < rows; ++r) {
+                const int ec = exp_bound(panel[r * S + c]);
+                col_e = ec > col_e ? ec : col_e;
+            }
+        }
 
         if constexpr (SYRK) {
 #pragma unroll
@@ -216,6 +241,7 @@ k_rowpass(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m, int n
             }
         }
     }
+    if (colexp && threadIdx.x < n && col_e > kNoExp) atomicMax(&colexp[threadIdx.x], col_e);
     if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(info, RPCHOLQR_ERR_NONFINITE);
 }
 
@@ -247,24 +273,28 @@ size_t rowpass_smem_bytes(int np) {
 template <int NP, bool SYRK>
 static cudaError_t launch_rowpass_t(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
                                     int n, const double* frag, const double* diag, double* gpart,
-                                    int32_t* info, int grid, cudaStream_t st, bool check) {
+                                    int32_t* info, int grid, cudaStream_t st, bool check, int32_t* rowexp,
+                                    int rowexp_mode, int32_t* colexp) {
     const size_t smem = rowpass_smem_bytes(NP);
     cudaError_t err = cudaFuncSetAttribute(k_rowpass<NP, SYRK>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
     k_rowpass<NP, SYRK><<<grid, 32 * rowpass_warps(NP), smem, st>>>(X, ldx, Y, ldy, m, n, frag, diag, gpart, info,
-                                                                    check);
+                                                                    check, rowexp, rowexp_mode, colexp);
     return cudaGetLastError();
 }
 
 template <bool SYRK>
 static cudaError_t launch_rowpass_np(int np, const double* X, int64_t ldx, double* Y, int64_t ldy,
                                      int64_t m, int n, const double* frag, const double* diag,
-                                     double* gpart, int32_t* info, int grid, cudaStream_t st, bool check) {
+                                     double* gpart, int32_t* info, int grid, cudaStream_t st, bool check,
+                                     int32_t* rowexp, int rowexp_mode, int32_t* colexp) {
     switch (np) {
-#define RPQ_CASE(V) \
-    case V: return launch_rowpass_t<V, SYRK>(X, ldx, Y, ldy, m, n, frag, diag, gpart, info, grid, st, check);
+#define RPQ_CASE(V)                                                                                     \
+    case V:                                                                                             \
+        return launch_rowpass_t<V, SYRK>(X, ldx, Y, ldy, m, n, frag, diag, gpart, info, grid, st, check, \
+                                         rowexp, rowexp_mode, colexp);
         RPQ_CASE(16) RPQ_CASE(32) RPQ_CASE(48) RPQ_CASE(64) RPQ_CASE(80) RPQ_CASE(96) RPQ_CASE(112)
         RPQ_CASE(128)
 #undef RPQ_CASE
@@ -272,21 +302,25 @@ static cudaError_t launch_rowpass_np(int np, const double* X, int64_t ldx, doubl
     }
 }
 
-// check_finite: set NONFINITE when an input entry is NaN/Inf.
+// check_finite: set NONFINITE when an input entry is NaN/Inf.  rowexp (optional): exponent bound of
+// every solved row over its n columns, stored (rowexp_mode 1) or max-merged (2); colexp (optional,
+// pre-filled with kNoExp): exponent bound of every column over all rows (atomicMax).
 cudaError_t launch_rowpass_ex(bool syrk, int np, const double* X, int64_t ldx, double* Y, int64_t ldy,
                               int64_t m, int n, const double* frag, const double* diag, double* gpart,
-                              int32_t* info, int grid, cudaStream_t st, bool check_finite) {
+                              int32_t* info, int grid, cudaStream_t st, bool check_finite, int32_t* rowexp,
+                              int rowexp_mode, int32_t* colexp) {
     return syrk ? launch_rowpass_np<true>(np, X, ldx, Y, ldy, m, n, frag, diag, gpart, info, grid, st,
-                                          check_finite)
+                                          check_finite, rowexp, rowexp_mode, colexp)
                 : launch_rowpass_np<false>(np, X, ldx, Y, ldy, m, n, frag, diag, gpart, info, grid, st,
-                                           check_finite);
+                                           check_finite, rowexp, rowexp_mode, colexp);
 }
 
 // The fused Gram pass checks its input for NaN/Inf, the plain solve does not.
 cudaError_t launch_rowpass(bool syrk, int np, const double* X, int64_t ldx, double* Y, int64_t ldy,
                            int64_t m, int n, const double* frag, const double* diag, double* gpart,
                            int32_t* info, int grid, cudaStream_t st) {
-    return launch_rowpass_ex(syrk, np, X, ldx, Y, ldy, m, n, frag, diag, gpart, info, grid, st, syrk);
+    return launch_rowpass_ex(syrk, np, X, ldx, Y, ldy, m, n, frag, diag, gpart, info, grid, st, syrk, nullptr, 0,
+                             nullptr);
 }
 
 void launch_gram_reduce(const double* gpart, int nparts, int np, int n, double* G, int64_t ldg,

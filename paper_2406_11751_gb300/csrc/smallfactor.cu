@@ -178,22 +178,46 @@ __global__ void k_triu_mul(const double* __restrict__ R1, int64_t ld1, const dou
     }
 }
 
-// W = T^{-1} for upper-triangular T (n x n, ld ldt), by back substitution, one column per thread:
+// W = T^{-1} for upper-triangular T (n x n, ld ldt, n <= 128): back substitution, one warp per column.
 //   W[j][j] = 1/T[j][j],  W[i][j] = -(sum_{k=i+1..j} T[i][k] W[k][j]) / T[i][i]  (i < j).
+// Column j lives in the registers of its warp (lane l holds rows l, l+32, l+64, l+96); the dot product
+// of each step is split over the lanes and summed with shuffles; reciprocal diagonals are formed once.
 // W: np x np row-major (ld np), padded with the identity.
 __global__ void __launch_bounds__(256) k_triu_inv(const double* __restrict__ T, int64_t ldt, int n, int np,
                                                   double* __restrict__ W, const int32_t* info) {
     if (info && load_status(info) != 0) return;
-    for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nwarps_total = (gridDim.x * blockDim.x) >> 5;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < np * np; e += gridDim.x * blockDim.x) {
         const int r = e / np, c = e - r * np;
         if (r >= n || c >= n || r > c) W[e] = (r == c) ? 1.0 : 0.0;
     }
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        W[j * np + j] = 1.0 / T[static_cast<int64_t>(j) * ldt + j];
+    double rinv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = lane + 32 * q;
+        rinv[q] = i < n ? 1.0 / T[static_cast<int64_t>(i) * ldt + i] : 0.0;
+    }
+    for (int j = gw; j < n; j += nwarps_total) {
+        double w[4] = {0.0, 0.0, 0.0, 0.0};   // W[lane + 32q][j]
+        if ((j & 31) == lane) w[j >> 5] = rinv[j >> 5];
         for (int i = j - 1; i >= 0; --i) {
-            double acc = 0.0;
-            for (int k = i + 1; k <= j; ++k) acc += T[static_cast<int64_t>(i) * ldt + k] * W[k * np + j];
-            W[i * np + j] = -acc / T[static_cast<int64_t>(i) * ldt + i];
+            const double* Ti = T + static_cast<int64_t>(i) * ldt;
+            double part = 0.0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = lane + 32 * q;
+                if (k > i && k <= j) part = fma(Ti[k], w[q], part);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            const double ri = __shfl_sync(0xffffffffu, rinv[i >> 5], i & 31);
+            if ((i & 31) == lane) w[i >> 5] = -part * ri;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = lane + 32 * q;
+            if (k <= j) W[k * np + j] = w[q];
         }
     }
 }
@@ -257,6 +281,6 @@ void launch_triu_mul(const double* R1, int64_t ld1, const double* Rs, int64_t ld
 namespace rpq {
 void launch_triu_inv(const double* T, int64_t ldt, int n, int np, double* W, const int32_t* info,
                      cudaStream_t st) {
-    k_triu_inv<<<1, 128, 0, st>>>(T, ldt, n, np, W, info);
+    k_triu_inv<<<(n + 7) / 8, 256, 0, st>>>(T, ldt, n, np, W, info);
 }
 }  // namespace rpq
