@@ -195,6 +195,48 @@ rpcholqr_status rpcholqr_precondition_gram_noalloc(const double* A, int64_t m, i
                                                    const double* Rs, double* A1, int64_t ld1,
                                                    double* G, int32_t* info, void* stream);
 
+/* ---- batches of independent matrices ----
+ * A batch object owns `slots` independent plans (each with its own workspace and CUDA stream).  The
+ * matrices of a batch call are dealt round-robin to the slots, so small matrices -- whose row passes
+ * fill only part of the GPU -- run concurrently; the caller's stream forks to the slot streams and
+ * joins them again (the call stays asynchronous on `stream`).  The sequence can be captured once into
+ * a CUDA graph and replayed as one launch (the spec batching pattern: block-Krylov / LOBPCG
+ * orthogonalisation of many blocks).  All per-matrix arrays below are HOST arrays of length count;
+ * the pointed-to matrices are device memory; info is a DEVICE int32 array of 2*count entries
+ * ({status, pivot} per matrix, see rpcholqr_factor).  Every matrix must fit the batch limits. */
+typedef struct rpcholqr_batch_s* rpcholqr_batch;
+
+rpcholqr_status rpcholqr_batch_create(rpcholqr_batch* batch, int device, rpcholqr_mode mode, int64_t max_m,
+                                      int32_t max_n, int32_t max_s, int32_t slots);
+rpcholqr_status rpcholqr_batch_destroy(rpcholqr_batch batch);
+
+/* Factor count matrices (rpcholqr_factor semantics each, Philox stream_id = 0, key = seed[i]). */
+rpcholqr_status rpcholqr_factor_batched(rpcholqr_batch batch, int32_t count, const double* const* A,
+                                        const int64_t* m, const int32_t* n, const int64_t* lda,
+                                        const int32_t* s, const uint64_t* seed, double* const* Q,
+                                        const int64_t* ldq, double* const* R, int32_t* info, void* stream);
+
+/* Capture the same work as rpcholqr_factor_batched into a CUDA graph held by the batch (replacing a
+ * previous one); nothing runs until rpcholqr_batch_replay.  The buffers must stay valid while the
+ * graph is replayed.  Uses the slot count the batch currently has. */
+rpcholqr_status rpcholqr_batch_capture(rpcholqr_batch batch, int32_t count, const double* const* A,
+                                       const int64_t* m, const int32_t* n, const int64_t* lda,
+                                       const int32_t* s, const uint64_t* seed, double* const* Q,
+                                       const int64_t* ldq, double* const* R, int32_t* info, void* stream);
+
+/* Launch the captured graph on `stream` (RPCHOLQR_ERR_ARG if none was captured). */
+rpcholqr_status rpcholqr_batch_replay(rpcholqr_batch batch, void* stream);
+
+/* Autotuner: times rpcholqr_factor_batched on these matrices with 1, 2, 4, ... up to the batch's slot
+ * count of concurrent slots (one warm-up and `reps` timed runs each, synchronous), keeps the fastest
+ * as the batch's active slot count and returns it in *best_slots (host) and the per-run time in
+ * *best_ms (host). */
+rpcholqr_status rpcholqr_batch_autotune(rpcholqr_batch batch, int32_t count, const double* const* A,
+                                        const int64_t* m, const int32_t* n, const int64_t* lda,
+                                        const int32_t* s, const uint64_t* seed, double* const* Q,
+                                        const int64_t* ldq, double* const* R, int32_t* info, int32_t reps,
+                                        int32_t* best_slots, float* best_ms, void* stream);
+
 /* ---- per-phase timing (CUDA events on the call's stream) ----
  * Phases of one rpcholqr_factor call, in launch order. */
 enum {

@@ -19,7 +19,9 @@ __all__ = [
     "rpcholqr_sketch_r", "rpcholqr_precondition_gram", "rpcholqr_cholesky", "rpcholqr_solve_rows",
     "rpcholqr_triu_mul", "rpcholqr_probe_fp64_mma", "rpcholqr_status_string", "EXPORTED_SYMBOLS",
     "rpcholqr_plan_enable_timing", "rpcholqr_plan_collect_timing", "PHASES", "rpcholqr_ozaki_gemm",
-    "rpcholqr_ozaki_gram", "SPLIT64", "rpcholqr_cholqr", "rpcholqr_cholqr2",
+    "rpcholqr_ozaki_gram", "SPLIT64", "rpcholqr_cholqr", "rpcholqr_cholqr2", "Batch",
+    "rpcholqr_batch_create", "rpcholqr_batch_destroy", "rpcholqr_factor_batched", "rpcholqr_batch_capture",
+    "rpcholqr_batch_replay", "rpcholqr_batch_autotune",
 ]
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NONFINITE", 3: "ERR_SINGULAR_SKETCH", 4: "ERR_NOT_SPD",
@@ -35,7 +37,8 @@ EXPORTED_SYMBOLS = (
     "rpcholqr_precondition_gram", "rpcholqr_cholesky", "rpcholqr_solve_rows", "rpcholqr_triu_mul",
     "rpcholqr_probe_fp64_mma", "rpcholqr_status_string", "rpcholqr_plan_enable_timing",
     "rpcholqr_plan_collect_timing", "rpcholqr_ozaki_gemm", "rpcholqr_ozaki_gram", "rpcholqr_cholqr",
-    "rpcholqr_cholqr2",
+    "rpcholqr_cholqr2", "rpcholqr_batch_create", "rpcholqr_batch_destroy", "rpcholqr_factor_batched",
+    "rpcholqr_batch_capture", "rpcholqr_batch_replay", "rpcholqr_batch_autotune",
 )
 PHASES = ("sample", "sketch_qr", "prep_rs", "pass1", "pass1_update", "pass1_solve2", "gram_reduce",
           "cholesky", "prep_r1", "pass2", "recover_r")
@@ -83,6 +86,13 @@ def load_library():
         "rpcholqr_ozaki_gram": [P, P, I64, I32, I64, P, P, P],
         "rpcholqr_cholqr": [P, P, I64, I32, I64, P, I64, P, P, P],
         "rpcholqr_cholqr2": [P, P, I64, I32, I64, P, I64, P, P, P],
+        "rpcholqr_batch_create": [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, I64, I32, I32, I32],
+        "rpcholqr_batch_destroy": [P],
+        "rpcholqr_factor_batched": [P, I32, P, P, P, P, P, P, P, P, P, P, P],
+        "rpcholqr_batch_capture": [P, I32, P, P, P, P, P, P, P, P, P, P, P],
+        "rpcholqr_batch_replay": [P, P],
+        "rpcholqr_batch_autotune": [P, I32, P, P, P, P, P, P, P, P, P, P, I32, ctypes.POINTER(I32),
+                                    ctypes.POINTER(ctypes.c_float), P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -387,3 +397,108 @@ def rpcholqr_precondition_gram_noalloc(A, Rs, A1, G, info, stream=None):
         _ptr(A), m, n, A.stride(0), _ptr(Rs), _ptr(A1), A1.stride(0), _ptr(G), _ptr(info),
         _stream(stream, A.device)))
     return A1, G, info
+
+
+# ---- batches of independent matrices --------------------------------------------------------------
+class Batch:
+    """Owner of a C batch handle: `slots` independent plans/streams for concurrent small factorisations."""
+
+    def __init__(self, handle, device, slots):
+        self.handle = handle
+        self.device = device
+        self.slots = slots
+        self._keep = None
+
+    def close(self):
+        if self.handle:
+            load_library().rpcholqr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rpcholqr_batch_create(device: int, max_m: int, max_n: int, max_s: int, slots: int = 8,
+                          mode: int = FP64) -> Batch:
+    h = ctypes.c_void_p()
+    _check("rpcholqr_batch_create", load_library().rpcholqr_batch_create(
+        ctypes.byref(h), device, mode, max_m, max_n, max_s, slots))
+    return Batch(h, device, slots)
+
+
+def rpcholqr_batch_destroy(batch: Batch):
+    batch.close()
+
+
+def _batch_arrays(As, ss, seeds, Qs, Rs):
+    count = len(As)
+    P = ctypes.c_void_p * count
+    arrs = {
+        "A": P(*[t.data_ptr() for t in As]),
+        "m": (ctypes.c_int64 * count)(*[t.shape[0] for t in As]),
+        "n": (ctypes.c_int32 * count)(*[t.shape[1] for t in As]),
+        "lda": (ctypes.c_int64 * count)(*[t.stride(0) for t in As]),
+        "s": (ctypes.c_int32 * count)(*ss),
+        "seed": (ctypes.c_uint64 * count)(*seeds),
+        "Q": P(*[t.data_ptr() for t in Qs]),
+        "ldq": (ctypes.c_int64 * count)(*[t.stride(0) for t in Qs]),
+        "R": P(*[t.data_ptr() for t in Rs]),
+    }
+    args = [count] + [ctypes.cast(arrs[k], ctypes.c_void_p) for k in
+                      ("A", "m", "n", "lda", "s", "seed", "Q", "ldq", "R")]
+    return args, arrs
+
+
+def _batch_outputs(As, Qs, Rs, info):
+    torch = _torch()
+    dev = As[0].device
+    if Qs is None:
+        Qs = [torch.empty_like(a) for a in As]
+    if Rs is None:
+        Rs = [torch.empty((a.shape[1], a.shape[1]), dtype=torch.float64, device=dev) for a in As]
+    if info is None:
+        info = torch.empty(2 * len(As), dtype=torch.int32, device=dev)
+    for a in As:
+        _mat(a, "A")
+    return Qs, Rs, info
+
+
+def rpcholqr_factor_batched(batch: Batch, As, ss, seeds, Qs=None, Rs=None, info=None, stream=None):
+    """Factor the list of device matrices As (s[i] samples, seeds[i]); returns (Qs, Rs, info[2*count])."""
+    Qs, Rs, info = _batch_outputs(As, Qs, Rs, info)
+    args, _keep = _batch_arrays(As, ss, seeds, Qs, Rs)
+    _check("rpcholqr_factor_batched", load_library().rpcholqr_factor_batched(
+        batch.handle, *args, _ptr(info), _stream(stream, As[0].device)))
+    return Qs, Rs, info
+
+
+def rpcholqr_batch_capture(batch: Batch, As, ss, seeds, Qs=None, Rs=None, info=None, stream=None):
+    """Capture the batched factorisation into a CUDA graph (replay with rpcholqr_batch_replay)."""
+    Qs, Rs, info = _batch_outputs(As, Qs, Rs, info)
+    args, keep = _batch_arrays(As, ss, seeds, Qs, Rs)
+    _check("rpcholqr_batch_capture", load_library().rpcholqr_batch_capture(
+        batch.handle, *args, _ptr(info), _stream(stream, As[0].device)))
+    batch._keep = (As, Qs, Rs, info, keep)
+    return Qs, Rs, info
+
+
+def rpcholqr_batch_replay(batch: Batch, stream=None):
+    torch = _torch()
+    _check("rpcholqr_batch_replay", load_library().rpcholqr_batch_replay(
+        batch.handle, _stream(stream, torch.device("cuda", batch.device))))
+
+
+def rpcholqr_batch_autotune(batch: Batch, As, ss, seeds, Qs=None, Rs=None, info=None, reps: int = 2,
+                            stream=None):
+    """Pick the fastest number of concurrent slots for this batch; returns (slots, ms per batch)."""
+    Qs, Rs, info = _batch_outputs(As, Qs, Rs, info)
+    args, _keep = _batch_arrays(As, ss, seeds, Qs, Rs)
+    best = ctypes.c_int32()
+    ms = ctypes.c_float()
+    _check("rpcholqr_batch_autotune", load_library().rpcholqr_batch_autotune(
+        batch.handle, *args, _ptr(info), reps, ctypes.byref(best), ctypes.byref(ms),
+        _stream(stream, As[0].device)))
+    return int(best.value), float(ms.value)
