@@ -70,8 +70,9 @@ typedef enum {
                             Needs an extra max_m x n FP64 plan buffer for A1.                      */
 } rpcholqr_mode;
 
-/* Largest n a plan accepts. */
-#define RPCHOLQR_MAX_N 128
+/* Largest n a plan accepts.  Up to 128 columns the row passes keep a whole row panel in shared
+ * memory; above, both modes run left-looking blocked solves over 64-column blocks. */
+#define RPCHOLQR_MAX_N 512
 
 typedef struct rpcholqr_plan_s* rpcholqr_plan;
 
@@ -200,8 +201,8 @@ rpcholqr_status rpcholqr_precondition_gram_noalloc(const double* A, int64_t m, i
  * matrices of a batch call are dealt round-robin to the slots, so small matrices -- whose row passes
  * fill only part of the GPU -- run concurrently; the caller's stream forks to the slot streams and
  * joins them again (the call stays asynchronous on `stream`).  The sequence can be captured once into
- * a CUDA graph and replayed as one launch (the spec batching pattern: block-Krylov / LOBPCG
- * orthogonalisation of many blocks).  All per-matrix arrays below are HOST arrays of length count;
+ * a CUDA graph and replayed as one launch (the workload of block-Krylov / LOBPCG solvers, which
+ * orthogonalise many tall-skinny blocks).  All per-matrix arrays below are HOST arrays of length count;
  * the pointed-to matrices are device memory; info is a DEVICE int32 array of 2*count entries
  * ({status, pivot} per matrix, see rpcholqr_factor).  Every matrix must fit the batch limits. */
 typedef struct rpcholqr_batch_s* rpcholqr_batch;

@@ -72,14 +72,16 @@ def usv_torch(m: int, n: int, kappa: float, seed: int, device="cuda"):
     def haar(rows, cols):
         x = torch.randn((rows, cols), generator=g, dtype=torch.float64, device=device)
         q, r = torch.linalg.qr(x, mode="reduced")
+        del x
         d = torch.sign(torch.diagonal(r))
         d[d == 0] = 1.0
-        return q * d[None, :]
+        return q.mul_(d[None, :])
 
     u = haar(m, n)
     v = haar(n, n)
     s = torch.from_numpy(log_sigmas(n, kappa)).to(device)
-    return ((u * s[None, :]) @ v.T).contiguous()
+    u.mul_(s[None, :])   # in place: at m = 2^23, n = 512 one copy is 34 GB
+    return (u @ v.T).contiguous()
 
 
 def coherent_diag(m: int, n: int, seed: int) -> np.ndarray:

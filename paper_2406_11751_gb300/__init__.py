@@ -29,7 +29,7 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NONFINITE", 3: "ERR_SINGULAR_SKETCH", 4
 OK, ERR_ARG, ERR_NONFINITE, ERR_SINGULAR_SKETCH, ERR_NOT_SPD = 0, 1, 2, 3, 4
 FP64 = 0
 SPLIT64 = 1
-MAX_N = 128
+MAX_N = 512
 
 EXPORTED_SYMBOLS = (
     "rpcholqr_plan_create", "rpcholqr_plan_destroy", "rpcholqr_workspace_size", "rpcholqr_factor",

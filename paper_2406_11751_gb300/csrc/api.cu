@@ -54,6 +54,11 @@ cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, in
                               int nranges, double* gpart, int32_t* info, cudaStream_t st);
 void launch_row_exp(const double* X, int64_t ldx, int64_t m, int K, int32_t* rowexp, cudaStream_t st);
 void launch_col_exp(const double* X, int64_t ldx, int64_t m, int n, int32_t* colexp, cudaStream_t st);
+cudaError_t launch_gemm_sub_fp64(const double* X, int64_t ldx, const double* Y, int64_t ldy, const double* B,
+                                 int64_t ldb, double* C, int64_t ldc, int64_t m, int K, int N,
+                                 const int32_t* info, int grid, cudaStream_t st);
+cudaError_t launch_syrk_fp64(const double* X, int64_t ldx, int64_t m, int n, int np, int ranges, double* gpart,
+                             const int32_t* info, cudaStream_t st);
 }  // namespace rpq
 
 using namespace rpq;
@@ -106,7 +111,7 @@ struct WsLayout {
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 WsLayout ws_layout(int32_t max_n, int32_t max_s, int grid) {
-    const size_t np = static_cast<size_t>(pad16(max_n));
+    const size_t np = static_cast<size_t>(pad_np(max_n));
     WsLayout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
@@ -173,6 +178,14 @@ struct PhaseMarks {
     }
 };
 
+constexpr int kBlk = 64;   // column block of the blocked solves (n > 128)
+
+// CTAs of a row pass over m rows: one per 128-row panel, at most one per SM.
+int row_grid(const rpcholqr_plan_s* p, int64_t m) {
+    const int64_t panels = (m + 127) / 128;
+    return static_cast<int>(panels < p->grid ? panels : p->grid);
+}
+
 void free_events(rpcholqr_plan_s* p) {
     if (!p->events) return;
     for (int i = 0; i < p->timing_slots * (RPCHOLQR_NUM_PHASES + 1); ++i) cudaEventDestroy(p->events[i]);
@@ -224,7 +237,7 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
     p->max_m = max_m;
     p->max_n = max_n;
     p->max_s = max_s;
-    p->np = pad16(max_n);
+    p->np = pad_np(max_n);
     p->grid = default_grid(device);
     const WsLayout L = ws_layout(max_n, max_s, p->grid);
     if (cudaMalloc(&p->ws, L.total) != cudaSuccess) {
@@ -299,7 +312,7 @@ static rpcholqr_status sketch_internal(rpcholqr_plan p, const double* A, int64_t
                                        int64_t lda, int32_t s, uint64_t seed, uint64_t stream_id,
                                        double* Rs_user, int32_t* info, cudaStream_t st,
                                        const PhaseMarks* pm) {
-    const int np = pad16(n);
+    const int np = pad_np(n);
     const double scale = std::sqrt(static_cast<double>(m) / static_cast<double>(s));
     if (pm) pm->mark(RPCHOLQR_PHASE_SAMPLE);
     const int64_t lds = s;
@@ -313,17 +326,109 @@ static rpcholqr_status sketch_internal(rpcholqr_plan p, const double* A, int64_t
     return RPCHOLQR_OK;
 }
 
+static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const double* X, int64_t m, int K,
+                                           int64_t ldx, const double* Y, int N, int64_t ldy, const double* B,
+                                           int64_t ldb, double* C, int64_t ldc, int32_t* info, cudaStream_t st,
+                                           bool xexp_ready = false);
+
+// Diagonal-block setups for the blocked solve with T (n x n, ld ldt): block J (64 columns, the last
+// one ragged) gets frag + 4096 J and diag + 512 J.
+static void prep_blocks(rpcholqr_plan_s* p, const double* T, int64_t ldt, int n, double* frag, double* diag,
+                 const int32_t* info, cudaStream_t st) {
+    for (int J = 0; J * kBlk < n; ++J) {
+        const int nj = n - J * kBlk < kBlk ? n - J * kBlk : kBlk;
+        launch_prep_tri(T + static_cast<int64_t>(J) * kBlk * ldt + J * kBlk, ldt, nj, pad16(nj),
+                        frag + J * kBlk * kBlk, diag + J * (kBlk / 8) * 64, info, st);
+        ++p->launches;
+    }
+}
+
+// Left-looking blocked row solve Y = X T^{-1} (T upper triangular, n x n, ld ldt) over 64-column
+// blocks J:  Y[:, J] = X[:, J] - Y[:, <J] T[<J, J]  (FP64 mma, or the split tensor-core product when
+// split), then Y[:, J] <- Y[:, J] T[J, J]^{-1} by the row pass (NP = 64).  Y may equal X (ldy == ldx).
+// The diagonal blocks must have been set up by prep_blocks.  split: the row passes store (block 0) and
+// max-merge (later blocks) the row bounds of Y into p->xexp and max-merge its column bounds into
+// p->colexp, both needed by the split products; marks PASS1 / PASS1_UPDATE / PASS1_SOLVE2 when
+// pass1_marks (blocks 2.. fall in PASS1_SOLVE2).
+static rpcholqr_status solve_blocked(rpcholqr_plan_s* p, const double* X, int64_t ldx, const double* T, int64_t ldt,
+                              int64_t m, int n, double* Y, int64_t ldy, const double* frag, const double* diag,
+                              bool split, bool check_finite, int32_t* info, cudaStream_t st,
+                              const PhaseMarks* pm, bool pass1_marks) {
+    const int grid = row_grid(p, m);
+    for (int J = 0; J * kBlk < n; ++J) {
+        const int c0 = J * kBlk;
+        const int nj = n - c0 < kBlk ? n - c0 : kBlk;
+        const double* src = X + c0;
+        int64_t lsrc = ldx;
+        if (J > 0) {
+            if (pm && pass1_marks && J == 1) pm->mark(RPCHOLQR_PHASE_PASS1_UPDATE);
+            if (split) {
+                rpcholqr_status rc = ozaki_gemm_internal(p, true, Y, m, c0, ldy, T + c0, nj, ldt, X + c0, ldx,
+                                                         Y + c0, ldy, info, st, true);
+                if (rc != RPCHOLQR_OK) return rc;
+            } else {
+                if (launch_gemm_sub_fp64(Y, ldy, T + c0, ldt, X + c0, ldx, Y + c0, ldy, m, c0, nj, info,
+                                         2 * p->grid, st) != cudaSuccess)
+                    return RPCHOLQR_ERR_CUDA;
+                ++p->launches;
+            }
+            src = Y + c0;
+            lsrc = ldy;
+            if (pm && pass1_marks && J == 1) pm->mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
+        }
+        if (launch_rowpass_ex(false, pad16(nj), src, lsrc, Y + c0, ldy, m, nj, frag + J * kBlk * kBlk,
+                              diag + J * (kBlk / 8) * 64, nullptr, info, grid, st, check_finite,
+                              split ? p->xexp : nullptr, J == 0 ? 1 : 2, split ? p->colexp + c0 : nullptr) !=
+            cudaSuccess)
+            return RPCHOLQR_ERR_CUDA;
+        ++p->launches;
+    }
+    if (pm && pass1_marks && n <= kBlk) {
+        pm->mark(RPCHOLQR_PHASE_PASS1_UPDATE);
+        pm->mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
+    }
+    return check_launch();
+}
+
+// Row-range partials of G = X^T X in FP64 (n > 128) and their fixed-order sum into G (ld ldg).
+static rpcholqr_status gram_fp64_wide(rpcholqr_plan_s* p, const double* X, int64_t ldx, int64_t m, int n, double* G,
+                               int64_t ldg, int32_t* info, cudaStream_t st) {
+    const int np = pad_np(n);
+    const int nb = np / kBlk;
+    const int tiles = nb * (nb + 1) / 2;
+    int ranges = 2 * p->grid / tiles;   // two CTAs per SM fit
+    if (ranges < 1) ranges = 1;
+    if (ranges > p->grid) ranges = p->grid;
+    const int64_t max_ranges = (m + 31) / 32;
+    if (ranges > max_ranges) ranges = static_cast<int>(max_ranges);
+    if (launch_syrk_fp64(X, ldx, m, n, np, ranges, p->gpart, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    launch_gram_reduce(p->gpart, ranges, np, n, G, ldg, info, st);
+    p->launches += 2;
+    return check_launch();
+}
+
 static rpcholqr_status precondition_internal(rpcholqr_plan p, const double* A, int64_t m, int32_t n,
                                              int64_t lda, const double* Rs, int64_t ldrs, double* A1,
                                              int64_t ld1, double* G_user, int32_t* info,
                                              cudaStream_t st, const PhaseMarks* pm) {
-    const int np = pad16(n);
+    const int np = pad_np(n);
+    double* G = G_user ? G_user : p->G;
+    const int64_t ldg = G_user ? n : np;
     if (pm) pm->mark(RPCHOLQR_PHASE_PREP_RS);
+    if (np > kMaxNP) {
+        // wide: blocked solve into A1, then a separate Gram pass
+        prep_blocks(p, Rs, ldrs, n, p->frag_s, p->diag_s, info, st);
+        if (pm) pm->mark(RPCHOLQR_PHASE_PASS1);
+        rpcholqr_status rc = solve_blocked(p, A, lda, Rs, ldrs, m, n, A1, ld1, p->frag_s, p->diag_s, false, true,
+                                           info, st, pm, true);
+        if (rc != RPCHOLQR_OK) return rc;
+        if (pm) pm->mark(RPCHOLQR_PHASE_GRAM_REDUCE);
+        return gram_fp64_wide(p, A1, ld1, m, n, G, ldg, info, st);
+    }
     launch_prep_tri(Rs, ldrs, n, np, p->frag_s, p->diag_s, info, st);
     ++p->launches;
     if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
-    const int64_t panels = (m + 127) / 128;
-    const int grid = static_cast<int>(panels < p->grid ? panels : p->grid);
+    const int grid = row_grid(p, m);
     if (pm) pm->mark(RPCHOLQR_PHASE_PASS1);
     if (launch_rowpass(true, np, A, lda, A1, ld1, m, n, p->frag_s, p->diag_s, p->gpart, info, grid, st) !=
         cudaSuccess)
@@ -334,7 +439,7 @@ static rpcholqr_status precondition_internal(rpcholqr_plan p, const double* A, i
         pm->mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
         pm->mark(RPCHOLQR_PHASE_GRAM_REDUCE);
     }
-    launch_gram_reduce(p->gpart, grid, np, n, G_user ? G_user : p->G, G_user ? n : np, info, st);
+    launch_gram_reduce(p->gpart, grid, np, n, G, ldg, info, st);
     ++p->launches;
     return check_launch();
 }
@@ -342,13 +447,18 @@ static rpcholqr_status precondition_internal(rpcholqr_plan p, const double* A, i
 static rpcholqr_status solve_internal(rpcholqr_plan p, const double* X, int64_t m, int32_t n,
                                       int64_t ldx, const double* T, int64_t ldt, double* Y, int64_t ldy,
                                       int32_t* info, cudaStream_t st, const PhaseMarks* pm) {
-    const int np = pad16(n);
+    const int np = pad_np(n);
     if (pm) pm->mark(RPCHOLQR_PHASE_PREP_R1);
+    if (np > kMaxNP) {
+        prep_blocks(p, T, ldt, n, p->frag_1, p->diag_1, info, st);
+        if (pm) pm->mark(RPCHOLQR_PHASE_PASS2);
+        return solve_blocked(p, X, ldx, T, ldt, m, n, Y, ldy, p->frag_1, p->diag_1, false, false, info, st,
+                             nullptr, false);
+    }
     launch_prep_tri(T, ldt, n, np, p->frag_1, p->diag_1, info, st);
     ++p->launches;
     if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
-    const int64_t panels = (m + 127) / 128;
-    const int grid = static_cast<int>(panels < p->grid ? panels : p->grid);
+    const int grid = row_grid(p, m);
     if (pm) pm->mark(RPCHOLQR_PHASE_PASS2);
     if (launch_rowpass(false, np, X, ldx, Y, ldy, m, n, p->frag_1, p->diag_1, nullptr, info, grid, st) !=
         cudaSuccess)
@@ -362,7 +472,7 @@ static rpcholqr_status solve_internal(rpcholqr_plan p, const double* X, int64_t 
 static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const double* X, int64_t m, int K,
                                            int64_t ldx, const double* Y, int N, int64_t ldy, const double* B,
                                            int64_t ldb, double* C, int64_t ldc, int32_t* info, cudaStream_t st,
-                                           bool xexp_ready = false) {
+                                           bool xexp_ready) {
     if (!xexp_ready) {
         launch_row_exp(X, ldx, m, K, p->xexp, st);
         ++p->launches;
@@ -384,7 +494,7 @@ static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const doub
 static rpcholqr_status ozaki_gram_internal(rpcholqr_plan p, const double* X, int64_t m, int n, int64_t ldx,
                                            double* G, int64_t ldg, int32_t* info, cudaStream_t st,
                                            bool colexp_ready = false) {
-    const int np = pad16(n);
+    const int np = pad_np(n);
     if (!colexp_ready) {
         launch_col_exp(X, ldx, m, n, p->colexp, st);
         p->launches += 2;
@@ -406,49 +516,20 @@ static rpcholqr_status ozaki_gram_internal(rpcholqr_plan p, const double* X, int
 static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m, int32_t n, int64_t lda,
                                     int32_t s, uint64_t seed, double* Q, int64_t ldq, double* R,
                                     int32_t* info, cudaStream_t st, const PhaseMarks& pm) {
-    const int np = pad16(n);
+    const int np = pad_np(n);
     rpcholqr_status rc = sketch_internal(p, A, m, n, lda, s, seed, 0, nullptr, info, st, &pm);
     if (rc != RPCHOLQR_OK) return rc;
     double* A1 = p->A1;
     const int64_t ld1 = np;
-    const int64_t panels = (m + 127) / 128;
-    const int grid = static_cast<int>(panels < p->grid ? panels : p->grid);
     pm.mark(RPCHOLQR_PHASE_PREP_RS);
     launch_fill_noexp(p->colexp, n, st);   // column bounds of A1, atomically max-merged by the row passes
     ++p->launches;
-    if (n <= 64) {
-        launch_prep_tri(p->Rs, np, n, np, p->frag_s, p->diag_s, info, st);
-        ++p->launches;
-        pm.mark(RPCHOLQR_PHASE_PASS1);
-        if (launch_rowpass_ex(false, np, A, lda, A1, ld1, m, n, p->frag_s, p->diag_s, nullptr, info, grid, st,
-                              true, p->xexp, 1, p->colexp) != cudaSuccess)
-            return RPCHOLQR_ERR_CUDA;
-        ++p->launches;
-        pm.mark(RPCHOLQR_PHASE_PASS1_UPDATE);
-        pm.mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
-    } else {
-        const int n2 = n - 64;
-        launch_prep_tri(p->Rs, np, 64, 64, p->frag_s, p->diag_s, info, st);
-        launch_prep_tri(p->Rs + 64 * np + 64, np, n2, pad16(n2), p->frag_1, p->diag_1, info, st);
-        p->launches += 2;
-        pm.mark(RPCHOLQR_PHASE_PASS1);
-        // A1[:, :64] = A[:, :64] R11^{-1}
-        if (launch_rowpass_ex(false, 64, A, lda, A1, ld1, m, 64, p->frag_s, p->diag_s, nullptr, info, grid, st,
-                              true, p->xexp, 1, p->colexp) != cudaSuccess)
-            return RPCHOLQR_ERR_CUDA;
-        ++p->launches;
-        pm.mark(RPCHOLQR_PHASE_PASS1_UPDATE);
-        // A1[:, 64:] = A[:, 64:] - A1[:, :64] R12   (tensor cores)
-        if ((rc = ozaki_gemm_internal(p, true, A1, m, 64, ld1, p->Rs + 64, n2, np, A + 64, lda, A1 + 64, ld1,
-                                      info, st, true)) != RPCHOLQR_OK)
-            return rc;
-        pm.mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
-        // A1[:, 64:] = A1[:, 64:] R22^{-1}
-        if (launch_rowpass_ex(false, pad16(n2), A1 + 64, ld1, A1 + 64, ld1, m, n2, p->frag_1, p->diag_1, nullptr,
-                              info, grid, st, true, p->xexp, 2, p->colexp + 64) != cudaSuccess)
-            return RPCHOLQR_ERR_CUDA;
-        ++p->launches;
-    }
+    // A1 = A R_s^{-1}: one row pass for n <= 64, else the blocked solve with split off-diagonal updates
+    prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st);
+    pm.mark(RPCHOLQR_PHASE_PASS1);
+    if ((rc = solve_blocked(p, A, lda, p->Rs, np, m, n, A1, ld1, p->frag_s, p->diag_s, true, true, info, st, &pm,
+                            true)) != RPCHOLQR_OK)
+        return rc;
     pm.mark(RPCHOLQR_PHASE_GRAM_REDUCE);
     if ((rc = ozaki_gram_internal(p, A1, m, n, ld1, p->G, np, info, st, true)) != RPCHOLQR_OK) return rc;
     pm.mark(RPCHOLQR_PHASE_CHOLESKY);
@@ -476,7 +557,7 @@ rpcholqr_status rpcholqr_factor(rpcholqr_plan p, const double* A, int64_t m, int
     DeviceGuard guard(p->device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int np = pad16(n);
+    const int np = pad_np(n);
     const PhaseMarks pm(p, st);
     rpcholqr_status rc = reset_info(info, st);
     if (rc != RPCHOLQR_OK) return rc;
@@ -613,7 +694,7 @@ rpcholqr_status rpcholqr_cholesky(rpcholqr_plan p, const double* G, int32_t n, d
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rpcholqr_status rc = reset_info(info, st);
     if (rc != RPCHOLQR_OK) return rc;
-    const int np = pad16(n);
+    const int np = pad_np(n);
     return launch_cholesky(G, n, n, np, p->R1, R1, info, st) == cudaSuccess ? RPCHOLQR_OK
                                                                              : RPCHOLQR_ERR_CUDA;
 }
@@ -667,7 +748,14 @@ rpcholqr_status rpcholqr_ozaki_gram(rpcholqr_plan p, const double* X, int64_t m,
 // One Cholesky-QR step in FP64: Q = X R^{-1} with R = chol(X^T X) written to R_out (np x np, ld np).
 static rpcholqr_status cholqr_step(rpcholqr_plan p, const double* X, int64_t m, int32_t n, int64_t ldx,
                                    double* Q, int64_t ldq, double* R_out, int32_t* info, cudaStream_t st) {
-    const int np = pad16(n);
+    const int np = pad_np(n);
+    if (np > kMaxNP) {
+        rpcholqr_status rc = gram_fp64_wide(p, X, ldx, m, n, p->G, np, info, st);
+        if (rc != RPCHOLQR_OK) return rc;
+        if (launch_cholesky(p->G, np, n, np, R_out, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+        ++p->launches;
+        return solve_internal(p, X, m, n, ldx, R_out, np, Q, ldq, info, st, nullptr);
+    }
     launch_prep_tri(nullptr, 0, 0, np, p->frag_s, p->diag_s, info, st);   // identity preconditioner
     const int64_t panels = (m + 127) / 128;
     const int grid = static_cast<int>(panels < p->grid ? panels : p->grid);
@@ -696,7 +784,7 @@ rpcholqr_status rpcholqr_cholqr(rpcholqr_plan p, const double* A, int64_t m, int
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = reset_info(info, st)) != RPCHOLQR_OK) return rc;
     if ((rc = cholqr_step(p, A, m, n, lda, Q, ldq, p->R1, info, st)) != RPCHOLQR_OK) return rc;
-    const size_t np = static_cast<size_t>(pad16(n));
+    const size_t np = static_cast<size_t>(pad_np(n));
     if (cudaMemcpy2DAsync(R, sizeof(double) * n, p->R1, sizeof(double) * np, sizeof(double) * n,
                           static_cast<size_t>(n), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return RPCHOLQR_ERR_CUDA;
@@ -713,7 +801,7 @@ rpcholqr_status rpcholqr_cholqr2(rpcholqr_plan p, const double* A, int64_t m, in
     if ((rc = reset_info(info, st)) != RPCHOLQR_OK) return rc;
     if ((rc = cholqr_step(p, A, m, n, lda, Q, ldq, p->Rs, info, st)) != RPCHOLQR_OK) return rc;   // R_a
     if ((rc = cholqr_step(p, Q, m, n, ldq, Q, ldq, p->R1, info, st)) != RPCHOLQR_OK) return rc;   // R_b
-    const int np = pad16(n);
+    const int np = pad_np(n);
     launch_triu_mul(p->R1, np, p->Rs, np, n, R, n, info, st);
     ++p->launches;
     return check_launch();

@@ -10,9 +10,11 @@ namespace rpq {
 
 // Every matrix dimension is padded to a multiple of this (the k extent of mma m16n8k16).
 constexpr int kPad = 16;
-constexpr int kMaxNP = RPCHOLQR_MAX_N;  // padded n handled by the row-pass kernels
+constexpr int kMaxNP = 128;             // widest panel the row-pass kernels keep in shared memory
 
 __host__ __device__ constexpr int pad16(int n) { return (n + kPad - 1) / kPad * kPad; }
+// Padded width of the n x n factors: a multiple of 16 up to 128 columns, of 64 above (64-column blocks).
+__host__ __device__ constexpr int pad_np(int n) { return n <= kMaxNP ? pad16(n) : (n + 63) / 64 * 64; }
 
 // ---- power-of-two bounds used by the split-precision products ------------------------------------
 // exp_bound(v): |v| < 2^e for a normal v (e = unbiased exponent + 1); kNoExp for 0 or subnormal.

@@ -188,6 +188,29 @@ __device__ __forceinline__ double scale_pow2(long long I, int e) {
     return ldexp(v, e);
 }
 
+// Add the eight TMEM group sums of this thread's row and its warp's 32 columns (columns col0..col0+31 of
+// the 64-column tile) to int64 accumulators in units of 2^-53 (U53) or 2^-49 of the operand scale.
+// The sliced operands are below 0.51 of their power-of-two bounds, so a K-term sum stays below
+// 0.26 K scale: units of 2^-53 hold K <= 2^10 terms, units of 2^-49 hold 2^14 (a 64-window flush).
+template <bool U53>
+__device__ __forceinline__ void drain_acc(uint32_t tmem, int warp, int col0, long long (&acc)[32]) {
+#pragma unroll
+    for (int c0 = 0; c0 < 32; c0 += 8) {
+        float mg[kGroups][8];
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g)
+            tmem_ld8(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + g * kTileN + col0 + c0, mg[g]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float grp[kGroups];
+#pragma unroll
+            for (int g = 0; g < kGroups; ++g) grp[g] = mg[g][j];
+            acc[c0 + j] += U53 ? combine_units53(grp) : combine_units49(grp);
+        }
+    }
+}
+
 // Issue the 72 MMAs of one stage: all pairs (a, b), a + b <= 9, for the two K=16 steps.
 // first_window: the stage starts an exactness window (the first MMA into each accumulator clears it).
 __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, uint32_t b_base,
@@ -245,7 +268,9 @@ __global__ void __launch_bounds__(256) k_ozaki_slice_cols(const double* __restri
 // X: m x K FP64 (ldx) with row exponent bounds xexp[m] (max over the K columns used);
 // Y: pre-sliced by k_ozaki_slice_cols (K x N, column bounds yexp[N]);
 // B, C: m x N FP64 (ldb, ldc); C may equal B.  Persistent grid over 128-row x 64-column tiles.
-template <bool SUB>
+// WIN (128 < K <= 1024): the K range is cut into exactness windows of 128, each drained into int64
+// accumulators in units of 2^-53 of the scale (the same resolution as a single window).
+template <bool SUB, bool WIN>
 __global__ void __launch_bounds__(kThreads, 1)
 k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int K,
              const uint8_t* __restrict__ yblocks, const int32_t* __restrict__ yexp, int N,
@@ -277,10 +302,13 @@ k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int
     const int ntn = (N + kTileN - 1) / kTileN;
     const int64_t ntm = (m + kTileM - 1) / kTileM;
     const int64_t ntiles = ntm * ntn;
+    // K > 128: exactness windows of 4 stages, drained into int64 accumulators between windows
+    constexpr bool windowed = WIN;
     uint32_t phase[2] = {0u, 0u};
     bool pending[2] = {false, false};
     bool timed_out = false;
     int step = 0;
+    long long acc[32];
 
     for (int64_t tile = blockIdx.x; tile < ntiles && !timed_out; tile += gridDim.x) {
         const int64_t tm = tile / ntn;
@@ -290,6 +318,8 @@ k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int
         const int chalf = tid >> 7;         // producer K chunks 2*chalf, 2*chalf+1; drain columns 32*chalf..
         const int64_t myrow = row0 + lr;
         const int E = myrow < m ? xexp[myrow] : kNoExp;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = 0;
         for (int kw = 0; kw < nkw; ++kw, ++step) {
             const int s = step & 1;
             if (pending[s]) {
@@ -323,10 +353,25 @@ k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int
             __syncthreads();
             tc_after_sync();
             if (tid == 0) {
-                issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), kBSlice, kw == 0);
+                issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), kBSlice, (kw & 3) == 0);
                 mma_commit(&mbar[s]);
             }
             pending[s] = true;
+            if (windowed && (kw & 3) == 3 && kw < nkw - 1) {
+                // end of an exactness window that is not the last: drain into the int64 accumulators
+                for (int q = 0; q < 2 && !timed_out; ++q)
+                    if (pending[q]) {
+                        const bool ok = mbar_wait(&mbar[q], phase[q]);
+                        if (__syncthreads_or(!ok)) { timed_out = true; break; }
+                        phase[q] ^= 1u;
+                        pending[q] = false;
+                    }
+                if (timed_out) break;
+                tc_after_sync();
+                drain_acc<true>(tmem, warp, 32 * chalf, acc);
+                tc_before_sync();
+                __syncthreads();
+            }
         }
         if (timed_out) break;
         // all MMAs of the tile done
@@ -339,9 +384,24 @@ k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int
             }
         if (timed_out) break;
         tc_after_sync();
+        if (windowed) {
+            drain_acc<true>(tmem, warp, 32 * chalf, acc);
+            if (myrow < m) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = tn * kTileN + 32 * chalf + j;
+                    if (col < N) {
+                        const int ey = yexp[col];
+                        const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(acc[j], E + ey - 53) : 0.0;
+                        if (SUB) C[myrow * ldc + col] = B[myrow * ldb + col] - v;
+                        else C[myrow * ldc + col] = v;
+                    }
+                }
+            }
+        }
         // drain: lane = output row; this warp's 32 columns in chunks of 8
 #pragma unroll 1
-        for (int c0 = 32 * chalf; c0 < 32 * chalf + 32; c0 += 8) {
+        for (int c0 = 32 * chalf; c0 < 32 * chalf + 32 && !windowed; c0 += 8) {
             double bv[8];
             if (SUB) {
 #pragma unroll
@@ -388,28 +448,39 @@ k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
 }
 
-// ---- Gram partials G_rr = X_rr^T X_rr (upper and lower) -------------------------------------------------
-// X: m x n FP64 (ldx), column exponent bounds colexp[n] over all m rows.  Grid = nhalf x nranges CTAs;
-// CTA (h, rr) accumulates columns 64h..64h+63 of the Gram matrix of rows [rr*rows_per, ...) and writes
-// gpart[rr][p][q] (np x np, p < np, q in its 64 columns).  Exactness windows of 128 rows are drained
-// into int64 accumulators in units of 2^-49 of the scale 2^(Ep+Eq) (one output row per thread, 64
-// columns); every 64 windows (8192 rows, |sum| < 2^63 even for maximal slices) the accumulators are
-// added into the CTA's own FP64 partial and cleared.
+// ---- Gram partials G_rr = X_rr^T X_rr -------------------------------------------------------------------
+// X: m x n FP64 (ldx), column exponent bounds colexp[n] over all m rows.  Output tiles (P, Qb): rows
+// p in [128P, 128P+128) (TMEM lanes) x columns q in [64Qb, 64Qb+64), all tiles with Qb >= 2P (every
+// q >= p is covered).  Grid = ntiles x nranges CTAs; CTA (tile, rr) accumulates the rows
+// [rr*rows_per, ...) and writes gpart[rr][p][q] (np x np) for its tile.  The B operand reuses the A
+// slices when its 64 columns lie inside the P block, else it is sliced into its own stage.  Exactness
+// windows of 128 rows are drained into int64 accumulators in units of 2^-49 of the scale 2^(Ep+Eq)
+// (one output row per thread, 32 columns); every 64 windows (8192 rows, |sum| < 2^63 even for maximal
+// slices) they are added into the CTA's own FP64 partial and cleared.
+__device__ __forceinline__ void gram_tile_coords(int nqb, int tt, int& P, int& Qb) {
+    P = 0;
+    while (tt >= nqb - 2 * P) { tt -= nqb - 2 * P; ++P; }
+    Qb = 2 * P + tt;
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
 k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np,
-             const int32_t* __restrict__ colexp, int64_t rows_per, double* __restrict__ gpart,
+             const int32_t* __restrict__ colexp, int64_t rows_per, int ntiles, double* __restrict__ gpart,
              int32_t* info) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t mbar[2];
     __shared__ uint32_t tslot;
     if (load_status(info) != 0) return;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int nhalf = (np + kTileN - 1) / kTileN;
-    const int h = blockIdx.x % nhalf;
-    const int64_t rr = blockIdx.x / nhalf;
+    const int nqb = (np + kTileN - 1) / kTileN;
+    int P, Qb;
+    gram_tile_coords(nqb, blockIdx.x % ntiles, P, Qb);
+    const int64_t rr = blockIdx.x / ntiles;
     const int64_t r0 = rr * rows_per;
     const int64_t r1 = (r0 + rows_per < m) ? r0 + rows_per : m;
     uint8_t* stA[2] = {sm, sm + kAStage};
+    uint8_t* stB[2] = {sm + 2 * kAStage, sm + 2 * kAStage + kBStage};
+    const bool b_inside = 64 * Qb >= 128 * P && 64 * Qb + 64 <= 128 * P + 128;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -426,10 +497,13 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
     tc_after_sync();
     const uint32_t tmem = tslot;
 
-    const int p = tid & 127;                // producer column of X and drain output row (TMEM lane)
-    const int chalf = tid >> 7;             // producer row chunks 2*chalf.., drain columns 32*chalf..
+    const int lr = tid & 127;               // TMEM lane: output row p = 128P + lr; producer column of A
+    const int chalf = tid >> 7;             // producer row chunks 2*chalf..; drain columns 32*chalf..
+    const int p = 128 * P + lr;
     const int Ep = p < n ? colexp[p] : kNoExp;
-    constexpr int kCols = kTileN / 2;       // output columns drained by this thread
+    const int qb_col = 64 * Qb + (tid & 63);          // B producer column (when B is separate)
+    const int Eqb = qb_col < n ? colexp[qb_col] : kNoExp;
+    constexpr int kCols = kTileN / 2;
     long long acc[kCols];
 #pragma unroll
     for (int j = 0; j < kCols; ++j) acc[j] = 0;
@@ -437,7 +511,6 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
     bool pending[2] = {false, false};
     bool timed_out = false;
     const int64_t nstages = r1 > r0 ? (r1 - r0 + kKW - 1) / kKW : 0;
-    const uint32_t b_off = static_cast<uint32_t>(h * kTileN / 8) * kSBO;   // B = A slices, rows 64h..
 
     for (int64_t st = 0; st < nstages && !timed_out; ++st) {
         const int s = static_cast<int>(st & 1);
@@ -457,7 +530,17 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
                 const int64_t row = k0 + 8 * c + i;
                 x[i] = (row < r1 && p < n) ? X[row * ldx + p] : 0.0;
             }
-            slice_store8(x, Ep, stA[s] + core_off(p, 16 * c), kASlice);
+            slice_store8(x, Ep, stA[s] + core_off(lr, 16 * c), kASlice);
+        }
+        if (!b_inside) {
+            const int c = tid >> 6;         // 64 columns x 4 chunks of 8 rows
+            double x[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int64_t row = k0 + 8 * c + i;
+                x[i] = (row < r1 && qb_col < n) ? X[row * ldx + qb_col] : 0.0;
+            }
+            slice_store8(x, Eqb, stB[s] + core_off(tid & 63, 16 * c), kBSlice);
         }
         fence_async_smem();
         tc_before_sync();
@@ -465,13 +548,16 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
         tc_after_sync();
         const bool first_window = (st & 3) == 0;
         if (tid == 0) {
-            issue_stage(tmem, smem_u32(stA[s]), smem_u32(stA[s]) + b_off, kASlice, first_window);
+            if (b_inside)
+                issue_stage(tmem, smem_u32(stA[s]), smem_u32(stA[s]) + ((64 * Qb - 128 * P) / 8) * kSBO, kASlice,
+                            first_window);
+            else
+                issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), kBSlice, first_window);
             mma_commit(&mbar[s]);
         }
         pending[s] = true;
         const bool flush = ((st & 255) == 255) || st == nstages - 1;   // every 64 windows and at the end
         if ((st & 3) == 3 || st == nstages - 1) {
-            // end of an exactness window: wait for every MMA, drain into the int64 accumulators
             for (int q = 0; q < 2 && !timed_out; ++q)
                 if (pending[q]) {
                     const bool ok = mbar_wait(&mbar[q], phase[q]);
@@ -481,27 +567,12 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
                 }
             if (timed_out) break;
             tc_after_sync();
-#pragma unroll
-            for (int c0 = 0; c0 < kCols; c0 += 8) {
-                float mg[kGroups][8];
-#pragma unroll
-                for (int g = 0; g < kGroups; ++g)
-                    tmem_ld8(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + g * kTileN + kCols * chalf + c0,
-                             mg[g]);
-                tmem_wait_ld();
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    float grp[kGroups];
-#pragma unroll
-                    for (int g = 0; g < kGroups; ++g) grp[g] = mg[g][j];
-                    acc[c0 + j] += combine_units49(grp);
-                }
-            }
+            drain_acc<false>(tmem, warp, kCols * chalf, acc);
             if (flush && p < np) {
                 double* out = gpart + static_cast<size_t>(rr) * np * np + static_cast<size_t>(p) * np;
 #pragma unroll
                 for (int j = 0; j < kCols; ++j) {
-                    const int q = h * kTileN + kCols * chalf + j;
+                    const int q = 64 * Qb + kCols * chalf + j;
                     if (q < np) {
                         const int Eq = q < n ? colexp[q] : kNoExp;
                         const double v = (Ep > kNoExp && Eq > kNoExp) ? scale_pow2(acc[j], Ep + Eq - 49) : 0.0;
@@ -522,7 +593,7 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
     } else if (nstages == 0 && p < np) {
         double* out = gpart + static_cast<size_t>(rr) * np * np + static_cast<size_t>(p) * np;
         for (int j = 0; j < kCols; ++j) {
-            const int q = h * kTileN + kCols * chalf + j;
+            const int q = 64 * Qb + kCols * chalf + j;
             if (q < np) out[q] = 0.0;
         }
     }
@@ -581,18 +652,13 @@ cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int3
                               int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, int grid,
                               cudaStream_t st) {
     const int smem = 2 * (oz::kAStage + oz::kBStage);
-    cudaError_t err;
-    if (sub) {
-        err = cudaFuncSetAttribute(oz::k_ozaki_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (err != cudaSuccess) return err;
-        oz::k_ozaki_gemm<true><<<grid, oz::kThreads, smem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb,
-                                                                 C, ldc, m, info);
-    } else {
-        err = cudaFuncSetAttribute(oz::k_ozaki_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (err != cudaSuccess) return err;
-        oz::k_ozaki_gemm<false><<<grid, oz::kThreads, smem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B,
-                                                                  ldb, C, ldc, m, info);
-    }
+    if (K > 32 * oz::kKW) return cudaErrorInvalidValue;   // int64 accumulators hold K <= 1024
+    const bool win = K > 4 * oz::kKW;
+    auto kern = sub ? (win ? oz::k_ozaki_gemm<true, true> : oz::k_ozaki_gemm<true, false>)
+                    : (win ? oz::k_ozaki_gemm<false, true> : oz::k_ozaki_gemm<false, false>);
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err != cudaSuccess) return err;
+    kern<<<grid, oz::kThreads, smem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb, C, ldc, m, info);
     return cudaGetLastError();
 }
 
@@ -608,7 +674,13 @@ void launch_col_exp(const double* X, int64_t ldx, int64_t m, int n, int32_t* col
     oz::k_col_exp<<<static_cast<unsigned>(blocks), (n + 31) / 32 * 32, 0, st>>>(X, ldx, m, n, colexp);
 }
 
-int ozaki_gram_halves(int np) { return (np + oz::kTileN - 1) / oz::kTileN; }
+// Output tiles of the split Gram kernel for padded width np.
+int ozaki_gram_halves(int np) {
+    const int nqb = (np + oz::kTileN - 1) / oz::kTileN;
+    int c = 0;
+    for (int P = 0; 2 * P < nqb; ++P) c += nqb - 2 * P;
+    return c;
+}
 
 void launch_fill_noexp(int32_t* p, int n, cudaStream_t st) {
     oz::k_fill_i32<<<(n + 127) / 128, 128, 0, st>>>(p, n, kNoExp);
@@ -616,13 +688,14 @@ void launch_fill_noexp(int32_t* p, int n, cudaStream_t st) {
 
 cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
                               int nranges, double* gpart, int32_t* info, cudaStream_t st) {
-    const int smem = 2 * oz::kAStage;
+    const int smem = 2 * (oz::kAStage + oz::kBStage);
     cudaError_t err = cudaFuncSetAttribute(oz::k_ozaki_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (err != cudaSuccess) return err;
-    const int nh = ozaki_gram_halves(np);
+    const int nt = ozaki_gram_halves(np);
     int64_t rows_per = (m + nranges - 1) / nranges;
     rows_per = (rows_per + oz::kKW - 1) / oz::kKW * oz::kKW;
-    oz::k_ozaki_gram<<<nh * nranges, oz::kThreads, smem, st>>>(X, ldx, m, n, np, colexp, rows_per, gpart, info);
+    oz::k_ozaki_gram<<<nt * nranges, oz::kThreads, smem, st>>>(X, ldx, m, n, np, colexp, rows_per, nt, gpart,
+                                                               info);
     return cudaGetLastError();
 }
 

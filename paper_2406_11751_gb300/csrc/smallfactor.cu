@@ -165,6 +165,63 @@ k_cholesky(const double* __restrict__ G, int64_t ldg, int n, int np, double* __r
     }
 }
 
+// The same factorisation for np > 128, working in global memory: R (np x np) is the work array, held
+// column-major while factoring (column l of R contiguous, so the lanes of a warp read both operands of
+// a dot product coalesced) and transposed to row-major at the end.  Left-looking: step j forms row j,
+// R[j][l] = G[j][l] - sum_{k<j} R[k][j] R[k][l], one warp per column l splitting the sum over its lanes.
+__global__ void __launch_bounds__(1024)
+k_cholesky_wide(const double* __restrict__ G, int64_t ldg, int n, int np, double* __restrict__ R,
+                double* __restrict__ R_user, int32_t* info) {
+    __shared__ double diag_s;
+    __shared__ int fail_s;
+    if (load_status(info) != 0) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+    for (int e = tid; e < np * np; e += blockDim.x) R[e] = 0.0;
+    if (tid == 0) fail_s = -1;
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        const double* cj = R + static_cast<size_t>(j) * np;   // column j (rows < j are final)
+        for (int l = j + warp; l < n; l += nwarps) {
+            const double* cl = R + static_cast<size_t>(l) * np;
+            double part = 0.0;
+            for (int k = lane; k < j; k += 32) part = fma(cj[k], cl[k], part);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == 0) R[static_cast<size_t>(l) * np + j] = G[static_cast<int64_t>(j) * ldg + l] - part;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const double d = R[static_cast<size_t>(j) * np + j];
+            if (!(d > 0.0)) fail_s = j;
+            else { diag_s = sqrt(d); R[static_cast<size_t>(j) * np + j] = diag_s; }
+        }
+        __syncthreads();
+        if (fail_s >= 0) break;
+        const double inv = 1.0 / diag_s;
+        for (int l = j + 1 + tid; l < n; l += blockDim.x) R[static_cast<size_t>(l) * np + j] *= inv;
+        __syncthreads();
+    }
+    if (fail_s >= 0) {
+        if (tid == 0) set_status(info, RPCHOLQR_ERR_NOT_SPD, fail_s);
+        return;
+    }
+    // column-major -> row-major
+    for (int e = tid; e < np * np; e += blockDim.x) {
+        const int r = e / np, c = e - r * np;
+        if (r < c) {
+            const double t = R[e];
+            R[e] = R[static_cast<size_t>(c) * np + r];
+            R[static_cast<size_t>(c) * np + r] = t;
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < np * np; e += blockDim.x) {
+        const int r = e / np, c = e - r * np;
+        if (r >= n || c >= n) R[e] = (r == c) ? 1.0 : 0.0;
+        else if (R_user) R_user[r * n + c] = R[e];
+    }
+}
+
 // R[i][j] = sum_{k=i..j} R1[i][k] Rs[k][j] for j >= i, 0 below; block i = row i.
 __global__ void k_triu_mul(const double* __restrict__ R1, int64_t ld1, const double* __restrict__ Rs,
                            int64_t lds, int n, double* __restrict__ R, int64_t ldr,
@@ -178,11 +235,12 @@ __global__ void k_triu_mul(const double* __restrict__ R1, int64_t ld1, const dou
     }
 }
 
-// W = T^{-1} for upper-triangular T (n x n, ld ldt, n <= 128): back substitution, one warp per column.
+// W = T^{-1} for upper-triangular T (n x n, ld ldt, n <= 512): back substitution, one warp per column.
 //   W[j][j] = 1/T[j][j],  W[i][j] = -(sum_{k=i+1..j} T[i][k] W[k][j]) / T[i][i]  (i < j).
-// Column j lives in the registers of its warp (lane l holds rows l, l+32, l+64, l+96); the dot product
+// Column j lives in the registers of its warp (lane l holds rows l, l+32, ...); the dot product
 // of each step is split over the lanes and summed with shuffles; reciprocal diagonals are formed once.
-// W: np x np row-major (ld np), padded with the identity.
+// W: np x np row-major (ld np), padded with the identity.  kQ = rows per lane (n <= 32 kQ).
+template <int kQ>
 __global__ void __launch_bounds__(256) k_triu_inv(const double* __restrict__ T, int64_t ldt, int n, int np,
                                                   double* __restrict__ W, const int32_t* info) {
     if (info && load_status(info) != 0) return;
@@ -192,30 +250,40 @@ __global__ void __launch_bounds__(256) k_triu_inv(const double* __restrict__ T, 
         const int r = e / np, c = e - r * np;
         if (r >= n || c >= n || r > c) W[e] = (r == c) ? 1.0 : 0.0;
     }
-    double rinv[4];
+    double rinv[kQ];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kQ; ++q) {
         const int i = lane + 32 * q;
         rinv[q] = i < n ? 1.0 / T[static_cast<int64_t>(i) * ldt + i] : 0.0;
     }
     for (int j = gw; j < n; j += nwarps_total) {
-        double w[4] = {0.0, 0.0, 0.0, 0.0};   // W[lane + 32q][j]
-        if ((j & 31) == lane) w[j >> 5] = rinv[j >> 5];
+        double w[kQ];                         // W[lane + 32q][j]
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) w[q] = 0.0;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q)
+            if ((j & 31) == lane && (j >> 5) == q) w[q] = rinv[q];
         for (int i = j - 1; i >= 0; --i) {
             const double* Ti = T + static_cast<int64_t>(i) * ldt;
             double part = 0.0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < kQ; ++q) {
                 const int k = lane + 32 * q;
                 if (k > i && k <= j) part = fma(Ti[k], w[q], part);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            const double ri = __shfl_sync(0xffffffffu, rinv[i >> 5], i & 31);
-            if ((i & 31) == lane) w[i >> 5] = -part * ri;
+            double rq = 0.0;
+#pragma unroll
+            for (int q = 0; q < kQ; ++q)
+                if ((i >> 5) == q) rq = rinv[q];
+            const double ri = __shfl_sync(0xffffffffu, rq, i & 31);
+#pragma unroll
+            for (int q = 0; q < kQ; ++q)
+                if ((i & 31) == lane && (i >> 5) == q) w[q] = -part * ri;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kQ; ++q) {
             const int k = lane + 32 * q;
             if (k <= j) W[k * np + j] = w[q];
         }
@@ -262,6 +330,10 @@ cudaError_t launch_householder(double* W, int64_t lds, int s, int n, int np, dou
 
 cudaError_t launch_cholesky(const double* G, int64_t ldg, int n, int np, double* R, double* R_user,
                             int32_t* info, cudaStream_t st) {
+    if (np > kMaxNP) {
+        k_cholesky_wide<<<1, 1024, 0, st>>>(G, ldg, n, np, R, R_user, info);
+        return cudaGetLastError();
+    }
     const size_t smem = static_cast<size_t>(np) * np * sizeof(double);
     cudaError_t err = cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
@@ -281,6 +353,7 @@ void launch_triu_mul(const double* R1, int64_t ld1, const double* Rs, int64_t ld
 namespace rpq {
 void launch_triu_inv(const double* T, int64_t ldt, int n, int np, double* W, const int32_t* info,
                      cudaStream_t st) {
-    k_triu_inv<<<(n + 7) / 8, 256, 0, st>>>(T, ldt, n, np, W, info);
+    if (n <= 128) k_triu_inv<4><<<(n + 7) / 8, 256, 0, st>>>(T, ldt, n, np, W, info);
+    else k_triu_inv<16><<<(n + 7) / 8, 256, 0, st>>>(T, ldt, n, np, W, info);
 }
 }  // namespace rpq

@@ -38,7 +38,7 @@ def test_host_only_entry_points(lib):
     with pytest.raises(lib.RpcholqrError):
         lib.rpcholqr_workspace_size(100, 0, 10)         # n < 1
     with pytest.raises(lib.RpcholqrError):
-        lib.rpcholqr_workspace_size(100, 129, 200)      # n above the built maximum
+        lib.rpcholqr_workspace_size(1000, 513, 600)      # n above the built maximum
     with pytest.raises(lib.RpcholqrError):
         lib.rpcholqr_workspace_size(100, 10, 5)         # s < n
     h = ctypes.c_void_p()
