@@ -44,7 +44,8 @@ def parse_args():
     ap.add_argument("--kappa", type=float, default=1e8)
     ap.add_argument("--seed", type=int, default=20240617)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-sample-rows", type=int, default=1 << 17)
+    ap.add_argument("--cpu-sample-rows", type=int, default=None,
+                    help="rows of the oracle's bounded sample (default 2^17 at n = 128, scaled by (128/n)^2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--inputs", choices=["gpu", "cpu"], default="gpu",
                     help="draw A with torch on the GPU (fast) or with the numpy recipe on the host")
@@ -56,11 +57,23 @@ def parse_args():
                     help="single: one m x n matrix per step; batch: the 512-matrix heterogeneous batch "
                          "(m log-uniform in [4096, 2^20], n in {8..128}, s=3n, kappa log-uniform in "
                          "[1, 1e14]) per step, one CUDA-graph replay")
+    ap.add_argument("--preset", choices=["small", "headline", "precision", "large"], default=None,
+                    help="workload shapes: small m=10000 n=50 kappa=1e8; headline m=2^20 n=128 kappa=1e8 "
+                         "(the default); precision m=2^22 n=256 kappa=1e12; large m=2^23 n=512 "
+                         "sigma to 1e-18")
     ap.add_argument("--count", type=int, default=512, help="matrices in the batch workload")
     ap.add_argument("--slots", type=int, default=16, help="concurrent slots the batch autotuner may use")
     ap.add_argument("--no-compare", action="store_true",
                     help="do not also time the other mode (reported as 'other_mode')")
-    return ap.parse_args()
+    args = ap.parse_args()
+    presets = {"small": (10000, 50, 1e8), "headline": (1 << 20, 128, 1e8),
+               "precision": (1 << 22, 256, 1e12), "large": (1 << 23, 512, 1e18)}
+    if args.preset:
+        args.m, args.n, args.kappa = presets[args.preset]
+    if args.cpu_sample_rows is None:
+        # about the same oracle work (rows x n^2) at every width
+        args.cpu_sample_rows = max(4096, min(args.m, (1 << 17) * 128 * 128 // (args.n * args.n)))
+    return args
 
 
 def alg_flops(m, n, s):
@@ -166,27 +179,39 @@ def barrier(dist):
 
 
 # ---- metrics on the device (after timing) -----------------------------------------------------------
-def gpu_metrics(A, Q, R):
-    """||Q^T Q - I||_2 (4096-row blocks, FP64) and ||A - QR||_2 / ||A||_2."""
+def gpu_metrics(A, Q, R, rows=1 << 18):
+    """||Q^T Q - I||_2 and ||A - QR||_2 / ||A||_2 in FP64 from n x n Gram matrices of row chunks (each
+    chunk's Gram summed over 4096-row blocks, chunks added in order); no m x n temporaries."""
     import torch
     m, n = Q.shape
     blk = 4096
-    full = (m // blk) * blk
-    G = torch.zeros((n, n), dtype=torch.float64, device=Q.device)
-    if full:
-        parts = torch.bmm(Q[:full].view(-1, blk, n).transpose(1, 2), Q[:full].view(-1, blk, n))
-        while parts.shape[0] > 1:
-            h = parts.shape[0] // 2
-            rest = parts[2 * h:]
-            parts = torch.cat([parts[:h] + parts[h:2 * h], rest], 0)
-        G += parts[0]
-    if full < m:
-        G += Q[full:].T @ Q[full:]
-    E = G - torch.eye(n, dtype=torch.float64, device=Q.device)
+
+    def gram(X):
+        k = X.shape[0]
+        full = (k // blk) * blk
+        G = torch.zeros((n, n), dtype=torch.float64, device=X.device)
+        if full:
+            parts = torch.bmm(X[:full].view(-1, blk, n).transpose(1, 2), X[:full].view(-1, blk, n))
+            while parts.shape[0] > 1:
+                h = parts.shape[0] // 2
+                parts = torch.cat([parts[:h] + parts[h:2 * h], parts[2 * h:]], 0)
+            G += parts[0]
+        if full < k:
+            G += X[full:].T @ X[full:]
+        return G
+
+    QQ = torch.zeros((n, n), dtype=torch.float64, device=Q.device)
+    DD = torch.zeros_like(QQ)
+    AA = torch.zeros_like(QQ)
+    for i in range(0, m, rows):
+        q, a = Q[i:i + rows], A[i:i + rows]
+        QQ += gram(q)
+        DD += gram(a - q @ R)
+        AA += gram(a)
+    E = QQ - torch.eye(n, dtype=torch.float64, device=Q.device)
     orth = float(torch.linalg.eigvalsh(0.5 * (E + E.T)).abs().max())
-    D = A - Q @ R
-    nd = float(torch.linalg.eigvalsh(D.T @ D).abs().max().sqrt())
-    na = float(torch.linalg.eigvalsh(A.T @ A).abs().max().sqrt())
+    nd = float(torch.linalg.eigvalsh(DD).abs().max().sqrt())
+    na = float(torch.linalg.eigvalsh(AA).abs().max().sqrt())
     return orth, nd / na
 
 
@@ -341,7 +366,20 @@ def run_ours(args, ws, rank, local):
     np_ = (n + 15) // 16 * 16
     src = os.path.join(ROOT, "paper_2406_11751_gb300", "csrc", "rowpass.cu")
     c = max(calls, 1)
-    if args.mode == "fp64":
+    if n > 128:
+        # wide panels: pass 1 is a group of launches (64-column FP64 row passes + off-diagonal block
+        # updates: FP64 mma in fp64 mode, split tensor-core products in split mode); its phases are
+        # timed together, so the roofline is reported for the group against the FP64 pipe
+        nb = (n + 63) // 64
+        kname = ("pass-1 kernel group: %d x k_rowpass<64,false> + %d x %s" %
+                 (nb, nb - 1, "k_gemm_sub_fp64" if args.mode == "fp64" else "k_ozaki_gemm<SUB>"))
+        launches_per_call = 2 * nb - 1 if args.mode == "fp64" else 3 * nb - 2
+        k_ms = (phases["pass1"] + phases["pass1_update"] + phases["pass1_solve2"]) / c
+        # FP64 flops of the group: all of A R_s^-1 (fp64) or its diagonal blocks only (split)
+        k_flops = float(m) * n * n if args.mode == "fp64" else float(m) * n * 64
+        k_bytes = 16.0 * m * n + 8.0 * m * 64 * nb * (nb - 1)   # A in, A1 out, A1 re-read by the updates
+        traffic = None
+    elif args.mode == "fp64":
         # dominant kernel: fused pass 1 (row solve by R_s + Gram partials), FP64 pipe
         kname = "k_rowpass<%d,true> (FP64 pass 1: A1 = A Rs^-1 + Gram partials)" % np_
         launches_per_call = 1
