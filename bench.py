@@ -50,9 +50,10 @@ def parse_args():
     ap.add_argument("--inputs", choices=["gpu", "cpu"], default="gpu",
                     help="draw A with torch on the GPU (fast) or with the numpy recipe on the host")
     ap.add_argument("--no-metrics", action="store_true", help="skip the orthogonality/residual check")
-    ap.add_argument("--mode", choices=["fp64", "split"], default="split",
+    ap.add_argument("--mode", choices=["fp64", "split", "fp32"], default="split",
                     help="split (default): FP64-accurate Ozaki-split BF16 tensor-core products for the "
-                         "well-conditioned steps; fp64: every step in FP64")
+                         "well-conditioned steps; fp64: every step in FP64; fp32: float data, FP32 "
+                         "passes (FP64 sketch QR and Cholesky)")
     ap.add_argument("--workload", choices=["single", "batch"], default="single",
                     help="single: one m x n matrix per step; batch: the 512-matrix heterogeneous batch "
                          "(m log-uniform in [4096, 2^20], n in {8..128}, s=3n, kappa log-uniform in "
@@ -70,6 +71,8 @@ def parse_args():
                "precision": (1 << 22, 256, 1e12), "large": (1 << 23, 512, 1e18)}
     if args.preset:
         args.m, args.n, args.kappa = presets[args.preset]
+        if args.preset == "precision" and args.mode == "fp32":
+            args.kappa = 1e5     # the single-precision variant of that workload
     if args.cpu_sample_rows is None:
         # about the same oracle work (rows x n^2) at every width
         args.cpu_sample_rows = max(4096, min(args.m, (1 << 17) * 128 * 128 // (args.n * args.n)))
@@ -302,12 +305,23 @@ def run_ours(args, ws, rank, local):
     info = torch.empty(2, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     fp64_peak = rq.rpcholqr_probe_fp64_mma(local, 4096)
+    if args.mode == "fp32":
+        A32 = A.float()
+        Q32 = torch.empty_like(A32)
+        R32 = torch.empty((n, n), dtype=torch.float32, device=dev)
+    modes = {"fp64": rq.FP64, "split": rq.SPLIT64, "fp32": rq.FP32}
+
+    def factor(plan, mode, seed):
+        if mode == "fp32":
+            rq.rpcholqr_factor_f32(plan, A32, s, seed, Q=Q32, R=R32, info=info, stream=stream)
+        else:
+            rq.rpcholqr_factor(plan, A, s, seed, Q=Q, R=R, info=info, stream=stream)
 
     def timed(mode, clocks):
         """W warm-up + K timed factor calls on a fresh plan of `mode`: (ms, phases, calls, launches, plan)."""
-        plan = rq.rpcholqr_plan_create(local, m, n, s, mode=rq.SPLIT64 if mode == "split" else rq.FP64)
+        plan = rq.rpcholqr_plan_create(local, m, n, s, mode=modes[mode])
         for w in range(W):
-            rq.rpcholqr_factor(plan, A, s, 1 + w, Q=Q, R=R, info=info, stream=stream)
+            factor(plan, mode, 1 + w)
         torch.cuda.synchronize(dev)
         st0 = info.cpu().tolist()
         if st0[0] != 0:
@@ -321,7 +335,7 @@ def run_ours(args, ws, rank, local):
             torch.cuda.synchronize(dev)
             e0.record(stream)
             for k in range(K):
-                rq.rpcholqr_factor(plan, A, s, 1 + k, Q=Q, R=R, info=info, stream=stream)
+                factor(plan, mode, 1 + k)
             e1.record(stream)
             torch.cuda.synchronize(dev)
             barrier(dist)
@@ -331,18 +345,43 @@ def run_ours(args, ws, rank, local):
 
     other = None
     if not args.no_compare:
-        omode = "fp64" if args.mode == "split" else "split"
+        omode = {"split": "fp64", "fp64": "split", "fp32": "split"}[args.mode]
         o_ms, o_ph, o_calls, _, o_plan, _ = timed(omode, False)
         o_plan.close()
         other = {"mode": omode, "value": ws * K / (o_ms / 1e3), "ms_per_step": o_ms / K,
                  "phases_ms_per_step": {k: v / max(o_calls, 1) for k, v in o_ph.items()}}
     t_ms_max, phases, calls, launches, plan, clk = timed(args.mode, True)
     st = info.cpu().tolist()
-    orth, res = (None, None) if args.no_metrics else gpu_metrics(A, Q, R)
+    if args.no_metrics:
+        orth, res = None, None
+    elif args.mode == "fp32":
+        orth, res = gpu_metrics(A32.double(), Q32.double(), R32.double())
+    else:
+        orth, res = gpu_metrics(A, Q, R)
 
     # end to end through the host-buffer C-ABI call (H2D of A, D2H of Q, R, info inside the region)
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and args.mode == "fp32":
+        # through the public Python API: pinned host A -> device, factor, Q, R, info -> pinned host
+        Ah = A32.cpu().pin_memory()
+        Qh = torch.empty((m, n), dtype=torch.float32).pin_memory()
+        Rh = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        ih = torch.empty(2, dtype=torch.int32).pin_memory()
+        Ad = torch.empty_like(A32)
+        barrier(dist)
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            Ad.copy_(Ah, non_blocking=True)
+            rq.rpcholqr_factor_f32(plan, Ad, s, 1 + k, Q=Q32, R=R32, info=info, stream=stream)
+            Qh.copy_(Q32, non_blocking=True)
+            Rh.copy_(R32, non_blocking=True)
+            ih.copy_(info, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        barrier(dist)
+        e2e = {"value": ws * args.e2e_steps / e2e_s, "unit": "matrices/s",
+               "h2d_bytes_per_step": 4 * m * n, "d2h_bytes_per_step": 4 * m * n + 4 * n * n + 8}
+    elif args.e2e_steps > 0:
         Ah = A.cpu().pin_memory()
         Qh = torch.empty((m, n), dtype=torch.float64).pin_memory()
         Rh = torch.empty((n, n), dtype=torch.float64).pin_memory()
@@ -366,7 +405,15 @@ def run_ours(args, ws, rank, local):
     np_ = (n + 15) // 16 * 16
     src = os.path.join(ROOT, "paper_2406_11751_gb300", "csrc", "rowpass.cu")
     c = max(calls, 1)
-    if n > 128:
+    fp32_peak = 152 * 128 * 2 * 2.07e9   # FP32 FMA lanes x 2 flop x max SM clock
+    if args.mode == "fp32":
+        kname = "k_rowsolve_f32 (FP32 pass 1: A1 = A Rs^-1, one row per thread)"
+        launches_per_call = 1
+        k_ms = phases["pass1"] / c
+        k_flops = float(m) * n * n          # n^2/2 FMAs per row
+        k_bytes = 8.0 * m * n               # read A, write A1 (float)
+        traffic = None
+    elif n > 128:
         # wide panels: pass 1 is a group of launches (64-column FP64 row passes + off-diagonal block
         # updates: FP64 mma in fp64 mode, split tensor-core products in split mode); its phases are
         # timed together, so the roofline is reported for the group against the FP64 pipe
@@ -398,7 +445,7 @@ def run_ours(args, ws, rank, local):
         k_bytes = 16.0 * m * (n1 + n2) / launches_per_call
         traffic = traffic_from_profiles(f"k_rowpass<{min(np_, 64)},false>", src)
     achieved = k_flops / (k_ms / 1e3) / 1e12
-    peak = fp64_peak / 1e12
+    peak = (fp32_peak if args.mode == "fp32" else fp64_peak) / 1e12
 
     cpu = None
     if not args.no_cpu_baseline and N == 1:
@@ -411,23 +458,27 @@ def run_ours(args, ws, rank, local):
     out = {
         "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": N, "steps": K, "warmup": W,
         "ms_per_step": t_ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.mode == "fp64" else "f64+bf16",
+        "dtype": {"fp64": "f64", "split": "f64+bf16", "fp32": "f32+f64"}[args.mode],
         "data": "synthetic (A = U diag(sigma) V^T, Haar U/V from torch, sigma log-spaced)",
         "config": {"workload": f"rpCholesky-QR {args.mode.upper()} m={m} n={n} s={s} kappa={args.kappa:g}", "m": m,
                    "n": n, "s": s, "kappa": args.kappa, "mode": args.mode,
                    "l2": f"inputs larger than L2 (A = {8 * m * n / 1e9:.2f} GB > 129 MB), no flush"},
         "effective_tflops": flops * value / 1e12,
-        "orth": orth, "residual": res, "gate_orth_le_1e-13": None if orth is None else bool(orth <= 1e-13), "status": st[0],
+        "orth": orth, "residual": res, "gate_orth_le_1e-13": None if orth is None else bool(orth <= 1e-13),
+        "gate_orth_le_1e-5": None if orth is None else bool(orth <= 1e-5), "status": st[0],
         "phases_ms_per_step": {k: v / max(calls, 1) for k, v in phases.items()},
         "roofline": {"kernel": kname, "bound": "alu",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_flops": k_flops,
                      "algorithmic_bytes": k_bytes, "ms_per_launch": k_ms,
                      "launches_per_step": launches_per_call,
-                     "peak_source": "FP64 pipe (DFMA and FP64 mma.sync share it): in-run mma.sync "
-                                    "m16n8k16 probe; MEASURED_PEAKS.json has no FP64 figure "
-                                    "(unit count x clock: 152 SM x 4 x 32 lanes / 64 cycles x 2 flop "
-                                    "x 2.07 GHz = 1.26 TFLOP/s)"},
+                     "peak_source": ("FP32 FMA pipe from unit counts and clock: 152 SM x 128 lanes x 2 flop x "
+                                     "2.07 GHz = 80.5 TFLOP/s (MEASURED_PEAKS.json has no FP32 figure)"
+                                     if args.mode == "fp32" else
+                                     "FP64 pipe (DFMA and FP64 mma.sync share it): in-run mma.sync "
+                                     "m16n8k16 probe; MEASURED_PEAKS.json has no FP64 figure "
+                                     "(unit count x clock: 152 SM x 4 x 32 lanes / 64 cycles x 2 flop "
+                                     "x 2.07 GHz = 1.26 TFLOP/s)")},
         "other_mode": other,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -515,7 +566,7 @@ def run_batch(args, ws, rank, local):
     out = {
         "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.mode == "fp64" else "f64+bf16",
+        "dtype": {"fp64": "f64", "split": "f64+bf16", "fp32": "f32+f64"}[args.mode],
         "data": "synthetic (A = U diag(sigma) V^T per manifest entry, Haar U/V from torch)",
         "config": {"workload": f"rpCholesky-QR batch of {count} (m log-uniform 4096..2^20, n in "
                                f"{{8,16,32,64,128}}, s=3n, kappa log-uniform 1..1e14), {args.mode.upper()}, "

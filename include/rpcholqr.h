@@ -62,12 +62,17 @@ typedef enum {
 
 typedef enum {
     RPCHOLQR_FP64 = 0,   /* every step in FP64 (FP64 tensor-core mma.sync m16n8k16 + DFMA)        */
-    RPCHOLQR_SPLIT64 = 1 /* FP64-accurate split precision: sketch QR, Cholesky and the diagonal
+    RPCHOLQR_SPLIT64 = 1, /* FP64-accurate split precision: sketch QR, Cholesky and the diagonal
                             blocks of the row solves in FP64; the Gram matrix, the off-diagonal
                             block update of the row solve (n > 64) and Q = A1 R1^{-1} (explicit
                             inverse of the well-conditioned R1) as Ozaki-split BF16 tensor-core
                             (tcgen05) products with exact FP32 group sums and int64 combination.
                             Needs an extra max_m x n FP64 plan buffer for A1.                      */
+    RPCHOLQR_FP32 = 2    /* single precision for FP32 data (A, Q, R float; rpcholqr_factor_f32 only):
+                            the sample is widened to FP64, R_s (Householder) and R1 (Cholesky of
+                            the Gram matrix, summed in FP64 from FP32 partials) are FP64; both
+                            m-row passes run in FP32 on the FMA pipe.  Accuracy is that of FP32
+                            (||Q^T Q - I|| of order 1e-6 for well-sampled A up to kappa ~ 1e5). */
 } rpcholqr_mode;
 
 /* Largest n a plan accepts.  Up to 128 columns the row passes keep a whole row panel in shared
@@ -98,11 +103,22 @@ rpcholqr_status rpcholqr_workspace_size(int64_t max_m, int32_t max_n, int32_t ma
  *   Q    device, m x n row-major, ldq >= n; must not overlap A.  Holds A_1 between the passes.
  *   R    device, n x n row-major upper triangular (strict lower part set to 0).
  *   info device int32[2], see above; written by every call.
- * Requires 1 <= n <= plan max_n, s <= plan max_s, m <= plan max_m, m >= s >= n.
+ * Requires 1 <= n <= plan max_n, s <= plan max_s, m <= plan max_m, m >= s >= n, and an FP64 or
+ * SPLIT64 plan (ERR_ARG for an FP32 plan).
  * On a non-zero info status the contents of Q and R are unspecified. */
 rpcholqr_status rpcholqr_factor(rpcholqr_plan plan, const double* A, int64_t m, int32_t n,
                                 int64_t lda, int32_t s, uint64_t seed, double* Q, int64_t ldq,
                                 double* R, int32_t* info, void* stream);
+
+/* FP32 factorisation (the FP32 mode; no counterpart in the paper, which works in double precision):
+ * the same steps as rpcholqr_factor with A (m x n, lda), Q (m x n, ldq) and R (n x n, dense
+ * row-major, ld n) as device float arrays.  The plan must be an RPCHOLQR_FP32 plan (ERR_ARG
+ * otherwise).  Q receives A1 = A R_s^{-1} during the call and Q at its end.  info as in
+ * rpcholqr_factor; an R_s or R1 diagonal that is not a normal float sets SINGULAR_SKETCH or NOT_SPD
+ * with the pivot. */
+rpcholqr_status rpcholqr_factor_f32(rpcholqr_plan plan, const float* A, int64_t m, int32_t n, int64_t lda,
+                                    int32_t s, uint64_t seed, float* Q, int64_t ldq, float* R, int32_t* info,
+                                    void* stream);
 
 /* End-to-end variant of rpcholqr_factor on HOST buffers: copies A (host, m x n, lda) to a device
  * staging buffer the plan allocates on first use, factors it, copies Q (host, ldq) and R (host)

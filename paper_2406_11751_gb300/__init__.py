@@ -21,7 +21,7 @@ __all__ = [
     "rpcholqr_plan_enable_timing", "rpcholqr_plan_collect_timing", "PHASES", "rpcholqr_ozaki_gemm",
     "rpcholqr_ozaki_gram", "SPLIT64", "rpcholqr_cholqr", "rpcholqr_cholqr2", "Batch",
     "rpcholqr_batch_create", "rpcholqr_batch_destroy", "rpcholqr_factor_batched", "rpcholqr_batch_capture",
-    "rpcholqr_batch_replay", "rpcholqr_batch_autotune",
+    "rpcholqr_batch_replay", "rpcholqr_batch_autotune", "FP32", "rpcholqr_factor_f32",
 ]
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NONFINITE", 3: "ERR_SINGULAR_SKETCH", 4: "ERR_NOT_SPD",
@@ -29,6 +29,7 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NONFINITE", 3: "ERR_SINGULAR_SKETCH", 4
 OK, ERR_ARG, ERR_NONFINITE, ERR_SINGULAR_SKETCH, ERR_NOT_SPD = 0, 1, 2, 3, 4
 FP64 = 0
 SPLIT64 = 1
+FP32 = 2
 MAX_N = 512
 
 EXPORTED_SYMBOLS = (
@@ -38,7 +39,7 @@ EXPORTED_SYMBOLS = (
     "rpcholqr_probe_fp64_mma", "rpcholqr_status_string", "rpcholqr_plan_enable_timing",
     "rpcholqr_plan_collect_timing", "rpcholqr_ozaki_gemm", "rpcholqr_ozaki_gram", "rpcholqr_cholqr",
     "rpcholqr_cholqr2", "rpcholqr_batch_create", "rpcholqr_batch_destroy", "rpcholqr_factor_batched",
-    "rpcholqr_batch_capture", "rpcholqr_batch_replay", "rpcholqr_batch_autotune",
+    "rpcholqr_batch_capture", "rpcholqr_batch_replay", "rpcholqr_batch_autotune", "rpcholqr_factor_f32",
 )
 PHASES = ("sample", "sketch_qr", "prep_rs", "pass1", "pass1_update", "pass1_solve2", "gram_reduce",
           "cholesky", "prep_r1", "pass2", "recover_r")
@@ -73,6 +74,7 @@ def load_library():
         "rpcholqr_workspace_size": [I64, I32, I32, ctypes.POINTER(ctypes.c_size_t)],
         "rpcholqr_factor": [P, P, I64, I32, I64, I32, U64, P, I64, P, P, P],
         "rpcholqr_factor_host": [P, P, I64, I32, I64, I32, U64, P, I64, P, P, P],
+        "rpcholqr_factor_f32": [P, P, I64, I32, I64, I32, U64, P, I64, P, P, P],
         "rpcholqr_sample_indices": [U64, U64, I64, I32, P, P],
         "rpcholqr_sketch_r": [P, P, I64, I32, I64, I32, U64, P, P, P],
         "rpcholqr_precondition_gram": [P, P, I64, I32, I64, P, P, I64, P, P, P],
@@ -199,6 +201,24 @@ def rpcholqr_factor(plan: Plan, A, s: int, seed: int, Q=None, R=None, info=None,
     _mat(R, "R")
     info = _info(info, A.device)
     _check("rpcholqr_factor", load_library().rpcholqr_factor(
+        plan.handle, _ptr(A), m, n, A.stride(0), s, seed, _ptr(Q), Q.stride(0), _ptr(R), _ptr(info),
+        _stream(stream, A.device)))
+    return Q, R, info
+
+
+def rpcholqr_factor_f32(plan: Plan, A, s: int, seed: int, Q=None, R=None, info=None, stream=None):
+    """(Q, R, info) of the FP32 mode (float32 A, Q, R; an FP32 plan); info as in rpcholqr_factor."""
+    torch = _torch()
+    _mat(A, "A", torch.float32)
+    m, n = A.shape
+    if Q is None:
+        Q = torch.empty((m, n), dtype=torch.float32, device=A.device)
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float32, device=A.device)
+    _mat(Q, "Q", torch.float32)
+    _mat(R, "R", torch.float32)
+    info = _info(info, A.device)
+    _check("rpcholqr_factor_f32", load_library().rpcholqr_factor_f32(
         plan.handle, _ptr(A), m, n, A.stride(0), s, seed, _ptr(Q), Q.stride(0), _ptr(R), _ptr(info),
         _stream(stream, A.device)))
     return Q, R, info

@@ -59,6 +59,18 @@ cudaError_t launch_gemm_sub_fp64(const double* X, int64_t ldx, const double* Y, 
                                  const int32_t* info, int grid, cudaStream_t st);
 cudaError_t launch_syrk_fp64(const double* X, int64_t ldx, int64_t m, int n, int np, int ranges, double* gpart,
                              const int32_t* info, cudaStream_t st);
+void launch_sample_gather_f32(const float* A, int64_t m, int32_t n, int64_t lda, int32_t s, uint64_t seed,
+                              uint64_t stream_id, double scale, double* As, int64_t lds, int32_t np,
+                              int64_t* idx_out, int32_t* info, cudaStream_t st);
+int f32_pad(int n);
+void launch_prep_f32(const double* T, int64_t ldt, int n, float* T32, float* rinv32, int fail_status,
+                     int32_t* info, cudaStream_t st);
+cudaError_t launch_rowsolve_f32(const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t m, int n,
+                                const float* T32, const float* rinv32, int32_t* info, bool check_finite,
+                                cudaStream_t st);
+int launch_syrk_f32(const float* X, int64_t ldx, int64_t m, int n, int max_ranges, double* gpart,
+                    const int32_t* info, cudaStream_t st);
+void launch_f64_to_f32(const double* src, int64_t lds, int n, float* dst, int64_t ldd, cudaStream_t st);
 }  // namespace rpq
 
 using namespace rpq;
@@ -100,6 +112,9 @@ struct rpcholqr_plan_s {
     int32_t* yexp = nullptr;    // np
     uint8_t* yblocks = nullptr; // Ozaki column slices (K, N <= np)
     double* W = nullptr;        // np x np
+    // FP32 buffers (separate allocation)
+    float* T32 = nullptr;       // pad32(max_n)^2: R_s or R1 in FP32, identity-padded
+    float* rinv32 = nullptr;    // pad32(max_n)
 };
 
 namespace {
@@ -226,7 +241,7 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
     if (!plan) return RPCHOLQR_ERR_ARG;
     *plan = nullptr;
     if (max_n < 1 || max_n > RPCHOLQR_MAX_N || max_s < max_n || max_m < max_s) return RPCHOLQR_ERR_ARG;
-    if (mode != RPCHOLQR_FP64 && mode != RPCHOLQR_SPLIT64) return RPCHOLQR_ERR_UNSUPPORTED;
+    if (mode != RPCHOLQR_FP64 && mode != RPCHOLQR_SPLIT64 && mode != RPCHOLQR_FP32) return RPCHOLQR_ERR_UNSUPPORTED;
     if (householder_smem_bytes(max_s, max_n) > 200 * 1024) return RPCHOLQR_ERR_UNSUPPORTED;
     DeviceGuard guard(device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
@@ -239,7 +254,9 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
     p->max_s = max_s;
     p->np = pad_np(max_n);
     p->grid = default_grid(device);
-    const WsLayout L = ws_layout(max_n, max_s, p->grid);
+    // the FP32 Gram works on 64 x 64 tiles: size the shared FP64 buffers for max_n rounded up to 64
+    const int32_t ws_n = mode == RPCHOLQR_FP32 ? (max_n + 63) / 64 * 64 : max_n;
+    const WsLayout L = ws_layout(ws_n, max_s, p->grid);
     if (cudaMalloc(&p->ws, L.total) != cudaSuccess) {
         cudaGetLastError();
         delete p;
@@ -281,6 +298,21 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
         p->yblocks = reinterpret_cast<uint8_t*>(c + oB);
         p->W = reinterpret_cast<double*>(c + oW);
         p->ws_bytes += off;
+    }
+    if (mode == RPCHOLQR_FP32) {
+        const size_t n32 = static_cast<size_t>(f32_pad(max_n));
+        const size_t oT = 0, oR = align256(sizeof(float) * n32 * n32);
+        const size_t total = oR + sizeof(float) * n32;
+        if (cudaMalloc(&p->split_ws, total) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(p->ws);
+            delete p;
+            return RPCHOLQR_ERR_NOMEM;
+        }
+        char* c = static_cast<char*>(p->split_ws);
+        p->T32 = reinterpret_cast<float*>(c + oT);
+        p->rinv32 = reinterpret_cast<float*>(c + oR);
+        p->ws_bytes += total;
     }
     *plan = p;
     return RPCHOLQR_OK;
@@ -552,7 +584,7 @@ static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m,
 rpcholqr_status rpcholqr_factor(rpcholqr_plan p, const double* A, int64_t m, int32_t n, int64_t lda,
                                 int32_t s, uint64_t seed, double* Q, int64_t ldq, double* R,
                                 int32_t* info, void* stream) {
-    if (!p || !A || !Q || !R || !info) return RPCHOLQR_ERR_ARG;
+    if (!p || !A || !Q || !R || !info || p->mode == RPCHOLQR_FP32) return RPCHOLQR_ERR_ARG;
     if (!shape_ok(p, m, n, s) || lda < n || ldq < n) return RPCHOLQR_ERR_ARG;
     DeviceGuard guard(p->device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
@@ -573,6 +605,60 @@ rpcholqr_status rpcholqr_factor(rpcholqr_plan p, const double* A, int64_t m, int
     pm.mark(RPCHOLQR_PHASE_RECOVER_R);
     launch_triu_mul(p->R1, np, p->Rs, np, n, R, n, info, st);
     ++p->launches;
+    pm.mark(RPCHOLQR_NUM_PHASES);
+    return check_launch();
+}
+
+rpcholqr_status rpcholqr_factor_f32(rpcholqr_plan p, const float* A, int64_t m, int32_t n, int64_t lda,
+                                    int32_t s, uint64_t seed, float* Q, int64_t ldq, float* R, int32_t* info,
+                                    void* stream) {
+    if (!p || !A || !Q || !R || !info || p->mode != RPCHOLQR_FP32) return RPCHOLQR_ERR_ARG;
+    if (!shape_ok(p, m, n, s) || lda < n || ldq < n) return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int np = pad_np(n);
+    const PhaseMarks pm(p, st);
+    rpcholqr_status rc = reset_info(info, st);
+    if (rc != RPCHOLQR_OK) return rc;
+    // sample (widened to FP64) and the FP64 Householder R_s
+    pm.mark(RPCHOLQR_PHASE_SAMPLE);
+    const double scale = std::sqrt(static_cast<double>(m) / static_cast<double>(s));
+    launch_sample_gather_f32(A, m, n, lda, s, seed, 0, scale, p->As, s, np, nullptr, info, st);
+    ++p->launches;
+    pm.mark(RPCHOLQR_PHASE_SKETCH_QR);
+    if (launch_householder(p->As, s, s, n, np, p->Rs, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    ++p->launches;
+    // pass 1 in FP32: A1 = A R_s^{-1} into Q, then the Gram partials and their FP64 sum
+    pm.mark(RPCHOLQR_PHASE_PREP_RS);
+    launch_prep_f32(p->Rs, np, n, p->T32, p->rinv32, RPCHOLQR_ERR_SINGULAR_SKETCH, info, st);
+    ++p->launches;
+    pm.mark(RPCHOLQR_PHASE_PASS1);
+    if (launch_rowsolve_f32(A, lda, Q, ldq, m, n, p->T32, p->rinv32, info, true, st) != cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    ++p->launches;
+    pm.mark(RPCHOLQR_PHASE_PASS1_UPDATE);
+    pm.mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
+    pm.mark(RPCHOLQR_PHASE_GRAM_REDUCE);
+    const int np64 = (n + 63) / 64 * 64;
+    const int ranges = launch_syrk_f32(Q, ldq, m, n, p->grid, p->gpart, info, st);
+    launch_gram_reduce(p->gpart, ranges, np64, n, p->G, np, info, st);
+    p->launches += 2;
+    // FP64 Cholesky, pass 2 in FP32 (in place), R = R1 R_s in FP64 rounded to FP32
+    pm.mark(RPCHOLQR_PHASE_CHOLESKY);
+    if (launch_cholesky(p->G, np, n, np, p->R1, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    ++p->launches;
+    pm.mark(RPCHOLQR_PHASE_PREP_R1);
+    launch_prep_f32(p->R1, np, n, p->T32, p->rinv32, RPCHOLQR_ERR_NOT_SPD, info, st);
+    ++p->launches;
+    pm.mark(RPCHOLQR_PHASE_PASS2);
+    if (launch_rowsolve_f32(Q, ldq, Q, ldq, m, n, p->T32, p->rinv32, info, false, st) != cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    ++p->launches;
+    pm.mark(RPCHOLQR_PHASE_RECOVER_R);
+    launch_triu_mul(p->R1, np, p->Rs, np, n, p->frag_s, n, info, st);
+    launch_f64_to_f32(p->frag_s, n, n, R, n, st);
+    p->launches += 2;
     pm.mark(RPCHOLQR_NUM_PHASES);
     return check_launch();
 }

@@ -81,6 +81,7 @@ rpcholqr_status rpcholqr_batch_create(rpcholqr_batch* batch, int device, rpcholq
                                       int32_t max_n, int32_t max_s, int32_t slots) {
     if (!batch || slots < 1 || slots > 64) return RPCHOLQR_ERR_ARG;
     *batch = nullptr;
+    if (mode == RPCHOLQR_FP32) return RPCHOLQR_ERR_UNSUPPORTED;   // batches are FP64 matrices
     BatchDevice guard(device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
     auto* b = new (std::nothrow) rpcholqr_batch_s();

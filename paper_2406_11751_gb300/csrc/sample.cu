@@ -42,7 +42,8 @@ __global__ void k_sample_indices(uint64_t seed, uint64_t stream_id, int64_t m, i
 
 // One CTA per sampled row j: As (column-major, ld = lds, np columns) gets sqrt(m/s) * A[idx_j, :]
 // in columns < n and 0 in the padding columns.  A non-finite sampled entry sets NONFINITE.
-__global__ void k_sample_gather(const double* __restrict__ A, int64_t m, int32_t n, int64_t lda,
+template <typename TA>
+__global__ void k_sample_gather(const TA* __restrict__ A, int64_t m, int32_t n, int64_t lda,
                                 int32_t s, uint64_t seed, uint64_t stream_id, double scale,
                                 double* __restrict__ As, int64_t lds, int32_t np,
                                 int64_t* __restrict__ idx_out, int32_t* info) {
@@ -54,12 +55,12 @@ __global__ void k_sample_gather(const double* __restrict__ A, int64_t m, int32_t
         if (idx_out) idx_out[j] = r;
     }
     __syncthreads();
-    const double* src = A + row_s * lda;
+    const TA* src = A + row_s * lda;
     bool bad = false;
     for (int c = threadIdx.x; c < np; c += blockDim.x) {
         double v = 0.0;
         if (c < n) {
-            const double a = src[c];
+            const double a = static_cast<double>(src[c]);
             bad |= !isfinite(a);
             v = scale * a;
         }
@@ -76,8 +77,16 @@ void launch_sample_indices(uint64_t seed, uint64_t stream_id, int64_t m, int32_t
 void launch_sample_gather(const double* A, int64_t m, int32_t n, int64_t lda, int32_t s, uint64_t seed,
                           uint64_t stream_id, double scale, double* As, int64_t lds, int32_t np,
                           int64_t* idx_out, int32_t* info, cudaStream_t st) {
-    k_sample_gather<<<s, 128, 0, st>>>(A, m, n, lda, s, seed, stream_id, scale, As, lds, np, idx_out,
-                                       info);
+    k_sample_gather<double><<<s, 128, 0, st>>>(A, m, n, lda, s, seed, stream_id, scale, As, lds, np,
+                                               idx_out, info);
+}
+
+// FP32 input (the FP32 mode): the sampled rows are widened to FP64 before the scale.
+void launch_sample_gather_f32(const float* A, int64_t m, int32_t n, int64_t lda, int32_t s, uint64_t seed,
+                              uint64_t stream_id, double scale, double* As, int64_t lds, int32_t np,
+                              int64_t* idx_out, int32_t* info, cudaStream_t st) {
+    k_sample_gather<float><<<s, 128, 0, st>>>(A, m, n, lda, s, seed, stream_id, scale, As, lds, np,
+                                              idx_out, info);
 }
 
 }  // namespace rpq
