@@ -212,6 +212,32 @@ rpcholqr_status rpcholqr_precondition_gram_noalloc(const double* A, int64_t m, i
                                                    const double* Rs, double* A1, int64_t ld1,
                                                    double* G, int32_t* info, void* stream);
 
+/* ---- row-sharded factorisation (A split by contiguous row blocks over processes) ----
+ * Algorithm alg_2 with A partitioned by rows: both passes and the Gram partials are row-local, and
+ * the processes exchange only the s x n sample (before the sketch QR) and the n x n Gram partials
+ * (before the Cholesky factorisation).  The exchanges themselves belong to the caller's
+ * communication layer; these calls are the non-local steps around them.  The local passes are
+ * rpcholqr_precondition_gram, rpcholqr_cholesky, rpcholqr_solve_rows and rpcholqr_triu_mul. */
+
+/* The rows of the global sample owned by this block: As (device, s x n row-major, ld ld_as) row j =
+ * sqrt(m/s) A[idx_j - row_offset, :] when row_offset <= idx_j < row_offset + m_local (idx_j from
+ * the Philox stream of the whole m x n matrix, stream_id 0), else zeros.  Summing the blocks'
+ * As over all processes gives exactly the sample rpcholqr_factor draws.  A_local: device, m_local x n
+ * (lda), may be NULL when m_local = 0.  info: device int32[2] (NONFINITE for a non-finite owned
+ * sample entry). */
+rpcholqr_status rpcholqr_gather_owned_rows(const double* A_local, int64_t m_local, int32_t n, int64_t lda,
+                                           int64_t row_offset, int64_t m, int32_t s, uint64_t seed, double* As,
+                                           int64_t ld_as, int32_t* info, void* stream);
+
+/* R_s of a given s x n sample (device, row-major, ld ld_as): the Householder step of
+ * rpcholqr_sketch_r on an already gathered and scaled sample.  Rs: device n x n. */
+rpcholqr_status rpcholqr_sketch_r_from_sample(rpcholqr_plan plan, const double* As, int32_t s, int32_t n,
+                                              int64_t ld_as, double* Rs, int32_t* info, void* stream);
+
+/* G (device, n x n) = sum of parts[k] (device, nparts x n x n, contiguous) in the order k = 0, 1, ...
+ * (the same bits for the same parts on every process). */
+rpcholqr_status rpcholqr_sum_partials(const double* parts, int32_t nparts, int32_t n, double* G, void* stream);
+
 /* ---- batches of independent matrices ----
  * A batch object owns `slots` independent plans (each with its own workspace and CUDA stream).  The
  * matrices of a batch call are dealt round-robin to the slots, so small matrices -- whose row passes

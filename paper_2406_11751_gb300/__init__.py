@@ -22,6 +22,7 @@ __all__ = [
     "rpcholqr_ozaki_gram", "SPLIT64", "rpcholqr_cholqr", "rpcholqr_cholqr2", "Batch",
     "rpcholqr_batch_create", "rpcholqr_batch_destroy", "rpcholqr_factor_batched", "rpcholqr_batch_capture",
     "rpcholqr_batch_replay", "rpcholqr_batch_autotune", "FP32", "rpcholqr_factor_f32",
+    "rpcholqr_gather_owned_rows", "rpcholqr_sketch_r_from_sample", "rpcholqr_sum_partials",
 ]
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NONFINITE", 3: "ERR_SINGULAR_SKETCH", 4: "ERR_NOT_SPD",
@@ -40,6 +41,7 @@ EXPORTED_SYMBOLS = (
     "rpcholqr_plan_collect_timing", "rpcholqr_ozaki_gemm", "rpcholqr_ozaki_gram", "rpcholqr_cholqr",
     "rpcholqr_cholqr2", "rpcholqr_batch_create", "rpcholqr_batch_destroy", "rpcholqr_factor_batched",
     "rpcholqr_batch_capture", "rpcholqr_batch_replay", "rpcholqr_batch_autotune", "rpcholqr_factor_f32",
+    "rpcholqr_gather_owned_rows", "rpcholqr_sketch_r_from_sample", "rpcholqr_sum_partials",
 )
 PHASES = ("sample", "sketch_qr", "prep_rs", "pass1", "pass1_update", "pass1_solve2", "gram_reduce",
           "cholesky", "prep_r1", "pass2", "recover_r")
@@ -75,6 +77,9 @@ def load_library():
         "rpcholqr_factor": [P, P, I64, I32, I64, I32, U64, P, I64, P, P, P],
         "rpcholqr_factor_host": [P, P, I64, I32, I64, I32, U64, P, I64, P, P, P],
         "rpcholqr_factor_f32": [P, P, I64, I32, I64, I32, U64, P, I64, P, P, P],
+        "rpcholqr_gather_owned_rows": [P, I64, I32, I64, I64, I64, I32, U64, P, I64, P, P],
+        "rpcholqr_sketch_r_from_sample": [P, P, I32, I32, I64, P, P, P],
+        "rpcholqr_sum_partials": [P, I32, I32, P, P],
         "rpcholqr_sample_indices": [U64, U64, I64, I32, P, P],
         "rpcholqr_sketch_r": [P, P, I64, I32, I64, I32, U64, P, P, P],
         "rpcholqr_precondition_gram": [P, P, I64, I32, I64, P, P, I64, P, P, P],
@@ -222,6 +227,53 @@ def rpcholqr_factor_f32(plan: Plan, A, s: int, seed: int, Q=None, R=None, info=N
         plan.handle, _ptr(A), m, n, A.stride(0), s, seed, _ptr(Q), Q.stride(0), _ptr(R), _ptr(info),
         _stream(stream, A.device)))
     return Q, R, info
+
+
+def rpcholqr_gather_owned_rows(A_local, row_offset: int, m: int, s: int, seed: int, As=None, info=None,
+                               stream=None, device=None):
+    """The rows of the global s-row sample owned by the row block A_local (m_local x n, global rows
+    row_offset ..), zeros elsewhere: (As (s x n), info)."""
+    torch = _torch()
+    _mat(A_local, "A_local")
+    m_local, n = A_local.shape
+    dev = A_local.device
+    if As is None:
+        As = torch.empty((s, n), dtype=torch.float64, device=dev)
+    _mat(As, "As")
+    info = _info(info, dev)
+    _check("rpcholqr_gather_owned_rows", load_library().rpcholqr_gather_owned_rows(
+        _ptr(A_local) if m_local else None, m_local, n, A_local.stride(0) if m_local else n, row_offset, m, s,
+        seed, _ptr(As), As.stride(0), _ptr(info), _stream(stream, dev)))
+    return As, info
+
+
+def rpcholqr_sketch_r_from_sample(plan: Plan, As, Rs=None, info=None, stream=None):
+    """R_s (n x n) of a gathered s x n sample: (Rs, info)."""
+    torch = _torch()
+    _mat(As, "As")
+    s, n = As.shape
+    if Rs is None:
+        Rs = torch.empty((n, n), dtype=torch.float64, device=As.device)
+    _mat(Rs, "Rs")
+    info = _info(info, As.device)
+    _check("rpcholqr_sketch_r_from_sample", load_library().rpcholqr_sketch_r_from_sample(
+        plan.handle, _ptr(As), s, n, As.stride(0), _ptr(Rs), _ptr(info), _stream(stream, As.device)))
+    return Rs, info
+
+
+def rpcholqr_sum_partials(parts, G=None, stream=None):
+    """G = parts[0] + parts[1] + ... (in that order) for a contiguous (k, n, n) tensor."""
+    torch = _torch()
+    if not isinstance(parts, torch.Tensor) or not parts.is_cuda or parts.dim() != 3 or not parts.is_contiguous() \
+            or parts.dtype != torch.float64:
+        raise TypeError("parts must be a contiguous float64 CUDA tensor of shape (k, n, n)")
+    k, n, _ = parts.shape
+    if G is None:
+        G = torch.empty((n, n), dtype=torch.float64, device=parts.device)
+    _mat(G, "G")
+    _check("rpcholqr_sum_partials", load_library().rpcholqr_sum_partials(
+        _ptr(parts), k, n, _ptr(G), _stream(stream, parts.device)))
+    return G
 
 
 def rpcholqr_factor_host(plan: Plan, A, s: int, seed: int, Q=None, R=None, stream=None):

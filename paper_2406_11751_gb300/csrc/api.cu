@@ -71,6 +71,12 @@ cudaError_t launch_rowsolve_f32(const float* X, int64_t ldx, float* Y, int64_t l
 int launch_syrk_f32(const float* X, int64_t ldx, int64_t m, int n, int max_ranges, double* gpart,
                     const int32_t* info, cudaStream_t st);
 void launch_f64_to_f32(const double* src, int64_t lds, int n, float* dst, int64_t ldd, cudaStream_t st);
+void launch_gather_owned_rows(const double* A, int64_t m_local, int32_t n, int64_t lda, int64_t row_offset,
+                              int64_t m, int32_t s, uint64_t seed, uint64_t stream_id, double scale, double* As,
+                              int64_t ld_as, int32_t* info, cudaStream_t st);
+void launch_sample_to_colmajor(const double* src, int64_t ld_src, int32_t s, int32_t n, int32_t np, double* dst,
+                               int64_t lds, cudaStream_t st);
+void launch_sum_parts(const double* parts, int32_t nparts, int32_t n, double* G, cudaStream_t st);
 }  // namespace rpq
 
 using namespace rpq;
@@ -890,6 +896,42 @@ rpcholqr_status rpcholqr_cholqr2(rpcholqr_plan p, const double* A, int64_t m, in
     const int np = pad_np(n);
     launch_triu_mul(p->R1, np, p->Rs, np, n, R, n, info, st);
     ++p->launches;
+    return check_launch();
+}
+
+rpcholqr_status rpcholqr_gather_owned_rows(const double* A_local, int64_t m_local, int32_t n, int64_t lda,
+                                           int64_t row_offset, int64_t m, int32_t s, uint64_t seed, double* As,
+                                           int64_t ld_as, int32_t* info, void* stream) {
+    if (!As || !info || n < 1 || s < 1 || m < 1 || m_local < 0 || row_offset < 0 || row_offset > m - m_local ||
+        ld_as < n || (m_local > 0 && (!A_local || lda < n)))
+        return RPCHOLQR_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rpcholqr_status rc = reset_info(info, st);
+    if (rc != RPCHOLQR_OK) return rc;
+    const double scale = std::sqrt(static_cast<double>(m) / static_cast<double>(s));
+    launch_gather_owned_rows(A_local, m_local, n, lda, row_offset, m, s, seed, 0, scale, As, ld_as, info, st);
+    return check_launch();
+}
+
+rpcholqr_status rpcholqr_sketch_r_from_sample(rpcholqr_plan p, const double* As, int32_t s, int32_t n,
+                                              int64_t ld_as, double* Rs, int32_t* info, void* stream) {
+    if (!p || !As || !Rs || !info || n < 1 || n > p->max_n || s < n || s > p->max_s || ld_as < n)
+        return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rpcholqr_status rc = reset_info(info, st);
+    if (rc != RPCHOLQR_OK) return rc;
+    const int np = pad_np(n);
+    launch_sample_to_colmajor(As, ld_as, s, n, np, p->As, s, st);
+    if (launch_householder(p->As, s, s, n, np, p->Rs, Rs, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    p->launches += 2;
+    return check_launch();
+}
+
+rpcholqr_status rpcholqr_sum_partials(const double* parts, int32_t nparts, int32_t n, double* G, void* stream) {
+    if (!parts || !G || nparts < 1 || n < 1) return RPCHOLQR_ERR_ARG;
+    launch_sum_parts(parts, nparts, n, G, static_cast<cudaStream_t>(stream));
     return check_launch();
 }
 

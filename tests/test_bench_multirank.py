@@ -1,0 +1,51 @@
+"""bench.py's multi-process host logic on CPU ranks (gloo, world size 2): the max-over-ranks timing,
+the barrier, and the reference arm's rank-0-only output."""
+import io
+import os
+import socket
+import sys
+import tempfile
+from contextlib import redirect_stdout
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, outdir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world), RANK=str(rank),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    ws, r, _ = bench.dist_env()
+    dist = bench.init_dist(ws, "gloo")
+    try:
+        t = bench.max_over_ranks(10.0 + 5 * r, dist)       # rank 1 is the slowest
+        bench.barrier(dist)
+        # the reference arm: rank 0 prints one line, the others return 0 without work
+        sys.argv = ["bench.py", "--impl", "reference", "--gpus", str(world), "--steps", "1", "--warmup", "0",
+                    "--m", "300", "--n", "4", "--cpu-sample-rows", "300"]
+        buf = io.StringIO()
+        with redirect_stdout(buf):
+            rc = bench.main()
+        with open(os.path.join(outdir, f"r{r}.txt"), "w") as f:
+            f.write(f"{t}\n{rc}\n{buf.getvalue()}")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_bench_rank_logic_world2():
+    with tempfile.TemporaryDirectory() as d:
+        mp.start_processes(_rank, args=(2, _free_port(), d), nprocs=2, join=True, start_method="spawn")
+        outs = [open(os.path.join(d, f"r{r}.txt")).read().split("\n", 2) for r in range(2)]
+    assert [float(o[0]) for o in outs] == [15.0, 15.0]
+    assert [int(o[1]) for o in outs] == [0, 0]
+    assert '"impl": "reference"' in outs[0][2] and outs[0][2].count("\n") == 1
+    assert outs[1][2] == ""
