@@ -93,6 +93,15 @@ def coherent_diag(m: int, n: int, seed: int) -> np.ndarray:
     return a
 
 
+def coherent_randsvd(m: int, n: int, kappa: float, seed: int) -> np.ndarray:
+    """A = Q_A R_A with Q_A = [I_n; 0] and R_A an n x n matrix with singular values log-spaced from 1
+    to 1/kappa and Haar singular vectors (the maximally coherent inputs of Section 5.1, Eq.
+    e_ErrorRange; R_A plays the part of a randsvd matrix)."""
+    a = np.zeros((m, n))
+    a[:n] = usv(n, n, kappa, seed)
+    return a
+
+
 def batch_manifest(count: int = 512, seed: int = 20240617):
     """Seeded heterogeneous batch description: list of dicts (m, n, s, kappa, seed)."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -70,7 +70,7 @@ def _load():
         lib.oracle_cholesky_upper.restype = I
         lib.oracle_triu_mul.argtypes = [P, P, I64, P, I]
         lib.oracle_rpcholqr.argtypes = [P, I64, I64, I64, I64, U64, U64, P, I64, P, P, P, P, P,
-                                        P, P, I]
+                                        P, P, I, I]
         lib.oracle_rpcholqr.restype = I
         lib.oracle_cholqr.argtypes = [P, I64, I64, I64, P, I64, P, P, I]
         lib.oracle_cholqr.restype = I
@@ -79,6 +79,11 @@ def _load():
         lib.oracle_orth_matrix.argtypes = [P, I64, I64, I64, P]
         lib.oracle_residual_matrix.argtypes = [P, I64, I64, I64, P, I64, P, P]
         lib.oracle_num_threads.restype = I
+        lib.oracle_smooth_order.argtypes = [I64]
+        lib.oracle_smooth_order.restype = I64
+        lib.oracle_rademacher.argtypes = [U64, U64, I64, P]
+        lib.oracle_smooth_rows.argtypes = [P, I64, I64, I64, P, I64, P, I64, P]
+        lib.oracle_smoothed_sample.argtypes = [P, I64, I64, I64, I64, U64, U64, P, P]
         _lib = lib
         return lib
 
@@ -166,8 +171,9 @@ def triu_mul(R2, Rs, variant: int = 0) -> np.ndarray:
     return R
 
 
-def rpcholqr(A, s: int, seed: int, stream: int = 0, variant: int = 0, intermediates=False):
-    """rpCholesky-QR of A (m x n).  Returns dict with Q, R, status, pivot (+ idx, Rs, A1, G1, R1)."""
+def rpcholqr(A, s: int, seed: int, stream: int = 0, variant: int = 0, intermediates=False, smoothing: int = 0):
+    """rpCholesky-QR of A (m x n).  Returns dict with Q, R, status, pivot (+ idx, Rs, A1, G1, R1).
+    smoothing = 1 samples the Walsh-Hadamard smoothed F A instead of A (Algorithm alg_2, line 2)."""
     A = _f64(A)
     m, n = A.shape
     Q = np.zeros((m, n))
@@ -180,12 +186,46 @@ def rpcholqr(A, s: int, seed: int, stream: int = 0, variant: int = 0, intermedia
     A1 = np.zeros((m, n)) if intermediates else None
     st = _load().oracle_rpcholqr(_ptr(A), m, n, n, s, seed, stream, _ptr(Q), n, _ptr(R),
                                  _ptr(idx), _ptr(Rs), _ptr(A1), _ptr(G1), _ptr(R1), _ptr(piv),
-                                 variant)
+                                 variant, smoothing)
     out = {"Q": Q, "R": R, "status": int(st), "pivot": int(piv[0]), "idx": idx, "Rs": Rs,
            "G1": G1, "R1": R1}
     if intermediates:
         out["A1"] = A1
     return out
+
+
+def smooth_order(m: int) -> int:
+    """m' = 2^ceil(log2 m), the order of the Walsh-Hadamard smoothing transform."""
+    return int(_load().oracle_smooth_order(m))
+
+
+def rademacher(seed: int, stream: int, m: int) -> np.ndarray:
+    """D_ii in {-1, +1} from bit 63 of the Philox words under key (seed, stream)."""
+    d = np.zeros(m)
+    _load().oracle_rademacher(seed, stream, m, _ptr(d))
+    return d
+
+
+def smooth_rows(A, d, rows) -> np.ndarray:
+    """Rows `rows` of F_T D [A; 0] (F_T the orthogonal Walsh-Hadamard transform of order m')."""
+    A = _f64(A)
+    m, n = A.shape
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    d = _f64(d)
+    out = np.zeros((rows.shape[0], n))
+    _load().oracle_smooth_rows(_ptr(A), m, n, n, _ptr(d), smooth_order(m), _ptr(rows), rows.shape[0],
+                               _ptr(out))
+    return out
+
+
+def smoothed_sample(A, s: int, seed: int, stream: int = 0):
+    """(A_s, idx): the s-row sample of the smoothed F A, scaled by sqrt(m'/s)."""
+    A = _f64(A)
+    m, n = A.shape
+    idx = np.zeros(s, dtype=np.int64)
+    As = np.zeros((s, n))
+    _load().oracle_smoothed_sample(_ptr(A), m, n, n, s, seed, stream, _ptr(idx), _ptr(As))
+    return As, idx
 
 
 def cholqr(A, variant: int = 0):

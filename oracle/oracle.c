@@ -9,8 +9,9 @@
  *
  * It follows Algorithm alg_2 ("rpCholesky-QR", Section 4) step by step:
  *   sample        A_s = S A            c rows drawn uniformly, independently, with replacement and
- *                                      scaled by sqrt(m/c) as in Remark r_exp (Section 5); the
- *                                      smoothing transform F is not applied on this path
+ *                                      scaled by sqrt(m/c) as in Remark r_exp (Section 5); or, with
+ *                                      smoothing, A_s = S F A with F = F_T D (Walsh-Hadamard F_T,
+ *                                      Rademacher D; the Blendenpik remark of Section 4)
  *   factor        A_s = Q_s R_s        Householder QR, R_s only
  *   precondition  A_1 = A R_s^{-1}     m row-wise lower-triangular solves R_s^T a1_i^T = a_i^T
  *   Gram          G_1 = A_1^T A_1
@@ -279,16 +280,76 @@ static int orc_all_finite(const double* A, int64_t m, int64_t n, int64_t lda) {
 }
 
 /* ---------------------------------------------------------------------------------------------
- * rpCholesky-QR (Algorithm alg_2, Section 4, without smoothing).  Q: m x n (ldq), R: n x n.
+ * Smoothing F = F_T D.  Algorithm alg_2 samples rows of F A; the remark after Theorem t_prob
+ * (Section 4) takes F_T a Walsh-Hadamard, discrete cosine or Hartley transform and D a diagonal of
+ * independent Rademacher signs.  Readings:
+ *   - F_T is the Walsh-Hadamard transform of order m' = 2^ceil(log2 m) in natural (Sylvester)
+ *     order, normalised to be orthogonal: F_T[k][i] = (-1)^popcount(k & i) / sqrt(m');
+ *     it acts on A padded with m' - m zero rows (same R factor as A);
+ *   - D_i = -1 when bit 63 of word (i mod 4) of Philox block i/4 under key (seed, stream + 1) is
+ *     set, else +1;
+ *   - the c sampled rows are drawn from [0, m') and scaled by sqrt(m'/c).
+ * ------------------------------------------------------------------------------------------- */
+int64_t oracle_smooth_order(int64_t m) {
+    int64_t p = 1;
+    while (p < m) p <<= 1;
+    return p;
+}
+
+void oracle_rademacher(uint64_t seed, uint64_t stream, int64_t m, double* d) {
+    uint64_t key[2] = {seed, stream};
+    for (int64_t blk = 0; blk * 4 < m; ++blk) {
+        uint64_t ctr[4] = {(uint64_t)blk, 0, 0, 0}, w[4];
+        oracle_philox4x64_10(ctr, key, w);
+        for (int q = 0; q < 4 && blk * 4 + q < m; ++q) d[blk * 4 + q] = (w[q] >> 63) ? -1.0 : 1.0;
+    }
+}
+
+/* out (nrows x n) = rows `rows` of F_T D [A; 0] (m' = mp rows), each a plain sum over i < m of
+ * (-1)^popcount(k & i) d_i A[i, :], times 1/sqrt(m'). */
+void oracle_smooth_rows(const double* A, int64_t m, int64_t n, int64_t lda, const double* d, int64_t mp,
+                        const int64_t* rows, int64_t nrows, double* out) {
+    const double inv = 1.0 / sqrt((double)mp);
+    #pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < nrows; ++j) {
+        const uint64_t k = (uint64_t)rows[j];
+        double* o = out + j * n;
+        for (int64_t c = 0; c < n; ++c) o[c] = 0.0;
+        for (int64_t i = 0; i < m; ++i) {
+            const double sg = (__builtin_popcountll(k & (uint64_t)i) & 1) ? -d[i] : d[i];
+            const double* a = A + i * lda;
+            for (int64_t c = 0; c < n; ++c) o[c] += sg * a[c];
+        }
+        for (int64_t c = 0; c < n; ++c) o[c] *= inv;
+    }
+}
+
+/* The smoothed sample A_s = sqrt(m'/c) (F A)(idx, :), idx drawn from [0, m') (key (seed, stream)). */
+void oracle_smoothed_sample(const double* A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
+                            uint64_t stream, int64_t* idx, double* As) {
+    const int64_t mp = oracle_smooth_order(m);
+    double* d = (double*)malloc(sizeof(double) * (size_t)m);
+    oracle_rademacher(seed, stream + 1, m, d);
+    oracle_sample_indices(seed, stream, mp, s, idx);
+    oracle_smooth_rows(A, m, n, lda, d, mp, idx, s, As);
+    const double scale = sqrt((double)mp / (double)s);
+    for (int64_t e = 0; e < s * n; ++e) As[e] *= scale;
+    free(d);
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * rpCholesky-QR (Algorithm alg_2, Section 4).  Q: m x n (ldq), R: n x n.  smoothing = 0: A_s = S A;
+ * 1: A_s = S F A with the Walsh-Hadamard smoothing above (idx then indexes the m' rows of F A).
  * Optional outputs (may be NULL): idx (s), Rs (n x n), A1 (m x n, ld n), G1 (n x n), R1 (n x n).
- * Status order: ARG, NONFINITE (a sampled row), SINGULAR_SKETCH, NONFINITE (any row), NOT_SPD.
+ * Status order: ARG, NONFINITE (a sampled row; with smoothing any row, since every row enters the
+ * sample), SINGULAR_SKETCH, NONFINITE (any row), NOT_SPD.
  * ------------------------------------------------------------------------------------------- */
 int oracle_rpcholqr(const double* A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
                     uint64_t stream, double* Q, int64_t ldq, double* R, int64_t* idx_out,
                     double* Rs_out, double* A1_out, double* G1_out, double* R1_out,
-                    int64_t* pivot, int variant) {
+                    int64_t* pivot, int variant, int smoothing) {
     if (pivot) *pivot = -1;
-    if (n < 1 || s < n || m < s || lda < n || ldq < n) return ORC_ERR_ARG;
+    if (n < 1 || s < n || m < s || lda < n || ldq < n || smoothing < 0 || smoothing > 1) return ORC_ERR_ARG;
     size_t nn = (size_t)n * (size_t)n;
     int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)s);
     double* As = (double*)malloc(sizeof(double) * (size_t)s * (size_t)n);
@@ -298,8 +359,13 @@ int oracle_rpcholqr(const double* A, int64_t m, int64_t n, int64_t lda, int64_t 
     double* R1 = (double*)malloc(sizeof(double) * nn);
     int status = ORC_OK;
 
-    oracle_sample_indices(seed, stream, m, s, idx);
-    oracle_gather_scale(A, m, n, lda, idx, s, As);
+    if (smoothing) {
+        if (!orc_all_finite(A, m, n, lda)) { status = ORC_ERR_NONFINITE; goto done; }
+        oracle_smoothed_sample(A, m, n, lda, s, seed, stream, idx, As);
+    } else {
+        oracle_sample_indices(seed, stream, m, s, idx);
+        oracle_gather_scale(A, m, n, lda, idx, s, As);
+    }
     if (idx_out) memcpy(idx_out, idx, sizeof(int64_t) * (size_t)s);
     if (!orc_all_finite(As, s, n, n)) { status = ORC_ERR_NONFINITE; goto done; }
     status = oracle_householder_r(As, s, n, Rs, variant);

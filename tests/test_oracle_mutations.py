@@ -30,6 +30,13 @@ MUTATIONS = {
                                   "for (int64_t k = i; k < j; ++k) t += R2[i * n + k] * Rs[k * n + j];"),
     "second solve uses R_s": ("oracle_trsm_rows(A1, m, n, n, R1, Q, ldq, variant);",
                               "oracle_trsm_rows(A1, m, n, n, Rs, Q, ldq, variant);"),
+    "hadamard parity sign flipped": ("(__builtin_popcountll(k & (uint64_t)i) & 1) ? -d[i] : d[i];",
+                                     "(__builtin_popcountll(k & (uint64_t)i) & 1) ? d[i] : -d[i];"),
+    "rademacher from the low bit": ("(w[q] >> 63) ? -1.0 : 1.0;", "(w[q] & 1) ? -1.0 : 1.0;"),
+    "smoothing normalisation dropped": ("const double inv = 1.0 / sqrt((double)mp);", "const double inv = 1.0;"),
+    "smoothing order one too large": ("while (p < m) p <<= 1;", "while (p <= m) p <<= 1;"),
+    "smoothed sample scale uses m": ("const double scale = sqrt((double)mp / (double)s);",
+                                     "const double scale = sqrt((double)m / (double)s);"),
 }
 
 
@@ -46,6 +53,7 @@ def test_pins_catch_planted_mistake(name):
                         "-o", mutant_so, mutant_c, "-lm"], check=True)
         env = dict(os.environ, RPQ_ORACLE_LIB=mutant_so)
         r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle.py"),
+                            os.path.join(ROOT, "tests", "test_oracle_smoothing.py"),
                             "-x", "-q", "-p", "no:cacheprovider", "-k", "not thread_count"],
                            env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"planted mistake {name!r} passed every pin:\n{r.stdout[-2000:]}"
