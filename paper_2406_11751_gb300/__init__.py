@@ -23,6 +23,8 @@ __all__ = [
     "rpcholqr_batch_create", "rpcholqr_batch_destroy", "rpcholqr_factor_batched", "rpcholqr_batch_capture",
     "rpcholqr_batch_replay", "rpcholqr_batch_autotune", "FP32", "rpcholqr_factor_f32",
     "rpcholqr_gather_owned_rows", "rpcholqr_sketch_r_from_sample", "rpcholqr_sum_partials",
+    "rpcholqr_plan_set_smoothing", "rpcholqr_smoothed_sample", "SMOOTH_NONE", "SMOOTH_WHT",
+    "rpcholqr_plan_split_pass2_fp64",
 ]
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NONFINITE", 3: "ERR_SINGULAR_SKETCH", 4: "ERR_NOT_SPD",
@@ -31,6 +33,7 @@ OK, ERR_ARG, ERR_NONFINITE, ERR_SINGULAR_SKETCH, ERR_NOT_SPD = 0, 1, 2, 3, 4
 FP64 = 0
 SPLIT64 = 1
 FP32 = 2
+SMOOTH_NONE, SMOOTH_WHT = 0, 1
 MAX_N = 512
 
 EXPORTED_SYMBOLS = (
@@ -42,6 +45,7 @@ EXPORTED_SYMBOLS = (
     "rpcholqr_cholqr2", "rpcholqr_batch_create", "rpcholqr_batch_destroy", "rpcholqr_factor_batched",
     "rpcholqr_batch_capture", "rpcholqr_batch_replay", "rpcholqr_batch_autotune", "rpcholqr_factor_f32",
     "rpcholqr_gather_owned_rows", "rpcholqr_sketch_r_from_sample", "rpcholqr_sum_partials",
+    "rpcholqr_plan_set_smoothing", "rpcholqr_smoothed_sample", "rpcholqr_plan_split_pass2_fp64",
 )
 PHASES = ("sample", "sketch_qr", "prep_rs", "pass1", "pass1_update", "pass1_solve2", "gram_reduce",
           "cholesky", "prep_r1", "pass2", "recover_r")
@@ -80,6 +84,9 @@ def load_library():
         "rpcholqr_gather_owned_rows": [P, I64, I32, I64, I64, I64, I32, U64, P, I64, P, P],
         "rpcholqr_sketch_r_from_sample": [P, P, I32, I32, I64, P, P, P],
         "rpcholqr_sum_partials": [P, I32, I32, P, P],
+        "rpcholqr_plan_set_smoothing": [P, I32],
+        "rpcholqr_plan_split_pass2_fp64": [P, ctypes.POINTER(I32)],
+        "rpcholqr_smoothed_sample": [P, P, I64, I32, I64, I32, U64, P, I64, P, P],
         "rpcholqr_sample_indices": [U64, U64, I64, I32, P, P],
         "rpcholqr_sketch_r": [P, P, I64, I32, I64, I32, U64, P, P, P],
         "rpcholqr_precondition_gram": [P, P, I64, I32, I64, P, P, I64, P, P, P],
@@ -274,6 +281,34 @@ def rpcholqr_sum_partials(parts, G=None, stream=None):
     _check("rpcholqr_sum_partials", load_library().rpcholqr_sum_partials(
         _ptr(parts), k, n, _ptr(G), _stream(stream, parts.device)))
     return G
+
+
+def rpcholqr_plan_set_smoothing(plan: Plan, kind: int = SMOOTH_WHT):
+    """Sample the Walsh-Hadamard smoothed F A (kind 1) or A itself (kind 0) on this plan."""
+    _check("rpcholqr_plan_set_smoothing", load_library().rpcholqr_plan_set_smoothing(plan.handle, kind))
+
+
+def rpcholqr_plan_split_pass2_fp64(plan: Plan) -> bool:
+    """Whether the last split factorisation on plan took the FP64 second pass (synchronises)."""
+    v = ctypes.c_int32()
+    _check("rpcholqr_plan_split_pass2_fp64",
+           load_library().rpcholqr_plan_split_pass2_fp64(plan.handle, ctypes.byref(v)))
+    return bool(v.value)
+
+
+def rpcholqr_smoothed_sample(plan: Plan, A, s: int, seed: int, As=None, info=None, stream=None):
+    """(A_s, info): the s x n smoothed sample sqrt(m'/s) (F A)(idx, :) (smoothing enabled on plan)."""
+    torch = _torch()
+    _mat(A, "A")
+    m, n = A.shape
+    if As is None:
+        As = torch.empty((s, n), dtype=torch.float64, device=A.device)
+    _mat(As, "As")
+    info = _info(info, A.device)
+    _check("rpcholqr_smoothed_sample", load_library().rpcholqr_smoothed_sample(
+        plan.handle, _ptr(A), m, n, A.stride(0), s, seed, _ptr(As), As.stride(0), _ptr(info),
+        _stream(stream, A.device)))
+    return As, info
 
 
 def rpcholqr_factor_host(plan: Plan, A, s: int, seed: int, Q=None, R=None, stream=None):

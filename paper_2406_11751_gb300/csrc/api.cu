@@ -77,6 +77,18 @@ void launch_gather_owned_rows(const double* A, int64_t m_local, int32_t n, int64
 void launch_sample_to_colmajor(const double* src, int64_t ld_src, int32_t s, int32_t n, int32_t np, double* dst,
                                int64_t lds, cudaStream_t st);
 void launch_sum_parts(const double* parts, int32_t nparts, int32_t n, double* G, cudaStream_t st);
+bool smooth_supported(int64_t m);
+size_t smooth_buffer_bytes(int64_t max_m, int max_n);
+cudaError_t launch_smoothed_sample(const double* A, int64_t m, int n, int64_t lda, int s, uint64_t seed, double* T,
+                                   int64_t* idx, double* As, int64_t lds, int np, int32_t* info, cudaStream_t st);
+cudaError_t launch_smoothed_sample_f32(const float* A, int64_t m, int n, int64_t lda, int s, uint64_t seed,
+                                       double* T, int64_t* idx, double* As, int64_t lds, int np, int32_t* info,
+                                       cudaStream_t st);
+void launch_colmajor_to_rows(const double* src, int64_t lds, int s, int n, double* dst, int64_t ldd,
+                             cudaStream_t st);
+void launch_pass2_gate(const double* R1, const double* W, int n, int np, double tau, const int32_t* info,
+                       int32_t* gates, cudaStream_t st);
+void launch_gate_merge(int32_t* info, const int32_t* gates, cudaStream_t st);
 }  // namespace rpq
 
 using namespace rpq;
@@ -118,9 +130,15 @@ struct rpcholqr_plan_s {
     int32_t* yexp = nullptr;    // np
     uint8_t* yblocks = nullptr; // Ozaki column slices (K, N <= np)
     double* W = nullptr;        // np x np
+    int32_t* gates = nullptr;   // split pass-2 gate words: {split status, pivot, fp64 status, pivot, used fp64}
     // FP32 buffers (separate allocation)
     float* T32 = nullptr;       // pad32(max_n)^2: R_s or R1 in FP32, identity-padded
     float* rinv32 = nullptr;    // pad32(max_n)
+    // smoothing (allocated by rpcholqr_plan_set_smoothing)
+    int32_t smoothing = 0;
+    void* smooth_ws = nullptr;
+    double* smooth_T = nullptr;     // Walsh-Hadamard transform buffer, 8-column blocks of m' rows
+    int64_t* smooth_idx = nullptr;  // max_s sample rows of F A
 };
 
 namespace {
@@ -200,6 +218,9 @@ struct PhaseMarks {
 };
 
 constexpr int kBlk = 64;   // column block of the blocked solves (n > 128)
+// Split mode: the explicit-inverse second pass is used while ||R1||_F ||R1^{-1}||_F / n <= this
+// (about 1.2 for well-sampled incoherent A; the estimate lies in [kappa(A1)/n, kappa(A1)]).
+constexpr double kSplitPass2Tau = 4.0;
 
 // CTAs of a row pass over m rows: one per 128-row panel, at most one per SM.
 int row_grid(const rpcholqr_plan_s* p, int64_t m) {
@@ -290,6 +311,7 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
         const size_t oY = take(sizeof(int32_t) * np);
         const size_t oB = take(ozaki_yblocks_bytes(p->np, p->np));
         const size_t oW = take(sizeof(double) * np * np);
+        const size_t oG = take(sizeof(int32_t) * 8);
         if (cudaMalloc(&p->split_ws, off) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(p->ws);
@@ -303,6 +325,8 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
         p->yexp = reinterpret_cast<int32_t*>(c + oY);
         p->yblocks = reinterpret_cast<uint8_t*>(c + oB);
         p->W = reinterpret_cast<double*>(c + oW);
+        p->gates = reinterpret_cast<int32_t*>(c + oG);
+        if (cudaMemset(p->gates, 0, sizeof(int32_t) * 8) != cudaSuccess) cudaGetLastError();
         p->ws_bytes += off;
     }
     if (mode == RPCHOLQR_FP32) {
@@ -334,6 +358,7 @@ rpcholqr_status rpcholqr_plan_destroy(rpcholqr_plan plan) {
     cudaFree(plan->hR);
     cudaFree(plan->hinfo);
     cudaFree(plan->split_ws);
+    cudaFree(plan->smooth_ws);
     free_events(plan);
     delete plan;
     return RPCHOLQR_OK;
@@ -354,8 +379,15 @@ static rpcholqr_status sketch_internal(rpcholqr_plan p, const double* A, int64_t
     const double scale = std::sqrt(static_cast<double>(m) / static_cast<double>(s));
     if (pm) pm->mark(RPCHOLQR_PHASE_SAMPLE);
     const int64_t lds = s;
-    launch_sample_gather(A, m, n, lda, s, seed, stream_id, scale, p->As, lds, np, nullptr, info, st);
-    ++p->launches;
+    if (p->smoothing) {
+        if (launch_smoothed_sample(A, m, n, lda, s, seed, p->smooth_T, p->smooth_idx, p->As, lds, np, info, st) !=
+            cudaSuccess)
+            return RPCHOLQR_ERR_CUDA;
+        p->launches += 3;
+    } else {
+        launch_sample_gather(A, m, n, lda, s, seed, stream_id, scale, p->As, lds, np, nullptr, info, st);
+        ++p->launches;
+    }
     if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
     if (pm) pm->mark(RPCHOLQR_PHASE_SKETCH_QR);
     if (launch_householder(p->As, lds, s, n, np, p->Rs, Rs_user, info, st) != cudaSuccess)
@@ -575,11 +607,18 @@ static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m,
     ++p->launches;
     pm.mark(RPCHOLQR_PHASE_PREP_R1);
     launch_triu_inv(p->R1, np, n, np, p->W, info, st);
-    ++p->launches;
+    launch_pass2_gate(p->R1, p->W, n, np, kSplitPass2Tau, info, p->gates, st);
+    p->launches += 2;
     pm.mark(RPCHOLQR_PHASE_PASS2);
-    if ((rc = ozaki_gemm_internal(p, false, A1, m, n, ld1, p->W, n, np, nullptr, 0, Q, ldq, info, st, true)) !=
-        RPCHOLQR_OK)
+    // Q = A1 R1^{-1}: the split product with the explicit inverse when A1 is well conditioned, else the
+    // FP64 row-wise substitution; both are launched, the gate words make the other one return at once
+    if ((rc = ozaki_gemm_internal(p, false, A1, m, n, ld1, p->W, n, np, nullptr, 0, Q, ldq, p->gates, st,
+                                  true)) != RPCHOLQR_OK)
         return rc;
+    if ((rc = solve_internal(p, A1, m, n, ld1, p->R1, np, Q, ldq, p->gates + 2, st, nullptr)) != RPCHOLQR_OK)
+        return rc;
+    launch_gate_merge(info, p->gates, st);
+    ++p->launches;
     pm.mark(RPCHOLQR_PHASE_RECOVER_R);
     launch_triu_mul(p->R1, np, p->Rs, np, n, R, n, info, st);
     ++p->launches;
@@ -630,8 +669,15 @@ rpcholqr_status rpcholqr_factor_f32(rpcholqr_plan p, const float* A, int64_t m, 
     // sample (widened to FP64) and the FP64 Householder R_s
     pm.mark(RPCHOLQR_PHASE_SAMPLE);
     const double scale = std::sqrt(static_cast<double>(m) / static_cast<double>(s));
-    launch_sample_gather_f32(A, m, n, lda, s, seed, 0, scale, p->As, s, np, nullptr, info, st);
-    ++p->launches;
+    if (p->smoothing) {
+        if (launch_smoothed_sample_f32(A, m, n, lda, s, seed, p->smooth_T, p->smooth_idx, p->As, s, np, info,
+                                       st) != cudaSuccess)
+            return RPCHOLQR_ERR_CUDA;
+        p->launches += 3;
+    } else {
+        launch_sample_gather_f32(A, m, n, lda, s, seed, 0, scale, p->As, s, np, nullptr, info, st);
+        ++p->launches;
+    }
     pm.mark(RPCHOLQR_PHASE_SKETCH_QR);
     if (launch_householder(p->As, s, s, n, np, p->Rs, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
     ++p->launches;
@@ -933,6 +979,55 @@ rpcholqr_status rpcholqr_sum_partials(const double* parts, int32_t nparts, int32
     if (!parts || !G || nparts < 1 || n < 1) return RPCHOLQR_ERR_ARG;
     launch_sum_parts(parts, nparts, n, G, static_cast<cudaStream_t>(stream));
     return check_launch();
+}
+
+rpcholqr_status rpcholqr_plan_set_smoothing(rpcholqr_plan p, int32_t kind) {
+    if (!p || kind < 0 || kind > 1) return RPCHOLQR_ERR_ARG;
+    if (kind == 1 && !p->smooth_ws) {
+        if (!smooth_supported(p->max_m)) return RPCHOLQR_ERR_UNSUPPORTED;
+        DeviceGuard guard(p->device);
+        if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+        const size_t tb = align256(smooth_buffer_bytes(p->max_m, p->max_n));
+        const size_t total = tb + sizeof(int64_t) * static_cast<size_t>(p->max_s);
+        if (cudaMalloc(&p->smooth_ws, total) != cudaSuccess) {
+            cudaGetLastError();
+            p->smooth_ws = nullptr;
+            return RPCHOLQR_ERR_NOMEM;
+        }
+        p->smooth_T = static_cast<double*>(p->smooth_ws);
+        p->smooth_idx = reinterpret_cast<int64_t*>(static_cast<char*>(p->smooth_ws) + tb);
+        p->ws_bytes += total;
+    }
+    p->smoothing = kind;
+    return RPCHOLQR_OK;
+}
+
+rpcholqr_status rpcholqr_smoothed_sample(rpcholqr_plan p, const double* A, int64_t m, int32_t n, int64_t lda,
+                                         int32_t s, uint64_t seed, double* As, int64_t ld_as, int32_t* info,
+                                         void* stream) {
+    if (!p || !A || !As || !info || !p->smoothing) return RPCHOLQR_ERR_ARG;
+    if (n < 1 || n > p->max_n || s < 1 || s > p->max_s || m < 1 || m > p->max_m || lda < n || ld_as < n)
+        return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rpcholqr_status rc = reset_info(info, st);
+    if (rc != RPCHOLQR_OK) return rc;
+    const int np = pad_np(n);
+    if (launch_smoothed_sample(A, m, n, lda, s, seed, p->smooth_T, p->smooth_idx, p->As, s, np, info, st) !=
+        cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    launch_colmajor_to_rows(p->As, s, s, n, As, ld_as, st);
+    return check_launch();
+}
+
+rpcholqr_status rpcholqr_plan_split_pass2_fp64(rpcholqr_plan p, int32_t* used_fp64) {
+    if (!p || !used_fp64 || p->mode != RPCHOLQR_SPLIT64) return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    return cudaMemcpy(used_fp64, p->gates + 4, sizeof(int32_t), cudaMemcpyDeviceToHost) == cudaSuccess
+               ? RPCHOLQR_OK
+               : RPCHOLQR_ERR_CUDA;
 }
 
 rpcholqr_status rpcholqr_probe_fp64_mma(int device, int32_t iters, double* flops_per_s) {

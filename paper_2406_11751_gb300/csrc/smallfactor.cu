@@ -357,3 +357,67 @@ void launch_triu_inv(const double* T, int64_t ldt, int n, int np, double* W, con
     else k_triu_inv<16><<<(n + 7) / 8, 256, 0, st>>>(T, ldt, n, np, W, info);
 }
 }  // namespace rpq
+
+// ---- choice of the split mode's second pass -------------------------------------------------------
+// Q = A1 R1^{-1} as a split tensor-core product with the explicit inverse W = R1^{-1} is accurate to
+// ~u times the product of the row bounds of A1 and the column bounds of W; its residual ||A - QR||
+// grows with kappa(A1), while an FP64 row-wise substitution stays backward stable.  est =
+// ||R1||_F ||W||_F / n lies between kappa(A1)/n and kappa(A1) (about 1.2 for well-sampled incoherent
+// A).  The kernel writes two gate status words: the branch not taken gets kGateSkip (its kernels
+// return at once), the taken one 0, and both carry an earlier error of info.
+namespace rpq {
+
+constexpr int kGateSkip = 1000;
+
+__global__ void __launch_bounds__(1024)
+k_pass2_gate(const double* __restrict__ R1, const double* __restrict__ W, int n, int np, double tau,
+             const int32_t* info, int32_t* gate_split, int32_t* gate_fp64, int32_t* used_fp64) {
+    __shared__ double red[2][32];
+    double a = 0.0, b = 0.0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int r = e / n, c = e - r * n;
+        const double x = R1[r * np + c], y = W[r * np + c];
+        a = fma(x, x, a);
+        b = fma(y, y, b);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[0][warp] = a; red[1][warp] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sa += red[0][w]; sb += red[1][w]; }
+        const int st = load_status(info);
+        const double est = sqrt(sa) * sqrt(sb) / n;
+        const bool fp = !(est <= tau);
+        gate_split[0] = st ? st : (fp ? kGateSkip : 0);
+        gate_fp64[0] = st ? st : (fp ? 0 : kGateSkip);
+        gate_split[1] = gate_fp64[1] = -1;
+        *used_fp64 = fp ? 1 : 0;
+    }
+}
+
+// The first real error of the taken branch into info.
+__global__ void k_gate_merge(int32_t* info, const int32_t* gate_split, const int32_t* gate_fp64) {
+    if (threadIdx.x != 0 || load_status(info) != 0) return;
+    const int32_t* g[2] = {gate_split, gate_fp64};
+    for (int k = 0; k < 2; ++k)
+        if (g[k][0] != 0 && g[k][0] != kGateSkip) {
+            info[1] = g[k][1];
+            info[0] = g[k][0];
+            return;
+        }
+}
+
+void launch_pass2_gate(const double* R1, const double* W, int n, int np, double tau, const int32_t* info,
+                       int32_t* gates, cudaStream_t st) {
+    k_pass2_gate<<<1, 1024, 0, st>>>(R1, W, n, np, tau, info, gates, gates + 2, gates + 4);
+}
+void launch_gate_merge(int32_t* info, const int32_t* gates, cudaStream_t st) {
+    k_gate_merge<<<1, 32, 0, st>>>(info, gates, gates + 2);
+}
+}  // namespace rpq

@@ -90,6 +90,8 @@ def test_split_factor_matches_oracle(lib, oracle_mod, splan, m, n, kappa):
     if kappa <= 1e8:
         floor = np.linalg.norm(o["Q"] - oracle_mod.rpcholqr(A, s, 5, variant=1)["Q"], 2)
         assert np.linalg.norm(Qh - o["Q"], 2) <= max(1e-10, 10 * floor)
+    # incoherent A: A1 is well conditioned and the tensor-core second pass is kept
+    assert not lib.rpcholqr_plan_split_pass2_fp64(splan)
 
 
 def test_split_factor_nonfinite(lib, oracle_mod, splan):
