@@ -62,6 +62,8 @@ def parse_args():
                     help="workload shapes: small m=10000 n=50 kappa=1e8; headline m=2^20 n=128 kappa=1e8 "
                          "(the default); precision m=2^22 n=256 kappa=1e12; large m=2^23 n=512 "
                          "sigma to 1e-18")
+    ap.add_argument("--smoothing", action="store_true",
+                    help="sample the Walsh-Hadamard smoothed F A (Algorithm alg_2 with F = F_T D)")
     ap.add_argument("--count", type=int, default=512, help="matrices in the batch workload")
     ap.add_argument("--slots", type=int, default=16, help="concurrent slots the batch autotuner may use")
     ap.add_argument("--no-compare", action="store_true",
@@ -320,6 +322,8 @@ def run_ours(args, ws, rank, local):
     def timed(mode, clocks):
         """W warm-up + K timed factor calls on a fresh plan of `mode`: (ms, phases, calls, launches, plan)."""
         plan = rq.rpcholqr_plan_create(local, m, n, s, mode=modes[mode])
+        if args.smoothing:
+            rq.rpcholqr_plan_set_smoothing(plan, rq.SMOOTH_WHT)
         for w in range(W):
             factor(plan, mode, 1 + w)
         torch.cuda.synchronize(dev)
@@ -435,15 +439,16 @@ def run_ours(args, ws, rank, local):
         k_bytes = 16.0 * m * n                          # read A, write A1
         traffic = traffic_from_profiles(f"k_rowpass<{np_},true>", src)
     else:
-        # dominant kernel: the FP64 block row solves of pass 1 (<= 64 columns each)
-        n1 = min(n, 64)
-        n2 = n - n1
-        kname = "k_rowpass<%d,false> (SPLIT64 pass 1: FP64 block row solves by R_s)" % min(np_, 64)
-        launches_per_call = 2 if n2 > 0 else 1
-        k_ms = (phases["pass1"] + phases["pass1_solve2"]) / c / launches_per_call
-        k_flops = m * (n1 * n1 + n2 * n2) / launches_per_call
-        k_bytes = 16.0 * m * (n1 + n2) / launches_per_call
-        traffic = traffic_from_profiles(f"k_rowpass<{min(np_, 64)},false>", src)
+        # dominant kernel: the FP64 32-column diagonal-block row solves of pass 1 (one launch per block;
+        # the PASS1 phase is exactly the first block's launch, the other blocks do the same work)
+        b0 = min(n, 32)
+        nb0 = (b0 + 15) // 16 * 16
+        kname = "k_rowpass<%d,false> (SPLIT64 pass 1: FP64 32-column diagonal-block row solves by R_s)" % nb0
+        launches_per_call = (n + 31) // 32
+        k_ms = phases["pass1"] / c
+        k_flops = float(m) * b0 * b0
+        k_bytes = 16.0 * m * b0
+        traffic = traffic_from_profiles(f"k_rowpass<{nb0},false>", src)
     achieved = k_flops / (k_ms / 1e3) / 1e12
     peak = (fp32_peak if args.mode == "fp32" else fp64_peak) / 1e12
 
@@ -460,8 +465,9 @@ def run_ours(args, ws, rank, local):
         "ms_per_step": t_ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "split": "f64+bf16", "fp32": "f32+f64"}[args.mode],
         "data": "synthetic (A = U diag(sigma) V^T, Haar U/V from torch, sigma log-spaced)",
-        "config": {"workload": f"rpCholesky-QR {args.mode.upper()} m={m} n={n} s={s} kappa={args.kappa:g}", "m": m,
-                   "n": n, "s": s, "kappa": args.kappa, "mode": args.mode,
+        "config": {"workload": f"rpCholesky-QR {args.mode.upper()} m={m} n={n} s={s} kappa={args.kappa:g}"
+                               + (" smoothing=WHT" if args.smoothing else ""), "m": m,
+                   "n": n, "s": s, "kappa": args.kappa, "mode": args.mode, "smoothing": bool(args.smoothing),
                    "l2": f"inputs larger than L2 (A = {8 * m * n / 1e9:.2f} GB > 129 MB), no flush"},
         "effective_tflops": flops * value / 1e12,
         "orth": orth, "residual": res, "gate_orth_le_1e-13": None if orth is None else bool(orth <= 1e-13),

@@ -217,7 +217,10 @@ struct PhaseMarks {
     }
 };
 
-constexpr int kBlk = 64;   // column block of the blocked solves (n > 128)
+constexpr int kBlk = 64;   // column block of the FP64 blocked solves (n > 128)
+// Diagonal block of the split mode's first pass: its FP64 work per row is n * kSplitBlk, the rest of
+// the solve runs as split tensor-core updates.
+constexpr int kSplitBlk = 32;
 // Split mode: the explicit-inverse second pass is used while ||R1||_F ||R1^{-1}||_F / n <= this
 // (about 1.2 for well-sampled incoherent A; the estimate lies in [kappa(A1)/n, kappa(A1)]).
 constexpr double kSplitPass2Tau = 4.0;
@@ -404,13 +407,53 @@ static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const doub
 // Diagonal-block setups for the blocked solve with T (n x n, ld ldt): block J (64 columns, the last
 // one ragged) gets frag + 4096 J and diag + 512 J.
 static void prep_blocks(rpcholqr_plan_s* p, const double* T, int64_t ldt, int n, double* frag, double* diag,
-                 const int32_t* info, cudaStream_t st) {
-    for (int J = 0; J * kBlk < n; ++J) {
-        const int nj = n - J * kBlk < kBlk ? n - J * kBlk : kBlk;
-        launch_prep_tri(T + static_cast<int64_t>(J) * kBlk * ldt + J * kBlk, ldt, nj, pad16(nj),
-                        frag + J * kBlk * kBlk, diag + J * (kBlk / 8) * 64, info, st);
+                        const int32_t* info, cudaStream_t st, int blk = kBlk) {
+    for (int J = 0; J * blk < n; ++J) {
+        const int nj = n - J * blk < blk ? n - J * blk : blk;
+        launch_prep_tri(T + static_cast<int64_t>(J) * blk * ldt + J * blk, ldt, nj, pad16(nj),
+                        frag + J * blk * blk, diag + J * (blk / 8) * 64, info, st);
         ++p->launches;
     }
+}
+
+// Right-looking blocked row solve for the split mode, Y = X T^{-1} over kSplitBlk-column blocks J:
+// Y[:, J] <- (current X[:, J]) T[J, J]^{-1} by the FP64 row pass, then every later column is updated
+// at once, Y[:, >J] = (X or Y)[:, >J] - Y[:, J] T[J, >J], as one split tensor-core product with
+// K = kSplitBlk (one exactness stage) and N = the remaining width.  The diagonal blocks must have been
+// set up by prep_blocks with blk = kSplitBlk.  The row passes store (block 0) and max-merge the row
+// bounds of Y into p->xexp (the update's left operand uses the bound over the blocks solved so far)
+// and their column bounds into p->colexp.  Marks PASS1 / PASS1_UPDATE / PASS1_SOLVE2 as the first
+// row pass / the first update / the rest when pm is given.
+static rpcholqr_status solve_split_right(rpcholqr_plan_s* p, const double* X, int64_t ldx, const double* T,
+                                         int64_t ldt, int64_t m, int n, double* Y, int64_t ldy, const double* frag,
+                                         const double* diag, int32_t* info, cudaStream_t st, const PhaseMarks* pm) {
+    const int grid = row_grid(p, m);
+    const int blk = kSplitBlk;
+    for (int J = 0; J * blk < n; ++J) {
+        const int c0 = J * blk;
+        const int nj = n - c0 < blk ? n - c0 : blk;
+        const double* src = J == 0 ? X : Y;
+        const int64_t lsrc = J == 0 ? ldx : ldy;
+        if (launch_rowpass_ex(false, pad16(nj), src + c0, lsrc, Y + c0, ldy, m, nj, frag + J * blk * blk,
+                              diag + J * (blk / 8) * 64, nullptr, info, grid, st, true, p->xexp, J == 0 ? 1 : 2,
+                              p->colexp + c0) != cudaSuccess)
+            return RPCHOLQR_ERR_CUDA;
+        ++p->launches;
+        const int rest = n - c0 - nj;
+        if (rest > 0) {
+            if (pm && J == 0) pm->mark(RPCHOLQR_PHASE_PASS1_UPDATE);
+            rpcholqr_status rc = ozaki_gemm_internal(p, true, Y + c0, m, nj, ldy, T + static_cast<int64_t>(c0) * ldt +
+                                                     c0 + nj, rest, ldt, src + c0 + nj, lsrc, Y + c0 + nj, ldy, info,
+                                                     st, true);
+            if (rc != RPCHOLQR_OK) return rc;
+            if (pm && J == 0) pm->mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
+        }
+    }
+    if (pm && n <= blk) {
+        pm->mark(RPCHOLQR_PHASE_PASS1_UPDATE);
+        pm->mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
+    }
+    return check_launch();
 }
 
 // Left-looking blocked row solve Y = X T^{-1} (T upper triangular, n x n, ld ldt) over 64-column
@@ -594,12 +637,20 @@ static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m,
     pm.mark(RPCHOLQR_PHASE_PREP_RS);
     launch_fill_noexp(p->colexp, n, st);   // column bounds of A1, atomically max-merged by the row passes
     ++p->launches;
-    // A1 = A R_s^{-1}: one row pass for n <= 64, else the blocked solve with split off-diagonal updates
-    prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st);
-    pm.mark(RPCHOLQR_PHASE_PASS1);
-    if ((rc = solve_blocked(p, A, lda, p->Rs, np, m, n, A1, ld1, p->frag_s, p->diag_s, true, true, info, st, &pm,
-                            true)) != RPCHOLQR_OK)
-        return rc;
+    // A1 = A R_s^{-1}: FP64 row passes on the diagonal blocks, split tensor-core updates for the rest.
+    // Up to 128 columns: 32-column blocks, right-looking (every update one K stage, wide N); above:
+    // 64-column blocks, left-looking (long K windows; fewer passes over the trailing columns).
+    if (np <= kMaxNP) {
+        prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st, kSplitBlk);
+        pm.mark(RPCHOLQR_PHASE_PASS1);
+        rc = solve_split_right(p, A, lda, p->Rs, np, m, n, A1, ld1, p->frag_s, p->diag_s, info, st, &pm);
+    } else {
+        prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st);
+        pm.mark(RPCHOLQR_PHASE_PASS1);
+        rc = solve_blocked(p, A, lda, p->Rs, np, m, n, A1, ld1, p->frag_s, p->diag_s, true, true, info, st, &pm,
+                           true);
+    }
+    if (rc != RPCHOLQR_OK) return rc;
     pm.mark(RPCHOLQR_PHASE_GRAM_REDUCE);
     if ((rc = ozaki_gram_internal(p, A1, m, n, ld1, p->G, np, info, st, true)) != RPCHOLQR_OK) return rc;
     pm.mark(RPCHOLQR_PHASE_CHOLESKY);

@@ -37,7 +37,18 @@ constexpr int kGroups = 8;                 // d = 2..9
 constexpr int kTileM = 128;
 constexpr int kTileN = 64;
 constexpr int kKW = 32;                    // K per stage
-constexpr int kThreads = 256;            // 8 warps: 2 producers per tile row, 2 drain warps per TMEM lane quarter
+constexpr int kThreads = 512;            // 16 warps: 4 threads per tile row (TMEM lane), one per K chunk
+// Per-thread shares for a CTA of NT threads (NT/128 threads per tile row):
+template <int NT> struct Share {
+    static constexpr int kRowThreads = NT / 128;
+    static constexpr int kChunks = (32 / 8) / kRowThreads;   // 8-value K chunks sliced per stage
+    static constexpr int kDrainCols = 64 / kRowThreads;      // output columns drained
+};
+constexpr int kDrainCols = Share<kThreads>::kDrainCols;
+constexpr int kChunks = Share<kThreads>::kChunks;
+// The windowed GEMM (K > 128) keeps int64 accumulators live across stages: 256 threads leave it the
+// registers (512 threads cap a thread at 128).
+constexpr int kThreadsWin = 256;
 constexpr int kSBO = (kKW * 2 / 16) * 128; // 512 B between 8-row core-matrix groups
 constexpr int kLBO = 128;                  // 128 B between K-adjacent core matrices
 constexpr int kASlice = kTileM * kKW * 2;  // 8 KB
@@ -188,14 +199,14 @@ __device__ __forceinline__ double scale_pow2(long long I, int e) {
     return ldexp(v, e);
 }
 
-// Add the eight TMEM group sums of this thread's row and its warp's 32 columns (columns col0..col0+31 of
-// the 64-column tile) to int64 accumulators in units of 2^-53 (U53) or 2^-49 of the operand scale.
+// Add the eight TMEM group sums of this thread's row and its kDrainCols columns (col0.. of the 64-column
+// tile) to int64 accumulators in units of 2^-53 (U53) or 2^-49 of the operand scale.
 // The sliced operands are below 0.51 of their power-of-two bounds, so a K-term sum stays below
 // 0.26 K scale: units of 2^-53 hold K <= 2^10 terms, units of 2^-49 hold 2^14 (a 64-window flush).
-template <bool U53>
-__device__ __forceinline__ void drain_acc(uint32_t tmem, int warp, int col0, long long (&acc)[32]) {
+template <bool U53, int NC>
+__device__ __forceinline__ void drain_acc(uint32_t tmem, int warp, int col0, long long (&acc)[NC]) {
 #pragma unroll
-    for (int c0 = 0; c0 < 32; c0 += 8) {
+    for (int c0 = 0; c0 < NC; c0 += 8) {
         float mg[kGroups][8];
 #pragma unroll
         for (int g = 0; g < kGroups; ++g)
@@ -270,8 +281,69 @@ __global__ void __launch_bounds__(256) k_ozaki_slice_cols(const double* __restri
 // B, C: m x N FP64 (ldb, ldc); C may equal B.  Persistent grid over 128-row x 64-column tiles.
 // WIN (128 < K <= 1024): the K range is cut into exactness windows of 128, each drained into int64
 // accumulators in units of 2^-53 of the scale (the same resolution as a single window).
+//
+// Pipeline: the CTA's (tile, K-stage) sequence is one stream of stages over two shared-memory buffers.
+// Stage g is sliced into buffer g & 1 while the MMAs of stage g - 1 run; when stage g opens a new
+// exactness window (or a new tile), the accumulators of the previous window are drained (into the
+// int64 accumulators, or out to C at a tile end) after stage g has been produced and before its MMAs
+// are issued, so the slicing of a tile's first stage overlaps the MMAs of the tile before.
+template <bool SUB, bool WIN, int NC>
+__device__ __forceinline__ void gemm_drain_tile(uint32_t tmem, int warp, int rq, int64_t row, int tn, int E,
+                                                int N, const int32_t* __restrict__ yexp, const double* B,
+                                                int64_t ldb, double* C, int64_t ldc, int64_t m,
+                                                long long (&acc)[NC]) {
+    if (WIN) {
+        drain_acc<true>(tmem, warp, NC * rq, acc);
+        if (row < m) {
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                const int col = tn * kTileN + NC * rq + j;
+                if (col < N) {
+                    const int ey = yexp[col];
+                    const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(acc[j], E + ey - 53) : 0.0;
+                    if (SUB) C[row * ldc + col] = B[row * ldb + col] - v;
+                    else C[row * ldc + col] = v;
+                }
+            }
+        }
+        return;
+    }
+#pragma unroll 1
+    for (int c0 = NC * rq; c0 < NC * rq + NC; c0 += 8) {
+        double bv[8];
+        if (SUB) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int col = tn * kTileN + c0 + j;
+                bv[j] = (row < m && col < N) ? B[row * ldb + col] : 0.0;
+            }
+        }
+        float mg[kGroups][8];
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g)
+            tmem_ld8(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + g * kTileN + c0, mg[g]);
+        tmem_wait_ld();
+        if (row < m) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int col = tn * kTileN + c0 + j;
+                if (col < N) {
+                    float grp[kGroups];
+#pragma unroll
+                    for (int g = 0; g < kGroups; ++g) grp[g] = mg[g][j];
+                    const long long I = combine_units53(grp);
+                    const int ey = yexp[col];
+                    const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(I, E + ey - 53) : 0.0;
+                    if (SUB) C[row * ldc + col] = bv[j] - v;
+                    else C[row * ldc + col] = v;
+                }
+            }
+        }
+    }
+}
+
 template <bool SUB, bool WIN>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(WIN ? kThreadsWin : kThreads, 1)
 k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int K,
              const uint8_t* __restrict__ yblocks, const int32_t* __restrict__ yexp, int N,
              const double* B, int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info) {
@@ -297,84 +369,99 @@ k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = tslot;
+    constexpr int NT = WIN ? kThreadsWin : kThreads;
+    constexpr int NC = Share<NT>::kDrainCols, NCH = Share<NT>::kChunks;
 
     const int nkw = (K + kKW - 1) / kKW;
     const int ntn = (N + kTileN - 1) / kTileN;
     const int64_t ntm = (m + kTileM - 1) / kTileM;
     const int64_t ntiles = ntm * ntn;
-    // K > 128: exactness windows of 4 stages, drained into int64 accumulators between windows
-    constexpr bool windowed = WIN;
+    const int64_t my_tiles =
+        static_cast<int64_t>(blockIdx.x) < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t nstages = my_tiles * nkw;
+    const int lr = tid & (kTileM - 1);  // tile row: producer row and drain row (TMEM lane)
+    const int rq = tid >> 7;            // producer K chunk(s) NCH*rq..; drain columns NC*rq..
     uint32_t phase[2] = {0u, 0u};
     bool pending[2] = {false, false};
     bool timed_out = false;
-    int step = 0;
-    long long acc[32];
+    long long acc[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[j] = 0;
+    int64_t cur_row = 0;                // the tile whose accumulators are in TMEM
+    int cur_tn = 0, cur_E = kNoExp;
 
-    for (int64_t tile = blockIdx.x; tile < ntiles && !timed_out; tile += gridDim.x) {
-        const int64_t tm = tile / ntn;
-        const int tn = static_cast<int>(tile - tm * ntn);
-        const int64_t row0 = tm * kTileM;
-        const int lr = tid & (kTileM - 1);  // tile row: producer row and drain row (TMEM lane)
-        const int chalf = tid >> 7;         // producer K chunks 2*chalf, 2*chalf+1; drain columns 32*chalf..
-        const int64_t myrow = row0 + lr;
-        const int E = myrow < m ? xexp[myrow] : kNoExp;
+    for (int64_t g = 0; g < nstages; ++g) {
+        const int s = static_cast<int>(g & 1);
+        const int64_t t = blockIdx.x + (g / nkw) * gridDim.x;
+        const int kw = static_cast<int>(g % nkw);
+        const int64_t tm = t / ntn;
+        const int tn = static_cast<int>(t - tm * ntn);
+        const int64_t row = tm * kTileM + lr;
+        const int E = row < m ? xexp[row] : kNoExp;
+        // buffer s is free once the MMAs of stage g - 2 are done
+        if (pending[s]) {
+            const bool ok = mbar_wait(&mbar[s], phase[s]);
+            if (__syncthreads_or(!ok)) { timed_out = true; break; }
+            phase[s] ^= 1u;
+            pending[s] = false;
+        }
+        // produce stage g: B slices (one contiguous 32 KB block, 16-byte cp.async granules) and the A
+        // slices of this thread's row, two chunks of 8 K values
+        const uint8_t* src = yblocks + static_cast<size_t>((tn * nkw + kw) * kSlices) * kBSlice;
+        for (int e = tid; e < kBStage / 16; e += NT) {
+            const unsigned dst = smem_u32(stB[s] + 16 * e);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 16 * e));
+        }
+        asm volatile("cp.async.commit_group;\n");
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] = 0;
-        for (int kw = 0; kw < nkw; ++kw, ++step) {
-            const int s = step & 1;
-            if (pending[s]) {
-                const bool ok = mbar_wait(&mbar[s], phase[s]);
+        for (int cc = 0; cc < NCH; ++cc) {
+            const int c = NCH * rq + cc;
+            double x[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k = kw * kKW + 8 * c + i;
+                x[i] = (row < m && k < K) ? X[row * ldx + k] : 0.0;
+            }
+            slice_store8(x, E, stA[s] + core_off(lr, 16 * c), kASlice);
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        fence_async_smem();
+        // stage g opens an exactness window: drain the previous window's accumulators first
+        const bool new_window = (kw & 3) == 0;
+        if (g > 0 && new_window) {
+            const int sp = s ^ 1;
+            if (pending[sp]) {
+                const bool ok = mbar_wait(&mbar[sp], phase[sp]);
                 if (__syncthreads_or(!ok)) { timed_out = true; break; }
-                phase[s] ^= 1u;
-                pending[s] = false;
+                phase[sp] ^= 1u;
+                pending[sp] = false;
             }
-            // B slices: one contiguous 32 KB block, 16-byte cp.async granules
-            const uint8_t* src = yblocks + static_cast<size_t>((tn * nkw + kw) * kSlices) * kBSlice;
-            for (int e = tid; e < kBStage / 16; e += kThreads) {
-                const unsigned dst = smem_u32(stB[s] + 16 * e);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 16 * e));
-            }
-            asm volatile("cp.async.commit_group;\n");
-            // A slices: this thread's row, two chunks of 8 K values
-#pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
-                const int c = 2 * chalf + cc;
-                double x[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int k = kw * kKW + 8 * c + i;
-                    x[i] = (myrow < m && k < K) ? X[myrow * ldx + k] : 0.0;
-                }
-                slice_store8(x, E, stA[s] + core_off(lr, 16 * c), kASlice);
-            }
-            asm volatile("cp.async.wait_all;\n" ::: "memory");
-            fence_async_smem();
-            tc_before_sync();
-            __syncthreads();
             tc_after_sync();
-            if (tid == 0) {
-                issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), kBSlice, (kw & 3) == 0);
-                mma_commit(&mbar[s]);
-            }
-            pending[s] = true;
-            if (windowed && (kw & 3) == 3 && kw < nkw - 1) {
-                // end of an exactness window that is not the last: drain into the int64 accumulators
-                for (int q = 0; q < 2 && !timed_out; ++q)
-                    if (pending[q]) {
-                        const bool ok = mbar_wait(&mbar[q], phase[q]);
-                        if (__syncthreads_or(!ok)) { timed_out = true; break; }
-                        phase[q] ^= 1u;
-                        pending[q] = false;
-                    }
-                if (timed_out) break;
-                tc_after_sync();
-                drain_acc<true>(tmem, warp, 32 * chalf, acc);
-                tc_before_sync();
-                __syncthreads();
+            if (kw == 0) {
+                gemm_drain_tile<SUB, WIN, NC>(tmem, warp, rq, cur_row, cur_tn, cur_E, N, yexp, B, ldb, C, ldc, m,
+                                              acc);
+#pragma unroll
+                for (int j = 0; j < NC; ++j) acc[j] = 0;
+            } else if (WIN) {
+                drain_acc<true>(tmem, warp, NC * rq, acc);
             }
         }
-        if (timed_out) break;
-        // all MMAs of the tile done
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+        if (kw == 0) {
+            cur_row = row;
+            cur_tn = tn;
+            cur_E = E;
+        }
+        if (tid == 0) {
+            issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), kBSlice, new_window);
+            mma_commit(&mbar[s]);
+        }
+        pending[s] = true;
+    }
+    // the last tile
+    if (!timed_out && nstages > 0) {
         for (int s = 0; s < 2 && !timed_out; ++s)
             if (pending[s]) {
                 const bool ok = mbar_wait(&mbar[s], phase[s]);
@@ -382,58 +469,10 @@ k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int
                 phase[s] ^= 1u;
                 pending[s] = false;
             }
-        if (timed_out) break;
-        tc_after_sync();
-        if (windowed) {
-            drain_acc<true>(tmem, warp, 32 * chalf, acc);
-            if (myrow < m) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = tn * kTileN + 32 * chalf + j;
-                    if (col < N) {
-                        const int ey = yexp[col];
-                        const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(acc[j], E + ey - 53) : 0.0;
-                        if (SUB) C[myrow * ldc + col] = B[myrow * ldb + col] - v;
-                        else C[myrow * ldc + col] = v;
-                    }
-                }
-            }
+        if (!timed_out) {
+            tc_after_sync();
+            gemm_drain_tile<SUB, WIN, NC>(tmem, warp, rq, cur_row, cur_tn, cur_E, N, yexp, B, ldb, C, ldc, m, acc);
         }
-        // drain: lane = output row; this warp's 32 columns in chunks of 8
-#pragma unroll 1
-        for (int c0 = 32 * chalf; c0 < 32 * chalf + 32 && !windowed; c0 += 8) {
-            double bv[8];
-            if (SUB) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int col = tn * kTileN + c0 + j;
-                    bv[j] = (myrow < m && col < N) ? B[myrow * ldb + col] : 0.0;
-                }
-            }
-            float mg[kGroups][8];
-#pragma unroll
-            for (int g = 0; g < kGroups; ++g)
-                tmem_ld8(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + g * kTileN + c0, mg[g]);
-            tmem_wait_ld();
-            if (myrow < m) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int col = tn * kTileN + c0 + j;
-                    if (col < N) {
-                        float grp[kGroups];
-#pragma unroll
-                        for (int g = 0; g < kGroups; ++g) grp[g] = mg[g][j];
-                        const long long I = combine_units53(grp);
-                        const int ey = yexp[col];
-                        const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(I, E + ey - 53) : 0.0;
-                        if (SUB) C[myrow * ldc + col] = bv[j] - v;
-                        else C[myrow * ldc + col] = v;
-                    }
-                }
-            }
-        }
-        tc_before_sync();
-        __syncthreads();
     }
 
     if (timed_out) {
@@ -498,12 +537,12 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
     const uint32_t tmem = tslot;
 
     const int lr = tid & 127;               // TMEM lane: output row p = 128P + lr; producer column of A
-    const int chalf = tid >> 7;             // producer row chunks 2*chalf..; drain columns 32*chalf..
+    const int rq = tid >> 7;                // producer row chunk(s) kChunks*rq..; drain columns kDrainCols*rq..
     const int p = 128 * P + lr;
     const int Ep = p < n ? colexp[p] : kNoExp;
     const int qb_col = 64 * Qb + (tid & 63);          // B producer column (when B is separate)
     const int Eqb = qb_col < n ? colexp[qb_col] : kNoExp;
-    constexpr int kCols = kTileN / 2;
+    constexpr int kCols = kDrainCols;
     long long acc[kCols];
 #pragma unroll
     for (int j = 0; j < kCols; ++j) acc[j] = 0;
@@ -512,7 +551,31 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
     bool timed_out = false;
     const int64_t nstages = r1 > r0 ? (r1 - r0 + kKW - 1) / kKW : 0;
 
-    for (int64_t st = 0; st < nstages && !timed_out; ++st) {
+    // Drain the window just finished (its MMAs complete) into acc; every 64 windows, and at the end,
+    // add acc into the CTA's FP64 partial (the first flush initialises it) and clear it.
+    bool flushed = false;
+    auto drain_window = [&](bool flush) {
+        tc_after_sync();
+        drain_acc<false, kCols>(tmem, warp, kCols * rq, acc);
+        if (flush && p < np) {
+            double* out = gpart + static_cast<size_t>(rr) * np * np + static_cast<size_t>(p) * np;
+#pragma unroll
+            for (int j = 0; j < kCols; ++j) {
+                const int q = 64 * Qb + kCols * rq + j;
+                if (q < np) {
+                    const int Eq = q < n ? colexp[q] : kNoExp;
+                    const double v = (Ep > kNoExp && Eq > kNoExp) ? scale_pow2(acc[j], Ep + Eq - 49) : 0.0;
+                    out[q] = (flushed ? out[q] : 0.0) + v;
+                }
+                acc[j] = 0;
+            }
+        }
+        if (flush) flushed = true;
+    };
+
+    // Stage st is sliced into buffer st & 1 while the MMAs of stage st - 1 run; a stage that opens a
+    // window first drains the previous window (after being produced, before its MMAs are issued).
+    for (int64_t st = 0; st < nstages; ++st) {
         const int s = static_cast<int>(st & 1);
         if (pending[s]) {
             const bool ok = mbar_wait(&mbar[s], phase[s]);
@@ -522,8 +585,8 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
         }
         const int64_t k0 = r0 + st * kKW;
 #pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-            const int c = 2 * chalf + cc;
+        for (int cc = 0; cc < kChunks; ++cc) {
+            const int c = kChunks * rq + cc;
             double x[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -532,7 +595,7 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
             }
             slice_store8(x, Ep, stA[s] + core_off(lr, 16 * c), kASlice);
         }
-        if (!b_inside) {
+        if (!b_inside && (tid >> 6) < 4) {
             const int c = tid >> 6;         // 64 columns x 4 chunks of 8 rows
             double x[8];
 #pragma unroll
@@ -543,10 +606,20 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
             slice_store8(x, Eqb, stB[s] + core_off(tid & 63, 16 * c), kBSlice);
         }
         fence_async_smem();
+        const bool first_window = (st & 3) == 0;
+        if (st > 0 && first_window) {
+            const int sp = s ^ 1;
+            if (pending[sp]) {
+                const bool ok = mbar_wait(&mbar[sp], phase[sp]);
+                if (__syncthreads_or(!ok)) { timed_out = true; break; }
+                phase[sp] ^= 1u;
+                pending[sp] = false;
+            }
+            drain_window((st & 255) == 0);   // the window ending at stage st - 1; every 64 windows flush
+        }
         tc_before_sync();
         __syncthreads();
         tc_after_sync();
-        const bool first_window = (st & 3) == 0;
         if (tid == 0) {
             if (b_inside)
                 issue_stage(tmem, smem_u32(stA[s]), smem_u32(stA[s]) + ((64 * Qb - 128 * P) / 8) * kSBO, kASlice,
@@ -556,34 +629,16 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
             mma_commit(&mbar[s]);
         }
         pending[s] = true;
-        const bool flush = ((st & 255) == 255) || st == nstages - 1;   // every 64 windows and at the end
-        if ((st & 3) == 3 || st == nstages - 1) {
-            for (int q = 0; q < 2 && !timed_out; ++q)
-                if (pending[q]) {
-                    const bool ok = mbar_wait(&mbar[q], phase[q]);
-                    if (__syncthreads_or(!ok)) { timed_out = true; break; }
-                    phase[q] ^= 1u;
-                    pending[q] = false;
-                }
-            if (timed_out) break;
-            tc_after_sync();
-            drain_acc<false>(tmem, warp, kCols * chalf, acc);
-            if (flush && p < np) {
-                double* out = gpart + static_cast<size_t>(rr) * np * np + static_cast<size_t>(p) * np;
-#pragma unroll
-                for (int j = 0; j < kCols; ++j) {
-                    const int q = 64 * Qb + kCols * chalf + j;
-                    if (q < np) {
-                        const int Eq = q < n ? colexp[q] : kNoExp;
-                        const double v = (Ep > kNoExp && Eq > kNoExp) ? scale_pow2(acc[j], Ep + Eq - 49) : 0.0;
-                        out[q] = (st < 256 ? 0.0 : out[q]) + v;   // first flush initialises the slot
-                    }
-                    acc[j] = 0;
-                }
+    }
+    if (!timed_out && nstages > 0) {
+        for (int q = 0; q < 2 && !timed_out; ++q)
+            if (pending[q]) {
+                const bool ok = mbar_wait(&mbar[q], phase[q]);
+                if (__syncthreads_or(!ok)) { timed_out = true; break; }
+                phase[q] ^= 1u;
+                pending[q] = false;
             }
-            tc_before_sync();
-            __syncthreads();
-        }
+        if (!timed_out) drain_window(true);
     }
 
     if (timed_out) {
@@ -593,7 +648,7 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
     } else if (nstages == 0 && p < np) {
         double* out = gpart + static_cast<size_t>(rr) * np * np + static_cast<size_t>(p) * np;
         for (int j = 0; j < kCols; ++j) {
-            const int q = 64 * Qb + kCols * chalf + j;
+            const int q = 64 * Qb + kCols * rq + j;
             if (q < np) out[q] = 0.0;
         }
     }
@@ -658,7 +713,8 @@ cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int3
                     : (win ? oz::k_ozaki_gemm<false, true> : oz::k_ozaki_gemm<false, false>);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (err != cudaSuccess) return err;
-    kern<<<grid, oz::kThreads, smem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb, C, ldc, m, info);
+    kern<<<grid, win ? oz::kThreadsWin : oz::kThreads, smem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb, C,
+                                                                  ldc, m, info);
     return cudaGetLastError();
 }
 
