@@ -83,7 +83,8 @@ def _load():
         lib.oracle_smooth_order.restype = I64
         lib.oracle_rademacher.argtypes = [U64, U64, I64, P]
         lib.oracle_smooth_rows.argtypes = [P, I64, I64, I64, P, I64, P, I64, P]
-        lib.oracle_smoothed_sample.argtypes = [P, I64, I64, I64, I64, U64, U64, P, P]
+        lib.oracle_smoothed_sample.argtypes = [P, I64, I64, I64, I64, U64, U64, I, P, P]
+        lib.oracle_smooth_rows_dct.argtypes = [P, I64, I64, I64, P, I64, P, I64, P]
         _lib = lib
         return lib
 
@@ -173,7 +174,7 @@ def triu_mul(R2, Rs, variant: int = 0) -> np.ndarray:
 
 def rpcholqr(A, s: int, seed: int, stream: int = 0, variant: int = 0, intermediates=False, smoothing: int = 0):
     """rpCholesky-QR of A (m x n).  Returns dict with Q, R, status, pivot (+ idx, Rs, A1, G1, R1).
-    smoothing = 1 samples the Walsh-Hadamard smoothed F A instead of A (Algorithm alg_2, line 2)."""
+    smoothing = 1 / 2 samples the Walsh-Hadamard / cosine smoothed F A instead of A (Algorithm alg_2)."""
     A = _f64(A)
     m, n = A.shape
     Q = np.zeros((m, n))
@@ -218,13 +219,29 @@ def smooth_rows(A, d, rows) -> np.ndarray:
     return out
 
 
-def smoothed_sample(A, s: int, seed: int, stream: int = 0):
-    """(A_s, idx): the s-row sample of the smoothed F A, scaled by sqrt(m'/s)."""
+def smooth_rows_dct(A, d, rows) -> np.ndarray:
+    """Rows `rows` of F_T D [A; 0] with F_T the orthonormal DCT-II of order m'."""
+    A = _f64(A)
+    m, n = A.shape
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    d = _f64(d)
+    out = np.zeros((rows.shape[0], n))
+    _load().oracle_smooth_rows_dct(_ptr(A), m, n, n, _ptr(d), smooth_order(m), _ptr(rows), rows.shape[0],
+                                   _ptr(out))
+    return out
+
+
+SMOOTH_WHT, SMOOTH_DCT = 1, 2
+
+
+def smoothed_sample(A, s: int, seed: int, stream: int = 0, kind: int = SMOOTH_WHT):
+    """(A_s, idx): the s-row sample of the smoothed F A (kind 1 Walsh-Hadamard, 2 cosine), scaled by
+    sqrt(m'/s)."""
     A = _f64(A)
     m, n = A.shape
     idx = np.zeros(s, dtype=np.int64)
     As = np.zeros((s, n))
-    _load().oracle_smoothed_sample(_ptr(A), m, n, n, s, seed, stream, _ptr(idx), _ptr(As))
+    _load().oracle_smoothed_sample(_ptr(A), m, n, n, s, seed, stream, kind, _ptr(idx), _ptr(As))
     return As, idx
 
 

@@ -324,14 +324,39 @@ void oracle_smooth_rows(const double* A, int64_t m, int64_t n, int64_t lda, cons
     }
 }
 
-/* The smoothed sample A_s = sqrt(m'/c) (F A)(idx, :), idx drawn from [0, m') (key (seed, stream)). */
+/* The discrete cosine transform (the paper's MATLAB dct, Remark r_exp) as F_T: the orthonormal DCT-II
+ * of order m', F_T[k][i] = w_k cos(pi (2i + 1) k / (2 m')), w_0 = sqrt(1/m'), w_k = sqrt(2/m') for
+ * k > 0, on D [A; 0].  out (nrows x n) = rows `rows`, each a plain sum over i < m; the cosine argument
+ * is reduced exactly as the integer (2i + 1) k mod 4m' before it is scaled by pi / (2m'). */
+void oracle_smooth_rows_dct(const double* A, int64_t m, int64_t n, int64_t lda, const double* d, int64_t mp,
+                            const int64_t* rows, int64_t nrows, double* out) {
+    const double pi = 3.14159265358979323846;
+    #pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < nrows; ++j) {
+        const uint64_t k = (uint64_t)rows[j];
+        const double w = k == 0 ? sqrt(1.0 / (double)mp) : sqrt(2.0 / (double)mp);
+        double* o = out + j * n;
+        for (int64_t c = 0; c < n; ++c) o[c] = 0.0;
+        for (int64_t i = 0; i < m; ++i) {
+            const uint64_t r = ((2 * (uint64_t)i + 1) * k) % (4 * (uint64_t)mp);
+            const double cs = cos(pi * (double)r / (2.0 * (double)mp)) * d[i];
+            const double* a = A + i * lda;
+            for (int64_t c = 0; c < n; ++c) o[c] += cs * a[c];
+        }
+        for (int64_t c = 0; c < n; ++c) o[c] *= w;
+    }
+}
+
+/* The smoothed sample A_s = sqrt(m'/c) (F A)(idx, :), idx drawn from [0, m') (key (seed, stream));
+ * kind 1: Walsh-Hadamard F_T, kind 2: cosine F_T. */
 void oracle_smoothed_sample(const double* A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
-                            uint64_t stream, int64_t* idx, double* As) {
+                            uint64_t stream, int kind, int64_t* idx, double* As) {
     const int64_t mp = oracle_smooth_order(m);
     double* d = (double*)malloc(sizeof(double) * (size_t)m);
     oracle_rademacher(seed, stream + 1, m, d);
     oracle_sample_indices(seed, stream, mp, s, idx);
-    oracle_smooth_rows(A, m, n, lda, d, mp, idx, s, As);
+    if (kind == 2) oracle_smooth_rows_dct(A, m, n, lda, d, mp, idx, s, As);
+    else oracle_smooth_rows(A, m, n, lda, d, mp, idx, s, As);
     const double scale = sqrt((double)mp / (double)s);
     for (int64_t e = 0; e < s * n; ++e) As[e] *= scale;
     free(d);
@@ -339,7 +364,8 @@ void oracle_smoothed_sample(const double* A, int64_t m, int64_t n, int64_t lda, 
 
 /* ---------------------------------------------------------------------------------------------
  * rpCholesky-QR (Algorithm alg_2, Section 4).  Q: m x n (ldq), R: n x n.  smoothing = 0: A_s = S A;
- * 1: A_s = S F A with the Walsh-Hadamard smoothing above (idx then indexes the m' rows of F A).
+ * 1 / 2: A_s = S F A with the Walsh-Hadamard / cosine smoothing above (idx then indexes the m' rows
+ * of F A).
  * Optional outputs (may be NULL): idx (s), Rs (n x n), A1 (m x n, ld n), G1 (n x n), R1 (n x n).
  * Status order: ARG, NONFINITE (a sampled row; with smoothing any row, since every row enters the
  * sample), SINGULAR_SKETCH, NONFINITE (any row), NOT_SPD.
@@ -349,7 +375,7 @@ int oracle_rpcholqr(const double* A, int64_t m, int64_t n, int64_t lda, int64_t 
                     double* Rs_out, double* A1_out, double* G1_out, double* R1_out,
                     int64_t* pivot, int variant, int smoothing) {
     if (pivot) *pivot = -1;
-    if (n < 1 || s < n || m < s || lda < n || ldq < n || smoothing < 0 || smoothing > 1) return ORC_ERR_ARG;
+    if (n < 1 || s < n || m < s || lda < n || ldq < n || smoothing < 0 || smoothing > 2) return ORC_ERR_ARG;
     size_t nn = (size_t)n * (size_t)n;
     int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)s);
     double* As = (double*)malloc(sizeof(double) * (size_t)s * (size_t)n);
@@ -361,7 +387,7 @@ int oracle_rpcholqr(const double* A, int64_t m, int64_t n, int64_t lda, int64_t 
 
     if (smoothing) {
         if (!orc_all_finite(A, m, n, lda)) { status = ORC_ERR_NONFINITE; goto done; }
-        oracle_smoothed_sample(A, m, n, lda, s, seed, stream, idx, As);
+        oracle_smoothed_sample(A, m, n, lda, s, seed, stream, smoothing, idx, As);
     } else {
         oracle_sample_indices(seed, stream, m, s, idx);
         oracle_gather_scale(A, m, n, lda, idx, s, As);

@@ -37,6 +37,10 @@ MUTATIONS = {
     "smoothing order one too large": ("while (p < m) p <<= 1;", "while (p <= m) p <<= 1;"),
     "smoothed sample scale uses m": ("const double scale = sqrt((double)mp / (double)s);",
                                      "const double scale = sqrt((double)m / (double)s);"),
+    "dct first-row weight": ("const double w = k == 0 ? sqrt(1.0 / (double)mp) : sqrt(2.0 / (double)mp);",
+                             "const double w = sqrt(2.0 / (double)mp);"),
+    "dct half-sample shift dropped": ("const uint64_t r = ((2 * (uint64_t)i + 1) * k) % (4 * (uint64_t)mp);",
+                                      "const uint64_t r = ((2 * (uint64_t)i) * k) % (4 * (uint64_t)mp);"),
 }
 
 

@@ -116,3 +116,49 @@ def test_smoothing_reports_nonfinite_anywhere(oracle_mod):
     A = inputs.usv(500, 4, 10.0, 1)
     A[123, 2] = np.nan
     assert oracle_mod.rpcholqr(A, 12, 1, smoothing=1)["status"] == oracle_mod.ERR_NONFINITE
+
+
+# ---- the cosine transform (Remark r_exp uses MATLAB's dct) ----------------------------------------------
+@pytest.mark.parametrize("mp", [1, 2, 8, 64, 1024])
+def test_dct_rows_are_scipy_orthonormal_dct(oracle_mod, mp):
+    import scipy.fft
+    d = oracle_mod.rademacher(6, 1, mp)
+    F = oracle_mod.smooth_rows_dct(np.eye(mp), d, np.arange(mp))
+    ref = scipy.fft.dct(np.diag(d), type=2, norm="ortho", axis=0)
+    assert np.max(np.abs(F - ref)) <= 4 * np.finfo(float).eps
+
+
+def test_dct_is_orthogonal_and_pads_with_zeros(oracle_mod):
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((300, 6))
+    d = oracle_mod.rademacher(8, 1, 300)
+    FA = oracle_mod.smooth_rows_dct(A, d, np.arange(512))
+    G = A.T @ A
+    assert np.linalg.norm(FA.T @ FA - G, 2) <= 1e-13 * np.linalg.norm(G, 2)
+    Ap = np.vstack([A, np.zeros((212, 6))])
+    dp = np.concatenate([d, oracle_mod.rademacher(5, 1, 212)])
+    assert np.array_equal(oracle_mod.smooth_rows_dct(Ap, dp, np.arange(512)), FA)
+
+
+def test_dct_smoothed_sample(oracle_mod):
+    rng = np.random.default_rng(9)
+    m, n, s, seed = 700, 5, 15, 4
+    A = rng.standard_normal((m, n))
+    As, idx = oracle_mod.smoothed_sample(A, s, seed, kind=oracle_mod.SMOOTH_DCT)
+    assert np.array_equal(idx, oracle_mod.sample_indices(seed, 1024, s))
+    rows = oracle_mod.smooth_rows_dct(A, oracle_mod.rademacher(seed, 1, m), idx)
+    assert np.array_equal(As, rows * np.sqrt(1024 / s))
+
+
+def test_dct_smoothing_section_5_1_at_c_2n(oracle_mod):
+    # with the cosine transform even c = 2n gives deviation from orthonormality below 1e-12
+    # (Section 5.1, Figure fig_ErrorRange3); the Walsh-Hadamard rows restricted to the first n
+    # columns repeat with period 2^ceil(log2 n), which c = 2n draws do not reliably cover
+    g = GOLD["section_5_1"]
+    m, n, kappa = g["workload"]["m"], g["workload"]["n"], g["workload"]["kappa"]
+    A = inputs.coherent_randsvd(m, n, kappa, 5)
+    for seed in (1, 2, 3):
+        o = oracle_mod.rpcholqr(A, 2 * n, seed, smoothing=oracle_mod.SMOOTH_DCT)
+        assert o["status"] == 0
+        assert oracle_mod.orth_error(o["Q"]) <= g["orthogonality_c_2n"]["value"]
+        assert oracle_mod.residual(A, o["Q"], o["R"]) <= 10 * g["residual"]["value"]
