@@ -62,8 +62,8 @@ def parse_args():
                     help="workload shapes: small m=10000 n=50 kappa=1e8; headline m=2^20 n=128 kappa=1e8 "
                          "(the default); precision m=2^22 n=256 kappa=1e12; large m=2^23 n=512 "
                          "sigma to 1e-18")
-    ap.add_argument("--smoothing", action="store_true",
-                    help="sample the Walsh-Hadamard smoothed F A (Algorithm alg_2 with F = F_T D)")
+    ap.add_argument("--smoothing", choices=["none", "wht", "dct"], default="none",
+                    help="sample the smoothed F A (Algorithm alg_2 with F = F_T D): Walsh-Hadamard or cosine F_T")
     ap.add_argument("--count", type=int, default=512, help="matrices in the batch workload")
     ap.add_argument("--slots", type=int, default=16, help="concurrent slots the batch autotuner may use")
     ap.add_argument("--no-compare", action="store_true",
@@ -322,8 +322,8 @@ def run_ours(args, ws, rank, local):
     def timed(mode, clocks):
         """W warm-up + K timed factor calls on a fresh plan of `mode`: (ms, phases, calls, launches, plan)."""
         plan = rq.rpcholqr_plan_create(local, m, n, s, mode=modes[mode])
-        if args.smoothing:
-            rq.rpcholqr_plan_set_smoothing(plan, rq.SMOOTH_WHT)
+        if args.smoothing != "none":
+            rq.rpcholqr_plan_set_smoothing(plan, rq.SMOOTH_WHT if args.smoothing == "wht" else rq.SMOOTH_DCT)
         for w in range(W):
             factor(plan, mode, 1 + w)
         torch.cuda.synchronize(dev)
@@ -466,8 +466,8 @@ def run_ours(args, ws, rank, local):
         "dtype": {"fp64": "f64", "split": "f64+bf16", "fp32": "f32+f64"}[args.mode],
         "data": "synthetic (A = U diag(sigma) V^T, Haar U/V from torch, sigma log-spaced)",
         "config": {"workload": f"rpCholesky-QR {args.mode.upper()} m={m} n={n} s={s} kappa={args.kappa:g}"
-                               + (" smoothing=WHT" if args.smoothing else ""), "m": m,
-                   "n": n, "s": s, "kappa": args.kappa, "mode": args.mode, "smoothing": bool(args.smoothing),
+                               + ("" if args.smoothing == "none" else f" smoothing={args.smoothing.upper()}"), "m": m,
+                   "n": n, "s": s, "kappa": args.kappa, "mode": args.mode, "smoothing": args.smoothing,
                    "l2": f"inputs larger than L2 (A = {8 * m * n / 1e9:.2f} GB > 129 MB), no flush"},
         "effective_tflops": flops * value / 1e12,
         "orth": orth, "residual": res, "gate_orth_le_1e-13": None if orth is None else bool(orth <= 1e-13),

@@ -67,7 +67,7 @@ typedef enum {
                             block update of the row solve (n > 64) and Q = A1 R1^{-1} (explicit
                             inverse of the well-conditioned R1) as Ozaki-split BF16 tensor-core
                             (tcgen05) products with exact FP32 group sums and int64 combination.
-                            Q = A1 R1^{-1} takes that path only while ||R1||_F ||R1^{-1}||_F / n <= 4
+                            Q = A1 R1^{-1} takes that path only while ||R1||_F ||R1^{-1}||_F / n <= 2
                             (A1 well conditioned, as for incoherent or smoothed A); otherwise an FP64
                             row-wise substitution keeps the residual at the FP64 level (decided on
                             the device, see rpcholqr_plan_split_pass2_fp64).
@@ -224,16 +224,20 @@ rpcholqr_status rpcholqr_plan_split_pass2_fp64(rpcholqr_plan plan, int32_t* used
 /* ---- smoothing F = F_T D before sampling ----
  * Algorithm alg_2 samples rows of F A, F = F_T D (the Blendenpik remark of Section 4; Remark r_exp).
  * kind 0 (the default): F = I, rows of A are sampled directly.  kind 1: F_T is the orthogonal
- * Walsh-Hadamard transform of order m' = 2^ceil(log2 m) (natural order) acting on A padded with zero
- * rows, D_ii = -1 when bit 63 of Philox word (i mod 4) of block i/4 under key (seed, 1) is set, the
- * s sampled rows are drawn from [0, m') and scaled by sqrt(m'/s).  Needed for coherent A (rows of A
- * carrying most of its column space, e.g. [R_A; 0]), whose unsmoothed sample is singular.  Costs two
- * extra passes over an m' x n buffer the plan allocates here (8 m' pad8(max_n) bytes for m' of max_m);
+ * Walsh-Hadamard transform of order m' = 2^ceil(log2 m) (natural order); kind 2: the orthonormal
+ * DCT-II of order m' (MATLAB's dct, which Remark r_exp uses).  Both act on A padded with zero rows;
+ * D_ii = -1 when bit 63 of Philox word (i mod 4) of block i/4 under key (seed, 1) is set; the s sampled
+ * rows are drawn from [0, m') and scaled by sqrt(m'/s).  Needed for coherent A (rows of A carrying
+ * most of its column space, e.g. [R_A; 0]), whose unsmoothed sample is singular.  The Walsh-Hadamard
+ * rows restricted to the first n columns repeat with period 2^ceil(log2 n), so on such inputs it needs
+ * s >~ n ln n samples; the cosine rows are all distinct.  Costs two extra passes over an m' x n buffer
+ * the plan allocates here (8 m' pad8(max_n) bytes for m' of max_m, twice that for the cosine);
  * m' <= 2^25.  Applies to rpcholqr_factor, rpcholqr_factor_f32, rpcholqr_factor_host and
  * rpcholqr_sketch_r on this plan.  Errors: ARG (kind), UNSUPPORTED (max_m > 2^25), NOMEM. */
 rpcholqr_status rpcholqr_plan_set_smoothing(rpcholqr_plan plan, int32_t kind);
 
-/* The smoothed sample alone: As (device, s x n row-major, ld ld_as) = sqrt(m'/s) (F A)(idx, :).
+/* The smoothed sample alone (the plan's kind): As (device, s x n row-major, ld ld_as) =
+ * sqrt(m'/s) (F A)(idx, :).
  * The plan must have smoothing enabled (ERR_ARG otherwise).  info as in rpcholqr_factor
  * (NONFINITE for any non-finite entry of A: every row enters the sample). */
 rpcholqr_status rpcholqr_smoothed_sample(rpcholqr_plan plan, const double* A, int64_t m, int32_t n, int64_t lda,

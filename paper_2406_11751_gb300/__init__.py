@@ -23,7 +23,7 @@ __all__ = [
     "rpcholqr_batch_create", "rpcholqr_batch_destroy", "rpcholqr_factor_batched", "rpcholqr_batch_capture",
     "rpcholqr_batch_replay", "rpcholqr_batch_autotune", "FP32", "rpcholqr_factor_f32",
     "rpcholqr_gather_owned_rows", "rpcholqr_sketch_r_from_sample", "rpcholqr_sum_partials",
-    "rpcholqr_plan_set_smoothing", "rpcholqr_smoothed_sample", "SMOOTH_NONE", "SMOOTH_WHT",
+    "rpcholqr_plan_set_smoothing", "rpcholqr_smoothed_sample", "SMOOTH_NONE", "SMOOTH_WHT", "SMOOTH_DCT",
     "rpcholqr_plan_split_pass2_fp64",
 ]
 
@@ -33,7 +33,7 @@ OK, ERR_ARG, ERR_NONFINITE, ERR_SINGULAR_SKETCH, ERR_NOT_SPD = 0, 1, 2, 3, 4
 FP64 = 0
 SPLIT64 = 1
 FP32 = 2
-SMOOTH_NONE, SMOOTH_WHT = 0, 1
+SMOOTH_NONE, SMOOTH_WHT, SMOOTH_DCT = 0, 1, 2
 MAX_N = 512
 
 EXPORTED_SYMBOLS = (
@@ -284,7 +284,7 @@ def rpcholqr_sum_partials(parts, G=None, stream=None):
 
 
 def rpcholqr_plan_set_smoothing(plan: Plan, kind: int = SMOOTH_WHT):
-    """Sample the Walsh-Hadamard smoothed F A (kind 1) or A itself (kind 0) on this plan."""
+    """Sample the smoothed F A (kind 1 Walsh-Hadamard, 2 cosine) or A itself (kind 0) on this plan."""
     _check("rpcholqr_plan_set_smoothing", load_library().rpcholqr_plan_set_smoothing(plan.handle, kind))
 
 

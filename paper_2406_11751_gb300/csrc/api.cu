@@ -86,6 +86,13 @@ cudaError_t launch_smoothed_sample_f32(const float* A, int64_t m, int n, int64_t
                                        cudaStream_t st);
 void launch_colmajor_to_rows(const double* src, int64_t lds, int s, int n, double* dst, int64_t ldd,
                              cudaStream_t st);
+size_t smooth_dct_buffer_bytes(int64_t max_m, int max_n);
+cudaError_t launch_dct_sample(const double* A, int64_t m, int n, int64_t lda, int s, uint64_t seed, void* T,
+                              int8_t* sgn, int64_t* idx, double* As, int64_t lds, int np, int32_t* info,
+                              cudaStream_t st);
+cudaError_t launch_dct_sample_f32(const float* A, int64_t m, int n, int64_t lda, int s, uint64_t seed, void* T,
+                                  int8_t* sgn, int64_t* idx, double* As, int64_t lds, int np, int32_t* info,
+                                  cudaStream_t st);
 void launch_pass2_gate(const double* R1, const double* W, int n, int np, double tau, const int32_t* info,
                        int32_t* gates, cudaStream_t st);
 void launch_gate_merge(int32_t* info, const int32_t* gates, cudaStream_t st);
@@ -135,10 +142,12 @@ struct rpcholqr_plan_s {
     float* T32 = nullptr;       // pad32(max_n)^2: R_s or R1 in FP32, identity-padded
     float* rinv32 = nullptr;    // pad32(max_n)
     // smoothing (allocated by rpcholqr_plan_set_smoothing)
-    int32_t smoothing = 0;
+    int32_t smoothing = 0;          // 0 none, 1 Walsh-Hadamard, 2 cosine
+    int32_t smooth_capacity = 0;    // the largest kind the buffers below were sized for
     void* smooth_ws = nullptr;
-    double* smooth_T = nullptr;     // Walsh-Hadamard transform buffer, 8-column blocks of m' rows
+    double* smooth_T = nullptr;     // transform buffer, 8-column blocks of m' rows (complex for the cosine)
     int64_t* smooth_idx = nullptr;  // max_s sample rows of F A
+    int8_t* smooth_sgn = nullptr;   // max_m Rademacher signs (cosine transform)
 };
 
 namespace {
@@ -222,13 +231,37 @@ constexpr int kBlk = 64;   // column block of the FP64 blocked solves (n > 128)
 // the solve runs as split tensor-core updates.
 constexpr int kSplitBlk = 32;
 // Split mode: the explicit-inverse second pass is used while ||R1||_F ||R1^{-1}||_F / n <= this
-// (about 1.2 for well-sampled incoherent A; the estimate lies in [kappa(A1)/n, kappa(A1)]).
-constexpr double kSplitPass2Tau = 4.0;
+// (1.1-1.25 for well-sampled incoherent A; the estimate lies in [kappa(A1)/n, kappa(A1)]; at 3.3
+// (kappa(A1) ~ 30) the explicit inverse already costs 10x in residual).
+constexpr double kSplitPass2Tau = 2.0;
 
 // CTAs of a row pass over m rows: one per 128-row panel, at most one per SM.
 int row_grid(const rpcholqr_plan_s* p, int64_t m) {
     const int64_t panels = (m + 127) / 128;
     return static_cast<int>(panels < p->grid ? panels : p->grid);
+}
+
+// The smoothed sample of the plan's kind into p->As (column-major, ld s, np columns).
+template <typename TA>
+cudaError_t plan_smoothed_sample(rpcholqr_plan_s* p, const TA* A, int64_t m, int n, int64_t lda, int s,
+                                 uint64_t seed, int np, int32_t* info, cudaStream_t st);
+template <>
+cudaError_t plan_smoothed_sample<double>(rpcholqr_plan_s* p, const double* A, int64_t m, int n, int64_t lda, int s,
+                                         uint64_t seed, int np, int32_t* info, cudaStream_t st) {
+    p->launches += 3;
+    if (p->smoothing == 2)
+        return launch_dct_sample(A, m, n, lda, s, seed, p->smooth_T, p->smooth_sgn, p->smooth_idx, p->As, s, np,
+                                 info, st);
+    return launch_smoothed_sample(A, m, n, lda, s, seed, p->smooth_T, p->smooth_idx, p->As, s, np, info, st);
+}
+template <>
+cudaError_t plan_smoothed_sample<float>(rpcholqr_plan_s* p, const float* A, int64_t m, int n, int64_t lda, int s,
+                                        uint64_t seed, int np, int32_t* info, cudaStream_t st) {
+    p->launches += 3;
+    if (p->smoothing == 2)
+        return launch_dct_sample_f32(A, m, n, lda, s, seed, p->smooth_T, p->smooth_sgn, p->smooth_idx, p->As, s,
+                                     np, info, st);
+    return launch_smoothed_sample_f32(A, m, n, lda, s, seed, p->smooth_T, p->smooth_idx, p->As, s, np, info, st);
 }
 
 void free_events(rpcholqr_plan_s* p) {
@@ -383,10 +416,8 @@ static rpcholqr_status sketch_internal(rpcholqr_plan p, const double* A, int64_t
     if (pm) pm->mark(RPCHOLQR_PHASE_SAMPLE);
     const int64_t lds = s;
     if (p->smoothing) {
-        if (launch_smoothed_sample(A, m, n, lda, s, seed, p->smooth_T, p->smooth_idx, p->As, lds, np, info, st) !=
-            cudaSuccess)
+        if (plan_smoothed_sample<double>(p, A, m, n, lda, s, seed, np, info, st) != cudaSuccess)
             return RPCHOLQR_ERR_CUDA;
-        p->launches += 3;
     } else {
         launch_sample_gather(A, m, n, lda, s, seed, stream_id, scale, p->As, lds, np, nullptr, info, st);
         ++p->launches;
@@ -721,10 +752,8 @@ rpcholqr_status rpcholqr_factor_f32(rpcholqr_plan p, const float* A, int64_t m, 
     pm.mark(RPCHOLQR_PHASE_SAMPLE);
     const double scale = std::sqrt(static_cast<double>(m) / static_cast<double>(s));
     if (p->smoothing) {
-        if (launch_smoothed_sample_f32(A, m, n, lda, s, seed, p->smooth_T, p->smooth_idx, p->As, s, np, info,
-                                       st) != cudaSuccess)
+        if (plan_smoothed_sample<float>(p, A, m, n, lda, s, seed, np, info, st) != cudaSuccess)
             return RPCHOLQR_ERR_CUDA;
-        p->launches += 3;
     } else {
         launch_sample_gather_f32(A, m, n, lda, s, seed, 0, scale, p->As, s, np, nullptr, info, st);
         ++p->launches;
@@ -1033,20 +1062,30 @@ rpcholqr_status rpcholqr_sum_partials(const double* parts, int32_t nparts, int32
 }
 
 rpcholqr_status rpcholqr_plan_set_smoothing(rpcholqr_plan p, int32_t kind) {
-    if (!p || kind < 0 || kind > 1) return RPCHOLQR_ERR_ARG;
-    if (kind == 1 && !p->smooth_ws) {
+    if (!p || kind < 0 || kind > 2) return RPCHOLQR_ERR_ARG;
+    if (kind > p->smooth_capacity) {
         if (!smooth_supported(p->max_m)) return RPCHOLQR_ERR_UNSUPPORTED;
         DeviceGuard guard(p->device);
         if (!guard.ok) return RPCHOLQR_ERR_CUDA;
-        const size_t tb = align256(smooth_buffer_bytes(p->max_m, p->max_n));
-        const size_t total = tb + sizeof(int64_t) * static_cast<size_t>(p->max_s);
-        if (cudaMalloc(&p->smooth_ws, total) != cudaSuccess) {
+        const size_t tb = align256(kind == 2 ? smooth_dct_buffer_bytes(p->max_m, p->max_n)
+                                             : smooth_buffer_bytes(p->max_m, p->max_n));
+        const size_t ib = align256(sizeof(int64_t) * static_cast<size_t>(p->max_s));
+        const size_t total = tb + ib + static_cast<size_t>(p->max_m);
+        void* ws = nullptr;
+        cudaStreamSynchronize(nullptr);
+        if (cudaMalloc(&ws, total) != cudaSuccess) {
             cudaGetLastError();
-            p->smooth_ws = nullptr;
             return RPCHOLQR_ERR_NOMEM;
         }
-        p->smooth_T = static_cast<double*>(p->smooth_ws);
-        p->smooth_idx = reinterpret_cast<int64_t*>(static_cast<char*>(p->smooth_ws) + tb);
+        if (p->smooth_ws) {
+            cudaDeviceSynchronize();
+            cudaFree(p->smooth_ws);
+        }
+        p->smooth_ws = ws;
+        p->smooth_T = static_cast<double*>(ws);
+        p->smooth_idx = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + tb);
+        p->smooth_sgn = reinterpret_cast<int8_t*>(static_cast<char*>(ws) + tb + ib);
+        p->smooth_capacity = kind;
         p->ws_bytes += total;
     }
     p->smoothing = kind;
@@ -1065,9 +1104,7 @@ rpcholqr_status rpcholqr_smoothed_sample(rpcholqr_plan p, const double* A, int64
     rpcholqr_status rc = reset_info(info, st);
     if (rc != RPCHOLQR_OK) return rc;
     const int np = pad_np(n);
-    if (launch_smoothed_sample(A, m, n, lda, s, seed, p->smooth_T, p->smooth_idx, p->As, s, np, info, st) !=
-        cudaSuccess)
-        return RPCHOLQR_ERR_CUDA;
+    if (plan_smoothed_sample<double>(p, A, m, n, lda, s, seed, np, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
     launch_colmajor_to_rows(p->As, s, s, n, As, ld_as, st);
     return check_launch();
 }

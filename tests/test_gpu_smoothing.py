@@ -38,6 +38,17 @@ def nrm2(x):
 
 
 @pytest.fixture(scope="module")
+def dct_plans(lib):
+    ps = {"fp64": lib.rpcholqr_plan_create(0, 1 << 20, 512, 1536),
+          "split": lib.rpcholqr_plan_create(0, 1 << 20, 512, 1536, mode=lib.SPLIT64)}
+    for p in ps.values():
+        lib.rpcholqr_plan_set_smoothing(p, lib.SMOOTH_DCT)
+    yield ps
+    for p in ps.values():
+        p.close()
+
+
+@pytest.fixture(scope="module")
 def smooth_plans(lib):
     ps = {"fp64": lib.rpcholqr_plan_create(0, 1 << 20, 300, 1536),
           "split": lib.rpcholqr_plan_create(0, 1 << 20, 300, 1536, mode=lib.SPLIT64),
@@ -143,3 +154,48 @@ def test_smoothing_toggles_and_rejects(lib):
         assert not torch.equal(R0, R1)
     finally:
         p.close()
+
+
+# ---- the cosine transform (Remark r_exp) -------------------------------------------------------------
+@pytest.mark.parametrize("m,n,s", [(1, 1, 1), (3, 2, 2), (1000, 7, 21), (2048, 8, 24), (4097, 17, 51),
+                                   (70000, 50, 150), ((1 << 20) - 3, 128, 384), (9000, 300, 900)])
+def test_dct_sample_matches_oracle(lib, oracle_mod, dct_plans, m, n, s):
+    rng = np.random.default_rng(m + 3 * n)
+    A = rng.standard_normal((m, n)) * 10.0 ** rng.uniform(-2, 2, size=(1, n))
+    As, info = lib.rpcholqr_smoothed_sample(dct_plans["fp64"], cu(A), s, 5)
+    assert status(info)[0] == 0
+    As_o, _ = oracle_mod.smoothed_sample(A, s, 5, kind=oracle_mod.SMOOTH_DCT)
+    p = int(np.log2(oracle_mod.smooth_order(m)))
+    # the oracle's plain sum (m terms, each with a rounded cosine) and the FFT's p stages of rounded
+    # twiddles: entrywise below (m + 8p) u sqrt(2/s) sum_i |A_ic|
+    bound = (m + 8 * p + 8) * EPS * np.sqrt(2.0 / s) * np.sum(np.abs(A), axis=0)[None, :]
+    assert np.all(np.abs(host(As) - As_o) <= bound)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+def test_dct_factor_matches_oracle(lib, oracle_mod, dct_plans, mode):
+    A = inputs.usv(30000, 128, 1e12, 77)
+    Q, R, info = lib.rpcholqr_factor(dct_plans[mode], cu(A), 384, 3)
+    assert status(info) == (0, -1)
+    o = oracle_mod.rpcholqr(A, 384, 3, smoothing=oracle_mod.SMOOTH_DCT)
+    Qh, Rh = host(Q), host(R)
+    assert nrm2(Rh - o["R"]) <= 1e-12 * nrm2(o["R"])
+    assert oracle_mod.orth_error(Qh) <= 10 * oracle_mod.orth_error(o["Q"])
+    assert oracle_mod.residual(A, Qh, Rh) <= 10 * oracle_mod.residual(A, o["Q"], o["R"])
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+def test_dct_section_5_1_at_c_2n(lib, oracle_mod, dct_plans, mode):
+    # Section 5.1 (Figure fig_ErrorRange3): with the cosine transform even c = 2n = 200 gives a
+    # deviation from orthonormality below 1e-12 and residuals near 1e-16 on the coherent inputs
+    g = GOLD["section_5_1"]
+    m, n, kappa = g["workload"]["m"], g["workload"]["n"], g["workload"]["kappa"]
+    A = inputs.coherent_randsvd(m, n, kappa, 5)
+    for seed in (1, 2, 3):
+        Q, R, info = lib.rpcholqr_factor(dct_plans[mode], cu(A), 2 * n, seed)
+        assert status(info) == (0, -1)
+        Qh, Rh = host(Q), host(R)
+        o = oracle_mod.rpcholqr(A, 2 * n, seed, smoothing=oracle_mod.SMOOTH_DCT)
+        orth, res = oracle_mod.orth_error(Qh), oracle_mod.residual(A, Qh, Rh)
+        assert orth <= 10 * oracle_mod.orth_error(o["Q"]) and orth <= 10 * g["orthogonality_c_2n"]["value"]
+        assert res <= 10 * oracle_mod.residual(A, o["Q"], o["R"]) and res <= 10 * g["residual"]["value"]
