@@ -1,0 +1,147 @@
+"""The paper's numerical experiments (Section 5), run on the GPU at the paper's sizes (m = 6000),
+with the cosine smoothing of Remark r_exp and 10 trials (fewer at n = 512), gated on the levels the
+paper states (tests/golden/paper_accuracy_levels.json) with a 10x margin for the spread over trials:
+
+  Section 5.1, Figures fig_ErrorRange3 / fig_ErrorRange1 / fig_ErrorRangeG: maximally coherent
+      A = [R_A; 0] (Eq. e_ErrorRange, kappa = 1e15): residuals ~1e-16 for every c; orthogonality below
+      1e-12 at c = 2n, about 1e-15 and kappa(A_1) < 10 from c = 6n; at n = 1000 (here n = 512, the
+      largest width built) kappa(A_1) <= 100 and orthogonality below 1e-13 from c = 3n;
+  Section 5.2, Eq. e_ex1: orthogonality tracks 4 eps kappa(A_1);
+  Section 5.3, Figures fig_CQR2d / fig_CQR2G: Haar A with randsvd R_A (Eq. e_CQR2, kappa = 1e7):
+      rpCholesky-QR with c = 3n and Cholesky-QR2 both at residuals slightly above 1e-16 and
+      orthogonality slightly above 1e-15.
+
+The paper's levels are those of FP64 arithmetic, so they gate the FP64 mode.  The split mode runs on
+the same inputs and seeds and is gated within 10x of the FP64 mode's orthogonality and residual (its
+explicit-inverse second pass leaves A1 - Q R1 = A1 (I - R1^{-1} R1), of order u kappa(A1): about 4x
+the FP64 residual at kappa(A1) ~ 3-10).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+EPS = np.finfo(np.float64).eps
+DEV = torch.device("cuda", 0)
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_accuracy_levels.json")))
+M = 6000
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def plans(lib):
+    ps = {"fp64": lib.rpcholqr_plan_create(0, M, 512, M), "split": lib.rpcholqr_plan_create(0, M, 512, M,
+                                                                                          mode=lib.SPLIT64)}
+    for p in ps.values():
+        lib.rpcholqr_plan_set_smoothing(p, lib.SMOOTH_DCT)
+    yield ps
+    for p in ps.values():
+        p.close()
+
+
+def kappa_A1(lib, plan, A, s, seed):
+    """kappa(A_1) of the run with this (s, seed): the same R_s, A_1 = A R_s^{-1}, from its Gram matrix."""
+    Ad = cu(A)
+    Rs, _ = lib.rpcholqr_sketch_r(plan, Ad, s, seed)
+    _, G, _ = lib.rpcholqr_precondition_gram(plan, Ad, Rs)
+    w = np.linalg.eigvalsh(host(G))
+    return float(np.sqrt(w[-1] / w[0])) if w[0] > 0 else np.inf
+
+
+def run1(lib, oracle_mod, plan, A, s, seed):
+    Q, R, info = lib.rpcholqr_factor(plan, cu(A), s, seed)
+    assert info.cpu().tolist() == [0, -1]
+    Qh, Rh = host(Q), host(R)
+    return oracle_mod.orth_error(Qh), oracle_mod.residual(A, Qh, Rh)
+
+
+def run(lib, oracle_mod, plans, mode, A, s, seed):
+    """(orth, residual) of the FP64 mode; for the split mode also checks it against the FP64 mode on the
+    same input and seed and returns the FP64 mode's values for the paper-level gates."""
+    o, r = run1(lib, oracle_mod, plans["fp64"], A, s, seed)
+    if mode == "split":
+        os_, rs_ = run1(lib, oracle_mod, plans["split"], A, s, seed)
+        assert os_ <= 10 * o and rs_ <= 10 * r, (o, r, os_, rs_)
+    return o, r
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+def test_fig_error_range3_sampling_sweep(lib, oracle_mod, plans, mode):
+    g = GOLD["section_5_1"]
+    n = g["workload"]["n"]
+    A = inputs.coherent_randsvd(M, n, g["workload"]["kappa"], 11)
+    for c_over_n in (2, 3, 6, 10):
+        s = c_over_n * n
+        orths, ress, kappas = [], [], []
+        for seed in range(1, 11):
+            o, r = run(lib, oracle_mod, plans, mode, A, s, seed)
+            orths.append(o)
+            ress.append(r)
+            kappas.append(kappa_A1(lib, plans["fp64"], A, s, seed))
+        assert max(ress) <= 10 * g["residual"]["value"], (c_over_n, ress)
+        # Section 5.2: orthogonality captured by 4 eps kappa(A_1)
+        for o, k in zip(orths, kappas):
+            assert o <= 10 * 4 * EPS * k, (c_over_n, o, k)
+        if c_over_n == 2:
+            assert np.median(orths) <= g["orthogonality_c_2n"]["value"]
+            assert max(orths) <= 10 * g["orthogonality_c_2n"]["value"]
+        if c_over_n >= 6:
+            assert max(kappas) < g["kappa_A1_c_ge_6n"]["value"], kappas
+            assert max(orths) <= 10 * g["orthogonality_c_ge_6n"]["value"], orths
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+def test_fig_error_range1_wide(lib, oracle_mod, plans, mode):
+    # Figure fig_ErrorRange1 uses n = 1000; the widest panel built here is 512
+    n = 512
+    A = inputs.coherent_randsvd(M, n, 1e15, 12)
+    for c_over_n in (3, 6):
+        s = c_over_n * n
+        for seed in (1, 2):
+            o, r = run(lib, oracle_mod, plans, mode, A, s, seed)
+            k = kappa_A1(lib, plans["fp64"], A, s, seed)
+            assert k <= 100, (c_over_n, k)
+            assert o <= 10 * 1e-13, (c_over_n, o)
+            assert r <= 10 * GOLD["section_5_1"]["residual"]["value"]
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+def test_fig_error_range_g_columns(lib, oracle_mod, plans, mode):
+    g = GOLD["section_5_1"]
+    for n in (100, 256, 400):
+        A = inputs.coherent_randsvd(M, n, 1e15, 13 + n)
+        for seed in (1, 2):
+            o, r = run(lib, oracle_mod, plans, mode, A, 3 * n, seed)
+            assert o <= 10 * g["orthogonality_c_3n_all_n"]["value"], (n, o)
+            assert r <= 10 * g["residual"]["value"], (n, r)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+def test_fig_cqr2_against_cholesky_qr2(lib, oracle_mod, plans, mode):
+    g = GOLD
+    for n in (100, 256, 400):
+        A = inputs.usv(M, n, g["workload"]["kappa"], 31 + n)      # Eq. e_CQR2: Haar Q_A, randsvd R_A
+        Q2, R2, info = lib.rpcholqr_cholqr2(plans["fp64"], cu(A))
+        assert info.cpu().tolist() == [0, -1]
+        o2 = oracle_mod.orth_error(host(Q2))
+        r2 = oracle_mod.residual(A, host(Q2), host(R2))
+        for seed in (1, 2, 3):
+            o, r = run(lib, oracle_mod, plans, mode, A, 3 * n, seed)
+            assert o <= 10 * g["rpcholqr"]["orthogonality"]["value"], (n, o)
+            assert r <= 10 * g["rpcholqr"]["residual"]["value"], (n, r)
+            # "the same magnitude" as Cholesky-QR2
+            assert o <= 10 * max(o2, EPS) and r <= 10 * max(r2, EPS)
+        assert o2 <= 10 * g["cholqr2"]["orthogonality"]["value"]
+        assert r2 <= 10 * g["cholqr2"]["residual"]["value"]
