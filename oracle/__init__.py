@@ -79,6 +79,10 @@ def _load():
         lib.oracle_orth_matrix.argtypes = [P, I64, I64, I64, P]
         lib.oracle_residual_matrix.argtypes = [P, I64, I64, I64, P, I64, P, P]
         lib.oracle_num_threads.restype = I
+        lib.oracle_scholqr3.argtypes = [P, I64, I64, I64, P, I64, P, P, I]
+        lib.oracle_scholqr3.restype = I
+        lib.oracle_scholqr3_shift.argtypes = [P, I64, I64]
+        lib.oracle_scholqr3_shift.restype = ctypes.c_double
         lib.oracle_smooth_order.argtypes = [I64]
         lib.oracle_smooth_order.restype = I64
         lib.oracle_rademacher.argtypes = [U64, U64, I64, P]
@@ -263,6 +267,23 @@ def cholqr2(A, variant: int = 0):
     piv = np.zeros(1, dtype=np.int64)
     st = _load().oracle_cholqr2(_ptr(A), m, n, n, _ptr(Q), n, _ptr(R), _ptr(piv), variant)
     return {"Q": Q, "R": R, "status": int(st), "pivot": int(piv[0])}
+
+
+def scholqr3(A, variant: int = 0):
+    """Shifted Cholesky-QR3 (the remedy for Cholesky-QR2's breakdown cited in Section 1)."""
+    A = _f64(A)
+    m, n = A.shape
+    Q = np.zeros((m, n))
+    R = np.zeros((n, n))
+    piv = np.zeros(1, dtype=np.int64)
+    st = _load().oracle_scholqr3(_ptr(A), m, n, n, _ptr(Q), n, _ptr(R), _ptr(piv), variant)
+    return {"Q": Q, "R": R, "status": int(st), "pivot": int(piv[0])}
+
+
+def scholqr3_shift(G, m: int) -> float:
+    """The shift 11 (m n + n (n + 1)) u trace(G) of shifted Cholesky-QR3 for the n x n Gram matrix G."""
+    G = _f64(G)
+    return float(_load().oracle_scholqr3_shift(_ptr(G), m, G.shape[0]))
 
 
 def _sym_norm2(E) -> float:

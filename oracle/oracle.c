@@ -18,7 +18,8 @@
  *   Cholesky      G_1 = R_2^T R_2
  *   solve         Q   = A_1 R_2^{-1}   m row-wise solves
  *   recover       R   = R_2 R_s
- * and Algorithm alg_0 ("Basic Cholesky-QR", Section 2.1) for Cholesky-QR and Cholesky-QR2.
+ * and Algorithm alg_0 ("Basic Cholesky-QR", Section 2.1) for Cholesky-QR, Cholesky-QR2 and the shifted
+ * Cholesky-QR3 cited in Section 1.
  *
  * Readings where the paper is silent (each stated at the function that implements it):
  *   - the random numbers: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), key (seed, stream),
@@ -438,6 +439,46 @@ int oracle_cholqr2(const double* A, int64_t m, int64_t n, int64_t lda, double* Q
     if (st == ORC_OK) st = oracle_cholqr(Q1, m, n, n, Q, ldq, Rb, pivot, variant);
     if (st == ORC_OK) oracle_triu_mul(Rb, Ra, n, R, variant);
     free(Q1); free(Ra); free(Rb);
+    return st;
+}
+
+/* Shifted Cholesky-QR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa, SIAM J. Sci. Comput. 2020;
+ * the remedy for Cholesky-QR2's breakdown cited in Section 1): G = A^T A + sigma I with
+ * sigma = 11 (m n + n (n + 1)) u ||A||^2, R_1 = chol(G), Q_1 = A R_1^{-1}; then Cholesky-QR2 of Q_1;
+ * R = R_3 R_2 R_1.  Reading: u = 2^-53 and ||A||^2 bounded by ||A||_F^2 = trace(A^T A), summed in
+ * index order. */
+double oracle_scholqr3_shift(const double* G, int64_t m, int64_t n) {
+    double tr = 0.0;
+    for (int64_t i = 0; i < n; ++i) tr += G[i * n + i];
+    return 11.0 * ((double)m * (double)n + (double)n * (double)(n + 1)) * ldexp(1.0, -53) * tr;
+}
+
+int oracle_scholqr3(const double* A, int64_t m, int64_t n, int64_t lda, double* Q, int64_t ldq, double* R,
+                    int64_t* pivot, int variant) {
+    if (pivot) *pivot = -1;
+    if (n < 1 || m < n || lda < n || ldq < n) return ORC_ERR_ARG;
+    size_t nn = (size_t)n * (size_t)n;
+    double* Ac = (double*)malloc(sizeof(double) * (size_t)m * (size_t)n);
+    double* Q1 = (double*)malloc(sizeof(double) * (size_t)m * (size_t)n);
+    double* G = (double*)malloc(sizeof(double) * nn);
+    double* R1 = (double*)malloc(sizeof(double) * nn);
+    double* R23 = (double*)malloc(sizeof(double) * nn);
+    for (int64_t i = 0; i < m; ++i) memcpy(Ac + i * n, A + i * lda, sizeof(double) * (size_t)n);
+    int st = ORC_OK;
+    if (!orc_all_finite(Ac, m, n, n)) { st = ORC_ERR_NONFINITE; goto done; }
+    oracle_gram(Ac, m, n, n, G, variant);
+    {
+        const double sigma = oracle_scholqr3_shift(G, m, n);
+        for (int64_t i = 0; i < n; ++i) G[i * n + i] += sigma;
+    }
+    st = oracle_cholesky_upper(G, n, R1, pivot, variant);
+    if (st != ORC_OK) goto done;
+    oracle_trsm_rows(Ac, m, n, n, R1, Q1, n, variant);
+    st = oracle_cholqr2(Q1, m, n, n, Q, ldq, R23, pivot, variant);
+    if (st != ORC_OK) goto done;
+    oracle_triu_mul(R23, R1, n, R, variant);
+done:
+    free(Ac); free(Q1); free(G); free(R1); free(R23);
     return st;
 }
 

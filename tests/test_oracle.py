@@ -307,3 +307,40 @@ def test_two_roundings_agree_in_R_and_to_eps_kappa_in_Q(oracle_mod):
         b = oracle_mod.rpcholqr(A, 72, 8, variant=1)
         assert np.linalg.norm(a["R"] - b["R"], 2) <= 1e-14 * np.linalg.norm(a["R"], 2)
         assert np.linalg.norm(a["Q"] - b["Q"], 2) <= 1e3 * EPS * kappa
+
+
+# ---- shifted Cholesky-QR3 (cited in Section 1 as the remedy for Cholesky-QR2's breakdown) ------------
+def test_scholqr3_shift_closed_form(oracle_mod):
+    G = np.diag([4.0, 9.0, 1.0])
+    assert oracle_mod.scholqr3_shift(G, 10) == 11.0 * (10 * 3 + 3 * 4) * 2.0 ** -53 * 14.0
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e8, 1e12])
+def test_scholqr3_succeeds_where_cholqr2_breaks_down(oracle_mod, kappa):
+    m, n = 3000, 40
+    A = inputs.usv(m, n, kappa, 51)
+    o3 = oracle_mod.scholqr3(A)
+    assert o3["status"] == 0
+    # LAPACK QR fixes the answer up to column signs; sCholQR3's R has a positive diagonal
+    q, r = np.linalg.qr(A)
+    sgn = np.sign(np.diag(r))
+    assert np.all(np.diag(o3["R"]) > 0)
+    assert oracle_mod.orth_error(o3["Q"]) <= 1e-14
+    assert oracle_mod.residual(A, o3["Q"], o3["R"]) <= 1e-15
+    if kappa <= 1e8:
+        assert np.linalg.norm(o3["R"] - sgn[:, None] * r, 2) <= 1e-12 * kappa * np.linalg.norm(r, 2)
+    if kappa >= 1e12:
+        assert oracle_mod.cholqr2(A)["status"] == oracle_mod.ERR_NOT_SPD
+
+
+def test_scholqr3_range_ends_where_rpcholqr_still_works(oracle_mod):
+    # the shifted first stage leaves kappa(Q_1) ~ sqrt(sigma) kappa(A) (sigma the shift), which
+    # Cholesky-QR2 needs below ~u^-1/2: at kappa(A) = 1e15 the method breaks down, while
+    # rpCholesky-QR handles numerically singular A (Section 5.1)
+    A = inputs.usv(3000, 40, 1e15, 51)
+    G = oracle_mod.gram(A)
+    sigma = oracle_mod.scholqr3_shift(G, 3000)
+    assert 1e-11 < sigma < 1e-9
+    assert oracle_mod.scholqr3(A)["status"] == oracle_mod.ERR_NOT_SPD
+    o = oracle_mod.rpcholqr(A, 120, 1)
+    assert o["status"] == 0 and oracle_mod.orth_error(o["Q"]) <= 1e-13

@@ -39,6 +39,8 @@ MUTATIONS = {
                                      "const double scale = sqrt((double)m / (double)s);"),
     "dct first-row weight": ("const double w = k == 0 ? sqrt(1.0 / (double)mp) : sqrt(2.0 / (double)mp);",
                              "const double w = sqrt(2.0 / (double)mp);"),
+    "scholqr3 shift dropped": ("for (int64_t i = 0; i < n; ++i) G[i * n + i] += sigma;",
+                               "for (int64_t i = 0; i < n; ++i) G[i * n + i] += 0.0 * sigma;"),
     "dct half-sample shift dropped": ("const uint64_t r = ((2 * (uint64_t)i + 1) * k) % (4 * (uint64_t)mp);",
                                       "const uint64_t r = ((2 * (uint64_t)i) * k) % (4 * (uint64_t)mp);"),
 }
