@@ -216,6 +216,14 @@ rpcholqr_status rpcholqr_precondition_gram_noalloc(const double* A, int64_t m, i
                                                    const double* Rs, double* A1, int64_t ld1,
                                                    double* G, int32_t* info, void* stream);
 
+/* Shifted Cholesky-QR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa 2020; the remedy for
+ * Cholesky-QR2's breakdown cited in Section 1): G = A^T A + sigma I, sigma = 11 (m n + n (n + 1)) u
+ * trace(A^T A) (u = 2^-53), R_1 = chol(G), Q_1 = A R_1^{-1}, then Cholesky-QR2 of Q_1; R = R_3 R_2 R_1.
+ * FP64 kernels; arguments and errors as rpcholqr_cholqr2.  Works while sqrt(sigma) kappa(A) stays
+ * below ~u^-1/2 (about kappa(A) < 1e13 at m = 3000, n = 40); beyond, NOT_SPD. */
+rpcholqr_status rpcholqr_scholqr3(rpcholqr_plan plan, const double* A, int64_t m, int32_t n, int64_t lda,
+                                  double* Q, int64_t ldq, double* R, int32_t* info, void* stream);
+
 /* SPLIT64 plans: *used_fp64 = 1 when the last factorisation on this plan computed Q = A1 R1^{-1}
  * by FP64 substitution (A1 judged ill conditioned), 0 when by the split tensor-core product.
  * Synchronises with the device. */

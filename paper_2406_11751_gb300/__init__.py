@@ -24,7 +24,7 @@ __all__ = [
     "rpcholqr_batch_replay", "rpcholqr_batch_autotune", "FP32", "rpcholqr_factor_f32",
     "rpcholqr_gather_owned_rows", "rpcholqr_sketch_r_from_sample", "rpcholqr_sum_partials",
     "rpcholqr_plan_set_smoothing", "rpcholqr_smoothed_sample", "SMOOTH_NONE", "SMOOTH_WHT", "SMOOTH_DCT",
-    "rpcholqr_plan_split_pass2_fp64",
+    "rpcholqr_plan_split_pass2_fp64", "rpcholqr_scholqr3",
 ]
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NONFINITE", 3: "ERR_SINGULAR_SKETCH", 4: "ERR_NOT_SPD",
@@ -46,6 +46,7 @@ EXPORTED_SYMBOLS = (
     "rpcholqr_batch_capture", "rpcholqr_batch_replay", "rpcholqr_batch_autotune", "rpcholqr_factor_f32",
     "rpcholqr_gather_owned_rows", "rpcholqr_sketch_r_from_sample", "rpcholqr_sum_partials",
     "rpcholqr_plan_set_smoothing", "rpcholqr_smoothed_sample", "rpcholqr_plan_split_pass2_fp64",
+    "rpcholqr_scholqr3",
 )
 PHASES = ("sample", "sketch_qr", "prep_rs", "pass1", "pass1_update", "pass1_solve2", "gram_reduce",
           "cholesky", "prep_r1", "pass2", "recover_r")
@@ -100,6 +101,7 @@ def load_library():
         "rpcholqr_ozaki_gram": [P, P, I64, I32, I64, P, P, P],
         "rpcholqr_cholqr": [P, P, I64, I32, I64, P, I64, P, P, P],
         "rpcholqr_cholqr2": [P, P, I64, I32, I64, P, I64, P, P, P],
+        "rpcholqr_scholqr3": [P, P, I64, I32, I64, P, I64, P, P, P],
         "rpcholqr_batch_create": [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, I64, I32, I32, I32],
         "rpcholqr_batch_destroy": [P],
         "rpcholqr_factor_batched": [P, I32, P, P, P, P, P, P, P, P, P, P, P],
@@ -430,6 +432,11 @@ def rpcholqr_cholqr(plan: Plan, A, Q=None, R=None, info=None, stream=None):
 def rpcholqr_cholqr2(plan: Plan, A, Q=None, R=None, info=None, stream=None):
     """Cholesky-QR2 on the GPU (the paper's comparison method); (Q, R, info)."""
     return _cholqr_call("rpcholqr_cholqr2", plan, A, Q, R, info, stream)
+
+
+def rpcholqr_scholqr3(plan: Plan, A, Q=None, R=None, info=None, stream=None):
+    """Shifted Cholesky-QR3 on the GPU (cited in Section 1 as the remedy for Cholesky-QR2's breakdown)."""
+    return _cholqr_call("rpcholqr_scholqr3", plan, A, Q, R, info, stream)
 
 
 def rpcholqr_ozaki_gemm(plan: Plan, X, Y, C=None, info=None, stream=None):

@@ -96,6 +96,7 @@ cudaError_t launch_dct_sample_f32(const float* A, int64_t m, int n, int64_t lda,
 void launch_pass2_gate(const double* R1, const double* W, int n, int np, double tau, const int32_t* info,
                        int32_t* gates, cudaStream_t st);
 void launch_gate_merge(int32_t* info, const int32_t* gates, cudaStream_t st);
+void launch_scholqr3_shift(double* G, int64_t ldg, int n, int64_t m, const int32_t* info, cudaStream_t st);
 }  // namespace rpq
 
 using namespace rpq;
@@ -965,11 +966,16 @@ rpcholqr_status rpcholqr_ozaki_gram(rpcholqr_plan p, const double* X, int64_t m,
 
 // One Cholesky-QR step in FP64: Q = X R^{-1} with R = chol(X^T X) written to R_out (np x np, ld np).
 static rpcholqr_status cholqr_step(rpcholqr_plan p, const double* X, int64_t m, int32_t n, int64_t ldx,
-                                   double* Q, int64_t ldq, double* R_out, int32_t* info, cudaStream_t st) {
+                                   double* Q, int64_t ldq, double* R_out, int32_t* info, cudaStream_t st,
+                                   bool shifted = false) {
     const int np = pad_np(n);
     if (np > kMaxNP) {
         rpcholqr_status rc = gram_fp64_wide(p, X, ldx, m, n, p->G, np, info, st);
         if (rc != RPCHOLQR_OK) return rc;
+        if (shifted) {
+            launch_scholqr3_shift(p->G, np, n, m, info, st);
+            ++p->launches;
+        }
         if (launch_cholesky(p->G, np, n, np, R_out, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
         ++p->launches;
         return solve_internal(p, X, m, n, ldx, R_out, np, Q, ldq, info, st, nullptr);
@@ -981,6 +987,10 @@ static rpcholqr_status cholqr_step(rpcholqr_plan p, const double* X, int64_t m, 
         cudaSuccess)
         return RPCHOLQR_ERR_CUDA;
     launch_gram_reduce(p->gpart, grid, np, n, p->G, np, info, st);
+    if (shifted) {
+        launch_scholqr3_shift(p->G, np, n, m, info, st);
+        ++p->launches;
+    }
     if (launch_cholesky(p->G, np, n, np, R_out, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
     p->launches += 4;
     return solve_internal(p, Q, m, n, ldq, R_out, np, Q, ldq, info, st, nullptr);
@@ -1022,6 +1032,27 @@ rpcholqr_status rpcholqr_cholqr2(rpcholqr_plan p, const double* A, int64_t m, in
     const int np = pad_np(n);
     launch_triu_mul(p->R1, np, p->Rs, np, n, R, n, info, st);
     ++p->launches;
+    return check_launch();
+}
+
+rpcholqr_status rpcholqr_scholqr3(rpcholqr_plan p, const double* A, int64_t m, int32_t n, int64_t lda,
+                                  double* Q, int64_t ldq, double* R, int32_t* info, void* stream) {
+    rpcholqr_status rc = cholqr_args(p, A, m, n, lda, Q, ldq, R, info);
+    if (rc != RPCHOLQR_OK) return rc;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int np = pad_np(n);
+    if ((rc = reset_info(info, st)) != RPCHOLQR_OK) return rc;
+    if ((rc = cholqr_step(p, A, m, n, lda, Q, ldq, p->Rs, info, st, true)) != RPCHOLQR_OK) return rc;   // R_1
+    if ((rc = cholqr_step(p, Q, m, n, ldq, Q, ldq, p->R1, info, st)) != RPCHOLQR_OK) return rc;         // R_2
+    launch_triu_mul(p->R1, np, p->Rs, np, n, R, n, info, st);                                       // R_2 R_1
+    if ((rc = cholqr_step(p, Q, m, n, ldq, Q, ldq, p->R1, info, st)) != RPCHOLQR_OK) return rc;         // R_3
+    if (cudaMemcpy2DAsync(p->Rs, sizeof(double) * np, R, sizeof(double) * n, sizeof(double) * n,
+                          static_cast<size_t>(n), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    launch_triu_mul(p->R1, np, p->Rs, np, n, R, n, info, st);                                       // R_3 R_2 R_1
+    p->launches += 2;
     return check_launch();
 }
 

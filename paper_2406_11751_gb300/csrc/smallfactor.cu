@@ -421,3 +421,24 @@ void launch_gate_merge(int32_t* info, const int32_t* gates, cudaStream_t st) {
     k_gate_merge<<<1, 32, 0, st>>>(info, gates, gates + 2);
 }
 }  // namespace rpq
+
+namespace rpq {
+// Shifted Cholesky-QR3's first stage (Fukaya et al. 2020, cited in Section 1): G += sigma I with
+// sigma = 11 (m n + n (n + 1)) u trace(G), the trace summed in index order by one thread.
+__global__ void k_scholqr3_shift(double* G, int64_t ldg, int n, int64_t m, const int32_t* info) {
+    __shared__ double sigma;
+    if (load_status(info) != 0) return;
+    if (threadIdx.x == 0) {
+        double tr = 0.0;
+        for (int i = 0; i < n; ++i) tr += G[static_cast<int64_t>(i) * ldg + i];
+        sigma = 11.0 * (static_cast<double>(m) * static_cast<double>(n) +
+                        static_cast<double>(n) * static_cast<double>(n + 1)) * 0x1p-53 * tr;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) G[static_cast<int64_t>(i) * ldg + i] += sigma;
+}
+
+void launch_scholqr3_shift(double* G, int64_t ldg, int n, int64_t m, const int32_t* info, cudaStream_t st) {
+    k_scholqr3_shift<<<1, 256, 0, st>>>(G, ldg, n, m, info);
+}
+}  // namespace rpq

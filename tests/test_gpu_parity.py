@@ -316,3 +316,35 @@ def test_cholqr2_breaks_down_where_rpcholqr_succeeds(lib, oracle_mod, plan):
     Q, R, info = lib.rpcholqr_factor(plan, cu(A), 192, 1)
     assert status(info) == (0, -1)
     assert oracle_mod.orth_error(host(Q)) <= 1e-13
+
+
+# ---- shifted Cholesky-QR3 (the remedy for Cholesky-QR2's breakdown cited in Section 1) ----------------
+@pytest.mark.parametrize("m,n,kappa", [(3000, 40, 1e2), (3000, 40, 1e12), (20000, 128, 1e10), (6000, 200, 1e11)])
+def test_scholqr3_matches_oracle(lib, oracle_mod, m, n, kappa):
+    A = inputs.usv(m, n, kappa, 51 if n == 40 else 700 + n)
+    plan = lib.rpcholqr_plan_create(0, m, n, 3 * n)
+    try:
+        Q, R, info = lib.rpcholqr_scholqr3(plan, cu(A))
+        assert status(info) == (0, -1)
+    finally:
+        plan.close()
+    o = oracle_mod.scholqr3(A)
+    assert o["status"] == 0
+    # the first stage's factor carries kappa(A)-level sensitivity: R is gated on the oracle's own floor
+    floor = nrm2(o["R"] - oracle_mod.scholqr3(A, variant=1)["R"])
+    assert nrm2(host(R) - o["R"]) <= max(1e-12 * nrm2(o["R"]), 10 * floor)
+    assert oracle_mod.orth_error(host(Q)) <= 10 * oracle_mod.orth_error(o["Q"]) + 1e-15
+    assert oracle_mod.residual(A, host(Q), host(R)) <= 10 * oracle_mod.residual(A, o["Q"], o["R"]) + 1e-16
+
+
+def test_scholqr3_breaks_down_beyond_its_range(lib, oracle_mod):
+    A = inputs.usv(3000, 40, 1e15, 51)
+    plan = lib.rpcholqr_plan_create(0, 3000, 40, 120)
+    try:
+        _, _, info = lib.rpcholqr_scholqr3(plan, cu(A))
+        assert status(info)[0] == lib.ERR_NOT_SPD
+        Q, R, info = lib.rpcholqr_factor(plan, cu(A), 120, 1)
+        assert status(info) == (0, -1)
+        assert oracle_mod.orth_error(host(Q)) <= 1e-13
+    finally:
+        plan.close()
