@@ -88,12 +88,22 @@ k_hh_cluster(double* __restrict__ W, int64_t lds, int s, int n, int np, double* 
             const int k0 = j + 1 + static_cast<int>((rank + csize - static_cast<unsigned>((j + 1) % csize)) % csize);
             for (int k = k0 + warp * static_cast<int>(csize); k < n; k += nwarps * static_cast<int>(csize)) {
                 double* colk = W + static_cast<int64_t>(k) * lds;
-                double w = 0.0;
-                for (int i = j + lane; i < s; i += 32) w += v[i] * colk[i];
+                // four independent partial sums keep four column loads in flight per lane
+                double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
+                int i = j + lane;
+                for (; i + 96 < s; i += 128) {
+                    w0 += v[i] * colk[i];
+                    w1 += v[i + 32] * colk[i + 32];
+                    w2 += v[i + 64] * colk[i + 64];
+                    w3 += v[i + 96] * colk[i + 96];
+                }
+                for (; i < s; i += 32) w0 += v[i] * colk[i];
+                double w = (w0 + w1) + (w2 + w3);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
                 const double tw = tau * w;
-                for (int i = j + lane; i < s; i += 32) colk[i] -= v[i] * tw;
+#pragma unroll 4
+                for (int i2 = j + lane; i2 < s; i2 += 32) colk[i2] -= v[i2] * tw;
             }
         }
         __syncthreads();
