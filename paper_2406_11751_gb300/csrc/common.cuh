@@ -48,6 +48,16 @@ __device__ __forceinline__ void mma_f64_16816(double (&d)[4], const double (&a)[
           "d"(b[0]), "d"(b[1]), "d"(b[2]), "d"(b[3]));
 }
 
+// D(16x8) += A(16x8) * B(8x8), FP64: the same fragment layouts restricted to k < 8
+// (a[i] = A[g + 8*(i&1)][t + 4*(i>>1)], i = 0..3;  b[i] = B[t + 4*i][g], i = 0..1).
+__device__ __forceinline__ void mma_f64_1688(double (&d)[4], const double (&a)[4], const double (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, "
+        "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+d"(d[0]), "+d"(d[1]), "+d"(d[2]), "+d"(d[3])
+        : "d"(a[0]), "d"(a[1]), "d"(a[2]), "d"(a[3]), "d"(b[0]), "d"(b[1]));
+}
+
 // ---- cp.async (Ampere+ LDGSTS), 8-byte granules with zero fill ----------------------------------
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src, bool valid) {
     unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));

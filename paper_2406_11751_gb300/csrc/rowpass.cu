@@ -132,7 +132,9 @@ k_rowpass(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m, int n
                     acc2[mt][i] = 0.0;
                     if (check_finite) bad |= !isfinite(acc[mt][i]);
                 }
-            const int nk = (8 * J + 15) / 16;
+            // the 8J solved columns: full 16-wide chunks as m16n8k16, an 8-wide remainder (odd J) as
+            // m16n8k8 with the first half of the chunk's fragments (its upper half is zero padding)
+            const int nk = (8 * J) / 16;
             for (int kc = 0; kc < nk; ++kc) {
                 const double2* fb = reinterpret_cast<const double2*>(
                     frag + ((static_cast<size_t>(kc) * NB + J) * 32 + lane) * 4);
@@ -146,6 +148,20 @@ k_rowpass(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m, int n
                         a[i] = panel[(wr0 + mt * 16 + g + 8 * (i & 1)) * S + kc * 16 + t + 4 * (i >> 1)];
                     if (kc & 1) mma_f64_16816(acc2[mt], a, b);
                     else mma_f64_16816(acc[mt], a, b);
+                }
+            }
+            if (J & 1) {
+                const double2 b01 = __ldg(reinterpret_cast<const double2*>(
+                    frag + ((static_cast<size_t>(nk) * NB + J) * 32 + lane) * 4));
+                const double b[2] = {b01.x, b01.y};
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    double a[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        a[i] = panel[(wr0 + mt * 16 + g + 8 * (i & 1)) * S + nk * 16 + t + 4 * (i >> 1)];
+                    if (nk & 1) mma_f64_1688(acc2[mt], a, b);
+                    else mma_f64_1688(acc[mt], a, b);
                 }
             }
 #pragma unroll
