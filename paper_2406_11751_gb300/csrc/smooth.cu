@@ -85,8 +85,16 @@ k_wht_high_sample(const double* __restrict__ T, int64_t mp, int n, int l1, int l
                   const int64_t* __restrict__ idx, int s, double inv_sqrt_mp, double scale,
                   double* __restrict__ As, int64_t lds, const int32_t* info) {
     extern __shared__ double hs[];
+    __shared__ int needed;
     if (load_status(info) != 0) return;
     const int L = 1 << l1, H2 = 1 << l2, G = 1 << lg;
+    // only low-index groups that hold a sampled row are transformed
+    if (threadIdx.x == 0) needed = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < s; j += blockDim.x)
+        if ((static_cast<int>(idx[j] & (L - 1)) >> lg) == static_cast<int>(blockIdx.x)) needed = 1;
+    __syncthreads();
+    if (!needed) return;
     const int per_block = kWhtCols / csub;
     const int cb = blockIdx.y / per_block, cs0 = (blockIdx.y - cb * per_block) * csub;
     const int lo0 = blockIdx.x * G;
