@@ -44,7 +44,7 @@ __global__ void k_prep_f32(const double* __restrict__ T, int64_t ldt, int n, int
 __global__ void __launch_bounds__(kF32Rows)
 k_rowsolve_f32(const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t m, int n,
                const float* __restrict__ T32, int np32, const float* __restrict__ rinv32, int32_t* info,
-               bool check_finite) {
+               bool check_finite, bool vec) {
     extern __shared__ float4 ts4[];   // rows 0 .. 32J+31 of the 32 columns of block J (8 float4 per row)
     if (load_status(info) != 0) return;
     const int64_t r = static_cast<int64_t>(blockIdx.x) * kF32Rows + threadIdx.x;
@@ -66,27 +66,55 @@ k_rowsolve_f32(const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t m, in
             acc[c] = c0 + c < n ? xr[c0 + c] : 0.0f;
             bad |= !isfinite(acc[c]);
         }
-        // acc -= Y[r, 0:c0] T[0:c0, c0:c0+32]
-        for (int k = 0; k < c0; ++k) {
-            const float yk = -yr[k];
-            const float4* tk = ts4 + k * 8;
+        // acc -= Y[r, 0:c0] T[0:c0, c0:c0+32]; with 16-byte aligned rows, 8 solved values per two
+        // vector loads, two such groups in flight
+        if (vec) {
+#pragma unroll 2
+            for (int k = 0; k < c0; k += 8) {
+                const float4 ya = *reinterpret_cast<const float4*>(yr + k);
+                const float4 yb = *reinterpret_cast<const float4*>(yr + k + 4);
+                const float yv[8] = {-ya.x, -ya.y, -ya.z, -ya.w, -yb.x, -yb.y, -yb.z, -yb.w};
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float4 t = tk[q];
-                acc[4 * q + 0] = fmaf(yk, t.x, acc[4 * q + 0]);
-                acc[4 * q + 1] = fmaf(yk, t.y, acc[4 * q + 1]);
-                acc[4 * q + 2] = fmaf(yk, t.z, acc[4 * q + 2]);
-                acc[4 * q + 3] = fmaf(yk, t.w, acc[4 * q + 3]);
+                for (int kk = 0; kk < 8; ++kk) {
+                    const float4* tk = ts4 + (k + kk) * 8;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 t = tk[q];
+                        acc[4 * q + 0] = fmaf(yv[kk], t.x, acc[4 * q + 0]);
+                        acc[4 * q + 1] = fmaf(yv[kk], t.y, acc[4 * q + 1]);
+                        acc[4 * q + 2] = fmaf(yv[kk], t.z, acc[4 * q + 2]);
+                        acc[4 * q + 3] = fmaf(yv[kk], t.w, acc[4 * q + 3]);
+                    }
+                }
+            }
+        } else {
+            for (int k = 0; k < c0; ++k) {
+                const float yk = -yr[k];
+                const float4* tk = ts4 + k * 8;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 t = tk[q];
+                    acc[4 * q + 0] = fmaf(yk, t.x, acc[4 * q + 0]);
+                    acc[4 * q + 1] = fmaf(yk, t.y, acc[4 * q + 1]);
+                    acc[4 * q + 2] = fmaf(yk, t.z, acc[4 * q + 2]);
+                    acc[4 * q + 3] = fmaf(yk, t.w, acc[4 * q + 3]);
+                }
             }
         }
-        // diagonal block: forward substitution
-        const float* td = reinterpret_cast<const float*>(ts4 + c0 * 8);
+        // diagonal block: forward substitution, row j of the block's T read as float4s
 #pragma unroll
         for (int j = 0; j < kF32Blk; ++j) {
             acc[j] *= rinv32[c0 + j];
             const float xj = -acc[j];
+            const float4* trow = ts4 + (c0 + j) * 8;
 #pragma unroll
-            for (int c = j + 1; c < kF32Blk; ++c) acc[c] = fmaf(xj, td[j * kF32Blk + c], acc[c]);
+            for (int q = (j + 1) / 4; q < 8; ++q) {
+                const float4 t = trow[q];
+                if (4 * q + 0 > j) acc[4 * q + 0] = fmaf(xj, t.x, acc[4 * q + 0]);
+                if (4 * q + 1 > j) acc[4 * q + 1] = fmaf(xj, t.y, acc[4 * q + 1]);
+                if (4 * q + 2 > j) acc[4 * q + 2] = fmaf(xj, t.z, acc[4 * q + 2]);
+                if (4 * q + 3 > j) acc[4 * q + 3] = fmaf(xj, t.w, acc[4 * q + 3]);
+            }
         }
 #pragma unroll
         for (int c = 0; c < kF32Blk; ++c)
@@ -101,7 +129,7 @@ k_rowsolve_f32(const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t m, in
 __global__ void __launch_bounds__(256)
 k_syrk_f32(const float* __restrict__ X, int64_t ldx, int64_t m, int n, int np64, int64_t rows_per,
            double* __restrict__ gpart, const int32_t* info) {
-    __shared__ __align__(16) float xs[32][2 * 64 + 4];
+    __shared__ __align__(16) float xs[2][32][2 * 64 + 4];   // double-buffered 32-row chunks
     if (load_status(info) != 0) return;
     const int nb = np64 / 64;
     int tt = blockIdx.x, I = 0;
@@ -116,20 +144,31 @@ k_syrk_f32(const float* __restrict__ X, int64_t ldx, int64_t m, int n, int np64,
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) { acc[i][j] = 0.0f; tot[i][j] = 0.0; }
-    int64_t chunk_end = rb + kSyrkChunkRows;
-    for (int64_t k0 = rb; k0 < re; k0 += 32) {
-        __syncthreads();
+    // rows k0 .. k0+31 of the two 64-column blocks into xs[b] (4-byte cp.async, zero-filled outside X)
+    auto stage = [&](int64_t k0, int b) {
         for (int e = tid; e < 32 * 128; e += 256) {
             const int rr = e >> 7, cc = e & 127;
             const int col = cc < 64 ? 64 * I + cc : 64 * J + (cc - 64);
-            xs[rr][cc] = (k0 + rr < re && col < n) ? X[(k0 + rr) * ldx + col] : 0.0f;
+            const bool ok = k0 + rr < re && col < n;
+            const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(&xs[b][rr][cc]));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst),
+                         "l"(ok ? X + (k0 + rr) * ldx + col : X), "r"(ok ? 4 : 0));
         }
+    };
+    if (rb < re) stage(rb, 0);
+    asm volatile("cp.async.commit_group;\n");
+    int64_t chunk_end = rb + kSyrkChunkRows;
+    int b = 0;
+    for (int64_t k0 = rb; k0 < re; k0 += 32, b ^= 1) {
+        if (k0 + 32 < re) stage(k0 + 32, b ^ 1);   // xs[b ^ 1] was last read before the barrier below
+        asm volatile("cp.async.commit_group;\n");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         __syncthreads();
 #pragma unroll 8
         for (int kk = 0; kk < 32; ++kk) {
-            const float4 a = *reinterpret_cast<const float4*>(&xs[kk][4 * ty]);
-            const float4 b = *reinterpret_cast<const float4*>(&xs[kk][64 + 4 * tx]);
-            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+            const float4 a = *reinterpret_cast<const float4*>(&xs[b][kk][4 * ty]);
+            const float4 bb = *reinterpret_cast<const float4*>(&xs[b][kk][64 + 4 * tx]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -142,7 +181,9 @@ k_syrk_f32(const float* __restrict__ X, int64_t ldx, int64_t m, int n, int np64,
 #pragma unroll
                 for (int j = 0; j < 4; ++j) { tot[i][j] += acc[i][j]; acc[i][j] = 0.0f; }
         }
+        __syncthreads();   // every thread is done with xs[b] before it is refilled
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     double* out = gpart + static_cast<size_t>(blockIdx.y) * np64 * np64;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -179,8 +220,10 @@ cudaError_t launch_rowsolve_f32(const float* X, int64_t ldx, float* Y, int64_t l
     cudaError_t err = cudaFuncSetAttribute(k_rowsolve_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (err != cudaSuccess) return err;
     const int64_t grid = (m + kF32Rows - 1) / kF32Rows;
+    // vector loads of solved values need 16-byte aligned rows
+    const bool vec = (reinterpret_cast<uintptr_t>(Y) % 16 == 0) && (ldy % 4 == 0);
     k_rowsolve_f32<<<static_cast<unsigned>(grid), kF32Rows, smem, st>>>(X, ldx, Y, ldy, m, n, T32, np32, rinv32,
-                                                                         info, check_finite);
+                                                                         info, check_finite, vec);
     return cudaGetLastError();
 }
 
