@@ -169,9 +169,9 @@ rpcholqr_status rpcholqr_triu_mul(const double* R1, const double* Rs, int32_t n,
                                   void* stream);
 
 /* Split-precision FP64 product C = X Y on the BF16 tensor cores (the kernel SPLIT64 uses):
- * X device m x K (ldx), Y device K x N (ldy), C device m x N (ldc), K, N <= plan max_n; each entry
- * carries an absolute error below ~2^-53 * 2^(Ex+Ey) (Ex, Ey: power-of-two bounds of row i of X and
- * column j of Y).  The plan must be a SPLIT64 plan.  info as above (RPCHOLQR_ERR_TIMEOUT if a bounded
+ * X device m x K (ldx), Y device K x N (ldy), C device m x N (ldc; must not overlap X), K, N <= plan
+ * max_n; each entry carries an absolute error below ~2^-53 * 2^(Ex+Ey) (Ex, Ey: power-of-two bounds
+ * of row i of X and column j of Y).  The plan must be a SPLIT64 plan.  info as above (RPCHOLQR_ERR_TIMEOUT if a bounded
  * tensor-core wait gave up). */
 rpcholqr_status rpcholqr_ozaki_gemm(rpcholqr_plan plan, const double* X, int64_t m, int32_t K, int64_t ldx,
                                     const double* Y, int32_t N, int64_t ldy, double* C, int64_t ldc,

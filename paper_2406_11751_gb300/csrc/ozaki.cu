@@ -55,6 +55,17 @@ constexpr int kASlice = kTileM * kKW * 2;  // 8 KB
 constexpr int kBSlice = kTileN * kKW * 2;  // 4 KB
 constexpr int kAStage = kSlices * kASlice; // 64 KB
 constexpr int kBStage = kSlices * kBSlice; // 32 KB
+// k_ozaki_gemm_ws shared memory: two stages (A slices, then B slices: 96 KB each), then the raw FP64 X
+// rows of the next stage (row stride kRawLd doubles: 16-byte reads of one row per thread are
+// conflict-free).  At a tile end the drained stage's 96 KB stage the 128 x 64 output tile (row stride
+// kEpiLd doubles) so that B is read and C written in whole rows.
+constexpr int kStageBytes = kAStage + kBStage;
+constexpr int kRawLd = kKW + 2;
+constexpr int kRawBytes = kTileM * kRawLd * 8;
+constexpr int kEpiLd = kTileN + 1;
+constexpr int kGemmSmem = 2 * kStageBytes + kRawBytes;
+static_assert(kTileM * kEpiLd * 8 <= kStageBytes, "output tile must fit in one stage");
+static_assert(kGemmSmem + 1024 <= 232448, "k_ozaki_gemm_ws exceeds the 227 KB shared-memory limit");
 constexpr int kTmemCols = 512;
 constexpr long kSpinLimit = 1L << 24;
 // BF16 x BF16 -> FP32, A and B K-major, M = 128, N = 64
@@ -94,6 +105,34 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     }
     return done != 0;
 }
+// mbar_wait that also gives up once *abort is set (by the other side of a warp-specialised pipeline).
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, const volatile int* abort) {
+    uint32_t done = 0;
+    for (long it = 0; it < kSpinLimit && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity));
+        if (!done && (it & 255) == 255 && *abort) return false;
+    }
+    return done != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+// Barrier 1 over the n producer threads only (the MMA warp does not take part).
+__device__ __forceinline__ void prod_sync(int n) { asm volatile("bar.sync 1, %0;\n" ::"r"(n) : "memory"); }
+__device__ __forceinline__ bool prod_sync_or(bool v, int n) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"(static_cast<uint32_t>(v)), "r"(n)
+        : "memory");
+    return r != 0;
+}
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
@@ -119,17 +158,16 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 // 56-bit fixed-point magnitude F = floor(|x| 2^{56-E}) of x relative to the bound 2^E > |x|, split in
 // two 28-bit halves (hi: slices 1..4, lo: slices 5..8).  0 for zero, subnormal, non-finite or unknown E.
+// Branch-free: F = (mantissa 2^3) >> (3 - sh) with sh = ex - 1019 - E <= 3 for a valid bound (a larger
+// sh, |x| >= 2^E, saturates).
 __device__ __forceinline__ void fixed56(double x, int E, uint32_t& fhi, uint32_t& flo) {
     const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
     const int ex = static_cast<int>((bits >> 52) & 0x7FF);
-    unsigned long long F = 0;
-    if (ex != 0 && ex != 0x7FF && E > kNoExp) {
-        const unsigned long long mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
-        const int sh = ex - 1019 - E;          // F = mant 2^sh, < 2^56 when |x| < 2^E
-        if (sh > 3) F = (1ull << 56) - 1;      // |x| >= 2^E: not a valid bound; saturate
-        else if (sh >= 0) F = mant << sh;
-        else if (sh > -64) F = mant >> (-sh);
-    }
+    const unsigned long long mant8 = ((bits & ((1ull << 52) - 1)) | (1ull << 52)) << 3;   // < 2^56
+    const int r = E + 1022 - ex;
+    unsigned long long F = mant8 >> (r < 63 ? (r > 0 ? r : 0) : 63);
+    F = r < 0 ? (1ull << 56) - 1 : F;
+    F = (ex != 0 && ex != 0x7FF && E > kNoExp) ? F : 0ull;
     fhi = static_cast<uint32_t>(F >> 28);
     flo = static_cast<uint32_t>(F) & 0x0FFFFFFFu;
 }
@@ -224,8 +262,12 @@ __device__ __forceinline__ void drain_acc(uint32_t tmem, int warp, int col0, lon
 
 // Issue the 72 MMAs of one stage: all pairs (a, b), a + b <= 9, for the two K=16 steps.
 // first_window: the stage starts an exactness window (the first MMA into each accumulator clears it).
+// The descriptors of the stage's two base addresses are formed once; every MMA adds its (constant)
+// offset to the 14-bit start field, which cannot carry (shared memory < 256 KB).
 __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, uint32_t b_base,
                                            uint32_t b_slice_bytes, bool first_window) {
+    const uint64_t a0 = sdesc(a_base), b0 = sdesc(b_base);
+    const uint32_t bstep = b_slice_bytes >> 4;
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
 #pragma unroll
@@ -234,8 +276,8 @@ __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, uint
 #pragma unroll
             for (int a = alo; a <= ahi; ++a) {
                 const int b = d - a;
-                const uint64_t ad = sdesc(a_base + (a - 1) * kASlice + kk * 256);   // K step = 2 core matrices
-                const uint64_t bd = sdesc(b_base + (b - 1) * b_slice_bytes + kk * 256);
+                const uint64_t ad = a0 + static_cast<uint32_t>(((a - 1) * kASlice + kk * 256) >> 4);
+                const uint64_t bd = b0 + (static_cast<uint32_t>(b - 1) * bstep + static_cast<uint32_t>(kk * 16));
                 const uint32_t acc = (first_window && kk == 0 && a == alo) ? 0u : 1u;
                 mma_bf16(tmem + (d - 2) * kTileN, ad, bd, acc);
             }
@@ -310,6 +352,7 @@ __device__ __forceinline__ void gemm_drain_tile(uint32_t tmem, int warp, int rq,
     }
 #pragma unroll 1
     for (int c0 = NC * rq; c0 < NC * rq + NC; c0 += 8) {
+        if (tn * kTileN + c0 >= N) break;   // (warp-uniform) no valid column left
         double bv[8];
         if (SUB) {
 #pragma unroll
@@ -483,6 +526,280 @@ k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// ---- C = X Y, warp-specialised: helpers ------------------------------------------------------------
+// 128 rows x 32 K values of X (rows row0.., columns k0..) into R, one 8-byte cp.async per value, zero
+// outside the matrix; the 32 lanes of a warp copy one row.
+template <int NT>
+__device__ __forceinline__ void prefetch_x(const double* X, int64_t ldx, int64_t m, int K, int64_t row0, int k0,
+                                           double* R, int tid) {
+#pragma unroll
+    for (int i = 0; i < kTileM * kKW / NT; ++i) {
+        const int e = tid + i * NT;
+        const int r = e >> 5, k = e & 31;
+        const int64_t row = row0 + r;
+        const bool ok = row < m && k0 + k < K;
+        cp_async8(R + r * kRawLd + k, ok ? X + row * ldx + k0 + k : X, ok);
+    }
+}
+
+// Write the finished tile (rows row0 + 0..127, columns 64 tn + 0..63) of C = X Y through the staging
+// buffer W (run by the NT producer threads): each thread puts its row's NC values into W, then the tile
+// is written in whole rows.  The values come from the TMEM accumulators (single window) or from acc (WIN).
+template <bool WIN, int NT, int NC>
+__device__ __forceinline__ void gemm_store_tile(uint32_t tmem, int warp, int tid, int64_t row0, int tn, int E,
+                                                int N, const int32_t* __restrict__ yexp, double* C, int64_t ldc,
+                                                int64_t m, double* W, long long (&acc)[NC]) {
+    const int lr = tid & (kTileM - 1), rq = tid / kTileM;
+    const int col0 = tn * kTileN;
+    const int ncols = N - col0 < kTileN ? N - col0 : kTileN;
+    double* wr = W + lr * kEpiLd + NC * rq;
+    if (WIN) {
+        drain_acc<true>(tmem, warp, NC * rq, acc);
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const int col = col0 + NC * rq + j;
+            const int ey = col < N ? yexp[col] : kNoExp;
+            const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(acc[j], E + ey - 53) : 0.0;
+            wr[j] = v;
+        }
+    } else {
+#pragma unroll 1
+        for (int c0 = 0; c0 < NC; c0 += 8) {
+            float mg[kGroups][8];
+#pragma unroll
+            for (int g = 0; g < kGroups; ++g)
+                tmem_ld8(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + g * kTileN + NC * rq + c0, mg[g]);
+            tmem_wait_ld();
+            if (col0 + NC * rq + c0 >= N) continue;   // (warp-uniform) no valid column in this chunk
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int col = col0 + NC * rq + c0 + j;
+                float grp[kGroups];
+#pragma unroll
+                for (int g = 0; g < kGroups; ++g) grp[g] = mg[g][j];
+                if (col < N) {
+                    const long long I = combine_units53(grp);
+                    const int ey = yexp[col];
+                    const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(I, E + ey - 53) : 0.0;
+                    wr[c0 + j] = v;
+                }
+            }
+        }
+    }
+    prod_sync(NT);
+#pragma unroll 8
+    for (int i = 0; i < kTileM * kTileN / NT; ++i) {
+        const int e = tid + i * NT;
+        const int r = e >> 6, c = e & 63;
+        const int64_t row = row0 + r;
+        if (row < m && c < ncols) C[row * ldc + col0 + c] = W[r * kEpiLd + c];
+    }
+    prod_sync(NT);   // W (a stage buffer) is free again
+}
+
+// ---- C = X Y, warp-specialised (the product of pass 2, Q = A_1 R_1^{-1}) -----------------------------
+// Same operands, tiles, exactness windows and results as k_ozaki_gemm<false, WIN>; the pipeline differs.
+// The raw X rows of stage g + 1 are copied (cp.async, whole rows per warp) while stage g is sliced, and
+// the finished tile is written in whole rows through a free stage buffer.  Warp roles: NT producer
+// threads (warps 0 .. NT/32 - 1) copy, slice and drain; the last warp issues the MMAs.  full[s]: the producer warps filled stage buffer s (one arrival per warp); empty[s]: the MMAs of
+// the stage in buffer s are done (tcgen05.commit).  A drain waits for empty of the stage before and
+// arrives on full of the next stage only after it, so the next tile's MMAs start once TMEM is read out.
+template <bool WIN>
+__global__ void __launch_bounds__((WIN ? kThreadsWin : kThreads) + 32, 1)
+k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int K,
+                const uint8_t* __restrict__ yblocks, const int32_t* __restrict__ yexp, int N, double* C,
+                int64_t ldc, int64_t m, int32_t* info) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint64_t empty_bar[2], full_bar[2], done_bar;
+    __shared__ uint32_t tslot;
+    __shared__ int abort_s;
+    if (load_status(info) != 0) return;
+    constexpr int NT = WIN ? kThreadsWin : kThreads;
+    constexpr int NC = Share<NT>::kDrainCols, NCH = Share<NT>::kChunks;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t* stA[2] = {sm, sm + kStageBytes};
+    uint8_t* stB[2] = {sm + kAStage, sm + kStageBytes + kAStage};
+    double* R = reinterpret_cast<double*>(sm + 2 * kStageBytes);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tslot)), "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty_bar[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full_bar[i])), "r"(NT / 32));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&done_bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+        abort_s = 0;
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tslot;
+
+    const int nkw = (K + kKW - 1) / kKW;
+    const int ntn = (N + kTileN - 1) / kTileN;
+    const int64_t ntm = (m + kTileM - 1) / kTileM;
+    const int64_t ntiles = ntm * ntn;
+    const int64_t my_tiles =
+        static_cast<int64_t>(blockIdx.x) < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t nstages = my_tiles * nkw;
+
+    if (warp == NT / 32) {
+        // MMA warp: one lane issues every stage once the producers have filled it
+        if (lane == 0) {
+            uint32_t fphase[2] = {0u, 0u};
+            for (int64_t g = 0; g < nstages; ++g) {
+                const int s = static_cast<int>(g & 1);
+                if (!mbar_wait_ab(&full_bar[s], fphase[s], &abort_s)) {
+                    abort_s = 1;
+                    break;
+                }
+                fphase[s] ^= 1u;
+                tc_after_sync();
+                issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), kBSlice, (g % nkw & 3) == 0);
+                mma_commit(&empty_bar[s]);
+            }
+            // every MMA issued here is complete before the tensor memory is released
+            mma_commit(&done_bar);
+            if (!mbar_wait(&done_bar, 0u)) abort_s = 1;
+        }
+        __syncwarp();
+    } else {
+        const int lr = tid & (kTileM - 1);  // tile row: producer row and drain row (TMEM lane)
+        const int rq = tid >> 7;            // producer K chunk(s) NCH*rq..; drain columns NC*rq..
+        uint32_t phase[2] = {0u, 0u};
+        bool pending[2] = {false, false};
+        bool timed_out = false;
+        long long acc[NC];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[j] = 0;
+        int64_t cur_row0 = 0;               // the tile whose accumulators are in TMEM
+        int cur_tn = 0, cur_E = kNoExp;
+        // first row and K offset of stage g
+        auto stage_origin = [&](int64_t g, int64_t& row0, int& k0) {
+            const int64_t t = blockIdx.x + (g / nkw) * gridDim.x;
+            row0 = (t / ntn) * kTileM;
+            k0 = static_cast<int>(g % nkw) * kKW;
+        };
+        if (nstages > 0) {
+            int64_t r0;
+            int k0;
+            stage_origin(0, r0, k0);
+            prefetch_x<NT>(X, ldx, m, K, r0, k0, R, tid);
+        }
+        cp_async_commit();
+
+        for (int64_t g = 0; g < nstages; ++g) {
+            const int s = static_cast<int>(g & 1);
+            const int64_t t = blockIdx.x + (g / nkw) * gridDim.x;
+            const int kw = static_cast<int>(g % nkw);
+            const int64_t tm = t / ntn;
+            const int tn = static_cast<int>(t - tm * ntn);
+            const int64_t row = tm * kTileM + lr;
+            const int E = row < m ? xexp[row] : kNoExp;
+            // buffer s is free once the MMAs of stage g - 2 are done
+            if (pending[s]) {
+                const bool ok = mbar_wait_ab(&empty_bar[s], phase[s], &abort_s);
+                if (prod_sync_or(!ok, NT)) { timed_out = true; break; }
+                phase[s] ^= 1u;
+                pending[s] = false;
+            }
+            // B slices of stage g: one contiguous 32 KB block, 16-byte cp.async granules
+            const uint8_t* src = yblocks + static_cast<size_t>((tn * nkw + kw) * kSlices) * kBSlice;
+            for (int e = tid; e < kBStage / 16; e += NT) {
+                const unsigned dst = smem_u32(stB[s] + 16 * e);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 16 * e));
+            }
+            cp_async_commit();
+            // the raw X rows of stage g (copied during stage g - 1) are complete: slice this thread's row
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            prod_sync(NT);
+#pragma unroll
+            for (int cc = 0; cc < NCH; ++cc) {
+                const int c = NCH * rq + cc;
+                const double2* rp = reinterpret_cast<const double2*>(R + lr * kRawLd + 8 * c);
+                double x[8];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const double2 v = rp[i];
+                    x[2 * i] = v.x;
+                    x[2 * i + 1] = v.y;
+                }
+                slice_store8(x, E, stA[s] + core_off(lr, 16 * c), kASlice);
+            }
+            // R is free: copy the raw X rows of stage g + 1
+            prod_sync(NT);
+            if (g + 1 < nstages) {
+                int64_t r0;
+                int k0;
+                stage_origin(g + 1, r0, k0);
+                prefetch_x<NT>(X, ldx, m, K, r0, k0, R, tid);
+            }
+            cp_async_commit();
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // the B slices of stage g
+            fence_async_smem();
+            // stage g opens an exactness window: drain the previous window's accumulators first
+            if (g > 0 && (kw & 3) == 0) {
+                const int sp = s ^ 1;
+                if (pending[sp]) {
+                    const bool ok = mbar_wait_ab(&empty_bar[sp], phase[sp], &abort_s);
+                    if (prod_sync_or(!ok, NT)) { timed_out = true; break; }
+                    phase[sp] ^= 1u;
+                    pending[sp] = false;
+                }
+                tc_after_sync();
+                if (kw == 0) {
+                    // every MMA so far is complete: stage sp's buffer stages the output tile
+                    gemm_store_tile<WIN, NT, NC>(tmem, warp, tid, cur_row0, cur_tn, cur_E, N, yexp, C, ldc, m,
+                                                 reinterpret_cast<double*>(stA[sp]), acc);
+#pragma unroll
+                    for (int j = 0; j < NC; ++j) acc[j] = 0;
+                } else if (WIN) {
+                    drain_acc<true>(tmem, warp, NC * rq, acc);
+                }
+            }
+            if (kw == 0) {
+                cur_row0 = tm * kTileM;
+                cur_tn = tn;
+                cur_E = E;
+            }
+            // stage g is ready (and TMEM drained if it opens a window): hand it to the MMA warp
+            tc_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full_bar[s]);
+            pending[s] = true;
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        // the last tile
+        if (!timed_out && nstages > 0) {
+            for (int s = 0; s < 2 && !timed_out; ++s)
+                if (pending[s]) {
+                    const bool ok = mbar_wait_ab(&empty_bar[s], phase[s], &abort_s);
+                    if (prod_sync_or(!ok, NT)) { timed_out = true; break; }
+                    phase[s] ^= 1u;
+                    pending[s] = false;
+                }
+            if (!timed_out) {
+                tc_after_sync();
+                gemm_store_tile<WIN, NT, NC>(tmem, warp, tid, cur_row0, cur_tn, cur_E, N, yexp, C, ldc, m,
+                                             reinterpret_cast<double*>(stA[0]), acc);
+            }
+        }
+        if (timed_out) abort_s = 1;
+    }
+
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid == 0 && abort_s) set_status(info, RPCHOLQR_ERR_TIMEOUT);
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
 }
@@ -706,15 +1023,22 @@ cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int3
                               const uint8_t* yblocks, const int32_t* yexp, int N, const double* B,
                               int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, int grid,
                               cudaStream_t st) {
-    const int smem = 2 * (oz::kAStage + oz::kBStage);
     if (K > 32 * oz::kKW) return cudaErrorInvalidValue;   // int64 accumulators hold K <= 1024
     const bool win = K > 4 * oz::kKW;
-    auto kern = sub ? (win ? oz::k_ozaki_gemm<true, true> : oz::k_ozaki_gemm<true, false>)
-                    : (win ? oz::k_ozaki_gemm<false, true> : oz::k_ozaki_gemm<false, false>);
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int nt = win ? oz::kThreadsWin : oz::kThreads;
+    cudaError_t err;
+    if (!sub) {
+        auto kern = win ? oz::k_ozaki_gemm_ws<true> : oz::k_ozaki_gemm_ws<false>;
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::kGemmSmem);
+        if (err != cudaSuccess) return err;
+        kern<<<grid, nt + 32, oz::kGemmSmem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, C, ldc, m, info);
+        return cudaGetLastError();
+    }
+    const int smem = 2 * (oz::kAStage + oz::kBStage);
+    auto kern = win ? oz::k_ozaki_gemm<true, true> : oz::k_ozaki_gemm<true, false>;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (err != cudaSuccess) return err;
-    kern<<<grid, win ? oz::kThreadsWin : oz::kThreads, smem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb, C,
-                                                                  ldc, m, info);
+    kern<<<grid, nt, smem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb, C, ldc, m, info);
     return cudaGetLastError();
 }
 
