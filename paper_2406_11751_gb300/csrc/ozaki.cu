@@ -804,6 +804,219 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
 }
 
+// ---- C = B - X Y for K <= 32 (the right-looking updates of the split first pass) -------------------------
+// Tiles of 128 rows x 32 output columns, so that one tile's eight group accumulators take 256 TMEM
+// columns and two tiles are in flight: the tensor core fills one buffer while the other is drained.
+// The X slices of a 128-row block (one K stage) are produced once and used by all N/32 column tiles of
+// the block; the Y slices (at most 128 columns) stay in shared memory for the whole launch.  Warp roles:
+// warps 0-3 produce (thread = row of the block), warps 4-11 drain (warp w reads TMEM lanes 32 (w % 4)..,
+// columns 16 ((w - 4) / 4)..), warp 12 issues the MMAs.  Barriers: stage_full/stage_empty per X stage
+// buffer, acc_full/acc_empty per TMEM buffer.  Same exactness window, combination and rounding as
+// k_ozaki_gemm<true, false>: the results are identical.
+constexpr int kUpdTileN = 32;
+constexpr int kUpdMaxN = 128;
+constexpr int kUpdProducers = 4, kUpdDrainers = 8;
+constexpr int kUpdThreads = 32 * (kUpdProducers + kUpdDrainers + 1);
+constexpr int kUpdSmem = 2 * kAStage + (kUpdMaxN / kTileN) * kBStage;   // 192 KB
+constexpr uint32_t kIdescN32 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kUpdTileN >> 3) << 17) |
+                               ((uint32_t)(kTileM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16_n32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(kIdescN32), "r"(acc));
+}
+
+// The 36 slice pairs of one 32-column tile for nkk K steps of 16 (group d into columns (d - 2) * 32 of
+// the tile's TMEM buffer); the first MMA into each group clears it.
+__device__ __forceinline__ void issue_tile_n32(uint32_t tmem, uint32_t a_base, uint32_t b_base, int nkk) {
+    const uint64_t a0 = sdesc(a_base), b0 = sdesc(b_base);
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+        if (kk >= nkk) break;
+#pragma unroll
+        for (int d = 2; d <= 9; ++d) {
+            const int alo = d - 8 > 1 ? d - 8 : 1, ahi = d - 1 < 8 ? d - 1 : 8;
+#pragma unroll
+            for (int a = alo; a <= ahi; ++a) {
+                const int b = d - a;
+                const uint64_t ad = a0 + static_cast<uint32_t>(((a - 1) * kASlice + kk * 256) >> 4);
+                const uint64_t bd = b0 + static_cast<uint32_t>(((b - 1) * kBSlice + kk * 256) >> 4);
+                mma_bf16_n32(tmem + (d - 2) * kUpdTileN, ad, bd, (kk == 0 && a == alo) ? 0u : 1u);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kUpdThreads, 1)
+k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int K,
+               const uint8_t* __restrict__ yblocks, const int32_t* __restrict__ yexp, int N, const double* B,
+               int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint64_t stage_full[2], stage_empty[2], acc_full[2], acc_empty[2], done_bar;
+    __shared__ uint32_t tslot;
+    __shared__ int abort_s;
+    if (load_status(info) != 0) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t* stA[2] = {sm, sm + kAStage};
+    uint8_t* yres = sm + 2 * kAStage;                 // Y slices: 64-column block j at j * kBStage
+    const int nsub = (N + kUpdTileN - 1) / kUpdTileN;
+    const int nkk = (K + 15) / 16;
+    const int64_t ntm = (m + kTileM - 1) / kTileM;
+    const int64_t my_tiles =
+        static_cast<int64_t>(blockIdx.x) < ntm ? (ntm - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tslot)), "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&stage_full[i])),
+                         "r"(kUpdProducers));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&stage_empty[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&acc_full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&acc_empty[i])),
+                         "r"(kUpdDrainers));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&done_bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+        abort_s = 0;
+    }
+    // the Y slices of every column block (K <= 32: one K stage each), resident for the launch
+    {
+        const int bytes = ((N + kTileN - 1) / kTileN) * kBStage;
+        for (int e = tid; e < bytes / 16; e += kUpdThreads) {
+            const unsigned dst = smem_u32(yres + 16 * e);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(yblocks + 16 * e));
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        fence_async_smem();
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tslot;
+
+    if (warp < kUpdProducers) {
+        // producers: thread = row of the 128-row block; slice its K values into the block's stage
+        const int lr = tid;
+        uint32_t ph[2] = {0u, 0u};
+        for (int64_t t = 0; t < my_tiles; ++t) {
+            const int s = static_cast<int>(t & 1);
+            if (t >= 2) {
+                if (!mbar_wait_ab(&stage_empty[s], ph[s], &abort_s)) { abort_s = 1; break; }
+                ph[s] ^= 1u;
+            }
+            const int64_t row = (blockIdx.x + t * gridDim.x) * kTileM + lr;
+            const int E = row < m ? xexp[row] : kNoExp;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (c >= 2 * nkk) break;          // chunks the MMAs read; values k >= K are zero
+                double x[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int k = 8 * c + i;
+                    x[i] = (row < m && k < K) ? X[row * ldx + k] : 0.0;
+                }
+                slice_store8(x, E, stA[s] + core_off(lr, 16 * c), kASlice);
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&stage_full[s]);
+        }
+    } else if (warp < kUpdProducers + kUpdDrainers) {
+        // drainers: warp w reads TMEM lanes 32 (w % 4).. and columns 16 h.. of every tile
+        const int q = warp & 3, h = (warp - kUpdProducers) >> 2;
+        const int lr = 32 * q + lane;
+        int64_t u = 0;   // tiles drained so far (TMEM buffer u & 1)
+        for (int64_t t = 0; t < my_tiles && !*reinterpret_cast<volatile int*>(&abort_s); ++t) {
+            const int64_t row = (blockIdx.x + t * gridDim.x) * kTileM + lr;
+            const int E = row < m ? xexp[row] : kNoExp;
+            for (int j = 0; j < nsub; ++j, ++u) {
+                const int b = static_cast<int>(u & 1);
+                if (!mbar_wait_ab(&acc_full[b], static_cast<uint32_t>((u >> 1) & 1), &abort_s)) {
+                    abort_s = 1;
+                    break;
+                }
+                tc_after_sync();
+                const uint32_t tb = tmem + (static_cast<uint32_t>(32 * q) << 16) + 256u * b + 16u * h;
+                const int cbase = j * kUpdTileN + 16 * h;
+#pragma unroll 1
+                for (int c0 = 0; c0 < 16; c0 += 4) {
+                    double bv[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int col = cbase + c0 + i;
+                        bv[i] = (row < m && col < N) ? B[row * ldb + col] : 0.0;
+                    }
+                    float mg[kGroups][4];
+#pragma unroll
+                    for (int g = 0; g < kGroups; ++g) tmem_ld4(tb + g * kUpdTileN + c0, mg[g]);
+                    tmem_wait_ld();
+                    if (row < m) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int col = cbase + c0 + i;
+                            if (col < N) {
+                                float grp[kGroups];
+#pragma unroll
+                                for (int g = 0; g < kGroups; ++g) grp[g] = mg[g][i];
+                                const long long I = combine_units53(grp);
+                                const int ey = yexp[col];
+                                const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(I, E + ey - 53) : 0.0;
+                                C[row * ldc + col] = bv[i] - v;
+                            }
+                        }
+                    }
+                }
+                tc_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[b]);
+            }
+        }
+    } else {
+        // MMA warp: one lane issues the column tiles of every block into alternating TMEM buffers
+        if (lane == 0) {
+            uint32_t phs[2] = {0u, 0u};
+            int64_t u = 0;
+            for (int64_t t = 0; t < my_tiles; ++t) {
+                const int s = static_cast<int>(t & 1);
+                if (!mbar_wait_ab(&stage_full[s], phs[s], &abort_s)) { abort_s = 1; break; }
+                phs[s] ^= 1u;
+                tc_after_sync();
+                bool ok = true;
+                for (int j = 0; j < nsub; ++j, ++u) {
+                    const int b = static_cast<int>(u & 1);
+                    if (u >= 2 && !mbar_wait_ab(&acc_empty[b], static_cast<uint32_t>(((u >> 1) + 1) & 1), &abort_s)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_after_sync();
+                    const uint32_t bbase = smem_u32(yres) + (j >> 1) * kBStage + (j & 1) * (kUpdTileN / 8) * kSBO;
+                    issue_tile_n32(tmem + 256u * b, smem_u32(stA[s]), bbase, nkk);
+                    mma_commit(&acc_full[b]);
+                }
+                if (!ok) { abort_s = 1; break; }
+                mma_commit(&stage_empty[s]);
+            }
+            mma_commit(&done_bar);
+            if (!mbar_wait(&done_bar, 0u)) abort_s = 1;
+        }
+        __syncwarp();
+    }
+
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid == 0 && abort_s) set_status(info, RPCHOLQR_ERR_TIMEOUT);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+}
+
 // ---- Gram partials G_rr = X_rr^T X_rr -------------------------------------------------------------------
 // X: m x n FP64 (ldx), column exponent bounds colexp[n] over all m rows.  Output tiles (P, Qb): rows
 // p in [128P, 128P+128) (TMEM lanes) x columns q in [64Qb, 64Qb+64), all tiles with Qb >= 2P (every
@@ -1032,6 +1245,15 @@ cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int3
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::kGemmSmem);
         if (err != cudaSuccess) return err;
         kern<<<grid, nt + 32, oz::kGemmSmem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, C, ldc, m, info);
+        return cudaGetLastError();
+    }
+    if (K <= oz::kKW && N <= oz::kUpdMaxN) {
+        const int64_t ntm = (m + oz::kTileM - 1) / oz::kTileM;
+        const int g = static_cast<int>(grid < ntm ? grid : ntm);
+        err = cudaFuncSetAttribute(oz::k_ozaki_update, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::kUpdSmem);
+        if (err != cudaSuccess) return err;
+        oz::k_ozaki_update<<<g, oz::kUpdThreads, oz::kUpdSmem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb, C,
+                                                                    ldc, m, info);
         return cudaGetLastError();
     }
     const int smem = 2 * (oz::kAStage + oz::kBStage);
