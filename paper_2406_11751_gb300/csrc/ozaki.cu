@@ -172,32 +172,36 @@ __device__ __forceinline__ void fixed56(double x, int E, uint32_t& fhi, uint32_t
     flo = static_cast<uint32_t>(F) & 0x0FFFFFFFu;
 }
 
-// Two 7-bit fields (bits pos..pos+6 of u0 and u1) as a packed BF16 pair (u0 in the low half): each
-// field v becomes the float 2^23 + v minus 2^23, whose upper 16 bits are the exact BF16 of v.
-__device__ __forceinline__ uint32_t bf16x2_field(uint32_t u0, uint32_t u1, int pos) {
-    const float f0 = __uint_as_float(0x4B000000u | ((u0 >> pos) & 0x7Fu)) - 8388608.0f;
-    const float f1 = __uint_as_float(0x4B000000u | ((u1 >> pos) & 0x7Fu)) - 8388608.0f;
-    return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+// Two 7-bit fields (bits pos..pos+6 of u0 and u1) as a packed BF16 pair (u0 in the low half), signed:
+// the pair of BF16 numbers 128 + v (exponent 7, mantissa v) goes through one packed BF16 FMA,
+// (128 + v) s - 128 s = s v, exact.  sgn2: the BF16 pair (s0, s1), s = +-1; off2: (-128 s0, -128 s1).
+__device__ __forceinline__ uint32_t bf16x2_field(uint32_t u0, uint32_t u1, int pos, uint32_t sgn2, uint32_t off2) {
+    const uint32_t t = ((u0 >> pos) & 0x7Fu) | (((u1 >> pos) & 0x7Fu) << 16) | 0x43004300u;
+    uint32_t r;
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;\n" : "=r"(r) : "r"(t), "r"(sgn2), "r"(off2));
+    return r;
 }
 
 // Slice the 8 values x[0..7] (consecutive K) and store slice a of all eight as one 16-byte core-matrix
 // row at dst + a * slice_bytes (x[i] in BF16 lane i).  Every slice carries the sign of its value.
 __device__ __forceinline__ void slice_store8(const double (&x)[8], int E, uint8_t* dst, int slice_bytes) {
-    uint32_t fh[8], fl[8], smask[4];
+    uint32_t fh[8], fl[8], sgn2[4], off2[4];
 #pragma unroll
     for (int i = 0; i < 8; ++i) fixed56(x[i], E, fh[i], fl[i]);
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-        smask[j] = ((__double_as_longlong(x[2 * j]) < 0) ? 0x8000u : 0u) |
-                   ((__double_as_longlong(x[2 * j + 1]) < 0) ? 0x80000000u : 0u);
+    for (int j = 0; j < 4; ++j) {
+        const bool n0 = __double_as_longlong(x[2 * j]) < 0, n1 = __double_as_longlong(x[2 * j + 1]) < 0;
+        sgn2[j] = (n0 ? 0xBF80u : 0x3F80u) | ((n1 ? 0xBF80u : 0x3F80u) << 16);    // -1 / +1
+        off2[j] = (n0 ? 0x4300u : 0xC300u) | ((n1 ? 0x4300u : 0xC300u) << 16);    // +128 / -128
+    }
 #pragma unroll
     for (int a = 0; a < kSlices; ++a) {
         const int pos = 21 - 7 * (a & 3);
         uint32_t w[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            w[j] = (a < 4 ? bf16x2_field(fh[2 * j], fh[2 * j + 1], pos) : bf16x2_field(fl[2 * j], fl[2 * j + 1], pos)) |
-                   smask[j];
+            w[j] = a < 4 ? bf16x2_field(fh[2 * j], fh[2 * j + 1], pos, sgn2[j], off2[j])
+                         : bf16x2_field(fl[2 * j], fl[2 * j + 1], pos, sgn2[j], off2[j]);
         *reinterpret_cast<uint4*>(dst + a * slice_bytes) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
@@ -212,6 +216,19 @@ __device__ __forceinline__ void combine_groups(const float (&m)[kGroups], long l
         (static_cast<long long>(__float2int_rn(m[3])) << 7) + static_cast<long long>(__float2int_rn(m[4]));
     L = (static_cast<long long>(__float2int_rn(m[5])) << 14) +
         (static_cast<long long>(__float2int_rn(m[6])) << 7) + static_cast<long long>(__float2int_rn(m[7]));
+}
+// For K <= 32 every group sum is below 8 * 127^2 * 32 < 2^22 in magnitude, so M + 1.5 2^23 holds M
+// exactly in its low mantissa bits: the integer is read from the bit pattern (no conversion instruction).
+__device__ __forceinline__ long long combine_units53_k32(const float (&m)[kGroups]) {
+    int v[kGroups];
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) v[g] = __float_as_int(m[g] + 12582912.0f) - 0x4B400000;
+    const long long I = (static_cast<long long>(v[0]) << 28) + (static_cast<long long>(v[1]) << 21) +
+                        (static_cast<long long>(v[2]) << 14) + (static_cast<long long>(v[3]) << 7) +
+                        static_cast<long long>(v[4]);
+    const long long L = (static_cast<long long>(v[5]) << 14) + (static_cast<long long>(v[6]) << 7) +
+                        static_cast<long long>(v[7]);
+    return (I << 11) + ((L + 512) >> 10);
 }
 // the value in units of 2^-53 (rounded), for a single-window product: |result| < 2^61
 __device__ __forceinline__ long long combine_units53(const float (&m)[kGroups]) {
@@ -237,21 +254,22 @@ __device__ __forceinline__ double scale_pow2(long long I, int e) {
     return ldexp(v, e);
 }
 
-// Add the eight TMEM group sums of this thread's row and its kDrainCols columns (col0.. of the 64-column
-// tile) to int64 accumulators in units of 2^-53 (U53) or 2^-49 of the operand scale.
+// Add the eight TMEM group sums of this thread's row and its NC columns (col0.. of the 64-column tile,
+// read CW at a time) to int64 accumulators in units of 2^-53 (U53) or 2^-49 of the operand scale.
 // The sliced operands are below 0.51 of their power-of-two bounds, so a K-term sum stays below
 // 0.26 K scale: units of 2^-53 hold K <= 2^10 terms, units of 2^-49 hold 2^14 (a 64-window flush).
-template <bool U53, int NC>
+template <bool U53, int NC, int CW = 8>
 __device__ __forceinline__ void drain_acc(uint32_t tmem, int warp, int col0, long long (&acc)[NC]) {
 #pragma unroll
-    for (int c0 = 0; c0 < NC; c0 += 8) {
-        float mg[kGroups][8];
+    for (int c0 = 0; c0 < NC; c0 += CW) {
+        float mg[kGroups][CW];
 #pragma unroll
         for (int g = 0; g < kGroups; ++g)
-            tmem_ld8(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + g * kTileN + col0 + c0, mg[g]);
+            if constexpr (CW == 8) tmem_ld8(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + g * kTileN + col0 + c0, mg[g]);
+            else tmem_ld4(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + g * kTileN + col0 + c0, mg[g]);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < CW; ++j) {
             float grp[kGroups];
 #pragma unroll
             for (int g = 0; g < kGroups; ++g) grp[g] = mg[g][j];
@@ -938,21 +956,22 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
             const int E = row < m ? xexp[row] : kNoExp;
             for (int j = 0; j < nsub; ++j, ++u) {
                 const int b = static_cast<int>(u & 1);
+                const int cbase = j * kUpdTileN + 16 * h;
+                // this thread's 16 values of B, read while the tile's MMAs run
+                double bv[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int col = cbase + i;
+                    bv[i] = (row < m && col < N) ? B[row * ldb + col] : 0.0;
+                }
                 if (!mbar_wait_ab(&acc_full[b], static_cast<uint32_t>((u >> 1) & 1), &abort_s)) {
                     abort_s = 1;
                     break;
                 }
                 tc_after_sync();
                 const uint32_t tb = tmem + (static_cast<uint32_t>(32 * q) << 16) + 256u * b + 16u * h;
-                const int cbase = j * kUpdTileN + 16 * h;
-#pragma unroll 1
-                for (int c0 = 0; c0 < 16; c0 += 4) {
-                    double bv[4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int col = cbase + c0 + i;
-                        bv[i] = (row < m && col < N) ? B[row * ldb + col] : 0.0;
-                    }
+                for (int c0 = 0; c0 < 16; c0 += 4) {
                     float mg[kGroups][4];
 #pragma unroll
                     for (int g = 0; g < kGroups; ++g) tmem_ld4(tb + g * kUpdTileN + c0, mg[g]);
@@ -965,10 +984,10 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
                                 float grp[kGroups];
 #pragma unroll
                                 for (int g = 0; g < kGroups; ++g) grp[g] = mg[g][i];
-                                const long long I = combine_units53(grp);
+                                const long long I = combine_units53_k32(grp);
                                 const int ey = yexp[col];
                                 const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(I, E + ey - 53) : 0.0;
-                                C[row * ldc + col] = bv[i] - v;
+                                C[row * ldc + col] = bv[c0 + i] - v;
                             }
                         }
                     }
@@ -1032,15 +1051,22 @@ __device__ __forceinline__ void gram_tile_coords(int nqb, int tt, int& P, int& Q
     Qb = 2 * P + tt;
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+// Warp roles: kGramNT producer threads slice and drain; the last warp issues the MMAs (full[s]: stage s
+// sliced, one arrival per producer warp; empty[s]: its MMAs done).  A window's drain waits for the
+// MMAs of the stage before and arrives on full of the next stage only after reading TMEM.
+constexpr int kGramNT = kThreads;
+__global__ void __launch_bounds__(kGramNT + 32, 1)
 k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np,
              const int32_t* __restrict__ colexp, int64_t rows_per, int ntiles, double* __restrict__ gpart,
              int32_t* info) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    __shared__ uint64_t mbar[2];
+    __shared__ uint64_t empty_bar[2], full_bar[2], done_bar;
     __shared__ uint32_t tslot;
+    __shared__ int abort_s;
     if (load_status(info) != 0) return;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    constexpr int NT = kGramNT;
+    constexpr int kCols = Share<NT>::kDrainCols, NCH = Share<NT>::kChunks;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nqb = (np + kTileN - 1) / kTileN;
     int P, Qb;
     gram_tile_coords(nqb, blockIdx.x % ntiles, P, Qb);
@@ -1057,134 +1083,154 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty_bar[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full_bar[i])), "r"(NT / 32));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&done_bar)));
         asm volatile("fence.mbarrier_init.release.cluster;\n");
+        abort_s = 0;
     }
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = tslot;
-
-    const int lr = tid & 127;               // TMEM lane: output row p = 128P + lr; producer column of A
-    const int rq = tid >> 7;                // producer row chunk(s) kChunks*rq..; drain columns kDrainCols*rq..
-    const int p = 128 * P + lr;
-    const int Ep = p < n ? colexp[p] : kNoExp;
-    const int qb_col = 64 * Qb + (tid & 63);          // B producer column (when B is separate)
-    const int Eqb = qb_col < n ? colexp[qb_col] : kNoExp;
-    constexpr int kCols = kDrainCols;
-    long long acc[kCols];
-#pragma unroll
-    for (int j = 0; j < kCols; ++j) acc[j] = 0;
-    uint32_t phase[2] = {0u, 0u};
-    bool pending[2] = {false, false};
-    bool timed_out = false;
     const int64_t nstages = r1 > r0 ? (r1 - r0 + kKW - 1) / kKW : 0;
 
-    // Drain the window just finished (its MMAs complete) into acc; every 64 windows, and at the end,
-    // add acc into the CTA's FP64 partial (the first flush initialises it) and clear it.
-    bool flushed = false;
-    auto drain_window = [&](bool flush) {
-        tc_after_sync();
-        drain_acc<false, kCols>(tmem, warp, kCols * rq, acc);
-        if (flush && p < np) {
-            double* out = gpart + static_cast<size_t>(rr) * np * np + static_cast<size_t>(p) * np;
+    if (warp == NT / 32) {
+        if (lane == 0) {
+            uint32_t fphase[2] = {0u, 0u};
+            const uint32_t boff = b_inside ? static_cast<uint32_t>(((64 * Qb - 128 * P) / 8) * kSBO) : 0u;
+            for (int64_t st = 0; st < nstages; ++st) {
+                const int s = static_cast<int>(st & 1);
+                if (!mbar_wait_ab(&full_bar[s], fphase[s], &abort_s)) {
+                    abort_s = 1;
+                    break;
+                }
+                fphase[s] ^= 1u;
+                tc_after_sync();
+                if (b_inside)
+                    issue_stage(tmem, smem_u32(stA[s]), smem_u32(stA[s]) + boff, kASlice, (st & 3) == 0);
+                else
+                    issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), kBSlice, (st & 3) == 0);
+                mma_commit(&empty_bar[s]);
+            }
+            mma_commit(&done_bar);
+            if (!mbar_wait(&done_bar, 0u)) abort_s = 1;
+        }
+        __syncwarp();
+    } else {
+        const int lr = tid & 127;               // TMEM lane: output row p = 128P + lr; producer column of A
+        const int rq = tid >> 7;                // producer row chunk(s) NCH*rq..; drain columns kCols*rq..
+        const int p = 128 * P + lr;
+        const int Ep = p < n ? colexp[p] : kNoExp;
+        const int qb_col = 64 * Qb + (tid & 63);          // B producer column (when B is separate)
+        const int Eqb = qb_col < n ? colexp[qb_col] : kNoExp;
+        long long acc[kCols];
 #pragma unroll
+        for (int j = 0; j < kCols; ++j) acc[j] = 0;
+        uint32_t phase[2] = {0u, 0u};
+        bool pending[2] = {false, false};
+        bool timed_out = false;
+
+        // Drain the window just finished (its MMAs complete) into acc; every 64 windows, and at the end,
+        // add acc into the CTA's FP64 partial (the first flush initialises it) and clear it.
+        bool flushed = false;
+        auto drain_window = [&](bool flush) {
+            tc_after_sync();
+            drain_acc<false, kCols, 4>(tmem, warp, kCols * rq, acc);
+            if (flush && p < np) {
+                double* out = gpart + static_cast<size_t>(rr) * np * np + static_cast<size_t>(p) * np;
+#pragma unroll
+                for (int j = 0; j < kCols; ++j) {
+                    const int q = 64 * Qb + kCols * rq + j;
+                    if (q < np) {
+                        const int Eq = q < n ? colexp[q] : kNoExp;
+                        const double v = (Ep > kNoExp && Eq > kNoExp) ? scale_pow2(acc[j], Ep + Eq - 49) : 0.0;
+                        out[q] = (flushed ? out[q] : 0.0) + v;
+                    }
+                    acc[j] = 0;
+                }
+            }
+            if (flush) flushed = true;
+        };
+
+        // Stage st is sliced into buffer st & 1 while the MMAs of stage st - 1 run; a stage that opens a
+        // window first drains the previous window (after being produced, before it is handed over).
+        for (int64_t st = 0; st < nstages; ++st) {
+            const int s = static_cast<int>(st & 1);
+            if (pending[s]) {
+                const bool ok = mbar_wait_ab(&empty_bar[s], phase[s], &abort_s);
+                if (prod_sync_or(!ok, NT)) { timed_out = true; break; }
+                phase[s] ^= 1u;
+                pending[s] = false;
+            }
+            const int64_t k0 = r0 + st * kKW;
+#pragma unroll
+            for (int cc = 0; cc < NCH; ++cc) {
+                const int c = NCH * rq + cc;
+                double x[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int64_t row = k0 + 8 * c + i;
+                    x[i] = (row < r1 && p < n) ? X[row * ldx + p] : 0.0;
+                }
+                slice_store8(x, Ep, stA[s] + core_off(lr, 16 * c), kASlice);
+            }
+            if (!b_inside) {
+                for (int e = tid; e < 4 * 64; e += NT) {
+                    const int c = e >> 6, col = 64 * Qb + (e & 63);   // 64 columns x 4 chunks of 8 rows
+                    const int Ec = col < n ? colexp[col] : kNoExp;
+                    double x[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int64_t row = k0 + 8 * c + i;
+                        x[i] = (row < r1 && col < n) ? X[row * ldx + col] : 0.0;
+                    }
+                    slice_store8(x, Ec, stB[s] + core_off(e & 63, 16 * c), kBSlice);
+                }
+            }
+            fence_async_smem();
+            if (st > 0 && (st & 3) == 0) {
+                const int sp = s ^ 1;
+                if (pending[sp]) {
+                    const bool ok = mbar_wait_ab(&empty_bar[sp], phase[sp], &abort_s);
+                    if (prod_sync_or(!ok, NT)) { timed_out = true; break; }
+                    phase[sp] ^= 1u;
+                    pending[sp] = false;
+                }
+                drain_window((st & 255) == 0);   // the window ending at stage st - 1; every 64 windows flush
+            }
+            tc_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full_bar[s]);
+            pending[s] = true;
+        }
+        if (!timed_out && nstages > 0) {
+            for (int q = 0; q < 2 && !timed_out; ++q)
+                if (pending[q]) {
+                    const bool ok = mbar_wait_ab(&empty_bar[q], phase[q], &abort_s);
+                    if (prod_sync_or(!ok, NT)) { timed_out = true; break; }
+                    phase[q] ^= 1u;
+                    pending[q] = false;
+                }
+            if (!timed_out) drain_window(true);
+        }
+        if (timed_out) {
+            abort_s = 1;
+        } else if (nstages == 0 && p < np) {
+            double* out = gpart + static_cast<size_t>(rr) * np * np + static_cast<size_t>(p) * np;
             for (int j = 0; j < kCols; ++j) {
                 const int q = 64 * Qb + kCols * rq + j;
-                if (q < np) {
-                    const int Eq = q < n ? colexp[q] : kNoExp;
-                    const double v = (Ep > kNoExp && Eq > kNoExp) ? scale_pow2(acc[j], Ep + Eq - 49) : 0.0;
-                    out[q] = (flushed ? out[q] : 0.0) + v;
-                }
-                acc[j] = 0;
+                if (q < np) out[q] = 0.0;
             }
         }
-        if (flush) flushed = true;
-    };
-
-    // Stage st is sliced into buffer st & 1 while the MMAs of stage st - 1 run; a stage that opens a
-    // window first drains the previous window (after being produced, before its MMAs are issued).
-    for (int64_t st = 0; st < nstages; ++st) {
-        const int s = static_cast<int>(st & 1);
-        if (pending[s]) {
-            const bool ok = mbar_wait(&mbar[s], phase[s]);
-            if (__syncthreads_or(!ok)) { timed_out = true; break; }
-            phase[s] ^= 1u;
-            pending[s] = false;
-        }
-        const int64_t k0 = r0 + st * kKW;
-#pragma unroll
-        for (int cc = 0; cc < kChunks; ++cc) {
-            const int c = kChunks * rq + cc;
-            double x[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int64_t row = k0 + 8 * c + i;
-                x[i] = (row < r1 && p < n) ? X[row * ldx + p] : 0.0;
-            }
-            slice_store8(x, Ep, stA[s] + core_off(lr, 16 * c), kASlice);
-        }
-        if (!b_inside && (tid >> 6) < 4) {
-            const int c = tid >> 6;         // 64 columns x 4 chunks of 8 rows
-            double x[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int64_t row = k0 + 8 * c + i;
-                x[i] = (row < r1 && qb_col < n) ? X[row * ldx + qb_col] : 0.0;
-            }
-            slice_store8(x, Eqb, stB[s] + core_off(tid & 63, 16 * c), kBSlice);
-        }
-        fence_async_smem();
-        const bool first_window = (st & 3) == 0;
-        if (st > 0 && first_window) {
-            const int sp = s ^ 1;
-            if (pending[sp]) {
-                const bool ok = mbar_wait(&mbar[sp], phase[sp]);
-                if (__syncthreads_or(!ok)) { timed_out = true; break; }
-                phase[sp] ^= 1u;
-                pending[sp] = false;
-            }
-            drain_window((st & 255) == 0);   // the window ending at stage st - 1; every 64 windows flush
-        }
-        tc_before_sync();
-        __syncthreads();
-        tc_after_sync();
-        if (tid == 0) {
-            if (b_inside)
-                issue_stage(tmem, smem_u32(stA[s]), smem_u32(stA[s]) + ((64 * Qb - 128 * P) / 8) * kSBO, kASlice,
-                            first_window);
-            else
-                issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), kBSlice, first_window);
-            mma_commit(&mbar[s]);
-        }
-        pending[s] = true;
-    }
-    if (!timed_out && nstages > 0) {
-        for (int q = 0; q < 2 && !timed_out; ++q)
-            if (pending[q]) {
-                const bool ok = mbar_wait(&mbar[q], phase[q]);
-                if (__syncthreads_or(!ok)) { timed_out = true; break; }
-                phase[q] ^= 1u;
-                pending[q] = false;
-            }
-        if (!timed_out) drain_window(true);
     }
 
-    if (timed_out) {
-        if (tid == 0) set_status(info, RPCHOLQR_ERR_TIMEOUT);
-        for (int s = 0; s < 2; ++s)
-            if (pending[s]) mbar_wait(&mbar[s], phase[s]);
-    } else if (nstages == 0 && p < np) {
-        double* out = gpart + static_cast<size_t>(rr) * np * np + static_cast<size_t>(p) * np;
-        for (int j = 0; j < kCols; ++j) {
-            const int q = 64 * Qb + kCols * rq + j;
-            if (q < np) out[q] = 0.0;
-        }
-    }
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
+    if (tid == 0 && abort_s) set_status(info, RPCHOLQR_ERR_TIMEOUT);
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
 }
@@ -1296,7 +1342,7 @@ cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, in
     const int nt = ozaki_gram_halves(np);
     int64_t rows_per = (m + nranges - 1) / nranges;
     rows_per = (rows_per + oz::kKW - 1) / oz::kKW * oz::kKW;
-    oz::k_ozaki_gram<<<nt * nranges, oz::kThreads, smem, st>>>(X, ldx, m, n, np, colexp, rows_per, nt, gpart,
+    oz::k_ozaki_gram<<<nt * nranges, oz::kGramNT + 32, smem, st>>>(X, ldx, m, n, np, colexp, rows_per, nt, gpart,
                                                                info);
     return cudaGetLastError();
 }
