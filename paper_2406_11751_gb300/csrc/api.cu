@@ -228,9 +228,13 @@ struct PhaseMarks {
 };
 
 constexpr int kBlk = 64;   // column block of the FP64 blocked solves (n > 128)
-// Diagonal block of the split mode's first pass: its FP64 work per row is n * kSplitBlk, the rest of
-// the solve runs as split tensor-core updates.
+// Blocks of the split mode's first pass (n <= 128): the FP64 row passes solve kSplitSub-column diagonal
+// blocks (FP64 work per row n * kSplitSub); the rest of the solve runs as split tensor-core updates,
+// K = kSplitBlk across blocks and K = kSplitSub inside one.  At m = 2^20, n = 128, sub-blocks of 16
+// measured the same step time as 32 (13.75 vs 13.79 ms: the FP64 work halves, the four extra K = 16
+// updates cost as much), so the blocks are not split.
 constexpr int kSplitBlk = 32;
+constexpr int kSplitSub = 32;
 // Split mode: the explicit-inverse second pass is used while ||R1||_F ||R1^{-1}||_F / n <= this
 // (1.1-1.25 for well-sampled incoherent A; the estimate lies in [kappa(A1)/n, kappa(A1)]; at 3.3
 // (kappa(A1) ~ 30) the explicit inverse already costs 10x in residual).
@@ -448,40 +452,58 @@ static void prep_blocks(rpcholqr_plan_s* p, const double* T, int64_t ldt, int n,
     }
 }
 
-// Right-looking blocked row solve for the split mode, Y = X T^{-1} over kSplitBlk-column blocks J:
-// Y[:, J] <- (current X[:, J]) T[J, J]^{-1} by the FP64 row pass, then every later column is updated
-// at once, Y[:, >J] = (X or Y)[:, >J] - Y[:, J] T[J, >J], as one split tensor-core product with
-// K = kSplitBlk (one exactness stage) and N = the remaining width.  The diagonal blocks must have been
-// set up by prep_blocks with blk = kSplitBlk.  The row passes store (block 0) and max-merge the row
-// bounds of Y into p->xexp (the update's left operand uses the bound over the blocks solved so far)
-// and their column bounds into p->colexp.  Marks PASS1 / PASS1_UPDATE / PASS1_SOLVE2 as the first
-// row pass / the first update / the rest when pm is given.
+// Right-looking blocked row solve for the split mode, Y = X T^{-1}, two-level: over kSplitBlk-column
+// blocks J, each solved as two kSplitSub-column halves.  A half is solved by the FP64 row pass,
+// Y[:, h] <- (current X[:, h]) T[h, h]^{-1}; after the first half, the second half is updated by one
+// split tensor-core product with K = N = kSplitSub; after the block, every later column is updated at
+// once, Y[:, >J] = (X or Y)[:, >J] - Y[:, J] T[J, >J], by one split product with K = kSplitBlk (one
+// exactness stage) and N = the remaining width.  The FP64 work per row is n * kSplitSub.  The diagonal
+// blocks must have been set up by prep_blocks with blk = kSplitSub.  The row passes store (first half)
+// and max-merge the row bounds of Y into p->xexp (the updates' left operands use the bound over the
+// columns solved so far) and their column bounds into p->colexp.  Marks PASS1 / PASS1_UPDATE /
+// PASS1_SOLVE2 as the first row pass / the first update / the rest when pm is given.
 static rpcholqr_status solve_split_right(rpcholqr_plan_s* p, const double* X, int64_t ldx, const double* T,
                                          int64_t ldt, int64_t m, int n, double* Y, int64_t ldy, const double* frag,
                                          const double* diag, int32_t* info, cudaStream_t st, const PhaseMarks* pm) {
     const int grid = row_grid(p, m);
-    const int blk = kSplitBlk;
+    const int blk = kSplitBlk, sub = kSplitSub;
+    bool first_update = true;
+    auto update = [&](int c0, int K, int c1, int N, const double* B, int64_t ldb) -> rpcholqr_status {
+        if (pm && first_update) pm->mark(RPCHOLQR_PHASE_PASS1_UPDATE);
+        rpcholqr_status rc = ozaki_gemm_internal(p, true, Y + c0, m, K, ldy, T + static_cast<int64_t>(c0) * ldt + c1,
+                                                 N, ldt, B, ldb, Y + c1, ldy, info, st, true);
+        if (pm && first_update) pm->mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
+        first_update = false;
+        return rc;
+    };
     for (int J = 0; J * blk < n; ++J) {
         const int c0 = J * blk;
         const int nj = n - c0 < blk ? n - c0 : blk;
-        const double* src = J == 0 ? X : Y;
-        const int64_t lsrc = J == 0 ? ldx : ldy;
-        if (launch_rowpass_ex(false, pad16(nj), src + c0, lsrc, Y + c0, ldy, m, nj, frag + J * blk * blk,
-                              diag + J * (blk / 8) * 64, nullptr, info, grid, st, true, p->xexp, J == 0 ? 1 : 2,
-                              p->colexp + c0) != cudaSuccess)
-            return RPCHOLQR_ERR_CUDA;
-        ++p->launches;
+        for (int h = 0; h * sub < nj; ++h) {
+            const int c1 = c0 + h * sub;
+            const int nh = nj - h * sub < sub ? nj - h * sub : sub;
+            // column c1 still holds A only in the very first half; later ones were written by an update
+            const double* src = c1 == 0 ? X : Y;
+            const int64_t lsrc = c1 == 0 ? ldx : ldy;
+            const int js = c1 / sub;
+            if (launch_rowpass_ex(false, pad16(nh), src + c1, lsrc, Y + c1, ldy, m, nh, frag + js * sub * sub,
+                                  diag + js * (sub / 8) * 64, nullptr, info, grid, st, true, p->xexp,
+                                  c1 == 0 ? 1 : 2, p->colexp + c1) != cudaSuccess)
+                return RPCHOLQR_ERR_CUDA;
+            ++p->launches;
+            if (h == 0 && nj > nh) {
+                const rpcholqr_status rc = update(c1, nh, c1 + nh, nj - nh, (J == 0 ? X : Y) + c1 + nh,
+                                                  J == 0 ? ldx : ldy);
+                if (rc != RPCHOLQR_OK) return rc;
+            }
+        }
         const int rest = n - c0 - nj;
         if (rest > 0) {
-            if (pm && J == 0) pm->mark(RPCHOLQR_PHASE_PASS1_UPDATE);
-            rpcholqr_status rc = ozaki_gemm_internal(p, true, Y + c0, m, nj, ldy, T + static_cast<int64_t>(c0) * ldt +
-                                                     c0 + nj, rest, ldt, src + c0 + nj, lsrc, Y + c0 + nj, ldy, info,
-                                                     st, true);
+            const rpcholqr_status rc = update(c0, nj, c0 + nj, rest, (J == 0 ? X : Y) + c0 + nj, J == 0 ? ldx : ldy);
             if (rc != RPCHOLQR_OK) return rc;
-            if (pm && J == 0) pm->mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
         }
     }
-    if (pm && n <= blk) {
+    if (pm && first_update) {
         pm->mark(RPCHOLQR_PHASE_PASS1_UPDATE);
         pm->mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
     }
@@ -673,7 +695,7 @@ static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m,
     // Up to 128 columns: 32-column blocks, right-looking (every update one K stage, wide N); above:
     // 64-column blocks, left-looking (long K windows; fewer passes over the trailing columns).
     if (np <= kMaxNP) {
-        prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st, kSplitBlk);
+        prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st, kSplitSub);
         pm.mark(RPCHOLQR_PHASE_PASS1);
         rc = solve_split_right(p, A, lda, p->Rs, np, m, n, A1, ld1, p->frag_s, p->diag_s, info, st, &pm);
     } else {

@@ -2,11 +2,11 @@
 //
 // Used by the SPLIT64 mode for the well-conditioned products of Algorithm alg_2 (Section 4):
 //   Gram          G_1 = A_1^T A_1               (k_ozaki_gram)
-//   solve         Q   = A_1 R_1^{-1}            (k_ozaki_gemm with the explicit R_1^{-1}; kappa(R_1) =
+//   solve         Q   = A_1 R_1^{-1}            (k_ozaki_gemm_ws with the explicit R_1^{-1}; kappa(R_1) =
 //                                                kappa(A_1) is small, Lemma l_31)
 //   precondition  the off-diagonal block update A[:,J] - A_1[:,<J] R_s[<J,J] of the blocked row solve
-//                                               (k_ozaki_gemm, subtract form; the diagonal blocks stay
-//                                                FP64 substitution)
+//                                               (k_ozaki_update for K <= 32, else k_ozaki_gemm, subtract
+//                                                form; the diagonal blocks stay FP64 substitution)
 //
 // Splitting (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix multiplication by using
 // fast routines of matrix multiplication and its applications", Numer. Algorithms 2012, restated): every
@@ -19,12 +19,12 @@
 // combined exactly in int64, I = sum_{d<=6} M_d 2^{7(6-d)} + rint(sum_{d>6} M_d 2^{7(6-d)}), and the
 // result is 2^{E_x + E_y - 42} I.
 //
-// Tile: M = 128 output rows (TMEM lanes) x N = 64 output columns; 8 groups x 64 columns = the 512 TMEM
-// columns of the SM.  K is staged 32 at a time in shared memory (core-matrix K-major layout, no
-// swizzle), two stages in flight: while the tensor core works on one stage the CTA slices the next.
-// One thread issues the 72 tcgen05.mma of a stage and commits them to the stage's mbarrier.  Every
-// mbarrier wait is bounded; on timeout the kernel records RPCHOLQR_ERR_TIMEOUT, waits (bounded) for
-// its own MMAs, frees its tensor memory and returns.
+// Tiles: M = 128 output rows (TMEM lanes) x N = 64 output columns, 8 groups x 64 columns = the 512 TMEM
+// columns of the SM (k_ozaki_update: N = 32, two tiles in TMEM).  K is staged 32 at a time in shared
+// memory (core-matrix K-major layout, no swizzle), two stages in flight: while the tensor core works on
+// one stage the CTA slices the next.  One thread issues the 72 tcgen05.mma of a stage and commits them
+// to the stage's mbarrier.  Every mbarrier wait is bounded; on timeout the kernel records
+// RPCHOLQR_ERR_TIMEOUT, waits (bounded) for its own MMAs, frees its tensor memory and returns.
 #include <climits>
 
 #include "common.cuh"
@@ -218,17 +218,18 @@ __device__ __forceinline__ void combine_groups(const float (&m)[kGroups], long l
         (static_cast<long long>(__float2int_rn(m[6])) << 7) + static_cast<long long>(__float2int_rn(m[7]));
 }
 // For K <= 32 every group sum is below 8 * 127^2 * 32 < 2^22 in magnitude, so M + 1.5 2^23 holds M
-// exactly in its low mantissa bits: the integer is read from the bit pattern (no conversion instruction).
+// exactly in its low mantissa bits: the integer is read from the bit pattern (no conversion
+// instruction), and pairs of neighbouring groups fit one int32 (M_d 2^7 + M_{d+1} < 2^30), leaving
+// three 32 x 32 -> 64-bit multiply-adds for the int64 part.
 __device__ __forceinline__ long long combine_units53_k32(const float (&m)[kGroups]) {
     int v[kGroups];
 #pragma unroll
     for (int g = 0; g < kGroups; ++g) v[g] = __float_as_int(m[g] + 12582912.0f) - 0x4B400000;
-    const long long I = (static_cast<long long>(v[0]) << 28) + (static_cast<long long>(v[1]) << 21) +
-                        (static_cast<long long>(v[2]) << 14) + (static_cast<long long>(v[3]) << 7) +
-                        static_cast<long long>(v[4]);
-    const long long L = (static_cast<long long>(v[5]) << 14) + (static_cast<long long>(v[6]) << 7) +
-                        static_cast<long long>(v[7]);
-    return (I << 11) + ((L + 512) >> 10);
+    const int u = v[1] * 128 + v[2], t = v[3] * 128 + v[4], w = v[6] * 128 + v[7];
+    const long long I = static_cast<long long>(v[0]) * (1ll << 28) +
+                        (static_cast<long long>(u) * (1ll << 14) + static_cast<long long>(t));
+    const long long L = static_cast<long long>(v[5]) * (1ll << 14) + static_cast<long long>(w);
+    return I * 2048 + ((L + 512) >> 10);
 }
 // the value in units of 2^-53 (rounded), for a single-window product: |result| < 2^61
 __device__ __forceinline__ long long combine_units53(const float (&m)[kGroups]) {
@@ -623,8 +624,9 @@ __device__ __forceinline__ void gemm_store_tile(uint32_t tmem, int warp, int tid
 // Same operands, tiles, exactness windows and results as k_ozaki_gemm<false, WIN>; the pipeline differs.
 // The raw X rows of stage g + 1 are copied (cp.async, whole rows per warp) while stage g is sliced, and
 // the finished tile is written in whole rows through a free stage buffer.  Warp roles: NT producer
-// threads (warps 0 .. NT/32 - 1) copy, slice and drain; the last warp issues the MMAs.  full[s]: the producer warps filled stage buffer s (one arrival per warp); empty[s]: the MMAs of
-// the stage in buffer s are done (tcgen05.commit).  A drain waits for empty of the stage before and
+// threads (warps 0 .. NT/32 - 1) copy, slice and drain; the last warp issues the MMAs.  full[s]: the
+// producer warps filled stage buffer s (one arrival per warp); empty[s]: the MMAs of the stage in
+// buffer s are done (tcgen05.commit).  A drain waits for empty of the stage before and
 // arrives on full of the next stage only after it, so the next tile's MMAs start once TMEM is read out.
 template <bool WIN>
 __global__ void __launch_bounds__((WIN ? kThreadsWin : kThreads) + 32, 1)
@@ -827,13 +829,14 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
 // columns and two tiles are in flight: the tensor core fills one buffer while the other is drained.
 // The X slices of a 128-row block (one K stage) are produced once and used by all N/32 column tiles of
 // the block; the Y slices (at most 128 columns) stay in shared memory for the whole launch.  Warp roles:
-// warps 0-3 produce (thread = row of the block), warps 4-11 drain (warp w reads TMEM lanes 32 (w % 4)..,
-// columns 16 ((w - 4) / 4)..), warp 12 issues the MMAs.  Barriers: stage_full/stage_empty per X stage
+// warps 0-3 produce (thread = row of the block), warps 4-19 drain (warp w reads TMEM lanes 32 (w % 4)..,
+// columns 8 ((w - 4) / 4)..: four warps per lane quarter keep enough independent FP64 conversions and
+// subtractions in flight), warp 20 issues the MMAs.  Barriers: stage_full/stage_empty per X stage
 // buffer, acc_full/acc_empty per TMEM buffer.  Same exactness window, combination and rounding as
 // k_ozaki_gemm<true, false>: the results are identical.
 constexpr int kUpdTileN = 32;
 constexpr int kUpdMaxN = 128;
-constexpr int kUpdProducers = 4, kUpdDrainers = 8;
+constexpr int kUpdProducers = 4, kUpdDrainers = 16;
 constexpr int kUpdThreads = 32 * (kUpdProducers + kUpdDrainers + 1);
 constexpr int kUpdSmem = 2 * kAStage + (kUpdMaxN / kTileN) * kBStage;   // 192 KB
 constexpr uint32_t kIdescN32 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kUpdTileN >> 3) << 17) |
@@ -947,7 +950,7 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
             if (lane == 0) mbar_arrive(&stage_full[s]);
         }
     } else if (warp < kUpdProducers + kUpdDrainers) {
-        // drainers: warp w reads TMEM lanes 32 (w % 4).. and columns 16 h.. of every tile
+        // drainers: warp w reads TMEM lanes 32 (w % 4).. and columns 8 h.. of every tile
         const int q = warp & 3, h = (warp - kUpdProducers) >> 2;
         const int lr = 32 * q + lane;
         int64_t u = 0;   // tiles drained so far (TMEM buffer u & 1)
@@ -956,11 +959,11 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
             const int E = row < m ? xexp[row] : kNoExp;
             for (int j = 0; j < nsub; ++j, ++u) {
                 const int b = static_cast<int>(u & 1);
-                const int cbase = j * kUpdTileN + 16 * h;
-                // this thread's 16 values of B, read while the tile's MMAs run
-                double bv[16];
+                const int cbase = j * kUpdTileN + 8 * h;
+                // this thread's 8 values of B, read while the tile's MMAs run
+                double bv[8];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
+                for (int i = 0; i < 8; ++i) {
                     const int col = cbase + i;
                     bv[i] = (row < m && col < N) ? B[row * ldb + col] : 0.0;
                 }
@@ -969,9 +972,9 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
                     break;
                 }
                 tc_after_sync();
-                const uint32_t tb = tmem + (static_cast<uint32_t>(32 * q) << 16) + 256u * b + 16u * h;
+                const uint32_t tb = tmem + (static_cast<uint32_t>(32 * q) << 16) + 256u * b + 8u * h;
 #pragma unroll
-                for (int c0 = 0; c0 < 16; c0 += 4) {
+                for (int c0 = 0; c0 < 8; c0 += 4) {
                     float mg[kGroups][4];
 #pragma unroll
                     for (int g = 0; g < kGroups; ++g) tmem_ld4(tb + g * kUpdTileN + c0, mg[g]);

@@ -131,36 +131,55 @@ k_hh_cluster(double* __restrict__ W, int64_t lds, int s, int n, int np, double* 
 
 // Upper Cholesky G = R^T R, row by row:
 //   t_l = G[j][l] - sum_{k<j} R[k][j] R[k][l]  (l >= j),  R[j][j] = sqrt(t_j),  R[j][l] = t_l / R[j][j].
-// G: n x n (ld ldg).  R: np x np row-major (ld np), padded with the identity; R_user (optional,
-// n x n, ld n).  A pivot t_j that is not > 0 sets NOT_SPD with pivot j.
-__global__ void __launch_bounds__(256)
+// G: n x n (ld ldg), n <= 128.  R: np x np row-major (ld np), padded with the identity; R_user
+// (optional, n x n, ld n).  A pivot t_j that is not > 0 sets NOT_SPD with pivot j.
+// Thread (part, l) = (tid / 128, tid % 128): each dot product is split over kCholParts threads
+// (k = part, part + kCholParts, ...), so that all four schedulers' FP64 units work on it; the partial
+// sums are subtracted in part order.  The upper triangle of G is copied into the working matrix first,
+// so a step touches shared memory only; the square root is taken once per step.
+constexpr int kCholParts = 8;
+constexpr int kCholThreads = 128 * kCholParts;
+__global__ void __launch_bounds__(kCholThreads)
 k_cholesky(const double* __restrict__ G, int64_t ldg, int n, int np, double* __restrict__ R,
            double* __restrict__ R_user, int32_t* info) {
-    extern __shared__ double csm[];  // np x np working copy of R (row-major)
+    extern __shared__ double csm[];  // np x np working copy of R (row-major), then kCholParts x np partials
+    double* psum = csm + np * np;
     __shared__ double diag_s;
     __shared__ int fail_s;
     if (load_status(info) != 0) return;
-    const int tid = threadIdx.x;
-    for (int e = tid; e < np * np; e += blockDim.x) csm[e] = 0.0;
+    const int tid = threadIdx.x, part = tid >> 7, l = tid & 127;
+    for (int e = tid; e < np * np; e += blockDim.x) {
+        const int r = e / np, c = e - r * np;
+        csm[e] = (r <= c && c < n) ? G[static_cast<int64_t>(r) * ldg + c] : 0.0;
+    }
     if (tid == 0) fail_s = -1;
     __syncthreads();
     for (int j = 0; j < n; ++j) {
-        for (int l = j + tid; l < n; l += blockDim.x) {
-            double tl = G[static_cast<int64_t>(j) * ldg + l];
-            for (int k = 0; k < j; ++k) tl -= csm[k * np + j] * csm[k * np + l];
-            csm[j * np + l] = tl;
+        if (l >= j && l < n) {
+            double acc = 0.0;
+            for (int k = part; k < j; k += kCholParts) acc += csm[k * np + j] * csm[k * np + l];
+            psum[part * np + l] = acc;
         }
         __syncthreads();
-        if (tid == 0) {
-            const double d = csm[j * np + j];
-            if (!(d > 0.0)) fail_s = j;
-            else diag_s = sqrt(d);
-            if (fail_s < 0) csm[j * np + j] = diag_s;
+        if (part == 0 && l > j && l < n) {
+            double tl = csm[j * np + l];
+#pragma unroll
+            for (int q = 0; q < kCholParts; ++q) tl -= psum[q * np + l];
+            csm[j * np + l] = tl;
+        } else if (tid == 0) {
+            double tj = csm[j * np + j];
+#pragma unroll
+            for (int q = 0; q < kCholParts; ++q) tj -= psum[q * np + j];
+            if (!(tj > 0.0)) {
+                fail_s = j;
+            } else {
+                diag_s = sqrt(tj);
+                csm[j * np + j] = diag_s;
+            }
         }
         __syncthreads();
         if (fail_s >= 0) break;
-        const double rjj = diag_s;
-        for (int l = j + 1 + tid; l < n; l += blockDim.x) csm[j * np + l] /= rjj;
+        if (part == 0 && l > j && l < n) csm[j * np + l] /= diag_s;
         __syncthreads();
     }
     if (fail_s >= 0) {
@@ -344,11 +363,11 @@ cudaError_t launch_cholesky(const double* G, int64_t ldg, int n, int np, double*
         k_cholesky_wide<<<1, 1024, 0, st>>>(G, ldg, n, np, R, R_user, info);
         return cudaGetLastError();
     }
-    const size_t smem = static_cast<size_t>(np) * np * sizeof(double);
+    const size_t smem = static_cast<size_t>(np + kCholParts) * np * sizeof(double);
     cudaError_t err = cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
-    k_cholesky<<<1, 256, smem, st>>>(G, ldg, n, np, R, R_user, info);
+    k_cholesky<<<1, kCholThreads, smem, st>>>(G, ldg, n, np, R, R_user, info);
     return cudaGetLastError();
 }
 
