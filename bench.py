@@ -220,8 +220,9 @@ def gpu_metrics(A, Q, R, rows=1 << 18):
     return orth, nd / na
 
 
-def traffic_from_profiles(kernel_tag, src_file):
-    """DRAM bytes per launch from profiles/traffic.txt when the kernel source is unchanged."""
+def traffic_from_profiles(kernel_tag, src_file, m=None):
+    """DRAM bytes per launch from profiles/traffic.txt when the kernel source is unchanged, scaled from
+    the captured row count to m (the row passes' traffic is proportional to the rows they process)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -230,7 +231,10 @@ def traffic_from_profiles(kernel_tag, src_file):
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
         if f.get("kernel") == kernel_tag and f.get("src_sha") == sha:
             try:
-                return float(f["dram_bytes_per_launch"])
+                t = float(f["dram_bytes_per_launch"])
+                if m is not None and "measured_m" in f:
+                    t *= m / float(f["measured_m"])
+                return t
             except (KeyError, ValueError):
                 return None
     return None
@@ -437,7 +441,7 @@ def run_ours(args, ws, rank, local):
         k_ms = phases["pass1"] / c
         k_flops = 2.0 * m * n * n                       # m rows x (n^2 solve + n^2 Gram)
         k_bytes = 16.0 * m * n                          # read A, write A1
-        traffic = traffic_from_profiles(f"k_rowpass<{np_},true>", src)
+        traffic = traffic_from_profiles(f"k_rowpass<{np_},true>", src, m)
     else:
         # dominant kernel: the FP64 32-column diagonal-block row solves of pass 1 (one launch per block;
         # the PASS1 phase is exactly the first block's launch, the other blocks do the same work)
@@ -448,7 +452,7 @@ def run_ours(args, ws, rank, local):
         k_ms = phases["pass1"] / c
         k_flops = float(m) * b0 * b0
         k_bytes = 16.0 * m * b0
-        traffic = traffic_from_profiles(f"k_rowpass<{nb0},false>", src)
+        traffic = traffic_from_profiles(f"k_rowpass<{nb0},false>", src, m)
     achieved = k_flops / (k_ms / 1e3) / 1e12
     peak = (fp32_peak if args.mode == "fp32" else fp64_peak) / 1e12
 
