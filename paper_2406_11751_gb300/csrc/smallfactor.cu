@@ -59,7 +59,7 @@ k_hh_cluster(double* __restrict__ W, int64_t lds, int s, int n, int np, double* 
     extern __shared__ double qsm[];
     double* v = qsm;                 // s
     double* betas = qsm + s;         // n
-    double* red = betas + n;         // 32
+    double* red = betas + n;         // 32 warp partials, then tau and 1 / (alpha - beta)
     // every CTA of the cluster sees the same status, so all take the same number of barriers
     if (load_status(info_in) != 0) return;
     const unsigned rank = cluster_rank(), csize = cluster_size();
@@ -69,19 +69,32 @@ k_hh_cluster(double* __restrict__ W, int64_t lds, int s, int n, int np, double* 
         const double* colj = W + static_cast<int64_t>(j) * lds;
         double part = 0.0;
         for (int i = j + 1 + tid; i < s; i += blockDim.x) part += colj[i] * colj[i];
-        const double sigma = block_sum(part, red);
-        const double alpha = colj[j];
-        double beta, tau, inv;
-        if (sigma == 0.0) {
-            beta = alpha; tau = 0.0; inv = 0.0;
-        } else {
-            const double nrm = sqrt(alpha * alpha + sigma);
-            beta = alpha >= 0.0 ? -nrm : nrm;
-            tau = (beta - alpha) / beta;
-            inv = 1.0 / (alpha - beta);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) red[warp] = part;
+        __syncthreads();
+        // the reflector's scalars in one thread (FP64 square root and divisions are long sequences on
+        // the FP64 units; formed once instead of by every thread), then shared
+        if (tid == 0) {
+            double sigma = 0.0;
+            for (int w = 0; w < nwarps; ++w) sigma += red[w];
+            const double alpha = colj[j];
+            double beta, tau, inv;
+            if (sigma == 0.0) {
+                beta = alpha; tau = 0.0; inv = 0.0;
+            } else {
+                const double nrm = sqrt(alpha * alpha + sigma);
+                beta = alpha >= 0.0 ? -nrm : nrm;
+                tau = (beta - alpha) / beta;
+                inv = 1.0 / (alpha - beta);
+            }
+            betas[j] = beta;
+            red[32] = tau;
+            red[33] = inv;
         }
+        __syncthreads();
+        const double tau = red[32], inv = red[33];
         for (int i = j + tid; i < s; i += blockDim.x) v[i] = (i == j) ? 1.0 : colj[i] * inv;
-        if (tid == 0) betas[j] = beta;
         __syncthreads();
         if (tau != 0.0) {
             // this CTA's columns k > j: k = rank (mod csize); one warp per column
