@@ -127,7 +127,13 @@ rpcholqr_status rpcholqr_factor_f32(rpcholqr_plan plan, const float* A, int64_t 
 /* End-to-end variant of rpcholqr_factor on HOST buffers: copies A (host, m x n, lda) to a device
  * staging buffer the plan allocates on first use, factors it, copies Q (host, ldq) and R (host)
  * back, and returns only after the copies completed.  info_host (int32[2], host) receives the
- * numerical status.  Staging buffers are kept for later calls and freed with the plan. */
+ * numerical status.  Staging buffers are kept for later calls and freed with the plan.  With a
+ * SPLIT64 plan, n <= 128, lda = ldq = n, no smoothing and m >= 512 the copies overlap the work: A
+ * goes over in four row blocks on a second stream (created with the plan's first such call, with
+ * pinned host buffers for the sample) while the sample, gathered on the host from the device-drawn
+ * indices, is factored and pass 1 solves the blocks that have arrived; Q comes back block by block
+ * behind pass 2.  The results equal rpcholqr_factor's.  A, Q should be pinned (page-locked) for the
+ * copies to overlap. */
 rpcholqr_status rpcholqr_factor_host(rpcholqr_plan plan, const double* A, int64_t m, int32_t n,
                                      int64_t lda, int32_t s, uint64_t seed, double* Q, int64_t ldq,
                                      double* R, int32_t* info_host, void* stream);

@@ -9,6 +9,8 @@
 
 namespace rpq {
 // sample.cu
+void launch_sample_rows(const double* rows, int32_t n, int32_t s, double scale, double* As, int64_t lds,
+                        int32_t np, int32_t* info, cudaStream_t st);
 void launch_sample_indices(uint64_t seed, uint64_t stream_id, int64_t m, int32_t s, int64_t* idx,
                            cudaStream_t st);
 void launch_sample_gather(const double* A, int64_t m, int32_t n, int64_t lda, int32_t s, uint64_t seed,
@@ -125,6 +127,14 @@ struct rpcholqr_plan_s {
     double* hR = nullptr;
     int32_t* hinfo = nullptr;
     size_t staged_elems = 0;
+    // rpcholqr_factor_host's copy pipeline (SPLIT64): a copy stream, chunk events, the sample indices
+    // (device and pinned host) and the sampled rows (pinned host and device)
+    cudaStream_t hcopy = nullptr;
+    cudaEvent_t hev[2 * 4] = {};
+    int64_t* hidx_dev = nullptr;
+    int64_t* hidx_host = nullptr;
+    double* hrows_host = nullptr;
+    double* hrows_dev = nullptr;
     // phase timing
     int32_t timing_slots = 0;
     int32_t timed_calls = 0;
@@ -398,6 +408,13 @@ rpcholqr_status rpcholqr_plan_destroy(rpcholqr_plan plan) {
     cudaFree(plan->hQ);
     cudaFree(plan->hR);
     cudaFree(plan->hinfo);
+    if (plan->hcopy) cudaStreamDestroy(plan->hcopy);
+    for (cudaEvent_t e : plan->hev)
+        if (e) cudaEventDestroy(e);
+    cudaFree(plan->hidx_dev);
+    cudaFreeHost(plan->hidx_host);
+    cudaFreeHost(plan->hrows_host);
+    cudaFree(plan->hrows_dev);
     cudaFree(plan->split_ws);
     cudaFree(plan->smooth_ws);
     free_events(plan);
@@ -438,7 +455,7 @@ static rpcholqr_status sketch_internal(rpcholqr_plan p, const double* A, int64_t
 static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const double* X, int64_t m, int K,
                                            int64_t ldx, const double* Y, int N, int64_t ldy, const double* B,
                                            int64_t ldb, double* C, int64_t ldc, int32_t* info, cudaStream_t st,
-                                           bool xexp_ready = false);
+                                           bool xexp_ready = false, int64_t row0 = 0, bool y_ready = false);
 
 // Diagonal-block setups for the blocked solve with T (n x n, ld ldt): block J (64 columns, the last
 // one ragged) gets frag + 4096 J and diag + 512 J.
@@ -461,17 +478,19 @@ static void prep_blocks(rpcholqr_plan_s* p, const double* T, int64_t ldt, int n,
 // blocks must have been set up by prep_blocks with blk = kSplitSub.  The row passes store (first half)
 // and max-merge the row bounds of Y into p->xexp (the updates' left operands use the bound over the
 // columns solved so far) and their column bounds into p->colexp.  Marks PASS1 / PASS1_UPDATE /
-// PASS1_SOLVE2 as the first row pass / the first update / the rest when pm is given.
+// PASS1_SOLVE2 as the first row pass / the first update / the rest when pm is given.  row0: X's first
+// row within the matrix whose row bounds p->xexp holds (a block of rows is solved on its own).
 static rpcholqr_status solve_split_right(rpcholqr_plan_s* p, const double* X, int64_t ldx, const double* T,
                                          int64_t ldt, int64_t m, int n, double* Y, int64_t ldy, const double* frag,
-                                         const double* diag, int32_t* info, cudaStream_t st, const PhaseMarks* pm) {
+                                         const double* diag, int32_t* info, cudaStream_t st, const PhaseMarks* pm,
+                                         int64_t row0 = 0) {
     const int grid = row_grid(p, m);
     const int blk = kSplitBlk, sub = kSplitSub;
     bool first_update = true;
     auto update = [&](int c0, int K, int c1, int N, const double* B, int64_t ldb) -> rpcholqr_status {
         if (pm && first_update) pm->mark(RPCHOLQR_PHASE_PASS1_UPDATE);
         rpcholqr_status rc = ozaki_gemm_internal(p, true, Y + c0, m, K, ldy, T + static_cast<int64_t>(c0) * ldt + c1,
-                                                 N, ldt, B, ldb, Y + c1, ldy, info, st, true);
+                                                 N, ldt, B, ldb, Y + c1, ldy, info, st, true, row0);
         if (pm && first_update) pm->mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
         first_update = false;
         return rc;
@@ -487,7 +506,7 @@ static rpcholqr_status solve_split_right(rpcholqr_plan_s* p, const double* X, in
             const int64_t lsrc = c1 == 0 ? ldx : ldy;
             const int js = c1 / sub;
             if (launch_rowpass_ex(false, pad16(nh), src + c1, lsrc, Y + c1, ldy, m, nh, frag + js * sub * sub,
-                                  diag + js * (sub / 8) * 64, nullptr, info, grid, st, true, p->xexp,
+                                  diag + js * (sub / 8) * 64, nullptr, info, grid, st, true, p->xexp + row0,
                                   c1 == 0 ? 1 : 2, p->colexp + c1) != cudaSuccess)
                 return RPCHOLQR_ERR_CUDA;
             ++p->launches;
@@ -635,21 +654,26 @@ static rpcholqr_status solve_internal(rpcholqr_plan p, const double* X, int64_t 
 }
 
 // C = X Y (sub = false) or C = B - X Y (sub = true) on the tensor cores; X row bounds computed here.
-// xexp_ready: p->xexp already holds the row bounds of X (written by the row pass that produced X).
+// xexp_ready: p->xexp already holds the row bounds of X (written by the row pass that produced X);
+// row0: X's first row within the matrix whose bounds p->xexp holds; y_ready: p->yblocks already holds
+// the slices of this Y.
 static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const double* X, int64_t m, int K,
                                            int64_t ldx, const double* Y, int N, int64_t ldy, const double* B,
                                            int64_t ldb, double* C, int64_t ldc, int32_t* info, cudaStream_t st,
-                                           bool xexp_ready) {
+                                           bool xexp_ready, int64_t row0, bool y_ready) {
+    int32_t* xexp = p->xexp + row0;
     if (!xexp_ready) {
-        launch_row_exp(X, ldx, m, K, p->xexp, st);
+        launch_row_exp(X, ldx, m, K, xexp, st);
         ++p->launches;
     }
-    launch_ozaki_slice_cols(Y, ldy, K, N, p->yblocks, p->yexp, info, st);
-    ++p->launches;
+    if (!y_ready) {
+        launch_ozaki_slice_cols(Y, ldy, K, N, p->yblocks, p->yexp, info, st);
+        ++p->launches;
+    }
     if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
     const int64_t tiles = ((m + 127) / 128) * ((N + 63) / 64);
     const int grid = static_cast<int>(tiles < p->grid ? tiles : p->grid);
-    if (launch_ozaki_gemm(sub, X, ldx, p->xexp, K, p->yblocks, p->yexp, N, B, ldb, C, ldc, m, info, grid, st) !=
+    if (launch_ozaki_gemm(sub, X, ldx, xexp, K, p->yblocks, p->yexp, N, B, ldb, C, ldc, m, info, grid, st) !=
         cudaSuccess)
         return RPCHOLQR_ERR_CUDA;
     ++p->launches;
@@ -864,6 +888,115 @@ rpcholqr_status rpcholqr_plan_collect_timing(rpcholqr_plan p, float* ms_per_phas
     return RPCHOLQR_OK;
 }
 
+// rpcholqr_factor_host for SPLIT64 (n <= 128, contiguous host matrices): the copies overlap the work.
+// A goes to the device in kHostChunks row blocks on a copy stream; meanwhile the sample indices are
+// computed on the device and read back, the host gathers the s sampled rows from its own copy of A
+// and sends them ahead, and the sketch QR runs; pass 1 then solves each row block as soon as it has
+// arrived.  After the Gram matrix, the Cholesky factor and R1^{-1}, pass 2 runs block by block and
+// each block of Q is copied back while the next is computed.  Every step is the one rpcholqr_factor
+// takes, on the same rows, so the results are identical to it.
+constexpr int kHostChunks = 4;
+static rpcholqr_status factor_host_split(rpcholqr_plan p, const double* A, int64_t m, int32_t n, int32_t s,
+                                         uint64_t seed, double* Q, double* R, int32_t* info_host, cudaStream_t st) {
+    const int np = pad_np(n);
+    const int64_t ld1 = np;
+    double* dA = p->hA;
+    double* dQ = p->hQ;
+    int32_t* info = p->hinfo;
+    if (!p->hcopy) {
+        if (cudaStreamCreateWithFlags(&p->hcopy, cudaStreamNonBlocking) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+        for (cudaEvent_t& e : p->hev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    }
+    if (!p->hidx_dev) {
+        const size_t ms = static_cast<size_t>(p->max_s);
+        if (cudaMalloc(&p->hidx_dev, ms * sizeof(int64_t)) != cudaSuccess ||
+            cudaMallocHost(&p->hidx_host, ms * sizeof(int64_t)) != cudaSuccess ||
+            cudaMallocHost(&p->hrows_host, ms * p->max_n * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&p->hrows_dev, ms * p->max_n * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return RPCHOLQR_ERR_NOMEM;
+        }
+    }
+    int64_t rows_per = (m + kHostChunks - 1) / kHostChunks;
+    rows_per = (rows_per + 127) / 128 * 128;
+    const int nchunks = static_cast<int>((m + rows_per - 1) / rows_per);
+    auto chunk = [&](int c, int64_t& r0, int64_t& rows) {
+        r0 = c * rows_per;
+        rows = m - r0 < rows_per ? m - r0 : rows_per;
+    };
+    const size_t row_bytes = static_cast<size_t>(n) * sizeof(double);
+    rpcholqr_status rc = reset_info(info, st);
+    if (rc != RPCHOLQR_OK) return rc;
+    // the sample first: indices on the device, rows gathered on the host and sent before A (a copy
+    // engine serves its queue in order, so the sample must not wait behind the row blocks of A)
+    launch_sample_indices(seed, 0, m, s, p->hidx_dev, st);
+    if (cudaMemcpyAsync(p->hidx_host, p->hidx_dev, static_cast<size_t>(s) * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    for (int j = 0; j < s; ++j) std::memcpy(p->hrows_host + static_cast<size_t>(j) * n, A + p->hidx_host[j] * n, row_bytes);
+    if (cudaMemcpyAsync(p->hrows_dev, p->hrows_host, static_cast<size_t>(s) * row_bytes, cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    // A in row blocks on the copy stream (st has nothing queued that touches the staging buffers)
+    for (int c = 0; c < nchunks; ++c) {
+        int64_t r0, rows;
+        chunk(c, r0, rows);
+        if (cudaMemcpyAsync(dA + r0 * n, A + r0 * n, static_cast<size_t>(rows) * row_bytes, cudaMemcpyHostToDevice,
+                            p->hcopy) != cudaSuccess ||
+            cudaEventRecord(p->hev[c], p->hcopy) != cudaSuccess)
+            return RPCHOLQR_ERR_CUDA;
+    }
+    launch_sample_rows(p->hrows_dev, n, s, std::sqrt(static_cast<double>(m) / static_cast<double>(s)), p->As, s, np,
+                       info, st);
+    if (launch_householder(p->As, s, s, n, np, p->Rs, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    p->launches += 3;
+    // pass 1, block by block as A arrives
+    launch_fill_noexp(p->colexp, n, st);
+    prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st, kSplitSub);
+    for (int c = 0; c < nchunks; ++c) {
+        int64_t r0, rows;
+        chunk(c, r0, rows);
+        if (cudaStreamWaitEvent(st, p->hev[c], 0) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+        if ((rc = solve_split_right(p, dA + r0 * n, n, p->Rs, np, rows, n, p->A1 + r0 * ld1, ld1, p->frag_s,
+                                    p->diag_s, info, st, nullptr, r0)) != RPCHOLQR_OK)
+            return rc;
+    }
+    if ((rc = ozaki_gram_internal(p, p->A1, m, n, ld1, p->G, np, info, st, true)) != RPCHOLQR_OK) return rc;
+    if (launch_cholesky(p->G, np, n, np, p->R1, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    launch_triu_inv(p->R1, np, n, np, p->W, info, st);
+    launch_pass2_gate(p->R1, p->W, n, np, kSplitPass2Tau, info, p->gates, st);
+    p->launches += 3;
+    // pass 2 block by block; each block of Q goes back while the next is computed
+    for (int c = 0; c < nchunks; ++c) {
+        int64_t r0, rows;
+        chunk(c, r0, rows);
+        if ((rc = ozaki_gemm_internal(p, false, p->A1 + r0 * ld1, rows, n, ld1, p->W, n, np, nullptr, 0, dQ + r0 * n, n,
+                                      p->gates, st, true, r0, c > 0)) != RPCHOLQR_OK)
+            return rc;
+        if ((rc = solve_internal(p, p->A1 + r0 * ld1, rows, n, ld1, p->R1, np, dQ + r0 * n, n, p->gates + 2, st,
+                                 nullptr)) != RPCHOLQR_OK)
+            return rc;
+        if (cudaEventRecord(p->hev[kHostChunks + c], st) != cudaSuccess ||
+            cudaStreamWaitEvent(p->hcopy, p->hev[kHostChunks + c], 0) != cudaSuccess ||
+            cudaMemcpyAsync(Q + r0 * n, dQ + r0 * n, static_cast<size_t>(rows) * row_bytes, cudaMemcpyDeviceToHost,
+                            p->hcopy) != cudaSuccess)
+            return RPCHOLQR_ERR_CUDA;
+    }
+    launch_gate_merge(info, p->gates, st);
+    launch_triu_mul(p->R1, np, p->Rs, np, n, p->hR, n, info, st);
+    p->launches += 2;
+    if (cudaMemcpyAsync(R, p->hR, static_cast<size_t>(n) * n * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(info_host, info, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return RPCHOLQR_ERR_CUDA;
+    if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess && cudaStreamSynchronize(p->hcopy) == cudaSuccess
+               ? RPCHOLQR_OK
+               : RPCHOLQR_ERR_CUDA;
+}
+
 rpcholqr_status rpcholqr_factor_host(rpcholqr_plan p, const double* A, int64_t m, int32_t n, int64_t lda,
                                      int32_t s, uint64_t seed, double* Q, int64_t ldq, double* R,
                                      int32_t* info_host, void* stream) {
@@ -886,14 +1019,23 @@ rpcholqr_status rpcholqr_factor_host(rpcholqr_plan p, const double* A, int64_t m
         }
         p->staged_elems = elems;
     }
+    if (p->mode == RPCHOLQR_SPLIT64 && !p->smoothing && pad_np(n) <= kMaxNP && lda == n && ldq == n &&
+        m >= 128 * kHostChunks)
+        return factor_host_split(p, A, m, n, s, seed, Q, R, info_host, st);
     const size_t row_bytes = static_cast<size_t>(n) * sizeof(double);
-    if (cudaMemcpy2DAsync(p->hA, row_bytes, A, static_cast<size_t>(lda) * sizeof(double), row_bytes,
-                          static_cast<size_t>(m), cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return RPCHOLQR_ERR_CUDA;
+    // contiguous host matrices (ld = n) go as one linear copy; strided ones row by row (2-D copy)
+    const cudaError_t ein =
+        lda == n ? cudaMemcpyAsync(p->hA, A, elems * sizeof(double), cudaMemcpyHostToDevice, st)
+                 : cudaMemcpy2DAsync(p->hA, row_bytes, A, static_cast<size_t>(lda) * sizeof(double), row_bytes,
+                                     static_cast<size_t>(m), cudaMemcpyHostToDevice, st);
+    if (ein != cudaSuccess) return RPCHOLQR_ERR_CUDA;
     rpcholqr_status rc = rpcholqr_factor(p, p->hA, m, n, n, s, seed, p->hQ, n, p->hR, p->hinfo, stream);
     if (rc != RPCHOLQR_OK) return rc;
-    if (cudaMemcpy2DAsync(Q, static_cast<size_t>(ldq) * sizeof(double), p->hQ, row_bytes, row_bytes,
-                          static_cast<size_t>(m), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    const cudaError_t eout =
+        ldq == n ? cudaMemcpyAsync(Q, p->hQ, elems * sizeof(double), cudaMemcpyDeviceToHost, st)
+                 : cudaMemcpy2DAsync(Q, static_cast<size_t>(ldq) * sizeof(double), p->hQ, row_bytes, row_bytes,
+                                     static_cast<size_t>(m), cudaMemcpyDeviceToHost, st);
+    if (eout != cudaSuccess ||
         cudaMemcpyAsync(R, p->hR, static_cast<size_t>(n) * n * sizeof(double), cudaMemcpyDeviceToHost,
                         st) != cudaSuccess ||
         cudaMemcpyAsync(info_host, p->hinfo, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=

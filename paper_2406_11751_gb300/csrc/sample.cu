@@ -40,6 +40,30 @@ __global__ void k_sample_gather(const TA* __restrict__ A, int64_t m, int32_t n, 
     if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(info, RPCHOLQR_ERR_NONFINITE);
 }
 
+// The same sample from rows already gathered in sample order (rows: s x n row-major, ld n): As gets
+// sqrt(m/s) * rows[j, :] exactly as k_sample_gather would from A[idx_j, :].
+__global__ void k_sample_rows(const double* __restrict__ rows, int32_t n, double scale, double* __restrict__ As,
+                              int64_t lds, int32_t np, int32_t* info) {
+    const int j = blockIdx.x;
+    const double* src = rows + static_cast<int64_t>(j) * n;
+    bool bad = false;
+    for (int c = threadIdx.x; c < np; c += blockDim.x) {
+        double v = 0.0;
+        if (c < n) {
+            const double a = src[c];
+            bad |= !isfinite(a);
+            v = scale * a;
+        }
+        As[static_cast<int64_t>(c) * lds + j] = v;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(info, RPCHOLQR_ERR_NONFINITE);
+}
+
+void launch_sample_rows(const double* rows, int32_t n, int32_t s, double scale, double* As, int64_t lds,
+                        int32_t np, int32_t* info, cudaStream_t st) {
+    k_sample_rows<<<s, 128, 0, st>>>(rows, n, scale, As, lds, np, info);
+}
+
 void launch_sample_indices(uint64_t seed, uint64_t stream_id, int64_t m, int32_t s, int64_t* idx,
                            cudaStream_t st) {
     k_sample_indices<<<(s + 127) / 128, 128, 0, st>>>(seed, stream_id, m, s, idx);

@@ -107,3 +107,29 @@ def test_split_factor_deterministic(lib, splan):
     Q1, R1, _ = lib.rpcholqr_factor(splan, A, 384, 11)
     Q2, R2, _ = lib.rpcholqr_factor(splan, A, 384, 11)
     assert torch.equal(Q1, Q2) and torch.equal(R1, R2)
+
+
+@pytest.mark.parametrize("m,n,s,kappa", [(70001, 128, 384, 1e8), (20011, 50, 150, 1e12), (600, 20, 60, 1e4)])
+def test_split_factor_host_matches_device(lib, splan, m, n, s, kappa):
+    # the host-buffer call overlaps its copies with the work (row blocks of A copied while earlier ones
+    # are solved, Q copied back block by block) but takes the same steps: results identical to the
+    # device-buffer call, on two calls in a row
+    A = inputs.usv(m, n, kappa, m % 97)
+    Qd, Rd, infod = lib.rpcholqr_factor(splan, cu(A), s, 21)
+    assert int(infod[0]) == 0
+    Ah = torch.from_numpy(A).pin_memory()
+    for _ in range(2):
+        Qh, Rh, st, piv = lib.rpcholqr_factor_host(splan, Ah, s, 21)
+        assert (st, piv) == (0, -1)
+        assert np.array_equal(Qh.numpy(), host(Qd)) and np.array_equal(Rh.numpy(), host(Rd))
+
+
+def test_split_factor_host_nonfinite(lib, oracle_mod, splan):
+    # a NaN outside the sample is caught by pass 1, one inside it by the sample (gathered on the host)
+    m, n, s = 9000, 100, 300
+    idx = oracle_mod.sample_indices(3, m, s).tolist()
+    for row in (next(i for i in range(m) if i not in set(idx)), idx[7]):
+        A = inputs.usv(m, n, 10.0, 5)
+        A[row, 77] = np.nan
+        _, _, st, _ = lib.rpcholqr_factor_host(splan, torch.from_numpy(A).pin_memory(), s, 3)
+        assert st == lib.ERR_NONFINITE
