@@ -49,3 +49,25 @@ def test_bench_rank_logic_world2():
     assert [int(o[1]) for o in outs] == [0, 0]
     assert '"impl": "reference"' in outs[0][2] and outs[0][2].count("\n") == 1
     assert outs[1][2] == ""
+
+
+def test_traffic_from_profiles_scales_and_checks_source(tmp_path, monkeypatch):
+    # the recorded DRAM bytes of a row pass are used only for an unchanged kernel source, and scaled
+    # from the captured row count to the run's
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("kernel source\n")
+    import hashlib
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic.txt").write_text(
+        "# comment\n"
+        f"kernel=k_rowpass<32,false> src_sha={sha} dram_bytes_per_launch=1000 measured_m=1024\n"
+        "kernel=k_rowpass<128,true> src_sha=0000000000000000 dram_bytes_per_launch=5 measured_m=1\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_from_profiles("k_rowpass<32,false>", str(src)) == 1000.0
+    assert bench.traffic_from_profiles("k_rowpass<32,false>", str(src), 256) == 250.0
+    assert bench.traffic_from_profiles("k_rowpass<128,true>", str(src), 1) is None      # source changed
+    assert bench.traffic_from_profiles("k_rowpass<64,false>", str(src), 1) is None     # never captured
