@@ -72,9 +72,14 @@ __global__ void k_prep_tri(const double* __restrict__ T, int64_t ldt, int n, int
 
 // Warps per CTA: 8 when the 256-row panel fits shared memory (NP <= 64), else 4 (128-row panel).
 __host__ __device__ constexpr int rowpass_warps(int np) { return np <= 64 ? 8 : 4; }
+// The plain solve up to 48 columns runs two CTAs per SM (128 registers a thread, two panels fit the
+// shared memory): one CTA's panel load overlaps the other's FP64 work and each scheduler has four
+// warps' dependent chains to interleave.  The fused Gram keeps one CTA per SM (its partials are sized
+// for one CTA per SM).
+__host__ __device__ constexpr int rowpass_ctas_per_sm(int np, bool syrk) { return !syrk && np <= 48 ? 2 : 1; }
 
 template <int NP, bool SYRK>
-__global__ void __launch_bounds__(rowpass_warps(NP) * 32, 1)
+__global__ void __launch_bounds__(rowpass_warps(NP) * 32, rowpass_ctas_per_sm(NP, SYRK))
 k_rowpass(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m, int n,
           const double* __restrict__ frag, const double* __restrict__ diag,
           double* __restrict__ gpart, int32_t* info, bool check_finite, int32_t* rowexp, int rowexp_mode,
@@ -296,6 +301,11 @@ static cudaError_t launch_rowpass_t(const double* X, int64_t ldx, double* Y, int
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
+    if (rowpass_ctas_per_sm(NP, SYRK) > 1) {
+        const int64_t npanels = (m + 32 * rowpass_warps(NP) - 1) / (32 * rowpass_warps(NP));
+        const int64_t g = static_cast<int64_t>(grid) * rowpass_ctas_per_sm(NP, SYRK);
+        grid = static_cast<int>(g < npanels ? g : npanels);
+    }
     k_rowpass<NP, SYRK><<<grid, 32 * rowpass_warps(NP), smem, st>>>(X, ldx, Y, ldy, m, n, frag, diag, gpart, info,
                                                                     check, rowexp, rowexp_mode, colexp);
     return cudaGetLastError();
