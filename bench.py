@@ -1,19 +1,24 @@
 #!/usr/bin/env python
 """Throughput of rpCholesky-QR (Garrison & Ipsen, arXiv 2406.11751, Algorithm alg_2) on GB300.
 
-One step = one full rpcholqr_factor call (sample + Householder R_s + fused preconditioning/Gram
-pass + Cholesky + second pass + R recovery) on an m x n FP64 matrix resident in HBM.
+One step = one full rpcholqr_factor call (sample + Householder R_s + preconditioning pass + Gram +
+Cholesky + second pass + R recovery) on an m x n FP64 matrix resident in HBM.
 
-Default workload: m = 2^20, n = 128, s = 3n = 384, A = U diag(sigma) V^T with sigma log-spaced
-from 1 to 1e-8 (kappa = 1e8), U, V Haar.  A (1.07 GB) is larger than L2, so consecutive steps do
-not reuse cached inputs.  Prints one JSON line (rank 0).
+Default workload (--config 5, the largest single-GPU workload): m = 2^23, n = 512, s = 3n = 1536,
+A = U diag(sigma) V^T with sigma log-spaced from 1 to 1e-18 (numerically singular), U, V Haar;
+SPLIT64 mode, with the plain FP64 mode timed beside it ("other_mode") and the m = 2^20, n = 128,
+kappa = 1e8 workload (--config 2) reported under "config2".  A (34.4 GB) is larger than L2, so
+consecutive steps do not reuse cached inputs.  Prints one JSON line (rank 0).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config 1|2|3|5]
 
 --impl reference times the FP64 CPU oracle (the only "reference" this project has: the paper
-ships no code) on the host cores, on a bounded row sample of the same workload.
+ships no code) on the host cores, each step one oracle call on a bounded row sample of the same
+workload; its ms_per_step is that measured call, its value the per-matrix rate extrapolated from two
+sample sizes (the oracle's cost is a fixed part plus a part linear in m).
 Under torchrun (N > 1) every rank factors its own matrix (independent problems, weak scaling,
 no collective on the data path); rank 0 prints the aggregate over max-over-ranks time.
+--profile-window brackets the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off).
 """
 from __future__ import annotations
 
@@ -32,18 +37,32 @@ sys.path.insert(0, ROOT)
 METRIC = "TS-QR matrices/s & effective TFLOP/s at ||Q^T Q - I||_2 <= 1e-13; % of roofline"
 
 
-def parse_args():
+# The workloads (sigma log-spaced from 1 to 1/kappa, s = 3n): 1 = 10,000 x 50, kappa 1e8; 2 = 2^20 x 128,
+# kappa 1e8; 3 = 2^22 x 256, kappa 1e12 (1e5 for the FP32 variant); 5 = 2^23 x 512, sigma to 1e-18.
+# (4 is the heterogeneous batch: --workload batch.)
+CONFIGS = {1: (10000, 50, 1e8), 2: (1 << 20, 128, 1e8), 3: (1 << 22, 256, 1e12), 5: (1 << 23, 512, 1e18)}
+PRESETS = {"small": 1, "headline": 2, "precision": 3, "large": 5}
+
+
+def parse_args(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--m", type=int, default=1 << 20)
-    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--config", type=int, choices=sorted(CONFIGS), default=5,
+                    help="workload: 1 = 10,000 x 50; 2 = 2^20 x 128; 3 = 2^22 x 256; 5 = 2^23 x 512 (default)")
+    ap.add_argument("--preset", choices=sorted(PRESETS), default=None,
+                    help="alias of --config: small 1, headline 2, precision 3, large 5")
+    ap.add_argument("--m", type=int, default=None)
+    ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--s", type=int, default=None, help="sampled rows (default 3n)")
-    ap.add_argument("--kappa", type=float, default=1e8)
+    ap.add_argument("--kappa", type=float, default=None)
     ap.add_argument("--seed", type=int, default=20240617)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="host-buffer end-to-end steps (default 3, 2 above 2^21 rows)")
+    ap.add_argument("--other-steps", type=int, default=None,
+                    help="timed steps of the other mode (default: --steps up to 2^21 x 128 elements, else 2)")
     ap.add_argument("--cpu-sample-rows", type=int, default=None,
                     help="rows of the oracle's bounded sample (default 2^17 at n = 128, scaled by (128/n)^2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -58,26 +77,33 @@ def parse_args():
                     help="single: one m x n matrix per step; batch: the 512-matrix heterogeneous batch "
                          "(m log-uniform in [4096, 2^20], n in {8..128}, s=3n, kappa log-uniform in "
                          "[1, 1e14]) per step, one CUDA-graph replay")
-    ap.add_argument("--preset", choices=["small", "headline", "precision", "large"], default=None,
-                    help="workload shapes: small m=10000 n=50 kappa=1e8; headline m=2^20 n=128 kappa=1e8 "
-                         "(the default); precision m=2^22 n=256 kappa=1e12; large m=2^23 n=512 "
-                         "sigma to 1e-18")
     ap.add_argument("--smoothing", choices=["none", "wht", "dct"], default="none",
                     help="sample the smoothed F A (Algorithm alg_2 with F = F_T D): Walsh-Hadamard or cosine F_T")
     ap.add_argument("--count", type=int, default=512, help="matrices in the batch workload")
     ap.add_argument("--slots", type=int, default=16, help="concurrent slots the batch autotuner may use")
     ap.add_argument("--no-compare", action="store_true",
                     help="do not also time the other mode (reported as 'other_mode')")
-    args = ap.parse_args()
-    presets = {"small": (10000, 50, 1e8), "headline": (1 << 20, 128, 1e8),
-               "precision": (1 << 22, 256, 1e12), "large": (1 << 23, 512, 1e18)}
+    ap.add_argument("--no-config2", action="store_true",
+                    help="with --config 5: do not also time the 2^20 x 128 workload ('config2')")
+    ap.add_argument("--profile-window", action="store_true",
+                    help="cudaProfilerStart/Stop around the timed steps of the main mode only")
+    args = ap.parse_args(argv)
     if args.preset:
-        args.m, args.n, args.kappa = presets[args.preset]
-        if args.preset == "precision" and args.mode == "fp32":
-            args.kappa = 1e5     # the single-precision variant of that workload
+        args.config = PRESETS[args.preset]
+    m, n, kappa = CONFIGS[args.config]
+    if args.config == 3 and args.mode == "fp32":
+        kappa = 1e5     # the single-precision variant of that workload
+    args.m = args.m or m
+    args.n = args.n or n
+    args.kappa = args.kappa or kappa
+    if args.e2e_steps is None:
+        args.e2e_steps = 3 if args.m <= (1 << 21) else 2
+    if args.other_steps is None:
+        args.other_steps = args.steps if args.m * args.n <= (1 << 21) * 128 else 2
     if args.cpu_sample_rows is None:
-        # about the same oracle work (rows x n^2) at every width
+        # about the same oracle work (rows x n^2) at every width, and at least twice the sample size
         args.cpu_sample_rows = max(4096, min(args.m, (1 << 17) * 128 * 128 // (args.n * args.n)))
+        args.cpu_sample_rows = min(args.m, max(args.cpu_sample_rows, 2 * (args.s or 3 * args.n)))
     return args
 
 
@@ -241,20 +267,48 @@ def traffic_from_profiles(kernel_tag, src_file, m=None):
 
 
 # ---- the oracle on the host cores --------------------------------------------------------------------
-def oracle_sample_time(m, n, s, kappa, seed, rows, reps):
+def oracle_calls(m, n, s, kappa, seed, rows, reps, warm=1):
+    """Times `reps` oracle rpCholesky-QR calls on the first `rows` rows of the workload (same n, s,
+    kappa), after `warm` untimed calls and the best of two calls on rows/2 rows: (per-call seconds of
+    the `reps` calls, half-sample seconds, rows, half rows, threads used).  The two sizes separate the
+    oracle's fixed cost (sample, Householder QR, Cholesky) from its per-row cost, so the full-m time
+    is extrapolated as t + (m - rows) * per_row."""
     import inputs
     import oracle
     oracle.build()
     rows = min(rows, m)
+    half = max(min(s, rows), rows // 2)
     A = inputs.usv(rows, n, kappa, seed)
-    times = []
-    for r in range(reps):
+    Ah = np_ascontig(A[:half])
+
+    def call(X, k):
         t0 = time.perf_counter()
-        o = oracle.rpcholqr(A, min(s, rows), 1 + r)
-        times.append(time.perf_counter() - t0)
+        o = oracle.rpcholqr(X, min(s, X.shape[0]), 1 + k)
+        dt = time.perf_counter() - t0
         if o["status"] != 0:
             raise RuntimeError(f"oracle status {o['status']}")
-    return times, rows, oracle.num_threads()
+        return dt
+
+    for w in range(max(warm, 1)):
+        call(A, w)
+    t_half = min(call(Ah, 0), call(Ah, 1))
+    times = [call(A, r) for r in range(reps)]
+    return times, t_half, rows, half, oracle.num_threads()
+
+
+def np_ascontig(a):
+    import numpy as np
+    return np.ascontiguousarray(a)
+
+
+def extrapolate_full(t_rows, t_half, rows, half, m):
+    """Seconds for the full m from calls on `rows` and `half` rows (cost = fixed + per_row * rows)."""
+    if rows >= m:
+        return t_rows
+    per_row = max(t_rows - t_half, 0.0) / max(rows - half, 1) if rows > half else t_rows / rows
+    if per_row <= 0.0:
+        per_row = t_rows / rows
+    return t_rows + (m - rows) * per_row
 
 
 def run_reference(args, ws, rank):
@@ -262,21 +316,24 @@ def run_reference(args, ws, rank):
         return 0
     m, n = args.m, args.n
     s = args.s or 3 * n
-    times, rows, cores = oracle_sample_time(m, n, s, args.kappa, args.seed, args.cpu_sample_rows,
-                                            args.warmup + args.steps)
-    timed = times[args.warmup:]
+    timed, t_half, rows, half, cores = oracle_calls(m, n, s, args.kappa, args.seed, args.cpu_sample_rows,
+                                                     args.steps, warm=args.warmup)
     per_step = sum(timed) / len(timed)
-    scale = m / rows
-    value = 1.0 / (per_step * scale)
-    sample = (f"oracle rpCholesky-QR on the first {rows} of {m} rows (same n, s, kappa), "
-              f"time x{scale:g} for the full m; {len(timed)} timed steps after {args.warmup} warm-up")
+    full = extrapolate_full(per_step, t_half, rows, half, m)
+    value = 1.0 / full
+    sample = (f"each step one oracle rpCholesky-QR call on the first {rows} of {m} rows (same n, s, kappa; "
+              f"{per_step * 1e3:.1f} ms measured per step); value = per-matrix rate extrapolated to the full m "
+              f"from that call and one on {half} rows ({t_half * 1e3:.1f} ms): {full * 1e3:.1f} ms per matrix")
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "matrices/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": per_step * scale * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"rpCholesky-QR m={m} n={n} s={s} kappa={args.kappa:g}", "m": m, "n": n,
                    "s": s, "kappa": args.kappa},
+        "value_basis": "extrapolated" if rows < m else "measured",
+        "extrapolated_ms_per_matrix": full * 1e3,
+        "sample_rows": rows,
         "effective_tflops": alg_flops(m, n, s) * value / 1e12,
         "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
@@ -287,8 +344,99 @@ def run_reference(args, ws, rank):
 
 
 # ---- our CUDA path -------------------------------------------------------------------------------------
+MODES = ("fp64", "split", "fp32")
+
+
+def preload_torch_linalg():
+    """Load torch's CUDA linear-algebra library by full path before torch.linalg first needs it (the
+    input generator's QR): under ncu's injection torch's own lazy dlopen of it by name fails."""
+    import ctypes
+    import torch
+    path = os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")
+    if os.path.exists(path):
+        ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+
+
+def timed_factor(rq, torch, local, dev, dist, m, n, s, mode, A, Q, R, info, stream, K, W, smoothing="none",
+                 clocks=False, profile=False, A32=None, Q32=None, R32=None):
+    """W warm-up + K timed factor calls on a fresh plan of `mode` (CUDA events on the launching stream,
+    barrier + synchronize on both sides): (ms over the K steps, phases, calls, launches, plan, clocks)."""
+    modes = {"fp64": rq.FP64, "split": rq.SPLIT64, "fp32": rq.FP32}
+
+    def factor(plan, seed):
+        if mode == "fp32":
+            rq.rpcholqr_factor_f32(plan, A32, s, seed, Q=Q32, R=R32, info=info, stream=stream)
+        else:
+            rq.rpcholqr_factor(plan, A, s, seed, Q=Q, R=R, info=info, stream=stream)
+
+    plan = rq.rpcholqr_plan_create(local, m, n, s, mode=modes[mode])
+    if smoothing != "none":
+        rq.rpcholqr_plan_set_smoothing(plan, rq.SMOOTH_WHT if smoothing == "wht" else rq.SMOOTH_DCT)
+    for w in range(W):
+        factor(plan, 1 + w)
+    torch.cuda.synchronize(dev)
+    st0 = info.cpu().tolist()
+    if st0[0] != 0:
+        raise RuntimeError(f"{mode} warm-up status {rq.rpcholqr_status_string(st0[0])}")
+    rq.rpcholqr_plan_collect_timing(plan)          # reset counters
+    rq.rpcholqr_plan_enable_timing(plan, K)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with (ClockSampler(local) if clocks else _NoClock()) as clk:
+        barrier(dist)
+        torch.cuda.synchronize(dev)
+        if profile:
+            torch.cuda.profiler.start()
+        e0.record(stream)
+        for k in range(K):
+            factor(plan, 1 + k)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if profile:
+            torch.cuda.profiler.stop()
+        barrier(dist)
+    ph, calls, launches = rq.rpcholqr_plan_collect_timing(plan)
+    rq.rpcholqr_plan_enable_timing(plan, 0)
+    return max_over_ranks(e0.elapsed_time(e1), dist, dev), ph, calls, launches, plan, clk
+
+
+def cpu_baseline_entry(m, n, s, kappa, seed, rows):
+    times, t_half, rows, half, cores = oracle_calls(m, n, s, kappa, seed, rows, 3)
+    full = extrapolate_full(min(times), t_half, rows, half, m)
+    return {"value": 1.0 / full, "unit": "matrices/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle rpCholesky-QR on the first {rows} of {m} rows (numpy-generated, same n, s, "
+                      f"kappa), best of 3 ({min(times) * 1e3:.1f} ms), and one call on {half} rows "
+                      f"({t_half * 1e3:.1f} ms); full-m time extrapolated from the two: {full * 1e3:.1f} ms"}
+
+
+def run_config2(args, rq, torch, local, dev, dist, stream, ws):
+    """The 2^20 x 128, kappa = 1e8, s = 3n workload in SPLIT64 and FP64 (reported beside config 5)."""
+    import inputs
+    m, n, kappa = CONFIGS[2]
+    s = 3 * n
+    A = inputs.usv_torch(m, n, kappa, args.seed + 7, dev)
+    Q = torch.empty_like(A)
+    R = torch.empty((n, n), dtype=torch.float64, device=dev)
+    info = torch.empty(2, dtype=torch.int32, device=dev)
+    out = {"workload": f"rpCholesky-QR m={m} n={n} s={s} kappa={kappa:g}", "m": m, "n": n, "s": s,
+           "kappa": kappa}
+    for mode in ("split", "fp64"):
+        ms, ph, calls, _, plan, _ = timed_factor(rq, torch, local, dev, dist, m, n, s, mode, A, Q, R, info, stream,
+                                                 args.steps, args.warmup)
+        plan.close()
+        st = info.cpu().tolist()
+        orth, res = (None, None) if args.no_metrics else gpu_metrics(A, Q, R)
+        out[mode] = {"value": ws * args.steps / (ms / 1e3), "unit": "matrices/s",
+                     "ms_per_step": ms / args.steps, "status": st[0], "orth": orth, "residual": res,
+                     "effective_tflops": alg_flops(m, n, s) * args.steps / (ms / 1e3) / 1e12,
+                     "phases_ms_per_step": {k: v / max(calls, 1) for k, v in ph.items()}}
+    out["split_over_fp64"] = out["split"]["value"] / out["fp64"]["value"]
+    del A, Q
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, ws, rank, local):
-    import numpy as np
     import torch
 
     import inputs
@@ -298,6 +446,7 @@ def run_ours(args, ws, rank, local):
     dev = torch.device("cuda", local)
     dist = init_dist(ws, "nccl")
     rq.build()
+    preload_torch_linalg()
     m, n = args.m, args.n
     s = args.s or 3 * n
     K, W = args.steps, args.warmup
@@ -311,54 +460,26 @@ def run_ours(args, ws, rank, local):
     info = torch.empty(2, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     fp64_peak = rq.rpcholqr_probe_fp64_mma(local, 4096)
+    A32 = Q32 = R32 = None
     if args.mode == "fp32":
         A32 = A.float()
         Q32 = torch.empty_like(A32)
         R32 = torch.empty((n, n), dtype=torch.float32, device=dev)
-    modes = {"fp64": rq.FP64, "split": rq.SPLIT64, "fp32": rq.FP32}
 
-    def factor(plan, mode, seed):
-        if mode == "fp32":
-            rq.rpcholqr_factor_f32(plan, A32, s, seed, Q=Q32, R=R32, info=info, stream=stream)
-        else:
-            rq.rpcholqr_factor(plan, A, s, seed, Q=Q, R=R, info=info, stream=stream)
-
-    def timed(mode, clocks):
-        """W warm-up + K timed factor calls on a fresh plan of `mode`: (ms, phases, calls, launches, plan)."""
-        plan = rq.rpcholqr_plan_create(local, m, n, s, mode=modes[mode])
-        if args.smoothing != "none":
-            rq.rpcholqr_plan_set_smoothing(plan, rq.SMOOTH_WHT if args.smoothing == "wht" else rq.SMOOTH_DCT)
-        for w in range(W):
-            factor(plan, mode, 1 + w)
-        torch.cuda.synchronize(dev)
-        st0 = info.cpu().tolist()
-        if st0[0] != 0:
-            raise RuntimeError(f"{mode} warm-up status {rq.rpcholqr_status_string(st0[0])}")
-        rq.rpcholqr_plan_collect_timing(plan)          # reset counters
-        rq.rpcholqr_plan_enable_timing(plan, K)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        with (ClockSampler(local) if clocks else _NoClock()) as clk:
-            barrier(dist)
-            torch.cuda.synchronize(dev)
-            e0.record(stream)
-            for k in range(K):
-                factor(plan, mode, 1 + k)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            barrier(dist)
-        ph, calls, launches = rq.rpcholqr_plan_collect_timing(plan)
-        rq.rpcholqr_plan_enable_timing(plan, 0)
-        return max_over_ranks(e0.elapsed_time(e1), dist, dev), ph, calls, launches, plan, clk
+    def run(mode, steps, warm, clocks=False, profile=False):
+        return timed_factor(rq, torch, local, dev, dist, m, n, s, mode, A, Q, R, info, stream, steps, warm,
+                            smoothing=args.smoothing, clocks=clocks, profile=profile, A32=A32, Q32=Q32, R32=R32)
 
     other = None
     if not args.no_compare:
         omode = {"split": "fp64", "fp64": "split", "fp32": "split"}[args.mode]
-        o_ms, o_ph, o_calls, _, o_plan, _ = timed(omode, False)
+        ok = args.other_steps
+        ow = W if ok == K else 1
+        o_ms, o_ph, o_calls, _, o_plan, _ = run(omode, ok, ow)
         o_plan.close()
-        other = {"mode": omode, "value": ws * K / (o_ms / 1e3), "ms_per_step": o_ms / K,
-                 "phases_ms_per_step": {k: v / max(o_calls, 1) for k, v in o_ph.items()}}
-    t_ms_max, phases, calls, launches, plan, clk = timed(args.mode, True)
+        other = {"mode": omode, "value": ws * ok / (o_ms / 1e3), "ms_per_step": o_ms / ok, "steps": ok,
+                 "warmup": ow, "phases_ms_per_step": {k: v / max(o_calls, 1) for k, v in o_ph.items()}}
+    t_ms_max, phases, calls, launches, plan, clk = run(args.mode, K, W, clocks=True, profile=args.profile_window)
     st = info.cpu().tolist()
     if args.no_metrics:
         orth, res = None, None
@@ -371,10 +492,11 @@ def run_ours(args, ws, rank, local):
     e2e = None
     if args.e2e_steps > 0 and args.mode == "fp32":
         # through the public Python API: pinned host A -> device, factor, Q, R, info -> pinned host
-        Ah = A32.cpu().pin_memory()
-        Qh = torch.empty((m, n), dtype=torch.float32).pin_memory()
-        Rh = torch.empty((n, n), dtype=torch.float32).pin_memory()
-        ih = torch.empty(2, dtype=torch.int32).pin_memory()
+        Ah = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
+        Ah.copy_(A32)
+        Qh = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
+        Rh = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+        ih = torch.empty(2, dtype=torch.int32, pin_memory=True)
         Ad = torch.empty_like(A32)
         barrier(dist)
         t0 = time.perf_counter()
@@ -387,12 +509,14 @@ def run_ours(args, ws, rank, local):
             torch.cuda.synchronize(dev)
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
         barrier(dist)
-        e2e = {"value": ws * args.e2e_steps / e2e_s, "unit": "matrices/s",
+        e2e = {"value": ws * args.e2e_steps / e2e_s, "unit": "matrices/s", "steps": args.e2e_steps,
                "h2d_bytes_per_step": 4 * m * n, "d2h_bytes_per_step": 4 * m * n + 4 * n * n + 8}
+        del Ah, Qh, Ad
     elif args.e2e_steps > 0:
-        Ah = A.cpu().pin_memory()
-        Qh = torch.empty((m, n), dtype=torch.float64).pin_memory()
-        Rh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        Ah = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+        Ah.copy_(A)
+        Qh = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+        Rh = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
         rq.rpcholqr_factor_host(plan, Ah, s, 1, Q=Qh, R=Rh, stream=stream)   # allocates staging
         barrier(dist)
         t0 = time.perf_counter()
@@ -400,11 +524,22 @@ def run_ours(args, ws, rank, local):
             rq.rpcholqr_factor_host(plan, Ah, s, 1 + k, Q=Qh, R=Rh, stream=stream)
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
         barrier(dist)
-        e2e = {"value": ws * args.e2e_steps / e2e_s, "unit": "matrices/s",
+        e2e = {"value": ws * args.e2e_steps / e2e_s, "unit": "matrices/s", "steps": args.e2e_steps,
                "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * m * n + 8 * n * n + 8}
+        del Ah, Qh
+
+    config2 = None
+    if args.config == 5 and not args.no_config2 and not args.profile_window and args.mode != "fp32" \
+            and args.smoothing == "none":
+        plan.close()
+        plan = None
+        del A, Q
+        torch.cuda.empty_cache()
+        config2 = run_config2(args, rq, torch, local, dev, dist, stream, ws)
 
     if rank != 0:
-        plan.close()
+        if plan is not None:
+            plan.close()
         return 0
 
     N = ws
@@ -458,11 +593,7 @@ def run_ours(args, ws, rank, local):
 
     cpu = None
     if not args.no_cpu_baseline and N == 1:
-        times, rows, cores = oracle_sample_time(m, n, s, args.kappa, args.seed, args.cpu_sample_rows, 3)
-        per = min(times) * (m / rows)
-        cpu = {"value": 1.0 / per, "unit": "matrices/s", "cores": cores, "kind": "oracle",
-               "sample": f"oracle on the first {rows} of {m} rows (numpy-generated, same n, s, kappa), "
-                         f"best of 3, time x{m / rows:g}"}
+        cpu = cpu_baseline_entry(m, n, s, args.kappa, args.seed, max(args.cpu_sample_rows, 4 * s))
 
     out = {
         "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": N, "steps": K, "warmup": W,
@@ -490,13 +621,15 @@ def run_ours(args, ws, rank, local):
                                      "(unit count x clock: 152 SM x 4 x 32 lanes / 64 cycles x 2 flop "
                                      "x 2.07 GHz = 1.26 TFLOP/s)")},
         "other_mode": other,
+        "config2": config2,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
     print(json.dumps(out), flush=True)
-    plan.close()
+    if plan is not None:
+        plan.close()
     return 0
 
 
@@ -511,6 +644,7 @@ def run_batch(args, ws, rank, local):
     dev = torch.device("cuda", local)
     dist = init_dist(ws, "nccl")
     rq.build()
+    preload_torch_linalg()
     K, W = args.steps, args.warmup
     man = inputs.batch_manifest(args.count, args.seed + 1000 * rank)
     As = [inputs.usv_torch(e["m"], e["n"], e["kappa"], e["seed"], dev) for e in man]

@@ -93,6 +93,31 @@ typedef struct rpcholqr_plan_s* rpcholqr_plan;
 rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_mode mode,
                                      int64_t max_m, int32_t max_n, int32_t max_s);
 
+/* Plan options (rpcholqr_plan_set_option / rpcholqr_plan_get_option); each holds until changed. */
+typedef enum {
+    RPCHOLQR_OPT_SPIN_LIMIT = 0,    /* polls a device-side pipeline wait makes before it gives up and the
+                                       call reports RPCHOLQR_ERR_TIMEOUT (default 2^24, 1 <= value <=
+                                       2^40).  A kernel's final wait for its own tensor-core work, before
+                                       it releases its tensor memory, always uses the default. */
+    RPCHOLQR_OPT_SCALE_SAMPLE = 1,  /* 1 (default): the sample is scaled by sqrt(m/s) (Remark r_exp);
+                                       0: unscaled.  R is the same in exact arithmetic either way. */
+    RPCHOLQR_OPT_DETERMINISTIC = 2, /* 1 (default, the only value built): every reduction is a
+                                       fixed-order sum, so results are bit-reproducible for a fixed plan
+                                       shape and seed; 0 returns RPCHOLQR_ERR_UNSUPPORTED. */
+    RPCHOLQR_OPT_BATCH_CAPACITY = 3 /* matrices rpcholqr_factor_batched can take without allocating:
+                                       setting it allocates (cudaMalloc) the batched kernel's workspace
+                                       now -- about (max_s + 5 np) np + 2 (np/8) 64 doubles per matrix,
+                                       np = max_n rounded up to 16, plus its work list; 0 frees it.
+                                       Default 0: the first batched call allocates for its count. */
+} rpcholqr_option;
+
+/* Set option `option` of the plan to `value` (host call; affects later calls).
+ * Errors: RPCHOLQR_ERR_ARG (unknown option or value out of range), RPCHOLQR_ERR_UNSUPPORTED. */
+rpcholqr_status rpcholqr_plan_set_option(rpcholqr_plan plan, int32_t option, int64_t value);
+
+/* Read option `option` of the plan into *value (host). */
+rpcholqr_status rpcholqr_plan_get_option(rpcholqr_plan plan, int32_t option, int64_t* value);
+
 /* Free the plan and its workspace (synchronises the plan's device first).  NULL is accepted. */
 rpcholqr_status rpcholqr_plan_destroy(rpcholqr_plan plan);
 
@@ -113,6 +138,28 @@ rpcholqr_status rpcholqr_workspace_size(int64_t max_m, int32_t max_n, int32_t ma
 rpcholqr_status rpcholqr_factor(rpcholqr_plan plan, const double* A, int64_t m, int32_t n,
                                 int64_t lda, int32_t s, uint64_t seed, double* Q, int64_t ldq,
                                 double* R, int32_t* info, void* stream);
+
+/* Batched rpCholesky-QR: Algorithm alg_2 for `count` independent matrices in ONE persistent kernel launch
+ * (plus a one-CTA setup launch), the workload of block-Krylov / LOBPCG solvers that orthogonalise many
+ * tall-skinny blocks of uneven size (Section 1).  Every per-matrix array is DEVICE-resident, of length
+ * count: A[i] (device pointer, m[i] x n[i], lda[i]), s[i], seed[i] (Philox key word 0, stream_id 0),
+ * Q[i] (device, m[i] x n[i], ldq[i]; holds A1 between the passes), R[i] (device, n[i] x n[i], ld n[i]);
+ * info: device int32[2 count], {status, pivot} per matrix as for rpcholqr_factor.  A matrix whose shape
+ * does not fit the plan (n[i] <= max_n, n[i] <= s[i] <= max_s, s[i] <= m[i] <= max_m, lda[i], ldq[i] >=
+ * n[i], non-NULL pointers) gets RPCHOLQR_ERR_ARG in its info and is skipped; the others are factored.
+ * Each matrix's Q, R and status are bit-identical to rpcholqr_factor on an FP64 plan with the same
+ * limits, whatever else is in the batch.  The kernel's CTAs (one per SM) take work items -- per matrix:
+ * sample + Householder R_s; pass-1 parts (row solve + Gram partial); Cholesky + R; pass-2 parts -- from
+ * a device work list in order and wait (bounded by RPCHOLQR_OPT_SPIN_LIMIT polls, sleeping between
+ * polls) for the items of the same matrix before them; a wait that gives up sets RPCHOLQR_ERR_TIMEOUT
+ * in that matrix's info.  The call is asynchronous on `stream` and can be captured in a CUDA graph once
+ * the plan's batch capacity covers count (RPCHOLQR_OPT_BATCH_CAPACITY; otherwise this call allocates).
+ * Requires an RPCHOLQR_FP64 plan with max_n <= 128 and no smoothing (RPCHOLQR_ERR_UNSUPPORTED
+ * otherwise); 1 <= count <= 65536.  Errors: ERR_ARG, ERR_UNSUPPORTED, ERR_NOMEM, ERR_CUDA. */
+rpcholqr_status rpcholqr_factor_batched(rpcholqr_plan plan, int32_t count, const double* const* A, const int64_t* m,
+                                        const int32_t* n, const int64_t* lda, const int32_t* s, const uint64_t* seed,
+                                        double* const* Q, const int64_t* ldq, double* const* R, int32_t* info,
+                                        void* stream);
 
 /* FP32 factorisation (the FP32 mode; no counterpart in the paper, which works in double precision):
  * the same steps as rpcholqr_factor with A (m x n, lda), Q (m x n, ldq) and R (n x n, dense
@@ -213,7 +260,8 @@ rpcholqr_status rpcholqr_probe_fp64_mma(int device, int32_t iters, double* flops
  * Scratch comes from one fixed __device__ array of about 5.3 MB inside the library, which every
  * GPU that loads the library holds until the process exits; it fits n <= 64 (larger n returns
  * RPCHOLQR_ERR_UNSUPPORTED; any m is accepted).  The call allocates nothing and calls no
- * allocating library routine.  Runs on the current device.  The first call on each device looks up
+ * allocating library routine.  Runs on the current device; `stream` must belong to it
+ * (RPCHOLQR_ERR_ARG otherwise).  The first call on each device looks up
  * the array's device address (cudaGetSymbolAddress) with that device current, so make that first
  * call before any stream capture.  Every call shares the array and leaves its contents behind:
  * calls whose kernels overlap on the GPU (other streams, other threads) race on it and must be
@@ -300,12 +348,12 @@ rpcholqr_status rpcholqr_batch_create(rpcholqr_batch* batch, int device, rpcholq
 rpcholqr_status rpcholqr_batch_destroy(rpcholqr_batch batch);
 
 /* Factor count matrices (rpcholqr_factor semantics each, Philox stream_id = 0, key = seed[i]). */
-rpcholqr_status rpcholqr_factor_batched(rpcholqr_batch batch, int32_t count, const double* const* A,
+rpcholqr_status rpcholqr_batch_factor(rpcholqr_batch batch, int32_t count, const double* const* A,
                                         const int64_t* m, const int32_t* n, const int64_t* lda,
                                         const int32_t* s, const uint64_t* seed, double* const* Q,
                                         const int64_t* ldq, double* const* R, int32_t* info, void* stream);
 
-/* Capture the same work as rpcholqr_factor_batched into a CUDA graph held by the batch (replacing a
+/* Capture the same work as rpcholqr_batch_factor into a CUDA graph held by the batch (replacing a
  * previous one); nothing runs until rpcholqr_batch_replay.  The buffers must stay valid while the
  * graph is replayed.  Uses the slot count the batch currently has. */
 rpcholqr_status rpcholqr_batch_capture(rpcholqr_batch batch, int32_t count, const double* const* A,
@@ -316,7 +364,7 @@ rpcholqr_status rpcholqr_batch_capture(rpcholqr_batch batch, int32_t count, cons
 /* Launch the captured graph on `stream` (RPCHOLQR_ERR_ARG if none was captured). */
 rpcholqr_status rpcholqr_batch_replay(rpcholqr_batch batch, void* stream);
 
-/* Autotuner: times rpcholqr_factor_batched on these matrices with 1, 2, 4, ... up to the batch's slot
+/* Autotuner: times rpcholqr_batch_factor on these matrices with 1, 2, 4, ... up to the batch's slot
  * count of concurrent slots (one warm-up and `reps` timed runs each, synchronous), keeps the fastest
  * as the batch's active slot count and returns it in *best_slots (host) and the per-run time in
  * *best_ms (host). */

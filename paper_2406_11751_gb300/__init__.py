@@ -20,7 +20,8 @@ __all__ = [
     "rpcholqr_triu_mul", "rpcholqr_probe_fp64_mma", "rpcholqr_status_string", "EXPORTED_SYMBOLS",
     "rpcholqr_plan_enable_timing", "rpcholqr_plan_collect_timing", "PHASES", "rpcholqr_ozaki_gemm",
     "rpcholqr_ozaki_gram", "SPLIT64", "rpcholqr_cholqr", "rpcholqr_cholqr2", "Batch",
-    "rpcholqr_batch_create", "rpcholqr_batch_destroy", "rpcholqr_factor_batched", "rpcholqr_batch_capture",
+    "rpcholqr_batch_create", "rpcholqr_batch_destroy", "rpcholqr_batch_factor", "rpcholqr_factor_batched",
+    "rpcholqr_batch_capture",
     "rpcholqr_batch_replay", "rpcholqr_batch_autotune", "FP32", "rpcholqr_factor_f32",
     "rpcholqr_gather_owned_rows", "rpcholqr_sketch_r_from_sample", "rpcholqr_sum_partials",
     "rpcholqr_plan_set_smoothing", "rpcholqr_smoothed_sample", "SMOOTH_NONE", "SMOOTH_WHT", "SMOOTH_DCT",
@@ -34,6 +35,8 @@ FP64 = 0
 SPLIT64 = 1
 FP32 = 2
 SMOOTH_NONE, SMOOTH_WHT, SMOOTH_DCT = 0, 1, 2
+OPT_SPIN_LIMIT, OPT_SCALE_SAMPLE, OPT_DETERMINISTIC, OPT_BATCH_CAPACITY = 0, 1, 2, 3
+ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM, ERR_UNSUPPORTED = 5, 6, 7, 8
 MAX_N = 512
 
 EXPORTED_SYMBOLS = (
@@ -42,11 +45,12 @@ EXPORTED_SYMBOLS = (
     "rpcholqr_precondition_gram", "rpcholqr_cholesky", "rpcholqr_solve_rows", "rpcholqr_triu_mul",
     "rpcholqr_probe_fp64_mma", "rpcholqr_status_string", "rpcholqr_plan_enable_timing",
     "rpcholqr_plan_collect_timing", "rpcholqr_ozaki_gemm", "rpcholqr_ozaki_gram", "rpcholqr_cholqr",
-    "rpcholqr_cholqr2", "rpcholqr_batch_create", "rpcholqr_batch_destroy", "rpcholqr_factor_batched",
+    "rpcholqr_cholqr2", "rpcholqr_batch_create", "rpcholqr_batch_destroy", "rpcholqr_batch_factor",
+    "rpcholqr_factor_batched",
     "rpcholqr_batch_capture", "rpcholqr_batch_replay", "rpcholqr_batch_autotune", "rpcholqr_factor_f32",
     "rpcholqr_gather_owned_rows", "rpcholqr_sketch_r_from_sample", "rpcholqr_sum_partials",
     "rpcholqr_plan_set_smoothing", "rpcholqr_smoothed_sample", "rpcholqr_plan_split_pass2_fp64",
-    "rpcholqr_scholqr3",
+    "rpcholqr_scholqr3", "rpcholqr_plan_set_option", "rpcholqr_plan_get_option",
 )
 PHASES = ("sample", "sketch_qr", "prep_rs", "pass1", "pass1_update", "pass1_solve2", "gram_reduce",
           "cholesky", "prep_r1", "pass2", "recover_r")
@@ -78,6 +82,8 @@ def load_library():
     sig = {
         "rpcholqr_plan_create": [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, I64, I32, I32],
         "rpcholqr_plan_destroy": [P],
+        "rpcholqr_plan_set_option": [P, I32, I64],
+        "rpcholqr_plan_get_option": [P, I32, ctypes.POINTER(I64)],
         "rpcholqr_workspace_size": [I64, I32, I32, ctypes.POINTER(ctypes.c_size_t)],
         "rpcholqr_factor": [P, P, I64, I32, I64, I32, U64, P, I64, P, P, P],
         "rpcholqr_factor_host": [P, P, I64, I32, I64, I32, U64, P, I64, P, P, P],
@@ -104,6 +110,7 @@ def load_library():
         "rpcholqr_scholqr3": [P, P, I64, I32, I64, P, I64, P, P, P],
         "rpcholqr_batch_create": [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, I64, I32, I32, I32],
         "rpcholqr_batch_destroy": [P],
+        "rpcholqr_batch_factor": [P, I32, P, P, P, P, P, P, P, P, P, P, P],
         "rpcholqr_factor_batched": [P, I32, P, P, P, P, P, P, P, P, P, P, P],
         "rpcholqr_batch_capture": [P, I32, P, P, P, P, P, P, P, P, P, P, P],
         "rpcholqr_batch_replay": [P, P],
@@ -186,6 +193,17 @@ def rpcholqr_plan_create(device: int, max_m: int, max_n: int, max_s: int, mode: 
 
 def rpcholqr_plan_destroy(plan: Plan):
     plan.close()
+
+
+def rpcholqr_plan_set_option(plan: Plan, option: int, value: int):
+    """Set a plan option (OPT_SPIN_LIMIT, OPT_SCALE_SAMPLE, OPT_DETERMINISTIC)."""
+    _check("rpcholqr_plan_set_option", load_library().rpcholqr_plan_set_option(plan.handle, option, int(value)))
+
+
+def rpcholqr_plan_get_option(plan: Plan, option: int) -> int:
+    v = ctypes.c_int64()
+    _check("rpcholqr_plan_get_option", load_library().rpcholqr_plan_get_option(plan.handle, option, ctypes.byref(v)))
+    return int(v.value)
 
 
 def rpcholqr_workspace_size(max_m: int, max_n: int, max_s: int) -> int:
@@ -492,11 +510,14 @@ def rpcholqr_plan_collect_timing(plan: Plan):
     return dict(zip(PHASES, [float(x) for x in ms])), int(calls.value), int(launches.value)
 
 
-def rpcholqr_precondition_gram_noalloc(A, Rs, A1, G, info, stream=None):
-    """Plan-free, allocation-free fused pass (n <= 64): every output buffer is the caller's.
+def rpcholqr_precondition_gram_noalloc(A, Rs, A1, G, info=None, stream=None):
+    """Plan-free, allocation-free fused pass (n <= 64): every buffer is the caller's.
 
     For callers that may not allocate device memory while running; the library's fixed device
-    scratch array is used instead (see include/rpcholqr.h).  Calls must not overlap on the GPU."""
+    scratch array is used instead (see include/rpcholqr.h).  Calls must not overlap on the GPU.
+    A1 (m x n), G (n x n, contiguous), Rs (n x n, contiguous) and info (int32, >= 2 entries) must
+    already exist on A's device: nothing is allocated or copied here."""
+    torch = _torch()
     lib = load_library()
     f = lib.rpcholqr_precondition_gram_noalloc
     f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
@@ -504,12 +525,27 @@ def rpcholqr_precondition_gram_noalloc(A, Rs, A1, G, info, stream=None):
     f.restype = ctypes.c_int
     _mat(A, "A")
     m, n = A.shape
-    Rs = _mat(Rs.contiguous(), "Rs")
+    _mat(Rs, "Rs")
     _mat(A1, "A1")
     _mat(G, "G")
-    _check("rpcholqr_precondition_gram_noalloc", f(
-        _ptr(A), m, n, A.stride(0), _ptr(Rs), _ptr(A1), A1.stride(0), _ptr(G), _ptr(info),
-        _stream(stream, A.device)))
+    if tuple(A1.shape) != (m, n):
+        raise ValueError(f"A1 must be {m} x {n}, got {tuple(A1.shape)}")
+    if tuple(G.shape) != (n, n) or not G.is_contiguous():
+        raise ValueError(f"G must be a contiguous {n} x {n} tensor")
+    if tuple(Rs.shape) != (n, n) or not Rs.is_contiguous():
+        raise ValueError(f"Rs must be a contiguous {n} x {n} tensor (no temporary copy is made)")
+    if info is None:
+        raise ValueError("info must be a device int32 tensor of >= 2 entries (nothing is allocated here)")
+    if not isinstance(info, torch.Tensor) or info.dtype != torch.int32 or info.numel() < 2 \
+            or not info.is_contiguous():
+        raise ValueError("info must be a contiguous device int32 tensor of >= 2 entries")
+    for name, t in (("Rs", Rs), ("A1", A1), ("G", G), ("info", info)):
+        if t.device != A.device:
+            raise ValueError(f"{name} is on {t.device}, A on {A.device}")
+    with torch.cuda.device(A.device):
+        _check("rpcholqr_precondition_gram_noalloc", f(
+            _ptr(A), m, n, A.stride(0), _ptr(Rs), _ptr(A1), A1.stride(0), _ptr(G), _ptr(info),
+            _stream(stream, A.device)))
     return A1, G, info
 
 
@@ -580,13 +616,58 @@ def _batch_outputs(As, Qs, Rs, info):
     return Qs, Rs, info
 
 
-def rpcholqr_factor_batched(batch: Batch, As, ss, seeds, Qs=None, Rs=None, info=None, stream=None):
-    """Factor the list of device matrices As (s[i] samples, seeds[i]); returns (Qs, Rs, info[2*count])."""
+def rpcholqr_batch_factor(batch: Batch, As, ss, seeds, Qs=None, Rs=None, info=None, stream=None):
+    """Factor the list of device matrices As (s[i] samples, seeds[i]) on the batch's slot plans; returns
+    (Qs, Rs, info[2*count])."""
     Qs, Rs, info = _batch_outputs(As, Qs, Rs, info)
     args, _keep = _batch_arrays(As, ss, seeds, Qs, Rs)
-    _check("rpcholqr_factor_batched", load_library().rpcholqr_factor_batched(
+    _check("rpcholqr_batch_factor", load_library().rpcholqr_batch_factor(
         batch.handle, *args, _ptr(info), _stream(stream, As[0].device)))
     return Qs, Rs, info
+
+
+class BatchArrays:
+    """Device-resident per-matrix arrays of a batch (pointers and shapes), as rpcholqr_factor_batched takes
+    them; built once from lists of tensors and reusable across calls (and CUDA-graph replays)."""
+
+    def __init__(self, As, ss, seeds, Qs, Rs):
+        torch = _torch()
+        dev = As[0].device
+        i64 = torch.int64
+
+        def arr(vals, dtype):
+            return torch.tensor(vals, dtype=dtype).to(dev)
+
+        def u64(v):   # uint64 bit patterns carried in int64
+            v = int(v) & 0xFFFFFFFFFFFFFFFF
+            return v - (1 << 64) if v >= (1 << 63) else v
+
+        self.count = len(As)
+        self.A = arr([t.data_ptr() for t in As], i64)
+        self.m = arr([t.shape[0] for t in As], i64)
+        self.n = arr([t.shape[1] for t in As], torch.int32)
+        self.lda = arr([t.stride(0) for t in As], i64)
+        self.s = arr(list(ss), torch.int32)
+        self.seed = arr([u64(x) for x in seeds], i64)
+        self.Q = arr([t.data_ptr() for t in Qs], i64)
+        self.ldq = arr([t.stride(0) for t in Qs], i64)
+        self.R = arr([t.data_ptr() for t in Rs], i64)
+        self.keep = (As, Qs, Rs)
+
+    def args(self):
+        return [self.count] + [_ptr(getattr(self, k)) for k in ("A", "m", "n", "lda", "s", "seed", "Q", "ldq", "R")]
+
+
+def rpcholqr_factor_batched(plan: Plan, As, ss, seeds, Qs=None, Rs=None, info=None, stream=None, arrays=None):
+    """All matrices of the list As in one persistent kernel launch (FP64 plan, n <= 128); returns
+    (Qs, Rs, info[2*count], arrays).  `arrays` (a BatchArrays of the same tensors) may be passed to reuse
+    the device-resident pointer/shape arrays."""
+    Qs, Rs, info = _batch_outputs(As, Qs, Rs, info)
+    if arrays is None:
+        arrays = BatchArrays(As, ss, seeds, Qs, Rs)
+    _check("rpcholqr_factor_batched", load_library().rpcholqr_factor_batched(
+        plan.handle, *arrays.args(), _ptr(info), _stream(stream, As[0].device)))
+    return Qs, Rs, info, arrays
 
 
 def rpcholqr_batch_capture(batch: Batch, As, ss, seeds, Qs=None, Rs=None, info=None, stream=None):

@@ -50,10 +50,10 @@ void launch_ozaki_slice_cols(const double* Y, int64_t ldy, int K, int N, uint8_t
 cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int32_t* xexp, int K,
                               const uint8_t* yblocks, const int32_t* yexp, int N, const double* B,
                               int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, int grid,
-                              cudaStream_t st);
+                              cudaStream_t st, long spin);
 int ozaki_gram_halves(int np);
 cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
-                              int nranges, double* gpart, int32_t* info, cudaStream_t st);
+                              int nranges, double* gpart, int32_t* info, cudaStream_t st, long spin);
 void launch_row_exp(const double* X, int64_t ldx, int64_t m, int K, int32_t* rowexp, cudaStream_t st);
 void launch_col_exp(const double* X, int64_t ldx, int64_t m, int n, int32_t* colexp, cudaStream_t st);
 cudaError_t launch_gemm_sub_fp64(const double* X, int64_t ldx, const double* Y, int64_t ldy, const double* B,
@@ -82,26 +82,44 @@ void launch_sum_parts(const double* parts, int32_t nparts, int32_t n, double* G,
 bool smooth_supported(int64_t m);
 size_t smooth_buffer_bytes(int64_t max_m, int max_n);
 cudaError_t launch_smoothed_sample(const double* A, int64_t m, int n, int64_t lda, int s, uint64_t seed, double* T,
-                                   int64_t* idx, double* As, int64_t lds, int np, int32_t* info, cudaStream_t st);
+                                   int64_t* idx, double* As, int64_t lds, int np, int32_t* info, cudaStream_t st, bool scale_sample);
 cudaError_t launch_smoothed_sample_f32(const float* A, int64_t m, int n, int64_t lda, int s, uint64_t seed,
                                        double* T, int64_t* idx, double* As, int64_t lds, int np, int32_t* info,
-                                       cudaStream_t st);
+                                       cudaStream_t st, bool scale_sample);
 void launch_colmajor_to_rows(const double* src, int64_t lds, int s, int n, double* dst, int64_t ldd,
                              cudaStream_t st);
 size_t smooth_dct_buffer_bytes(int64_t max_m, int max_n);
 cudaError_t launch_dct_sample(const double* A, int64_t m, int n, int64_t lda, int s, uint64_t seed, void* T,
                               int8_t* sgn, int64_t* idx, double* As, int64_t lds, int np, int32_t* info,
-                              cudaStream_t st);
+                              cudaStream_t st, bool scale_sample);
 cudaError_t launch_dct_sample_f32(const float* A, int64_t m, int n, int64_t lda, int s, uint64_t seed, void* T,
                                   int8_t* sgn, int64_t* idx, double* As, int64_t lds, int np, int32_t* info,
-                                  cudaStream_t st);
+                                  cudaStream_t st, bool scale_sample);
 void launch_pass2_gate(const double* R1, const double* W, int n, int np, double tau, const int32_t* info,
                        int32_t* gates, cudaStream_t st);
 void launch_gate_merge(int32_t* info, const int32_t* gates, cudaStream_t st);
 void launch_scholqr3_shift(double* G, int64_t ldg, int n, int64_t m, const int32_t* info, cudaStream_t st);
+// persist.cu
+struct BatchLayout {
+    int64_t mat_stride, off_rs, off_r1, off_g, off_frag_s, off_frag_1, off_diag_s, off_diag_1;
+    size_t mats_bytes, ctr_off, order_off, pre_off, items_off, queue_off, total;
+    int64_t max_items;
+};
+BatchLayout batch_layout(int32_t capacity, int32_t max_n, int32_t max_s, int sms);
+size_t batch_smem_bytes(int32_t max_n, int32_t max_s);
+int batch_max_np();
+cudaError_t launch_batch_persistent(int32_t count, const double* const* A, const int64_t* m, const int32_t* n,
+                                    const int64_t* lda, const int32_t* s, const uint64_t* seed, double* const* Q,
+                                    const int64_t* ldq, double* const* R, int32_t* info, void* ws, int32_t capacity,
+                                    int64_t max_m, int32_t max_n, int32_t max_s, int sms, int scale_sample,
+                                    long spin, int grid, cudaStream_t st);
+cudaError_t prepare_batch_persistent(int32_t max_n, int32_t max_s, int sms, int* grid);
 }  // namespace rpq
 
 using namespace rpq;
+
+constexpr int64_t kDefaultSpinLimit = int64_t{1} << 24;
+constexpr int64_t kMaxBatchCount = 1 << 16;   // matrices one rpcholqr_factor_batched call may take
 
 struct rpcholqr_plan_s {
     int device = 0;
@@ -140,6 +158,13 @@ struct rpcholqr_plan_s {
     int32_t timed_calls = 0;
     cudaEvent_t* events = nullptr;  // timing_slots x (RPCHOLQR_NUM_PHASES + 1)
     int64_t launches = 0;
+    // options (rpcholqr_plan_set_option)
+    int64_t spin_limit = kDefaultSpinLimit;   // polls of a pipeline wait before TIMEOUT
+    int32_t scale_sample = 1;                 // sample scaled by sqrt(m/s) (Remark r_exp)
+    // rpcholqr_factor_batched's workspace (RPCHOLQR_OPT_BATCH_CAPACITY or the first batched call)
+    void* batch_ws = nullptr;
+    int32_t batch_capacity = 0;
+    int batch_grid = 0;        // CTAs of the persistent kernel
     // SPLIT64 buffers (separate allocation)
     void* split_ws = nullptr;
     double* A1 = nullptr;       // max_m x np
@@ -219,6 +244,11 @@ rpcholqr_status reset_info(int32_t* info, cudaStream_t st) {
     return RPCHOLQR_OK;
 }
 
+// The sample's scale sqrt(m/s) (Remark r_exp) unless the plan turned it off.
+double sample_scale(const rpcholqr_plan_s* p, int64_t m, int32_t s) {
+    return p->scale_sample ? std::sqrt(static_cast<double>(m) / static_cast<double>(s)) : 1.0;
+}
+
 bool shape_ok(const rpcholqr_plan_s* p, int64_t m, int32_t n, int32_t s) {
     return n >= 1 && n <= p->max_n && s >= n && s <= p->max_s && m >= s && m <= p->max_m;
 }
@@ -266,8 +296,9 @@ cudaError_t plan_smoothed_sample<double>(rpcholqr_plan_s* p, const double* A, in
     p->launches += 3;
     if (p->smoothing == 2)
         return launch_dct_sample(A, m, n, lda, s, seed, p->smooth_T, p->smooth_sgn, p->smooth_idx, p->As, s, np,
-                                 info, st);
-    return launch_smoothed_sample(A, m, n, lda, s, seed, p->smooth_T, p->smooth_idx, p->As, s, np, info, st);
+                                 info, st, p->scale_sample != 0);
+    return launch_smoothed_sample(A, m, n, lda, s, seed, p->smooth_T, p->smooth_idx, p->As, s, np, info, st,
+                                  p->scale_sample != 0);
 }
 template <>
 cudaError_t plan_smoothed_sample<float>(rpcholqr_plan_s* p, const float* A, int64_t m, int n, int64_t lda, int s,
@@ -275,8 +306,9 @@ cudaError_t plan_smoothed_sample<float>(rpcholqr_plan_s* p, const float* A, int6
     p->launches += 3;
     if (p->smoothing == 2)
         return launch_dct_sample_f32(A, m, n, lda, s, seed, p->smooth_T, p->smooth_sgn, p->smooth_idx, p->As, s,
-                                     np, info, st);
-    return launch_smoothed_sample_f32(A, m, n, lda, s, seed, p->smooth_T, p->smooth_idx, p->As, s, np, info, st);
+                                     np, info, st, p->scale_sample != 0);
+    return launch_smoothed_sample_f32(A, m, n, lda, s, seed, p->smooth_T, p->smooth_idx, p->As, s, np, info, st,
+                                      p->scale_sample != 0);
 }
 
 void free_events(rpcholqr_plan_s* p) {
@@ -399,6 +431,65 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
     return RPCHOLQR_OK;
 }
 
+// (Re)allocates the persistent batched kernel's workspace for up to `capacity` matrices (0 frees it).
+static rpcholqr_status reserve_batch(rpcholqr_plan_s* p, int32_t capacity) {
+    if (capacity == p->batch_capacity) return RPCHOLQR_OK;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    if (p->batch_ws) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+        cudaFree(p->batch_ws);
+        p->batch_ws = nullptr;
+        p->batch_capacity = 0;
+    }
+    if (capacity == 0) return RPCHOLQR_OK;
+    if (prepare_batch_persistent(p->max_n, p->max_s, p->grid, &p->batch_grid) != cudaSuccess) {
+        cudaGetLastError();
+        return RPCHOLQR_ERR_CUDA;
+    }
+    const BatchLayout L = batch_layout(capacity, p->max_n, p->max_s, p->grid);
+    if (cudaMalloc(&p->batch_ws, L.total) != cudaSuccess) {
+        cudaGetLastError();
+        p->batch_ws = nullptr;
+        return RPCHOLQR_ERR_NOMEM;
+    }
+    p->batch_capacity = capacity;
+    return RPCHOLQR_OK;
+}
+
+rpcholqr_status rpcholqr_plan_set_option(rpcholqr_plan p, int32_t option, int64_t value) {
+    if (!p) return RPCHOLQR_ERR_ARG;
+    switch (option) {
+        case RPCHOLQR_OPT_SPIN_LIMIT:
+            if (value < 1 || value > (int64_t{1} << 40)) return RPCHOLQR_ERR_ARG;
+            p->spin_limit = value;
+            return RPCHOLQR_OK;
+        case RPCHOLQR_OPT_SCALE_SAMPLE:
+            if (value != 0 && value != 1) return RPCHOLQR_ERR_ARG;
+            p->scale_sample = static_cast<int32_t>(value);
+            return RPCHOLQR_OK;
+        case RPCHOLQR_OPT_DETERMINISTIC:
+            // every reduction is a fixed-order sum; no run-to-run varying variant is built
+            if (value == 1) return RPCHOLQR_OK;
+            return value == 0 ? RPCHOLQR_ERR_UNSUPPORTED : RPCHOLQR_ERR_ARG;
+        case RPCHOLQR_OPT_BATCH_CAPACITY:
+            if (value < 0 || value > kMaxBatchCount) return RPCHOLQR_ERR_ARG;
+            return reserve_batch(p, static_cast<int32_t>(value));
+        default: return RPCHOLQR_ERR_ARG;
+    }
+}
+
+rpcholqr_status rpcholqr_plan_get_option(rpcholqr_plan p, int32_t option, int64_t* value) {
+    if (!p || !value) return RPCHOLQR_ERR_ARG;
+    switch (option) {
+        case RPCHOLQR_OPT_SPIN_LIMIT: *value = p->spin_limit; return RPCHOLQR_OK;
+        case RPCHOLQR_OPT_SCALE_SAMPLE: *value = p->scale_sample; return RPCHOLQR_OK;
+        case RPCHOLQR_OPT_DETERMINISTIC: *value = 1; return RPCHOLQR_OK;
+        case RPCHOLQR_OPT_BATCH_CAPACITY: *value = p->batch_capacity; return RPCHOLQR_OK;
+        default: return RPCHOLQR_ERR_ARG;
+    }
+}
+
 rpcholqr_status rpcholqr_plan_destroy(rpcholqr_plan plan) {
     if (!plan) return RPCHOLQR_OK;
     DeviceGuard guard(plan->device);
@@ -417,6 +508,7 @@ rpcholqr_status rpcholqr_plan_destroy(rpcholqr_plan plan) {
     cudaFree(plan->hrows_dev);
     cudaFree(plan->split_ws);
     cudaFree(plan->smooth_ws);
+    cudaFree(plan->batch_ws);
     free_events(plan);
     delete plan;
     return RPCHOLQR_OK;
@@ -434,7 +526,7 @@ static rpcholqr_status sketch_internal(rpcholqr_plan p, const double* A, int64_t
                                        double* Rs_user, int32_t* info, cudaStream_t st,
                                        const PhaseMarks* pm) {
     const int np = pad_np(n);
-    const double scale = std::sqrt(static_cast<double>(m) / static_cast<double>(s));
+    const double scale = sample_scale(p, m, s);
     if (pm) pm->mark(RPCHOLQR_PHASE_SAMPLE);
     const int64_t lds = s;
     if (p->smoothing) {
@@ -673,7 +765,8 @@ static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const doub
     if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
     const int64_t tiles = ((m + 127) / 128) * ((N + 63) / 64);
     const int grid = static_cast<int>(tiles < p->grid ? tiles : p->grid);
-    if (launch_ozaki_gemm(sub, X, ldx, xexp, K, p->yblocks, p->yexp, N, B, ldb, C, ldc, m, info, grid, st) !=
+    if (launch_ozaki_gemm(sub, X, ldx, xexp, K, p->yblocks, p->yexp, N, B, ldb, C, ldc, m, info, grid, st,
+                          static_cast<long>(p->spin_limit)) !=
         cudaSuccess)
         return RPCHOLQR_ERR_CUDA;
     ++p->launches;
@@ -695,7 +788,8 @@ static rpcholqr_status ozaki_gram_internal(rpcholqr_plan p, const double* X, int
     if (nranges < 1) nranges = 1;
     const int64_t max_ranges = (m + 31) / 32;
     if (nranges > max_ranges) nranges = static_cast<int>(max_ranges);
-    if (launch_ozaki_gram(X, ldx, m, n, np, p->colexp, nranges, p->gpart, info, st) != cudaSuccess)
+    if (launch_ozaki_gram(X, ldx, m, n, np, p->colexp, nranges, p->gpart, info, st,
+                          static_cast<long>(p->spin_limit)) != cudaSuccess)
         return RPCHOLQR_ERR_CUDA;
     ++p->launches;
     launch_gram_reduce(p->gpart, nranges, np, n, G, ldg, info, st);
@@ -783,6 +877,32 @@ rpcholqr_status rpcholqr_factor(rpcholqr_plan p, const double* A, int64_t m, int
     return check_launch();
 }
 
+rpcholqr_status rpcholqr_factor_batched(rpcholqr_plan p, int32_t count, const double* const* A, const int64_t* m,
+                                        const int32_t* n, const int64_t* lda, const int32_t* s, const uint64_t* seed,
+                                        double* const* Q, const int64_t* ldq, double* const* R, int32_t* info,
+                                        void* stream) {
+    if (!p || count < 1 || count > kMaxBatchCount || !A || !m || !n || !lda || !s || !seed || !Q || !ldq || !R ||
+        !info)
+        return RPCHOLQR_ERR_ARG;
+    if (p->mode != RPCHOLQR_FP64 || pad_np(p->max_n) > batch_max_np() || p->smoothing)
+        return RPCHOLQR_ERR_UNSUPPORTED;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    if (count > p->batch_capacity) {
+        const rpcholqr_status rc = reserve_batch(p, count);
+        if (rc != RPCHOLQR_OK) return rc;
+    }
+    if (launch_batch_persistent(count, A, m, n, lda, s, seed, Q, ldq, R, info, p->batch_ws, p->batch_capacity,
+                                p->max_m, p->max_n, p->max_s, p->grid, p->scale_sample,
+                                static_cast<long>(p->spin_limit), p->batch_grid,
+                                static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return RPCHOLQR_ERR_CUDA;
+    }
+    p->launches += 2;
+    return RPCHOLQR_OK;
+}
+
 rpcholqr_status rpcholqr_factor_f32(rpcholqr_plan p, const float* A, int64_t m, int32_t n, int64_t lda,
                                     int32_t s, uint64_t seed, float* Q, int64_t ldq, float* R, int32_t* info,
                                     void* stream) {
@@ -797,7 +917,7 @@ rpcholqr_status rpcholqr_factor_f32(rpcholqr_plan p, const float* A, int64_t m, 
     if (rc != RPCHOLQR_OK) return rc;
     // sample (widened to FP64) and the FP64 Householder R_s
     pm.mark(RPCHOLQR_PHASE_SAMPLE);
-    const double scale = std::sqrt(static_cast<double>(m) / static_cast<double>(s));
+    const double scale = sample_scale(p, m, s);
     if (p->smoothing) {
         if (plan_smoothed_sample<float>(p, A, m, n, lda, s, seed, np, info, st) != cudaSuccess)
             return RPCHOLQR_ERR_CUDA;
@@ -950,7 +1070,7 @@ static rpcholqr_status factor_host_split(rpcholqr_plan p, const double* A, int64
             cudaEventRecord(p->hev[c], p->hcopy) != cudaSuccess)
             return RPCHOLQR_ERR_CUDA;
     }
-    launch_sample_rows(p->hrows_dev, n, s, std::sqrt(static_cast<double>(m) / static_cast<double>(s)), p->As, s, np,
+    launch_sample_rows(p->hrows_dev, n, s, sample_scale(p, m, s), p->As, s, np,
                        info, st);
     if (launch_householder(p->As, s, s, n, np, p->Rs, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
     p->launches += 3;

@@ -113,7 +113,7 @@ rpcholqr_status rpcholqr_batch_destroy(rpcholqr_batch batch) {
     return RPCHOLQR_OK;
 }
 
-rpcholqr_status rpcholqr_factor_batched(rpcholqr_batch b, int32_t count, const double* const* A,
+rpcholqr_status rpcholqr_batch_factor(rpcholqr_batch b, int32_t count, const double* const* A,
                                         const int64_t* m, const int32_t* n, const int64_t* lda,
                                         const int32_t* s, const uint64_t* seed, double* const* Q,
                                         const int64_t* ldq, double* const* R, int32_t* info, void* stream) {

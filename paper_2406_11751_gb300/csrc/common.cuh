@@ -16,6 +16,20 @@ __host__ __device__ constexpr int pad16(int n) { return (n + kPad - 1) / kPad * 
 // Padded width of the n x n factors: a multiple of 16 up to 128 columns, of 64 above (64-column blocks).
 __host__ __device__ constexpr int pad_np(int n) { return n <= kMaxNP ? pad16(n) : (n + 63) / 64 * 64; }
 
+// ---- launch shape of the FP64 row passes (rowpass.cu) ----------------------------------------------
+// Warps per CTA: 8 when the 256-row panel fits shared memory (NP <= 64), else 4 (128-row panel).
+__host__ __device__ constexpr int rowpass_warps(int np) { return np <= 64 ? 8 : 4; }
+// Rows of one panel (32 per warp).
+__host__ __device__ constexpr int rowpass_rows(int np) { return 32 * rowpass_warps(np); }
+// The plain solve up to 48 columns runs two CTAs per SM (128 registers a thread, two panels fit the
+// shared memory): one CTA's panel load overlaps the other's FP64 work and each scheduler has four
+// warps' dependent chains to interleave.  The fused Gram keeps one CTA per SM: the caller sizes its
+// per-CTA partials for the grid it passes, which the launcher then uses unchanged.
+__host__ __device__ constexpr int rowpass_ctas_per_sm(int np, bool syrk) { return !syrk && np <= 48 ? 2 : 1; }
+static_assert(rowpass_ctas_per_sm(16, true) == 1 && rowpass_ctas_per_sm(64, true) == 1 &&
+                  rowpass_ctas_per_sm(128, true) == 1,
+              "the fused Gram pass writes one partial per CTA of the grid its caller passes");
+
 // ---- power-of-two bounds used by the split-precision products ------------------------------------
 // exp_bound(v): |v| < 2^e for a normal v (e = unbiased exponent + 1); kNoExp for 0 or subnormal.
 constexpr int kNoExp = INT_MIN / 2;

@@ -14,8 +14,9 @@
 // device address is fetched with cudaGetSymbolAddress once per device, on the first call made on
 // that device with it current; that first call should therefore happen before any stream
 // capture.  All calls share the array: two calls whose kernels overlap on the GPU race on it.
-// Nothing in it has to start at zero -- every call rewrites the fragment tables and every CTA
-// rewrites all Gram tiles the reduction reads.
+// The call runs on the current device; a stream that belongs to another device is refused
+// (RPCHOLQR_ERR_ARG).  Nothing in the array has to start at zero -- every call rewrites the
+// fragment tables and every CTA rewrites all Gram tiles the reduction reads.
 #include <mutex>
 
 #include "common.cuh"
@@ -38,6 +39,8 @@ constexpr size_t kPartDoubles = static_cast<size_t>(kNoAllocMaxCtas) * kNoAllocM
 // fragment table | diagonal blocks | per-CTA Gram partials (each slice 256-byte aligned)
 constexpr size_t kScratchDoubles = kFragDoubles + kDiagDoubles + kPartDoubles;
 static_assert(kFragDoubles % 32 == 0 && kDiagDoubles % 32 == 0, "slices must stay 256-byte aligned");
+static_assert(rowpass_ctas_per_sm(kNoAllocMaxN, true) == 1,
+              "the partial slice holds one Gram partial per CTA of the grid this file launches");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
@@ -76,6 +79,16 @@ extern "C" rpcholqr_status rpcholqr_precondition_gram_noalloc(const double* A, i
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
         return RPCHOLQR_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the scratch address above belongs to the current device: a stream of another device is refused
+    // (the default-stream handles always name the current device's default stream)
+    if (st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread) {
+        int stream_dev = -1;
+        if (cudaStreamGetDevice(st, &stream_dev) != cudaSuccess) {
+            cudaGetLastError();
+            return RPCHOLQR_ERR_ARG;
+        }
+        if (stream_dev != dev) return RPCHOLQR_ERR_ARG;
+    }
     if (cudaMemsetAsync(info, 0, sizeof(int32_t), st) != cudaSuccess ||
         cudaMemsetAsync(info + 1, 0xFF, sizeof(int32_t), st) != cudaSuccess)
         return RPCHOLQR_ERR_CUDA;
@@ -86,7 +99,9 @@ extern "C" rpcholqr_status rpcholqr_precondition_gram_noalloc(const double* A, i
     double* gpart = scratch + kFragDoubles + kDiagDoubles;
     launch_prep_tri(Rs, n, n, np, frag, diag, info, st);
     if (cudaGetLastError() != cudaSuccess) return RPCHOLQR_ERR_CUDA;
-    const int64_t panels = (m + 127) / 128;
+    // one CTA per panel of the fused pass (256 rows for n <= 64), at most one per SM; the fused pass
+    // launches exactly this grid (one CTA per SM, checked in common.cuh), one Gram partial per CTA
+    const int64_t panels = (m + rowpass_rows(np) - 1) / rowpass_rows(np);
     int grid = sms < kNoAllocMaxCtas ? sms : kNoAllocMaxCtas;
     if (panels < grid) grid = static_cast<int>(panels);
     if (launch_rowpass(true, np, A, lda, A1, ld1, m, n, frag, diag, gpart, info, grid, st) != cudaSuccess)

@@ -23,7 +23,8 @@
 // columns of the SM (k_ozaki_update: N = 32, two tiles in TMEM).  K is staged 32 at a time in shared
 // memory (core-matrix K-major layout, no swizzle), two stages in flight: while the tensor core works on
 // one stage the CTA slices the next.  One thread issues the 72 tcgen05.mma of a stage and commits them
-// to the stage's mbarrier.  Every mbarrier wait is bounded; on timeout the kernel records
+// to the stage's mbarrier.  Every mbarrier wait is bounded: the pipeline waits by the caller's spin limit
+// (a plan option), the final wait for the kernel's own MMAs by kSpinLimit; on timeout the kernel records
 // RPCHOLQR_ERR_TIMEOUT, waits (bounded) for its own MMAs, frees its tensor memory and returns.
 #include <climits>
 
@@ -94,29 +95,41 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
         smem_u32(bar)));
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t done = 0;
-    for (long it = 0; it < kSpinLimit && !done; ++it) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity));
+__device__ __forceinline__ uint32_t mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity));
+    return done;
+}
+// The outcome of a wait is made uniform over the lanes that take part in it: once any of them saw the
+// phase complete it stays complete (its next completion needs arrivals this warp has not made yet), so
+// the others poll again until they see it too (acquire for every lane).  A lane can therefore never
+// leave a wait that its warp-mates passed, whatever the poll limit.
+__device__ __forceinline__ bool mbar_uniform(uint64_t* bar, uint32_t parity, uint32_t done) {
+    if (__any_sync(__activemask(), done != 0)) {
+        for (long it = 0; it < kSpinLimit && !done; ++it) done = mbar_try(bar, parity);
     }
     return done != 0;
 }
-// mbar_wait that also gives up once *abort is set (by the other side of a warp-specialised pipeline).
-__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, const volatile int* abort) {
+// Polls the phase up to `limit` times (the plan's spin limit for pipeline waits; kSpinLimit for a
+// kernel's final wait for its own MMAs, which must complete before the tensor memory is released).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long limit = kSpinLimit) {
     uint32_t done = 0;
-    for (long it = 0; it < kSpinLimit && !done; ++it) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity));
-        if (!done && (it & 255) == 255 && *abort) return false;
+    for (long it = 0; it < limit && !done; ++it) done = mbar_try(bar, parity);
+    return mbar_uniform(bar, parity, done);
+}
+// mbar_wait that also gives up once *abort is set (by the other side of a warp-specialised pipeline).
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, const volatile int* abort,
+                                             long limit) {
+    uint32_t done = 0;
+    for (long it = 0; it < limit && !done; ++it) {
+        done = mbar_try(bar, parity);
+        if (!done && (it & 255) == 255 && *abort) break;
     }
-    return done != 0;
+    return mbar_uniform(bar, parity, done);
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
@@ -408,7 +421,7 @@ template <bool SUB, bool WIN>
 __global__ void __launch_bounds__(WIN ? kThreadsWin : kThreads, 1)
 k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int K,
              const uint8_t* __restrict__ yblocks, const int32_t* __restrict__ yexp, int N,
-             const double* B, int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info) {
+             const double* B, int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, long spin) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t mbar[2];
     __shared__ uint32_t tslot;
@@ -462,7 +475,7 @@ k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int
         const int E = row < m ? xexp[row] : kNoExp;
         // buffer s is free once the MMAs of stage g - 2 are done
         if (pending[s]) {
-            const bool ok = mbar_wait(&mbar[s], phase[s]);
+            const bool ok = mbar_wait(&mbar[s], phase[s], spin);
             if (__syncthreads_or(!ok)) { timed_out = true; break; }
             phase[s] ^= 1u;
             pending[s] = false;
@@ -493,7 +506,7 @@ k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int
         if (g > 0 && new_window) {
             const int sp = s ^ 1;
             if (pending[sp]) {
-                const bool ok = mbar_wait(&mbar[sp], phase[sp]);
+                const bool ok = mbar_wait(&mbar[sp], phase[sp], spin);
                 if (__syncthreads_or(!ok)) { timed_out = true; break; }
                 phase[sp] ^= 1u;
                 pending[sp] = false;
@@ -526,7 +539,7 @@ k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int
     if (!timed_out && nstages > 0) {
         for (int s = 0; s < 2 && !timed_out; ++s)
             if (pending[s]) {
-                const bool ok = mbar_wait(&mbar[s], phase[s]);
+                const bool ok = mbar_wait(&mbar[s], phase[s], spin);
                 if (__syncthreads_or(!ok)) { timed_out = true; break; }
                 phase[s] ^= 1u;
                 pending[s] = false;
@@ -632,7 +645,7 @@ template <bool WIN>
 __global__ void __launch_bounds__((WIN ? kThreadsWin : kThreads) + 32, 1)
 k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int K,
                 const uint8_t* __restrict__ yblocks, const int32_t* __restrict__ yexp, int N, double* C,
-                int64_t ldc, int64_t m, int32_t* info) {
+                int64_t ldc, int64_t m, int32_t* info, long spin) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t empty_bar[2], full_bar[2], done_bar;
     __shared__ uint32_t tslot;
@@ -678,7 +691,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
             uint32_t fphase[2] = {0u, 0u};
             for (int64_t g = 0; g < nstages; ++g) {
                 const int s = static_cast<int>(g & 1);
-                if (!mbar_wait_ab(&full_bar[s], fphase[s], &abort_s)) {
+                if (!mbar_wait_ab(&full_bar[s], fphase[s], &abort_s, spin)) {
                     abort_s = 1;
                     break;
                 }
@@ -727,7 +740,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
             const int E = row < m ? xexp[row] : kNoExp;
             // buffer s is free once the MMAs of stage g - 2 are done
             if (pending[s]) {
-                const bool ok = mbar_wait_ab(&empty_bar[s], phase[s], &abort_s);
+                const bool ok = mbar_wait_ab(&empty_bar[s], phase[s], &abort_s, spin);
                 if (prod_sync_or(!ok, NT)) { timed_out = true; break; }
                 phase[s] ^= 1u;
                 pending[s] = false;
@@ -770,7 +783,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
             if (g > 0 && (kw & 3) == 0) {
                 const int sp = s ^ 1;
                 if (pending[sp]) {
-                    const bool ok = mbar_wait_ab(&empty_bar[sp], phase[sp], &abort_s);
+                    const bool ok = mbar_wait_ab(&empty_bar[sp], phase[sp], &abort_s, spin);
                     if (prod_sync_or(!ok, NT)) { timed_out = true; break; }
                     phase[sp] ^= 1u;
                     pending[sp] = false;
@@ -802,7 +815,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
         if (!timed_out && nstages > 0) {
             for (int s = 0; s < 2 && !timed_out; ++s)
                 if (pending[s]) {
-                    const bool ok = mbar_wait_ab(&empty_bar[s], phase[s], &abort_s);
+                    const bool ok = mbar_wait_ab(&empty_bar[s], phase[s], &abort_s, spin);
                     if (prod_sync_or(!ok, NT)) { timed_out = true; break; }
                     phase[s] ^= 1u;
                     pending[s] = false;
@@ -873,7 +886,7 @@ __device__ __forceinline__ void issue_tile_n32(uint32_t tmem, uint32_t a_base, u
 __global__ void __launch_bounds__(kUpdThreads, 1)
 k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int K,
                const uint8_t* __restrict__ yblocks, const int32_t* __restrict__ yexp, int N, const double* B,
-               int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info) {
+               int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, long spin) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t stage_full[2], stage_empty[2], acc_full[2], acc_empty[2], done_bar;
     __shared__ uint32_t tslot;
@@ -929,7 +942,7 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
         for (int64_t t = 0; t < my_tiles; ++t) {
             const int s = static_cast<int>(t & 1);
             if (t >= 2) {
-                if (!mbar_wait_ab(&stage_empty[s], ph[s], &abort_s)) { abort_s = 1; break; }
+                if (!mbar_wait_ab(&stage_empty[s], ph[s], &abort_s, spin)) { abort_s = 1; break; }
                 ph[s] ^= 1u;
             }
             const int64_t row = (blockIdx.x + t * gridDim.x) * kTileM + lr;
@@ -967,7 +980,7 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
                     const int col = cbase + i;
                     bv[i] = (row < m && col < N) ? B[row * ldb + col] : 0.0;
                 }
-                if (!mbar_wait_ab(&acc_full[b], static_cast<uint32_t>((u >> 1) & 1), &abort_s)) {
+                if (!mbar_wait_ab(&acc_full[b], static_cast<uint32_t>((u >> 1) & 1), &abort_s, spin)) {
                     abort_s = 1;
                     break;
                 }
@@ -1007,13 +1020,13 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
             int64_t u = 0;
             for (int64_t t = 0; t < my_tiles; ++t) {
                 const int s = static_cast<int>(t & 1);
-                if (!mbar_wait_ab(&stage_full[s], phs[s], &abort_s)) { abort_s = 1; break; }
+                if (!mbar_wait_ab(&stage_full[s], phs[s], &abort_s, spin)) { abort_s = 1; break; }
                 phs[s] ^= 1u;
                 tc_after_sync();
                 bool ok = true;
                 for (int j = 0; j < nsub; ++j, ++u) {
                     const int b = static_cast<int>(u & 1);
-                    if (u >= 2 && !mbar_wait_ab(&acc_empty[b], static_cast<uint32_t>(((u >> 1) + 1) & 1), &abort_s)) {
+                    if (u >= 2 && !mbar_wait_ab(&acc_empty[b], static_cast<uint32_t>(((u >> 1) + 1) & 1), &abort_s, spin)) {
                         ok = false;
                         break;
                     }
@@ -1061,7 +1074,7 @@ constexpr int kGramNT = kThreads;
 __global__ void __launch_bounds__(kGramNT + 32, 1)
 k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np,
              const int32_t* __restrict__ colexp, int64_t rows_per, int ntiles, double* __restrict__ gpart,
-             int32_t* info) {
+             int32_t* info, long spin) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t empty_bar[2], full_bar[2], done_bar;
     __shared__ uint32_t tslot;
@@ -1106,7 +1119,7 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
             const uint32_t boff = b_inside ? static_cast<uint32_t>(((64 * Qb - 128 * P) / 8) * kSBO) : 0u;
             for (int64_t st = 0; st < nstages; ++st) {
                 const int s = static_cast<int>(st & 1);
-                if (!mbar_wait_ab(&full_bar[s], fphase[s], &abort_s)) {
+                if (!mbar_wait_ab(&full_bar[s], fphase[s], &abort_s, spin)) {
                     abort_s = 1;
                     break;
                 }
@@ -1163,7 +1176,7 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
         for (int64_t st = 0; st < nstages; ++st) {
             const int s = static_cast<int>(st & 1);
             if (pending[s]) {
-                const bool ok = mbar_wait_ab(&empty_bar[s], phase[s], &abort_s);
+                const bool ok = mbar_wait_ab(&empty_bar[s], phase[s], &abort_s, spin);
                 if (prod_sync_or(!ok, NT)) { timed_out = true; break; }
                 phase[s] ^= 1u;
                 pending[s] = false;
@@ -1197,7 +1210,7 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
             if (st > 0 && (st & 3) == 0) {
                 const int sp = s ^ 1;
                 if (pending[sp]) {
-                    const bool ok = mbar_wait_ab(&empty_bar[sp], phase[sp], &abort_s);
+                    const bool ok = mbar_wait_ab(&empty_bar[sp], phase[sp], &abort_s, spin);
                     if (prod_sync_or(!ok, NT)) { timed_out = true; break; }
                     phase[sp] ^= 1u;
                     pending[sp] = false;
@@ -1212,7 +1225,7 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
         if (!timed_out && nstages > 0) {
             for (int q = 0; q < 2 && !timed_out; ++q)
                 if (pending[q]) {
-                    const bool ok = mbar_wait_ab(&empty_bar[q], phase[q], &abort_s);
+                    const bool ok = mbar_wait_ab(&empty_bar[q], phase[q], &abort_s, spin);
                     if (prod_sync_or(!ok, NT)) { timed_out = true; break; }
                     phase[q] ^= 1u;
                     pending[q] = false;
@@ -1284,7 +1297,7 @@ void launch_ozaki_slice_cols(const double* Y, int64_t ldy, int K, int N, uint8_t
 cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int32_t* xexp, int K,
                               const uint8_t* yblocks, const int32_t* yexp, int N, const double* B,
                               int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, int grid,
-                              cudaStream_t st) {
+                              cudaStream_t st, long spin) {
     if (K > 32 * oz::kKW) return cudaErrorInvalidValue;   // int64 accumulators hold K <= 1024
     const bool win = K > 4 * oz::kKW;
     const int nt = win ? oz::kThreadsWin : oz::kThreads;
@@ -1293,7 +1306,7 @@ cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int3
         auto kern = win ? oz::k_ozaki_gemm_ws<true> : oz::k_ozaki_gemm_ws<false>;
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::kGemmSmem);
         if (err != cudaSuccess) return err;
-        kern<<<grid, nt + 32, oz::kGemmSmem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, C, ldc, m, info);
+        kern<<<grid, nt + 32, oz::kGemmSmem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, C, ldc, m, info, spin);
         return cudaGetLastError();
     }
     if (K <= oz::kKW && N <= oz::kUpdMaxN) {
@@ -1302,14 +1315,14 @@ cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int3
         err = cudaFuncSetAttribute(oz::k_ozaki_update, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::kUpdSmem);
         if (err != cudaSuccess) return err;
         oz::k_ozaki_update<<<g, oz::kUpdThreads, oz::kUpdSmem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb, C,
-                                                                    ldc, m, info);
+                                                                    ldc, m, info, spin);
         return cudaGetLastError();
     }
     const int smem = 2 * (oz::kAStage + oz::kBStage);
     auto kern = win ? oz::k_ozaki_gemm<true, true> : oz::k_ozaki_gemm<true, false>;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (err != cudaSuccess) return err;
-    kern<<<grid, nt, smem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb, C, ldc, m, info);
+    kern<<<grid, nt, smem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb, C, ldc, m, info, spin);
     return cudaGetLastError();
 }
 
@@ -1338,7 +1351,7 @@ void launch_fill_noexp(int32_t* p, int n, cudaStream_t st) {
 }
 
 cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
-                              int nranges, double* gpart, int32_t* info, cudaStream_t st) {
+                              int nranges, double* gpart, int32_t* info, cudaStream_t st, long spin) {
     const int smem = 2 * (oz::kAStage + oz::kBStage);
     cudaError_t err = cudaFuncSetAttribute(oz::k_ozaki_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (err != cudaSuccess) return err;
@@ -1346,7 +1359,7 @@ cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, in
     int64_t rows_per = (m + nranges - 1) / nranges;
     rows_per = (rows_per + oz::kKW - 1) / oz::kKW * oz::kKW;
     oz::k_ozaki_gram<<<nt * nranges, oz::kGramNT + 32, smem, st>>>(X, ldx, m, n, np, colexp, rows_per, nt, gpart,
-                                                               info);
+                                                               info, spin);
     return cudaGetLastError();
 }
 

@@ -4,7 +4,7 @@
 //   'recover'  R = R_1 R_s     -- product of upper-triangular factors, one CTA per row.
 #include <cfloat>
 
-#include "common.cuh"
+#include "smallfactor.cuh"
 
 namespace rpq {
 
@@ -22,189 +22,21 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;
 }
 
-// Householder QR of the sample on one thread-block cluster.  FP64 on GB300 retires one warp-wide
-// DFMA per 64 cycles per SM sub-partition, so a single CTA would run this O(s n^2) step at 1/152 of
-// the GPU; instead kClusterQr CTAs (one per SM) share the columns round-robin and advance one
-// column per hardware cluster barrier:
-//   every CTA: read column j (rows j..s-1), form the reflector (beta = -sign(alpha)||x||,
-//              v = x / (alpha - beta) with v_j = 1, tau = (beta - alpha) / beta; no reflection when
-//              nothing is below the diagonal) -- identical in every CTA;
-//   every CTA: apply it to its own columns k > j;
-//   cluster barrier (release/acquire orders the global-memory column updates).
-// The diagonal betas are kept in shared memory (column j is still being read by the other CTAs
-// while it is reflected) and CTA 0 assembles R_s at the end: each row negated where its diagonal is
-// negative, padded with the identity; a diagonal that is 0, subnormal or not finite sets
-// SINGULAR_SKETCH.  W: s x n column-major (ld lds), overwritten.
-constexpr int kClusterQr = 16;
-constexpr int kClusterQrThreads = 256;
-
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
-    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-__device__ __forceinline__ unsigned cluster_rank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ unsigned cluster_size() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_nctarank;\n" : "=r"(r));
-    return r;
-}
-
 __global__ void __launch_bounds__(kClusterQrThreads)
 k_hh_cluster(double* __restrict__ W, int64_t lds, int s, int n, int np, double* __restrict__ Rs,
              double* __restrict__ Rs_user, const int32_t* info_in, int32_t* info) {
     extern __shared__ double qsm[];
-    double* v = qsm;                 // s
-    double* betas = qsm + s;         // n
-    double* red = betas + n;         // 32 warp partials, then tau and 1 / (alpha - beta)
     // every CTA of the cluster sees the same status, so all take the same number of barriers
     if (load_status(info_in) != 0) return;
-    const unsigned rank = cluster_rank(), csize = cluster_size();
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
-
-    for (int j = 0; j < n; ++j) {
-        const double* colj = W + static_cast<int64_t>(j) * lds;
-        double part = 0.0;
-        for (int i = j + 1 + tid; i < s; i += blockDim.x) part += colj[i] * colj[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) red[warp] = part;
-        __syncthreads();
-        // the reflector's scalars in one thread (FP64 square root and divisions are long sequences on
-        // the FP64 units; formed once instead of by every thread), then shared
-        if (tid == 0) {
-            double sigma = 0.0;
-            for (int w = 0; w < nwarps; ++w) sigma += red[w];
-            const double alpha = colj[j];
-            double beta, tau, inv;
-            if (sigma == 0.0) {
-                beta = alpha; tau = 0.0; inv = 0.0;
-            } else {
-                const double nrm = sqrt(alpha * alpha + sigma);
-                beta = alpha >= 0.0 ? -nrm : nrm;
-                tau = (beta - alpha) / beta;
-                inv = 1.0 / (alpha - beta);
-            }
-            betas[j] = beta;
-            red[32] = tau;
-            red[33] = inv;
-        }
-        __syncthreads();
-        const double tau = red[32], inv = red[33];
-        for (int i = j + tid; i < s; i += blockDim.x) v[i] = (i == j) ? 1.0 : colj[i] * inv;
-        __syncthreads();
-        if (tau != 0.0) {
-            // this CTA's columns k > j: k = rank (mod csize); one warp per column
-            const int k0 = j + 1 + static_cast<int>((rank + csize - static_cast<unsigned>((j + 1) % csize)) % csize);
-            for (int k = k0 + warp * static_cast<int>(csize); k < n; k += nwarps * static_cast<int>(csize)) {
-                double* colk = W + static_cast<int64_t>(k) * lds;
-                // four independent partial sums keep four column loads in flight per lane
-                double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
-                int i = j + lane;
-                for (; i + 96 < s; i += 128) {
-                    w0 += v[i] * colk[i];
-                    w1 += v[i + 32] * colk[i + 32];
-                    w2 += v[i + 64] * colk[i + 64];
-                    w3 += v[i + 96] * colk[i + 96];
-                }
-                for (; i < s; i += 32) w0 += v[i] * colk[i];
-                double w = (w0 + w1) + (w2 + w3);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-                const double tw = tau * w;
-#pragma unroll 4
-                for (int i2 = j + lane; i2 < s; i2 += 32) colk[i2] -= v[i2] * tw;
-            }
-        }
-        __syncthreads();
-        cluster_sync_all();
-    }
-
-    if (rank != 0) return;
-    bool singular = false;
-    for (int e = tid; e < np * np; e += blockDim.x) {
-        const int r = e / np, c = e - r * np;
-        double val;
-        if (r < n && c < n) {
-            const double d = betas[r];
-            const double sg = d < 0.0 ? -1.0 : 1.0;
-            val = c > r ? sg * W[static_cast<int64_t>(c) * lds + r] : (c == r ? fabs(d) : 0.0);
-            if (c == r && (!isfinite(d) || fabs(d) < DBL_MIN)) singular = true;
-            if (Rs_user) Rs_user[r * n + c] = val;
-        } else {
-            val = (r == c) ? 1.0 : 0.0;
-        }
-        Rs[e] = val;
-    }
-    if (__syncthreads_or(singular) && tid == 0) set_status(info, RPCHOLQR_ERR_SINGULAR_SKETCH);
+    hh_factor<true>(W, lds, s, n, np, Rs, Rs_user, info, cluster_rank(), cluster_size(), qsm);
 }
 
-// Upper Cholesky G = R^T R, row by row:
-//   t_l = G[j][l] - sum_{k<j} R[k][j] R[k][l]  (l >= j),  R[j][j] = sqrt(t_j),  R[j][l] = t_l / R[j][j].
-// G: n x n (ld ldg), n <= 128.  R: np x np row-major (ld np), padded with the identity; R_user
-// (optional, n x n, ld n).  A pivot t_j that is not > 0 sets NOT_SPD with pivot j.
-// Thread (part, l) = (tid / 128, tid % 128): each dot product is split over kCholParts threads
-// (k = part, part + kCholParts, ...), so that all four schedulers' FP64 units work on it; the partial
-// sums are subtracted in part order.  The upper triangle of G is copied into the working matrix first,
-// so a step touches shared memory only; the square root is taken once per step.
-constexpr int kCholParts = 8;
-constexpr int kCholThreads = 128 * kCholParts;
 __global__ void __launch_bounds__(kCholThreads)
 k_cholesky(const double* __restrict__ G, int64_t ldg, int n, int np, double* __restrict__ R,
            double* __restrict__ R_user, int32_t* info) {
     extern __shared__ double csm[];  // np x np working copy of R (row-major), then kCholParts x np partials
-    double* psum = csm + np * np;
-    __shared__ double diag_s;
-    __shared__ int fail_s;
     if (load_status(info) != 0) return;
-    const int tid = threadIdx.x, part = tid >> 7, l = tid & 127;
-    for (int e = tid; e < np * np; e += blockDim.x) {
-        const int r = e / np, c = e - r * np;
-        csm[e] = (r <= c && c < n) ? G[static_cast<int64_t>(r) * ldg + c] : 0.0;
-    }
-    if (tid == 0) fail_s = -1;
-    __syncthreads();
-    for (int j = 0; j < n; ++j) {
-        if (l >= j && l < n) {
-            double acc = 0.0;
-            for (int k = part; k < j; k += kCholParts) acc += csm[k * np + j] * csm[k * np + l];
-            psum[part * np + l] = acc;
-        }
-        __syncthreads();
-        if (part == 0 && l > j && l < n) {
-            double tl = csm[j * np + l];
-#pragma unroll
-            for (int q = 0; q < kCholParts; ++q) tl -= psum[q * np + l];
-            csm[j * np + l] = tl;
-        } else if (tid == 0) {
-            double tj = csm[j * np + j];
-#pragma unroll
-            for (int q = 0; q < kCholParts; ++q) tj -= psum[q * np + j];
-            if (!(tj > 0.0)) {
-                fail_s = j;
-            } else {
-                diag_s = sqrt(tj);
-                csm[j * np + j] = diag_s;
-            }
-        }
-        __syncthreads();
-        if (fail_s >= 0) break;
-        if (part == 0 && l > j && l < n) csm[j * np + l] /= diag_s;
-        __syncthreads();
-    }
-    if (fail_s >= 0) {
-        if (tid == 0) set_status(info, RPCHOLQR_ERR_NOT_SPD, fail_s);
-        return;
-    }
-    for (int e = tid; e < np * np; e += blockDim.x) {
-        const int r = e / np, c = e - r * np;
-        double val = (r < n && c < n) ? csm[e] : (r == c ? 1.0 : 0.0);
-        R[e] = val;
-        if (R_user && r < n && c < n) R_user[r * n + c] = val;
-    }
+    cholesky_small<kCholThreads>(G, ldg, n, np, R, R_user, info, csm);
 }
 
 // The same factorisation for np > 128, working in global memory: R (np x np) is the work array, held
@@ -270,11 +102,8 @@ __global__ void k_triu_mul(const double* __restrict__ R1, int64_t ld1, const dou
                            const int32_t* info) {
     if (info && load_status(info) != 0) return;
     const int i = blockIdx.x;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        double acc = 0.0;
-        for (int k = i; k <= j; ++k) acc += R1[i * ld1 + k] * Rs[k * lds + j];
-        R[static_cast<int64_t>(i) * ldr + j] = acc;
-    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+        R[static_cast<int64_t>(i) * ldr + j] = triu_mul_entry(R1, ld1, Rs, lds, i, j);
 }
 
 // W = T^{-1} for upper-triangular T (n x n, ld ldt, n <= 512): back substitution, one warp per column.

@@ -2,7 +2,8 @@
 // Section 4: F_T a Walsh-Hadamard, cosine or Hartley transform, D a Rademacher diagonal).  F_T is
 // the orthogonal Walsh-Hadamard transform of order m' = 2^p >= m in natural order, acting on A padded
 // with zero rows; D_i = -1 when bit 63 of Philox word (i mod 4) of block i/4 under key (seed, 1) is
-// set; the c sampled rows are drawn from [0, m') and scaled by sqrt(m'/c).
+// set; the c sampled rows are drawn from [0, m') and scaled by sqrt(m'/c) (unless the plan turned the
+// sample scale off).
 //
 // The fast transform runs in two passes over HBM (its p butterfly stages split by row-index bits):
 //   k_wht_low          tiles of L = 2^l1 consecutive rows x 8 columns in shared memory: the signs
@@ -161,7 +162,7 @@ void launch_sample_indices(uint64_t seed, uint64_t stream_id, int64_t m, int32_t
 template <typename TA>
 static cudaError_t smoothed_sample_t(const TA* A, int64_t m, int n, int64_t lda, int s, uint64_t seed, double* T,
                                      int64_t* idx, double* As, int64_t lds, int np, int32_t* info,
-                                     cudaStream_t st) {
+                                     cudaStream_t st, bool scale_sample) {
     const int p = smooth_bits(m);
     if (p > kWhtMaxBits) return cudaErrorInvalidValue;
     const int64_t mp = int64_t{1} << p;
@@ -191,21 +192,22 @@ static cudaError_t smoothed_sample_t(const TA* A, int64_t m, int n, int64_t lda,
         if (err != cudaSuccess) return err;
     }
     const double inv_sqrt_mp = 1.0 / std::sqrt(static_cast<double>(mp));
-    const double scale = std::sqrt(static_cast<double>(mp) / static_cast<double>(s));
+    const double scale = scale_sample ? std::sqrt(static_cast<double>(mp) / static_cast<double>(s)) : 1.0;
     k_wht_high_sample<<<dim3(static_cast<unsigned>(L >> lg), cbs * (kWhtCols / csub)), 256, smem2, st>>>(
         T, mp, n, l1, l2, lg, csub, idx, s, inv_sqrt_mp, scale, As, lds, info);
     return cudaGetLastError();
 }
 
 cudaError_t launch_smoothed_sample(const double* A, int64_t m, int n, int64_t lda, int s, uint64_t seed, double* T,
-                                   int64_t* idx, double* As, int64_t lds, int np, int32_t* info, cudaStream_t st) {
-    return smoothed_sample_t<double>(A, m, n, lda, s, seed, T, idx, As, lds, np, info, st);
+                                   int64_t* idx, double* As, int64_t lds, int np, int32_t* info, cudaStream_t st,
+                                   bool scale_sample) {
+    return smoothed_sample_t<double>(A, m, n, lda, s, seed, T, idx, As, lds, np, info, st, scale_sample);
 }
 
 cudaError_t launch_smoothed_sample_f32(const float* A, int64_t m, int n, int64_t lda, int s, uint64_t seed,
                                        double* T, int64_t* idx, double* As, int64_t lds, int np, int32_t* info,
-                                       cudaStream_t st) {
-    return smoothed_sample_t<float>(A, m, n, lda, s, seed, T, idx, As, lds, np, info, st);
+                                       cudaStream_t st, bool scale_sample) {
+    return smoothed_sample_t<float>(A, m, n, lda, s, seed, T, idx, As, lds, np, info, st, scale_sample);
 }
 
 void launch_colmajor_to_rows(const double* src, int64_t lds, int s, int n, double* dst, int64_t ldd,
@@ -367,7 +369,7 @@ size_t smooth_dct_buffer_bytes(int64_t max_m, int max_n) {
 template <typename TA>
 static cudaError_t dct_sample_t(const TA* A, int64_t m, int n, int64_t lda, int s, uint64_t seed, void* Tbuf,
                                 int8_t* sgn, int64_t* idx, double* As, int64_t lds, int np, int32_t* info,
-                                cudaStream_t st) {
+                                cudaStream_t st, bool scale_sample) {
     const int p = smooth_bits(m);
     if (p > kWhtMaxBits) return cudaErrorInvalidValue;
     const int64_t N = int64_t{1} << p;
@@ -408,7 +410,7 @@ static cudaError_t dct_sample_t(const TA* A, int64_t m, int n, int64_t lda, int 
         if (err != cudaSuccess) return err;
     }
     const double w0 = std::sqrt(1.0 / static_cast<double>(N)), w1 = std::sqrt(2.0 / static_cast<double>(N));
-    const double scale = std::sqrt(static_cast<double>(N) / static_cast<double>(s));
+    const double scale = scale_sample ? std::sqrt(static_cast<double>(N) / static_cast<double>(s)) : 1.0;
     k_dct_pass_b<<<dim3(static_cast<unsigned>(H >> lgb), (n + csb - 1) / csb), 256, smem_b, st>>>(
         T, p, l1, n, lgb, csb, idx, s, w0, w1, scale, As, lds, info);
     return cudaGetLastError();
@@ -416,14 +418,14 @@ static cudaError_t dct_sample_t(const TA* A, int64_t m, int n, int64_t lda, int 
 
 cudaError_t launch_dct_sample(const double* A, int64_t m, int n, int64_t lda, int s, uint64_t seed, void* T,
                               int8_t* sgn, int64_t* idx, double* As, int64_t lds, int np, int32_t* info,
-                              cudaStream_t st) {
-    return dct_sample_t<double>(A, m, n, lda, s, seed, T, sgn, idx, As, lds, np, info, st);
+                              cudaStream_t st, bool scale_sample) {
+    return dct_sample_t<double>(A, m, n, lda, s, seed, T, sgn, idx, As, lds, np, info, st, scale_sample);
 }
 
 cudaError_t launch_dct_sample_f32(const float* A, int64_t m, int n, int64_t lda, int s, uint64_t seed, void* T,
                                   int8_t* sgn, int64_t* idx, double* As, int64_t lds, int np, int32_t* info,
-                                  cudaStream_t st) {
-    return dct_sample_t<float>(A, m, n, lda, s, seed, T, sgn, idx, As, lds, np, info, st);
+                                  cudaStream_t st, bool scale_sample) {
+    return dct_sample_t<float>(A, m, n, lda, s, seed, T, sgn, idx, As, lds, np, info, st, scale_sample);
 }
 
 }  // namespace rpq

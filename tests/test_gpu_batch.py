@@ -33,7 +33,7 @@ def test_batched_equals_single_calls(lib, mode_name):
     batch = lib.rpcholqr_batch_create(0, 1 << 17, 128, 384, slots=4, mode=mode)
     plan = lib.rpcholqr_plan_create(0, 1 << 17, 128, 384, mode=mode)
     try:
-        Qs, Rs, info = lib.rpcholqr_factor_batched(batch, As, ss, seeds)
+        Qs, Rs, info = lib.rpcholqr_batch_factor(batch, As, ss, seeds)
         torch.cuda.synchronize()
         st = info.cpu().view(-1, 2).tolist()
         assert all(x == [0, -1] for x in st), st
@@ -64,7 +64,7 @@ def test_batched_matches_oracle_and_autotune(lib, oracle_mod):
     try:
         slots, ms = lib.rpcholqr_batch_autotune(batch, As, ss, seeds, reps=1)
         assert slots in (1, 2, 4, 8) and ms > 0
-        Qs, Rs, info = lib.rpcholqr_factor_batched(batch, As, ss, seeds)
+        Qs, Rs, info = lib.rpcholqr_batch_factor(batch, As, ss, seeds)
         torch.cuda.synchronize()
         for A, s, seed, Q, R in list(zip(As, ss, seeds, Qs, Rs))[:6]:
             Ah = A.cpu().numpy()
@@ -84,7 +84,7 @@ def test_batched_reports_per_matrix_status(lib):
     As[3] = bad
     batch = lib.rpcholqr_batch_create(0, 1 << 17, 128, 384, slots=2)
     try:
-        _, _, info = lib.rpcholqr_factor_batched(batch, As, ss, seeds)
+        _, _, info = lib.rpcholqr_batch_factor(batch, As, ss, seeds)
         st = info.cpu().view(-1, 2)[:, 0].tolist()
         assert st[3] == lib.ERR_NONFINITE
         assert all(v == 0 for i, v in enumerate(st) if i != 3)
