@@ -85,6 +85,9 @@ def parse_args(argv=None):
                     help="do not also time the other mode (reported as 'other_mode')")
     ap.add_argument("--no-config2", action="store_true",
                     help="with --config 5: do not also time the 2^20 x 128 workload ('config2')")
+    ap.add_argument("--sharded", action="store_true",
+                    help="one m x n matrix split by rows over the N processes (row-sharded factorisation: "
+                         "FP64 steps, the sample and the Gram partials exchanged over NCCL; strong scaling)")
     ap.add_argument("--profile-window", action="store_true",
                     help="cudaProfilerStart/Stop around the timed steps of the main mode only")
     args = ap.parse_args(argv)
@@ -395,9 +398,104 @@ def timed_factor(rq, torch, local, dev, dist, m, n, s, mode, A, Q, R, info, stre
         if profile:
             torch.cuda.profiler.stop()
         barrier(dist)
+    kt = rq.rpcholqr_plan_collect_kernel_timing(plan)
     ph, calls, launches = rq.rpcholqr_plan_collect_timing(plan)
     rq.rpcholqr_plan_enable_timing(plan, 0)
+    ph["kernels"] = kt
     return max_over_ranks(e0.elapsed_time(e1), dist, dev), ph, calls, launches, plan, clk
+
+
+def phases_per_step(ph, calls):
+    return {k: v / max(calls, 1) for k, v in ph.items() if k != "kernels"}
+
+
+def kernels_per_step(ph, calls):
+    """{class: {ms, launches, fp64_gflop}} per step, for the classes that ran."""
+    c = max(calls, 1)
+    return {k: {"ms": ms / c, "launches": nl / c, "fp64_gflop": fl / c / 1e9}
+            for k, (ms, nl, fl) in ph.get("kernels", {}).items() if nl > 0}
+
+
+# Each FP64-accurate split product runs 36 BF16 slice products (eight 7-bit slices per operand, the pairs
+# with a + b <= 9); the tensor roofline of a split kernel counts those BF16 flops.
+SLICE_PRODUCTS = 36
+SPLIT_CLASSES = ("split_update", "split_gemm_sub", "split_gemm", "split_gram")
+KERNEL_NAMES = {
+    "rowpass": "k_rowpass (FP64 row solves: mma.sync m16n8k16 + DFMA)",
+    "split_update": "oz::k_ozaki_update (split C = B - X Y, K <= 32)",
+    "split_gemm_sub": "oz::k_ozaki_gemm_ws<.,SUB> (split C = B - X Y, wide pass-1 block updates)",
+    "split_gemm": "oz::k_ozaki_gemm_ws (split Q = A1 R1^-1)",
+    "split_gram": "oz::k_ozaki_gram (split G1 = A1^T A1)",
+    "fp64_gemm": "k_gemm_sub_fp64 (FP64 block updates)",
+    "fp64_syrk": "k_syrk_fp64 (FP64 Gram)",
+    "sketch_qr": "k_hh_cluster (Householder QR of the sample)",
+    "cholesky": "k_cholesky (G1 = R1^T R1)",
+}
+
+
+CLASS_SOURCE = {"rowpass": "rowpass.cuh", "split_update": "ozaki.cu", "split_gemm_sub": "ozaki.cu",
+                "split_gemm": "ozaki.cu", "split_gram": "ozaki.cu", "fp64_gemm": "blocked.cu",
+                "fp64_syrk": "blocked.cu", "sketch_qr": "smallfactor.cuh", "cholesky": "smallfactor.cuh"}
+
+
+def class_bytes(cls, mode, m, n):
+    """Algorithmic DRAM bytes per step of a kernel class: what its launches must read and write at least
+    (FP64 values, each once per launch that needs it)."""
+    nb = (n + 63) // 64
+    if cls == "rowpass":
+        if mode == "split":
+            return 16.0 * m * n                     # pass-1 diagonal blocks: each column read and written once
+        return 32.0 * m * n                         # pass 1 and pass 2, each column read and written once
+    if cls == "split_gemm":
+        return 16.0 * m * n                         # read A1, write Q
+    if cls == "split_gram":
+        return 8.0 * m * n                          # read A1
+    if cls in ("split_gemm_sub", "fp64_gemm"):     # left-looking 64-column blocks: read A1[:, <J], B, write C
+        return sum(8.0 * m * (64 * J + 2 * 64) for J in range(1, nb))
+    if cls == "split_update":
+        return 8.0 * m * 3 * n                      # X, B, C columns of the updates, about n each
+    if cls == "fp64_syrk":
+        return 8.0 * m * n
+    return 0.0
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return {}
+
+
+def kernel_rooflines(phases, calls, fp64_peak_tflops):
+    """Roofline entry per kernel class from the per-launch CUDA events of the timed steps: FP64 classes
+    against the FP64 pipe (in-run probe), split classes against the BF16 tensor pipe (sustained cuBLAS
+    figure of MEASURED_PEAKS.json: these kernels run inside a seconds-long step) counting the 36 slice
+    products of each FP64-accurate product."""
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+    out = {}
+    for k, v in kernels_per_step(phases, calls).items():
+        if v["ms"] <= 0:
+            continue
+        fp64_tf = v["fp64_gflop"] / v["ms"]          # GFLOP / ms = TFLOP/s
+        if k in SPLIT_CLASSES:
+            achieved = SLICE_PRODUCTS * fp64_tf
+            e = {"kernel": KERNEL_NAMES[k], "bound": "tensor", "achieved": achieved, "peak": bf16,
+                 "unit": "TFLOP/s", "frac": achieved / bf16 if bf16 else None, "fp64_equivalent_tflops": fp64_tf,
+                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured); achieved counts "
+                                "36 BF16 slice products per FP64 product"}
+        else:
+            e = {"kernel": KERNEL_NAMES[k], "bound": "alu", "achieved": fp64_tf, "peak": fp64_peak_tflops,
+                 "unit": "TFLOP/s", "frac": fp64_tf / fp64_peak_tflops,
+                 "peak_source": "FP64 pipe: in-run mma.sync m16n8k16 probe (MEASURED_PEAKS.json has no FP64 "
+                                "figure; unit count x clock: 152 SM x 4 x 32 lanes / 64 cycles x 2 flop x "
+                                "2.07 GHz = 1.26 TFLOP/s)"}
+        e.update({"ms_per_step": v["ms"], "launches_per_step": v["launches"],
+                  "ms_per_launch": v["ms"] / v["launches"], "algorithmic_fp64_flops_per_launch":
+                  v["fp64_gflop"] * 1e9 / v["launches"]})
+        out[k] = e
+    return out
 
 
 def cpu_baseline_entry(m, n, s, kappa, seed, rows):
@@ -429,7 +527,7 @@ def run_config2(args, rq, torch, local, dev, dist, stream, ws):
         out[mode] = {"value": ws * args.steps / (ms / 1e3), "unit": "matrices/s",
                      "ms_per_step": ms / args.steps, "status": st[0], "orth": orth, "residual": res,
                      "effective_tflops": alg_flops(m, n, s) * args.steps / (ms / 1e3) / 1e12,
-                     "phases_ms_per_step": {k: v / max(calls, 1) for k, v in ph.items()}}
+                     "phases_ms_per_step": phases_per_step(ph, calls)}
     out["split_over_fp64"] = out["split"]["value"] / out["fp64"]["value"]
     del A, Q
     torch.cuda.empty_cache()
@@ -478,7 +576,7 @@ def run_ours(args, ws, rank, local):
         o_ms, o_ph, o_calls, _, o_plan, _ = run(omode, ok, ow)
         o_plan.close()
         other = {"mode": omode, "value": ws * ok / (o_ms / 1e3), "ms_per_step": o_ms / ok, "steps": ok,
-                 "warmup": ow, "phases_ms_per_step": {k: v / max(o_calls, 1) for k, v in o_ph.items()}}
+                 "warmup": ow, "phases_ms_per_step": phases_per_step(o_ph, o_calls)}
     t_ms_max, phases, calls, launches, plan, clk = run(args.mode, K, W, clocks=True, profile=args.profile_window)
     st = info.cpu().tolist()
     if args.no_metrics:
@@ -556,40 +654,25 @@ def run_ours(args, ws, rank, local):
         k_flops = float(m) * n * n          # n^2/2 FMAs per row
         k_bytes = 8.0 * m * n               # read A, write A1 (float)
         traffic = None
-    elif n > 128:
-        # wide panels: pass 1 is a group of launches (64-column FP64 row passes + off-diagonal block
-        # updates: FP64 mma in fp64 mode, split tensor-core products in split mode); its phases are
-        # timed together, so the roofline is reported for the group against the FP64 pipe
-        nb = (n + 63) // 64
-        kname = ("pass-1 kernel group: %d x k_rowpass<64,false> + %d x %s" %
-                 (nb, nb - 1, "k_gemm_sub_fp64" if args.mode == "fp64" else "k_ozaki_gemm<SUB>"))
-        launches_per_call = 2 * nb - 1 if args.mode == "fp64" else 3 * nb - 2
-        k_ms = (phases["pass1"] + phases["pass1_update"] + phases["pass1_solve2"]) / c
-        # FP64 flops of the group: all of A R_s^-1 (fp64) or its diagonal blocks only (split)
-        k_flops = float(m) * n * n if args.mode == "fp64" else float(m) * n * 64
-        k_bytes = 16.0 * m * n + 8.0 * m * 64 * nb * (nb - 1)   # A in, A1 out, A1 re-read by the updates
-        traffic = None
-    elif args.mode == "fp64":
-        # dominant kernel: fused pass 1 (row solve by R_s + Gram partials), FP64 pipe
-        kname = "k_rowpass<%d,true> (FP64 pass 1: A1 = A Rs^-1 + Gram partials)" % np_
-        launches_per_call = 1
-        k_ms = phases["pass1"] / c
-        k_flops = 2.0 * m * n * n                       # m rows x (n^2 solve + n^2 Gram)
-        k_bytes = 16.0 * m * n                          # read A, write A1
-        traffic = traffic_from_profiles(f"k_rowpass<{np_},true>", src, m)
+    rooflines = None
+    if args.mode == "fp32":
+        achieved = k_flops / (k_ms / 1e3) / 1e12
+        peak = fp32_peak / 1e12
+        roofline = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": traffic, "algorithmic_flops": k_flops,
+                    "algorithmic_bytes": k_bytes, "ms_per_launch": k_ms, "launches_per_step": launches_per_call,
+                    "peak_source": "FP32 FMA pipe from unit counts and clock: 152 SM x 128 lanes x 2 flop x "
+                                   "2.07 GHz = 80.5 TFLOP/s (MEASURED_PEAKS.json has no FP32 figure)"}
     else:
-        # dominant kernel: the FP64 32-column diagonal-block row solves of pass 1 (one launch per block;
-        # the PASS1 phase is exactly the first block's launch, the other blocks do the same work)
-        b0 = min(n, 32)
-        nb0 = (b0 + 15) // 16 * 16
-        kname = "k_rowpass<%d,false> (SPLIT64 pass 1: FP64 32-column diagonal-block row solves by R_s)" % nb0
-        launches_per_call = (n + 31) // 32
-        k_ms = phases["pass1"] / c
-        k_flops = float(m) * b0 * b0
-        k_bytes = 16.0 * m * b0
-        traffic = traffic_from_profiles(f"k_rowpass<{nb0},false>", src, m)
-    achieved = k_flops / (k_ms / 1e3) / 1e12
-    peak = (fp32_peak if args.mode == "fp32" else fp64_peak) / 1e12
+        # every kernel class from its own per-launch CUDA events inside the timed steps; the dominant one
+        # (the most time per step) is the line's roofline
+        rooflines = kernel_rooflines(phases, calls, fp64_peak / 1e12)
+        dom = max(rooflines, key=lambda k: rooflines[k]["ms_per_step"])
+        roofline = dict(rooflines[dom])
+        roofline["class"] = dom
+        roofline["algorithmic_bytes_per_launch"] = class_bytes(dom, args.mode, m, n) / roofline["launches_per_step"]
+        roofline["traffic"] = traffic_from_profiles(f"{dom} n={n}", os.path.join(
+            ROOT, "paper_2406_11751_gb300", "csrc", CLASS_SOURCE[dom]), m)
 
     cpu = None
     if not args.no_cpu_baseline and N == 1:
@@ -607,19 +690,10 @@ def run_ours(args, ws, rank, local):
         "effective_tflops": flops * value / 1e12,
         "orth": orth, "residual": res, "gate_orth_le_1e-13": None if orth is None else bool(orth <= 1e-13),
         "gate_orth_le_1e-5": None if orth is None else bool(orth <= 1e-5), "status": st[0],
-        "phases_ms_per_step": {k: v / max(calls, 1) for k, v in phases.items()},
-        "roofline": {"kernel": kname, "bound": "alu",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": traffic, "algorithmic_flops": k_flops,
-                     "algorithmic_bytes": k_bytes, "ms_per_launch": k_ms,
-                     "launches_per_step": launches_per_call,
-                     "peak_source": ("FP32 FMA pipe from unit counts and clock: 152 SM x 128 lanes x 2 flop x "
-                                     "2.07 GHz = 80.5 TFLOP/s (MEASURED_PEAKS.json has no FP32 figure)"
-                                     if args.mode == "fp32" else
-                                     "FP64 pipe (DFMA and FP64 mma.sync share it): in-run mma.sync "
-                                     "m16n8k16 probe; MEASURED_PEAKS.json has no FP64 figure "
-                                     "(unit count x clock: 152 SM x 4 x 32 lanes / 64 cycles x 2 flop "
-                                     "x 2.07 GHz = 1.26 TFLOP/s)")},
+        "phases_ms_per_step": phases_per_step(phases, calls),
+        "kernels_per_step": kernels_per_step(phases, calls),
+        "roofline": roofline,
+        "rooflines": rooflines,
         "other_mode": other,
         "config2": config2,
         "cpu_baseline": cpu,
@@ -630,6 +704,67 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(out), flush=True)
     if plan is not None:
         plan.close()
+    return 0
+
+
+def run_sharded(args, ws, rank, local):
+    """One global m x n matrix per step, its rows split over the N processes (contiguous blocks): the
+    row-sharded factorisation of the library (local FP64 passes, the s x n sample and the n x n Gram
+    partials exchanged over NCCL).  value = matrices/s of the whole job; scaling strong."""
+    import torch
+
+    import inputs
+    import paper_2406_11751_gb300 as rq
+    from paper_2406_11751_gb300 import sharded as sh
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = init_dist(ws, "nccl")
+    rq.build()
+    preload_torch_linalg()
+    m, n = args.m, args.n
+    s = args.s or 3 * n
+    K, W = args.steps, args.warmup
+    off, ml = sh.split_rows(m, ws, rank)
+    A = inputs.usv_torch(m, n, args.kappa, args.seed, dev)    # the same global matrix on every process
+    A_local = A[off:off + ml].contiguous()
+    del A
+    torch.cuda.empty_cache()
+    plan = rq.rpcholqr_plan_create(local, max(ml, s), n, s)
+    steps = sh.CudaSteps(plan)
+    comm = sh.TorchDistComm() if ws > 1 else sh.SingleComm()
+    stream = torch.cuda.current_stream(dev)
+    for w in range(W):
+        _, _, st = sh.factor_row_sharded(steps, comm, A_local, off, m, s, 1 + w)
+        if st != 0:
+            raise RuntimeError(f"sharded warm-up status {rq.rpcholqr_status_string(st)}")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(dist)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for k in range(K):
+            Q_local, R, st = sh.factor_row_sharded(steps, comm, A_local, off, m, s, 1 + k)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+    t_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    plan.close()
+    if rank != 0:
+        return 0
+    value = K / (t_ms / 1e3)
+    out = {
+        "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (A = U diag(sigma) V^T, Haar U/V from torch, sigma log-spaced)",
+        "config": {"workload": f"rpCholesky-QR row-sharded FP64 m={m} n={n} s={s} kappa={args.kappa:g} "
+                               f"over {ws} process(es)", "m": m, "n": n, "s": s, "kappa": args.kappa,
+                   "parallelism": f"rows{ws}", "l2": f"inputs larger than L2 (A = {8 * m * n / 1e9:.2f} GB)"},
+        "effective_tflops": alg_flops(m, n, s) * value / 1e12, "status": st,
+        "clocks": clk.summary(), "gpu_launches": None, "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -750,6 +885,8 @@ def main():
         return run_reference(args, ws, rank)
     if args.workload == "batch":
         return run_batch(args, ws, rank, local)
+    if args.sharded:
+        return run_sharded(args, ws, rank, local)
     return run_ours(args, ws, rank, local)
 
 

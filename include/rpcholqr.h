@@ -79,16 +79,16 @@ typedef enum {
                             (||Q^T Q - I|| of order 1e-6 for well-sampled A up to kappa ~ 1e5). */
 } rpcholqr_mode;
 
-/* Largest n a plan accepts.  Up to 128 columns the row passes keep a whole row panel in shared
- * memory; above, both modes run left-looking blocked solves over 64-column blocks. */
-#define RPCHOLQR_MAX_N 512
+/* Largest n a plan accepts (FP32 plans: 512).  Up to 128 columns the row passes keep a whole row panel
+ * in shared memory; above, both modes run left-looking blocked solves over 64-column blocks. */
+#define RPCHOLQR_MAX_N 2048
 
 typedef struct rpcholqr_plan_s* rpcholqr_plan;
 
 /* Create a plan for matrices up to max_m x max_n sampled with up to max_s rows, on `device`.
  * The plan owns its device workspace (sample, R_s, fragment tables, per-CTA Gram partials),
  * allocated here with cudaMalloc; *plan receives the handle.
- * Requires 1 <= max_n <= RPCHOLQR_MAX_N, max_s >= max_n, max_m >= max_s.
+ * Requires 1 <= max_n <= RPCHOLQR_MAX_N (512 for RPCHOLQR_FP32), max_s >= max_n, max_m >= max_s.
  * Errors: RPCHOLQR_ERR_ARG, RPCHOLQR_ERR_UNSUPPORTED (mode), RPCHOLQR_ERR_NOMEM, RPCHOLQR_ERR_CUDA. */
 rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_mode mode,
                                      int64_t max_m, int32_t max_n, int32_t max_s);
@@ -121,8 +121,11 @@ rpcholqr_status rpcholqr_plan_get_option(rpcholqr_plan plan, int32_t option, int
 /* Free the plan and its workspace (synchronises the plan's device first).  NULL is accepted. */
 rpcholqr_status rpcholqr_plan_destroy(rpcholqr_plan plan);
 
-/* Bytes of device workspace a plan with these limits allocates (host-only query). */
-rpcholqr_status rpcholqr_workspace_size(int64_t max_m, int32_t max_n, int32_t max_s,
+/* Bytes of device workspace a plan with these limits allocates at creation (host-only query): a plan of
+ * `plan`'s mode on its device, or, with plan = NULL, an RPCHOLQR_FP64 plan on a 152-SM GPU.  Not
+ * counted: the staging of rpcholqr_factor_host, smoothing buffers and the batch workspace, which are
+ * allocated when first needed. */
+rpcholqr_status rpcholqr_workspace_size(rpcholqr_plan plan, int64_t max_m, int32_t max_n, int32_t max_s,
                                         size_t* bytes);
 
 /* rpCholesky-QR of A (Algorithm alg_2, Section 4).
@@ -393,9 +396,24 @@ enum {
     RPCHOLQR_NUM_PHASES
 };
 
-/* Enable (max_calls > 0) or disable (0) event timing of the next rpcholqr_factor calls on this
- * plan: events are recorded on the call's stream around every phase for up to max_calls calls
- * (later calls are not timed).  Creating the events happens here, not in rpcholqr_factor. */
+/* Kernel classes of rpcholqr_plan_collect_kernel_timing. */
+enum {
+    RPCHOLQR_KERNEL_ROWPASS = 0,     /* FP64 row passes: fused pass 1, pass 2, diagonal-block solves       */
+    RPCHOLQR_KERNEL_SPLIT_UPDATE,    /* split C = B - X Y with K <= 32 (k_ozaki_update)                    */
+    RPCHOLQR_KERNEL_SPLIT_GEMM_SUB,  /* split C = B - X Y, K > 32 (wide pass-1 block updates)              */
+    RPCHOLQR_KERNEL_SPLIT_GEMM,      /* split C = X Y (pass 2, Q = A1 R1^{-1})                              */
+    RPCHOLQR_KERNEL_SPLIT_GRAM,      /* split Gram matrix                                                   */
+    RPCHOLQR_KERNEL_FP64_GEMM,       /* FP64 block updates of the wide solves                               */
+    RPCHOLQR_KERNEL_FP64_SYRK,       /* FP64 Gram matrix of wide panels                                     */
+    RPCHOLQR_KERNEL_SKETCH_QR,       /* Householder QR of the sample                                        */
+    RPCHOLQR_KERNEL_CHOLESKY,        /* Cholesky factorisation of G1                                        */
+    RPCHOLQR_NUM_KERNEL_CLASSES
+};
+
+/* Enable (max_calls > 0, at most 4096) or disable (0) event timing of the next rpcholqr_factor calls
+ * on this plan: events are recorded on the call's stream around every phase, and around every launch
+ * of the kernel classes above, for up to max_calls calls (later calls are not timed).  Creating the
+ * events happens here, not in rpcholqr_factor. */
 rpcholqr_status rpcholqr_plan_enable_timing(rpcholqr_plan plan, int32_t max_calls);
 
 /* Wait for the recorded events and report, summed over the timed calls since the last collect:
@@ -403,6 +421,16 @@ rpcholqr_status rpcholqr_plan_enable_timing(rpcholqr_plan plan, int32_t max_call
  * (host) = kernels this plan launched since the last collect (timed or not).  Resets the counts. */
 rpcholqr_status rpcholqr_plan_collect_timing(rpcholqr_plan plan, float* ms_per_phase, int32_t* calls,
                                              int64_t* launches);
+
+/* Per kernel class, summed over the timed calls since the last rpcholqr_plan_collect_timing (call this
+ * one first: that call resets the count): ms_per_class[RPCHOLQR_NUM_KERNEL_CLASSES] (host) = the classes'
+ * launch durations (CUDA events around each launch, on the call's stream), launches_per_class (host)
+ * and flops_per_class (host) = the launches' algorithmic FP64 flops (row solve of b columns: m b^2,
+ * fused with the Gram: 2 m n^2; product: 2 m K N, with an upper-triangular right factor
+ * m sum_j 2 min(j + 1, K); Gram: m n^2; Householder: 2 s n^2 - 2 n^3 / 3; Cholesky: n^3 / 3).  Any
+ * pointer may be NULL.  Synchronises with the recorded events. */
+rpcholqr_status rpcholqr_plan_collect_kernel_timing(rpcholqr_plan plan, float* ms_per_class,
+                                                    int64_t* launches_per_class, double* flops_per_class);
 
 /* Human-readable name of a status code (static string). */
 const char* rpcholqr_status_string(int status);

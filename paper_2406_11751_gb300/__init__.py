@@ -37,7 +37,7 @@ FP32 = 2
 SMOOTH_NONE, SMOOTH_WHT, SMOOTH_DCT = 0, 1, 2
 OPT_SPIN_LIMIT, OPT_SCALE_SAMPLE, OPT_DETERMINISTIC, OPT_BATCH_CAPACITY = 0, 1, 2, 3
 ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM, ERR_UNSUPPORTED = 5, 6, 7, 8
-MAX_N = 512
+MAX_N = 2048
 
 EXPORTED_SYMBOLS = (
     "rpcholqr_plan_create", "rpcholqr_plan_destroy", "rpcholqr_workspace_size", "rpcholqr_factor",
@@ -51,9 +51,12 @@ EXPORTED_SYMBOLS = (
     "rpcholqr_gather_owned_rows", "rpcholqr_sketch_r_from_sample", "rpcholqr_sum_partials",
     "rpcholqr_plan_set_smoothing", "rpcholqr_smoothed_sample", "rpcholqr_plan_split_pass2_fp64",
     "rpcholqr_scholqr3", "rpcholqr_plan_set_option", "rpcholqr_plan_get_option",
+    "rpcholqr_factor_batched", "rpcholqr_batch_factor", "rpcholqr_plan_collect_kernel_timing",
 )
 PHASES = ("sample", "sketch_qr", "prep_rs", "pass1", "pass1_update", "pass1_solve2", "gram_reduce",
           "cholesky", "prep_r1", "pass2", "recover_r")
+KERNEL_CLASSES = ("rowpass", "split_update", "split_gemm_sub", "split_gemm", "split_gram", "fp64_gemm",
+                  "fp64_syrk", "sketch_qr", "cholesky")
 
 
 class RpcholqrError(RuntimeError):
@@ -84,7 +87,7 @@ def load_library():
         "rpcholqr_plan_destroy": [P],
         "rpcholqr_plan_set_option": [P, I32, I64],
         "rpcholqr_plan_get_option": [P, I32, ctypes.POINTER(I64)],
-        "rpcholqr_workspace_size": [I64, I32, I32, ctypes.POINTER(ctypes.c_size_t)],
+        "rpcholqr_workspace_size": [P, I64, I32, I32, ctypes.POINTER(ctypes.c_size_t)],
         "rpcholqr_factor": [P, P, I64, I32, I64, I32, U64, P, I64, P, P, P],
         "rpcholqr_factor_host": [P, P, I64, I32, I64, I32, U64, P, I64, P, P, P],
         "rpcholqr_factor_f32": [P, P, I64, I32, I64, I32, U64, P, I64, P, P, P],
@@ -103,6 +106,7 @@ def load_library():
         "rpcholqr_probe_fp64_mma": [ctypes.c_int, I32, ctypes.POINTER(D)],
         "rpcholqr_plan_enable_timing": [P, I32],
         "rpcholqr_plan_collect_timing": [P, P, ctypes.POINTER(I32), ctypes.POINTER(I64)],
+        "rpcholqr_plan_collect_kernel_timing": [P, P, P, P],
         "rpcholqr_ozaki_gemm": [P, P, I64, I32, I64, P, I32, I64, P, I64, P, P],
         "rpcholqr_ozaki_gram": [P, P, I64, I32, I64, P, P, P],
         "rpcholqr_cholqr": [P, P, I64, I32, I64, P, I64, P, P, P],
@@ -206,10 +210,12 @@ def rpcholqr_plan_get_option(plan: Plan, option: int) -> int:
     return int(v.value)
 
 
-def rpcholqr_workspace_size(max_m: int, max_n: int, max_s: int) -> int:
+def rpcholqr_workspace_size(max_m: int, max_n: int, max_s: int, plan: Plan = None) -> int:
+    """Bytes of device workspace a plan with these limits allocates (plan: its mode and device; None: an
+    FP64 plan on a 152-SM GPU)."""
     b = ctypes.c_size_t()
-    _check("rpcholqr_workspace_size",
-           load_library().rpcholqr_workspace_size(max_m, max_n, max_s, ctypes.byref(b)))
+    _check("rpcholqr_workspace_size", load_library().rpcholqr_workspace_size(
+        plan.handle if plan is not None else None, max_m, max_n, max_s, ctypes.byref(b)))
     return int(b.value)
 
 
@@ -508,6 +514,18 @@ def rpcholqr_plan_collect_timing(plan: Plan):
     _check("rpcholqr_plan_collect_timing", load_library().rpcholqr_plan_collect_timing(
         plan.handle, ctypes.cast(ms, ctypes.c_void_p), ctypes.byref(calls), ctypes.byref(launches)))
     return dict(zip(PHASES, [float(x) for x in ms])), int(calls.value), int(launches.value)
+
+
+def rpcholqr_plan_collect_kernel_timing(plan: Plan):
+    """{class: (summed ms, launches, algorithmic FP64 flops)} over the timed calls (call before
+    rpcholqr_plan_collect_timing, which resets the timed calls)."""
+    k = len(KERNEL_CLASSES)
+    ms = (ctypes.c_float * k)()
+    nl = (ctypes.c_int64 * k)()
+    fl = (ctypes.c_double * k)()
+    _check("rpcholqr_plan_collect_kernel_timing", load_library().rpcholqr_plan_collect_kernel_timing(
+        plan.handle, ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(nl, ctypes.c_void_p), ctypes.cast(fl, ctypes.c_void_p)))
+    return {name: (float(ms[i]), int(nl[i]), float(fl[i])) for i, name in enumerate(KERNEL_CLASSES)}
 
 
 def rpcholqr_precondition_gram_noalloc(A, Rs, A1, G, info=None, stream=None):

@@ -40,6 +40,7 @@ void launch_fill_noexp(int32_t* p, int n, cudaStream_t st);
 // probe.cu
 cudaError_t run_fp64_mma_probe(int iters, double* flops_per_s);
 // smallfactor.cu
+void launch_fill_identity(double* W, int np, const int32_t* info, cudaStream_t st);
 void launch_triu_inv(const double* T, int64_t ldt, int n, int np, double* W, const int32_t* info,
                      cudaStream_t st);
 // ozaki.cu
@@ -50,7 +51,7 @@ void launch_ozaki_slice_cols(const double* Y, int64_t ldy, int K, int N, uint8_t
 cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int32_t* xexp, int K,
                               const uint8_t* yblocks, const int32_t* yexp, int N, const double* B,
                               int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, int grid,
-                              cudaStream_t st, long spin);
+                              cudaStream_t st, long spin, bool y_upper);
 int ozaki_gram_halves(int np);
 cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
                               int nranges, double* gpart, int32_t* info, cudaStream_t st, long spin);
@@ -120,6 +121,8 @@ using namespace rpq;
 
 constexpr int64_t kDefaultSpinLimit = int64_t{1} << 24;
 constexpr int64_t kMaxBatchCount = 1 << 16;   // matrices one rpcholqr_factor_batched call may take
+constexpr int32_t kMaxNF32 = 512;              // widest FP32 plan (the FP32 row solve stages T in shared memory)
+constexpr int kTriuInvMaxN = 512;              // widest R1^{-1} of the warp-per-column kernel
 
 struct rpcholqr_plan_s {
     int device = 0;
@@ -127,6 +130,7 @@ struct rpcholqr_plan_s {
     int64_t max_m = 0;
     int32_t max_n = 0, max_s = 0, np = 0;
     int grid = 0;  // CTAs of the row passes (one per SM)
+    int nparts = 0;  // Gram partials in gpart (gram_parts)
     void* ws = nullptr;
     size_t ws_bytes = 0;
     double* As = nullptr;       // max_s x np, column-major
@@ -157,6 +161,13 @@ struct rpcholqr_plan_s {
     int32_t timing_slots = 0;
     int32_t timed_calls = 0;
     cudaEvent_t* events = nullptr;  // timing_slots x (RPCHOLQR_NUM_PHASES + 1)
+    // per-launch timing of the timed calls: timing_slots x kMaxTimedLaunches event pairs, the class
+    // and algorithmic FP64 flops of each launch, and the launches recorded per slot
+    cudaEvent_t* kevents = nullptr;
+    int8_t* kclass = nullptr;
+    double* kflops = nullptr;
+    int32_t* klaunches = nullptr;
+    int32_t cur_slot = -1;          // the slot of the call being issued (-1: not timed)
     int64_t launches = 0;
     // options (rpcholqr_plan_set_option)
     int64_t spin_limit = kDefaultSpinLimit;   // polls of a pipeline wait before TIMEOUT
@@ -193,6 +204,19 @@ struct WsLayout {
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Per-CTA (or per-row-range) Gram partials a plan holds: one per SM for panels up to 128 columns (the
+// fused pass writes one per CTA) and in the FP32 mode; for wide panels (np x np doubles each) at most one
+// per 1024 rows of max_m and at most 1 GiB of them.
+int gram_parts(rpcholqr_mode mode, int64_t max_m, int32_t max_n, int grid) {
+    const int64_t np = pad_np(max_n);
+    if (np <= kMaxNP || mode == RPCHOLQR_FP32) return grid;
+    int64_t parts = (max_m + 1023) / 1024;
+    const int64_t cap = (int64_t{1} << 30) / (np * np * static_cast<int64_t>(sizeof(double)));
+    if (parts > cap) parts = cap;
+    if (parts > grid) parts = grid;
+    return parts < 1 ? 1 : static_cast<int>(parts);
+}
 
 WsLayout ws_layout(int32_t max_n, int32_t max_s, int grid) {
     const size_t np = static_cast<size_t>(pad_np(max_n));
@@ -255,17 +279,55 @@ bool shape_ok(const rpcholqr_plan_s* p, int64_t m, int32_t n, int32_t s) {
 
 // Records the start of `phase` (or the end of the call for phase == RPCHOLQR_NUM_PHASES) when
 // the plan times this call.
+constexpr int kMaxTimedLaunches = 256;   // per timed call
+
 struct PhaseMarks {
     rpcholqr_plan_s* p;
     cudaStream_t st;
     int slot;
     PhaseMarks(rpcholqr_plan_s* plan, cudaStream_t stream) : p(plan), st(stream), slot(-1) {
         if (p->events && p->timed_calls < p->timing_slots) slot = p->timed_calls++;
+        p->cur_slot = slot;
+        if (slot >= 0) p->klaunches[slot] = 0;
     }
+    ~PhaseMarks() { p->cur_slot = -1; }
     void mark(int phase) const {
         if (slot >= 0) cudaEventRecord(p->events[slot * (RPCHOLQR_NUM_PHASES + 1) + phase], st);
     }
 };
+
+// Events around one launch of kernel class `cls` (rpcholqr_plan_collect_kernel_timing) when the current
+// call is timed; `flops` = the launch's algorithmic FP64 flops.
+struct KTimer {
+    rpcholqr_plan_s* p;
+    cudaStream_t st;
+    int k = -1;
+    KTimer(rpcholqr_plan_s* plan, cudaStream_t stream, int cls, double flops) : p(plan), st(stream) {
+        const int slot = p->cur_slot;
+        if (slot < 0 || !p->kevents || p->klaunches[slot] >= kMaxTimedLaunches) return;
+        k = slot * kMaxTimedLaunches + p->klaunches[slot]++;
+        p->kclass[k] = static_cast<int8_t>(cls);
+        p->kflops[k] = flops;
+        cudaEventRecord(p->kevents[2 * k], st);
+    }
+    ~KTimer() {
+        if (k >= 0) cudaEventRecord(p->kevents[2 * k + 1], st);
+    }
+};
+
+// The kernel class and algorithmic FP64 flops of a split product (launch_ozaki_gemm picks the kernel the
+// same way): C = B - X Y with K <= 32 and N <= 128 runs k_ozaki_update, the other subtract forms and
+// C = X Y k_ozaki_gemm_ws; an upper-triangular Y needs sum_j 2 min(j + 1, K) flops per row.
+int ozaki_class(bool sub, int K, int N) {
+    if (sub) return K <= 32 && N <= 128 ? RPCHOLQR_KERNEL_SPLIT_UPDATE : RPCHOLQR_KERNEL_SPLIT_GEMM_SUB;
+    return RPCHOLQR_KERNEL_SPLIT_GEMM;
+}
+double ozaki_flops(bool sub, bool y_upper, int64_t m, int K, int N) {
+    if (sub || !y_upper) return 2.0 * m * K * N;
+    double per_row = 0.0;
+    for (int j = 0; j < N; ++j) per_row += 2.0 * (j + 1 < K ? j + 1 : K);
+    return per_row * m;
+}
 
 constexpr int kBlk = 64;   // column block of the FP64 blocked solves (n > 128)
 // Blocks of the split mode's first pass (n <= 128): the FP64 row passes solve kSplitSub-column diagonal
@@ -312,12 +374,23 @@ cudaError_t plan_smoothed_sample<float>(rpcholqr_plan_s* p, const float* A, int6
 }
 
 void free_events(rpcholqr_plan_s* p) {
-    if (!p->events) return;
-    for (int i = 0; i < p->timing_slots * (RPCHOLQR_NUM_PHASES + 1); ++i) cudaEventDestroy(p->events[i]);
+    if (p->events)
+        for (int i = 0; i < p->timing_slots * (RPCHOLQR_NUM_PHASES + 1); ++i) cudaEventDestroy(p->events[i]);
+    if (p->kevents)
+        for (int i = 0; i < 2 * p->timing_slots * kMaxTimedLaunches; ++i) cudaEventDestroy(p->kevents[i]);
     delete[] p->events;
+    delete[] p->kevents;
+    delete[] p->kclass;
+    delete[] p->kflops;
+    delete[] p->klaunches;
     p->events = nullptr;
+    p->kevents = nullptr;
+    p->kclass = nullptr;
+    p->kflops = nullptr;
+    p->klaunches = nullptr;
     p->timing_slots = 0;
     p->timed_calls = 0;
+    p->cur_slot = -1;
 }
 
 }  // namespace
@@ -339,10 +412,25 @@ const char* rpcholqr_status_string(int status) {
     }
 }
 
-rpcholqr_status rpcholqr_workspace_size(int64_t max_m, int32_t max_n, int32_t max_s, size_t* bytes) {
+rpcholqr_status rpcholqr_workspace_size(rpcholqr_plan p, int64_t max_m, int32_t max_n, int32_t max_s,
+                                        size_t* bytes) {
     if (!bytes || max_n < 1 || max_n > RPCHOLQR_MAX_N || max_s < max_n || max_m < max_s)
         return RPCHOLQR_ERR_ARG;
-    *bytes = ws_layout(max_n, max_s, 152).total;
+    const rpcholqr_mode mode = p ? p->mode : RPCHOLQR_FP64;
+    const int grid = p ? p->grid : 152;
+    const int32_t ws_n = mode == RPCHOLQR_FP32 ? (max_n + 63) / 64 * 64 : max_n;
+    size_t total = ws_layout(ws_n, max_s, gram_parts(mode, max_m, max_n, grid)).total;
+    const size_t np = static_cast<size_t>(pad_np(max_n));
+    if (mode == RPCHOLQR_SPLIT64)   // A1, row/column bounds, column slices, R1^{-1}, gate words
+        total += align256(sizeof(double) * static_cast<size_t>(max_m) * np) +
+                 align256(sizeof(int32_t) * static_cast<size_t>(max_m)) + 2 * align256(sizeof(int32_t) * np) +
+                 align256(ozaki_yblocks_bytes(static_cast<int>(np), static_cast<int>(np))) +
+                 align256(sizeof(double) * np * np) + align256(sizeof(int32_t) * 8);
+    if (mode == RPCHOLQR_FP32) {
+        const size_t n32 = static_cast<size_t>(f32_pad(max_n));
+        total += align256(sizeof(float) * n32 * n32) + sizeof(float) * n32;
+    }
+    *bytes = total;
     return RPCHOLQR_OK;
 }
 
@@ -352,6 +440,7 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
     *plan = nullptr;
     if (max_n < 1 || max_n > RPCHOLQR_MAX_N || max_s < max_n || max_m < max_s) return RPCHOLQR_ERR_ARG;
     if (mode != RPCHOLQR_FP64 && mode != RPCHOLQR_SPLIT64 && mode != RPCHOLQR_FP32) return RPCHOLQR_ERR_UNSUPPORTED;
+    if (mode == RPCHOLQR_FP32 && max_n > kMaxNF32) return RPCHOLQR_ERR_UNSUPPORTED;
     if (householder_smem_bytes(max_s, max_n) > 200 * 1024) return RPCHOLQR_ERR_UNSUPPORTED;
     DeviceGuard guard(device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
@@ -366,7 +455,8 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
     p->grid = default_grid(device);
     // the FP32 Gram works on 64 x 64 tiles: size the shared FP64 buffers for max_n rounded up to 64
     const int32_t ws_n = mode == RPCHOLQR_FP32 ? (max_n + 63) / 64 * 64 : max_n;
-    const WsLayout L = ws_layout(ws_n, max_s, p->grid);
+    p->nparts = gram_parts(mode, max_m, max_n, p->grid);
+    const WsLayout L = ws_layout(ws_n, max_s, p->nparts);
     if (cudaMalloc(&p->ws, L.total) != cudaSuccess) {
         cudaGetLastError();
         delete p;
@@ -538,8 +628,11 @@ static rpcholqr_status sketch_internal(rpcholqr_plan p, const double* A, int64_t
     }
     if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
     if (pm) pm->mark(RPCHOLQR_PHASE_SKETCH_QR);
-    if (launch_householder(p->As, lds, s, n, np, p->Rs, Rs_user, info, st) != cudaSuccess)
-        return RPCHOLQR_ERR_CUDA;
+    {
+        KTimer kt(p, st, RPCHOLQR_KERNEL_SKETCH_QR, 2.0 * s * n * n - 2.0 * n * n * n / 3.0);
+        if (launch_householder(p->As, lds, s, n, np, p->Rs, Rs_user, info, st) != cudaSuccess)
+            return RPCHOLQR_ERR_CUDA;
+    }
     ++p->launches;
     return RPCHOLQR_OK;
 }
@@ -547,7 +640,8 @@ static rpcholqr_status sketch_internal(rpcholqr_plan p, const double* A, int64_t
 static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const double* X, int64_t m, int K,
                                            int64_t ldx, const double* Y, int N, int64_t ldy, const double* B,
                                            int64_t ldb, double* C, int64_t ldc, int32_t* info, cudaStream_t st,
-                                           bool xexp_ready = false, int64_t row0 = 0, bool y_ready = false);
+                                           bool xexp_ready = false, int64_t row0 = 0, bool y_ready = false,
+                                           bool y_upper = false);
 
 // Diagonal-block setups for the blocked solve with T (n x n, ld ldt): block J (64 columns, the last
 // one ragged) gets frag + 4096 J and diag + 512 J.
@@ -597,10 +691,13 @@ static rpcholqr_status solve_split_right(rpcholqr_plan_s* p, const double* X, in
             const double* src = c1 == 0 ? X : Y;
             const int64_t lsrc = c1 == 0 ? ldx : ldy;
             const int js = c1 / sub;
-            if (launch_rowpass_ex(false, pad16(nh), src + c1, lsrc, Y + c1, ldy, m, nh, frag + js * sub * sub,
-                                  diag + js * (sub / 8) * 64, nullptr, info, grid, st, true, p->xexp + row0,
-                                  c1 == 0 ? 1 : 2, p->colexp + c1) != cudaSuccess)
-                return RPCHOLQR_ERR_CUDA;
+            {
+                KTimer kt(p, st, RPCHOLQR_KERNEL_ROWPASS, static_cast<double>(m) * nh * nh);
+                if (launch_rowpass_ex(false, pad16(nh), src + c1, lsrc, Y + c1, ldy, m, nh, frag + js * sub * sub,
+                                      diag + js * (sub / 8) * 64, nullptr, info, grid, st, true, p->xexp + row0,
+                                      c1 == 0 ? 1 : 2, p->colexp + c1) != cudaSuccess)
+                    return RPCHOLQR_ERR_CUDA;
+            }
             ++p->launches;
             if (h == 0 && nj > nh) {
                 const rpcholqr_status rc = update(c1, nh, c1 + nh, nj - nh, (J == 0 ? X : Y) + c1 + nh,
@@ -623,8 +720,10 @@ static rpcholqr_status solve_split_right(rpcholqr_plan_s* p, const double* X, in
 
 // Left-looking blocked row solve Y = X T^{-1} (T upper triangular, n x n, ld ldt) over 64-column
 // blocks J:  Y[:, J] = X[:, J] - Y[:, <J] T[<J, J]  (FP64 mma, or the split tensor-core product when
-// split), then Y[:, J] <- Y[:, J] T[J, J]^{-1} by the row pass (NP = 64).  Y may equal X (ldy == ldx).
-// The diagonal blocks must have been set up by prep_blocks.  split: the row passes store (block 0) and
+// split), then Y[:, J] <- Y[:, J] T[J, J]^{-1} by the row pass (NP = 64; split: two 32-column row
+// passes and a K = 32 split update between them, so the FP64 work per row is n * 32).  Y may equal X
+// (ldy == ldx).  The diagonal blocks must have been set up by prep_blocks (split: with blk =
+// kSplitSub).  split: the row passes store (block 0) and
 // max-merge (later blocks) the row bounds of Y into p->xexp and max-merge its column bounds into
 // p->colexp, both needed by the split products; marks PASS1 / PASS1_UPDATE / PASS1_SOLVE2 when
 // pass1_marks (blocks 2.. fall in PASS1_SOLVE2).
@@ -645,20 +744,53 @@ static rpcholqr_status solve_blocked(rpcholqr_plan_s* p, const double* X, int64_
                                                          Y + c0, ldy, info, st, true);
                 if (rc != RPCHOLQR_OK) return rc;
             } else {
-                if (launch_gemm_sub_fp64(Y, ldy, T + c0, ldt, X + c0, ldx, Y + c0, ldy, m, c0, nj, info,
-                                         2 * p->grid, st) != cudaSuccess)
-                    return RPCHOLQR_ERR_CUDA;
+                {
+                    KTimer kt(p, st, RPCHOLQR_KERNEL_FP64_GEMM, 2.0 * m * c0 * nj);
+                    if (launch_gemm_sub_fp64(Y, ldy, T + c0, ldt, X + c0, ldx, Y + c0, ldy, m, c0, nj, info,
+                                             2 * p->grid, st) != cudaSuccess)
+                        return RPCHOLQR_ERR_CUDA;
+                }
                 ++p->launches;
             }
             src = Y + c0;
             lsrc = ldy;
             if (pm && pass1_marks && J == 1) pm->mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
         }
-        if (launch_rowpass_ex(false, pad16(nj), src, lsrc, Y + c0, ldy, m, nj, frag + J * kBlk * kBlk,
-                              diag + J * (kBlk / 8) * 64, nullptr, info, grid, st, check_finite,
-                              split ? p->xexp : nullptr, J == 0 ? 1 : 2, split ? p->colexp + c0 : nullptr) !=
-            cudaSuccess)
-            return RPCHOLQR_ERR_CUDA;
+        if (split) {
+            // two 32-column FP64 solves joined by one K = 32 split update of the block's second half
+            // (diagonal tables from prep_blocks with blk = kSplitSub)
+            for (int h = 0; h * kSplitSub < nj; ++h) {
+                const int c1 = c0 + h * kSplitSub;
+                const int nh = nj - h * kSplitSub < kSplitSub ? nj - h * kSplitSub : kSplitSub;
+                const double* hsrc = h == 0 ? src : Y + c1;
+                const int64_t lh = h == 0 ? lsrc : ldy;
+                const int js = c1 / kSplitSub;
+                {
+                    KTimer kt(p, st, RPCHOLQR_KERNEL_ROWPASS, static_cast<double>(m) * nh * nh);
+                    if (launch_rowpass_ex(false, pad16(nh), hsrc, lh, Y + c1, ldy, m, nh, frag + js * kSplitSub * kSplitSub,
+                                          diag + js * (kSplitSub / 8) * 64, nullptr, info, grid, st, check_finite, p->xexp,
+                                          c1 == 0 ? 1 : 2, p->colexp + c1) != cudaSuccess)
+                        return RPCHOLQR_ERR_CUDA;
+                }
+                ++p->launches;
+                if (h == 0 && nj > nh) {
+                    const double* B = (J == 0 ? X : Y) + c1 + nh;
+                    const int64_t ldb = J == 0 ? ldx : ldy;
+                    rpcholqr_status rc = ozaki_gemm_internal(p, true, Y + c1, m, nh, ldy,
+                                                             T + static_cast<int64_t>(c1) * ldt + c1 + nh, nj - nh, ldt,
+                                                             B, ldb, Y + c1 + nh, ldy, info, st, true);
+                    if (rc != RPCHOLQR_OK) return rc;
+                }
+            }
+            continue;
+        }
+        {
+            KTimer kt(p, st, RPCHOLQR_KERNEL_ROWPASS, static_cast<double>(m) * nj * nj);
+            if (launch_rowpass_ex(false, pad16(nj), src, lsrc, Y + c0, ldy, m, nj, frag + J * kBlk * kBlk,
+                                  diag + J * (kBlk / 8) * 64, nullptr, info, grid, st, check_finite,
+                                  nullptr, 0, nullptr) != cudaSuccess)
+                return RPCHOLQR_ERR_CUDA;
+        }
         ++p->launches;
     }
     if (pm && pass1_marks && n <= kBlk) {
@@ -666,6 +798,22 @@ static rpcholqr_status solve_blocked(rpcholqr_plan_s* p, const double* X, int64_
         pm->mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
     }
     return check_launch();
+}
+
+// W = R1^{-1} (np x np, identity-padded) for the split second pass: the warp-per-column back
+// substitution up to kTriuInvMaxN columns; wider, the FP64 blocked row solve of the identity's first n
+// rows by R1 (row i of W solves w_i^T R1 = e_i^T), with R1's diagonal-block tables in frag_1 / diag_1.
+static rpcholqr_status inverse_r1(rpcholqr_plan_s* p, int n, int np, int32_t* info, cudaStream_t st) {
+    if (n <= kTriuInvMaxN) {
+        launch_triu_inv(p->R1, np, n, np, p->W, info, st);
+        ++p->launches;
+        return check_launch();
+    }
+    launch_fill_identity(p->W, np, info, st);
+    ++p->launches;
+    prep_blocks(p, p->R1, np, n, p->frag_1, p->diag_1, info, st);
+    return solve_blocked(p, p->W, np, p->R1, np, n, n, p->W, np, p->frag_1, p->diag_1, false, false, info, st,
+                         nullptr, false);
 }
 
 // Row-range partials of G = X^T X in FP64 (n > 128) and their fixed-order sum into G (ld ldg).
@@ -676,10 +824,13 @@ static rpcholqr_status gram_fp64_wide(rpcholqr_plan_s* p, const double* X, int64
     const int tiles = nb * (nb + 1) / 2;
     int ranges = 2 * p->grid / tiles;   // two CTAs per SM fit
     if (ranges < 1) ranges = 1;
-    if (ranges > p->grid) ranges = p->grid;
+    if (ranges > p->nparts) ranges = p->nparts;
     const int64_t max_ranges = (m + 31) / 32;
     if (ranges > max_ranges) ranges = static_cast<int>(max_ranges);
-    if (launch_syrk_fp64(X, ldx, m, n, np, ranges, p->gpart, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    {
+        KTimer kt(p, st, RPCHOLQR_KERNEL_FP64_SYRK, static_cast<double>(m) * n * n);
+        if (launch_syrk_fp64(X, ldx, m, n, np, ranges, p->gpart, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    }
     launch_gram_reduce(p->gpart, ranges, np, n, G, ldg, info, st);
     p->launches += 2;
     return check_launch();
@@ -708,9 +859,12 @@ static rpcholqr_status precondition_internal(rpcholqr_plan p, const double* A, i
     if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
     const int grid = row_grid(p, m);
     if (pm) pm->mark(RPCHOLQR_PHASE_PASS1);
-    if (launch_rowpass(true, np, A, lda, A1, ld1, m, n, p->frag_s, p->diag_s, p->gpart, info, grid, st) !=
-        cudaSuccess)
-        return RPCHOLQR_ERR_CUDA;
+    {
+        KTimer kt(p, st, RPCHOLQR_KERNEL_ROWPASS, 2.0 * m * n * n);
+        if (launch_rowpass(true, np, A, lda, A1, ld1, m, n, p->frag_s, p->diag_s, p->gpart, info, grid, st) !=
+            cudaSuccess)
+            return RPCHOLQR_ERR_CUDA;
+    }
     ++p->launches;
     if (pm) {
         pm->mark(RPCHOLQR_PHASE_PASS1_UPDATE);
@@ -738,9 +892,12 @@ static rpcholqr_status solve_internal(rpcholqr_plan p, const double* X, int64_t 
     if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
     const int grid = row_grid(p, m);
     if (pm) pm->mark(RPCHOLQR_PHASE_PASS2);
-    if (launch_rowpass(false, np, X, ldx, Y, ldy, m, n, p->frag_1, p->diag_1, nullptr, info, grid, st) !=
-        cudaSuccess)
-        return RPCHOLQR_ERR_CUDA;
+    {
+        KTimer kt(p, st, RPCHOLQR_KERNEL_ROWPASS, static_cast<double>(m) * n * n);
+        if (launch_rowpass(false, np, X, ldx, Y, ldy, m, n, p->frag_1, p->diag_1, nullptr, info, grid, st) !=
+            cudaSuccess)
+            return RPCHOLQR_ERR_CUDA;
+    }
     ++p->launches;
     return RPCHOLQR_OK;
 }
@@ -748,11 +905,11 @@ static rpcholqr_status solve_internal(rpcholqr_plan p, const double* X, int64_t 
 // C = X Y (sub = false) or C = B - X Y (sub = true) on the tensor cores; X row bounds computed here.
 // xexp_ready: p->xexp already holds the row bounds of X (written by the row pass that produced X);
 // row0: X's first row within the matrix whose bounds p->xexp holds; y_ready: p->yblocks already holds
-// the slices of this Y.
+// the slices of this Y; y_upper: Y is upper triangular (the product skips its zero K stages).
 static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const double* X, int64_t m, int K,
                                            int64_t ldx, const double* Y, int N, int64_t ldy, const double* B,
                                            int64_t ldb, double* C, int64_t ldc, int32_t* info, cudaStream_t st,
-                                           bool xexp_ready, int64_t row0, bool y_ready) {
+                                           bool xexp_ready, int64_t row0, bool y_ready, bool y_upper) {
     int32_t* xexp = p->xexp + row0;
     if (!xexp_ready) {
         launch_row_exp(X, ldx, m, K, xexp, st);
@@ -765,10 +922,13 @@ static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const doub
     if (check_launch() != RPCHOLQR_OK) return RPCHOLQR_ERR_CUDA;
     const int64_t tiles = ((m + 127) / 128) * ((N + 63) / 64);
     const int grid = static_cast<int>(tiles < p->grid ? tiles : p->grid);
-    if (launch_ozaki_gemm(sub, X, ldx, xexp, K, p->yblocks, p->yexp, N, B, ldb, C, ldc, m, info, grid, st,
-                          static_cast<long>(p->spin_limit)) !=
-        cudaSuccess)
-        return RPCHOLQR_ERR_CUDA;
+    {
+        KTimer kt(p, st, ozaki_class(sub, K, N), ozaki_flops(sub, y_upper, m, K, N));
+        if (launch_ozaki_gemm(sub, X, ldx, xexp, K, p->yblocks, p->yexp, N, B, ldb, C, ldc, m, info, grid, st,
+                              static_cast<long>(p->spin_limit), y_upper) !=
+            cudaSuccess)
+            return RPCHOLQR_ERR_CUDA;
+    }
     ++p->launches;
     return RPCHOLQR_OK;
 }
@@ -783,14 +943,25 @@ static rpcholqr_status ozaki_gram_internal(rpcholqr_plan p, const double* X, int
         launch_col_exp(X, ldx, m, n, p->colexp, st);
         p->launches += 2;
     }
+    // row ranges: the fewest that make (tiles x ranges) a whole number of waves over the SMs, so no SM
+    // idles in the last wave (p->gpart holds p->nparts partials)
     const int nh = ozaki_gram_halves(np);
     int nranges = p->grid / nh;
+    if (nranges > p->nparts) nranges = p->nparts;
+    for (int r = nranges > 1 ? nranges : 1; r <= p->nparts; ++r)
+        if ((static_cast<int64_t>(r) * nh) % p->grid == 0) {
+            nranges = r;
+            break;
+        }
     if (nranges < 1) nranges = 1;
     const int64_t max_ranges = (m + 31) / 32;
     if (nranges > max_ranges) nranges = static_cast<int>(max_ranges);
-    if (launch_ozaki_gram(X, ldx, m, n, np, p->colexp, nranges, p->gpart, info, st,
-                          static_cast<long>(p->spin_limit)) != cudaSuccess)
-        return RPCHOLQR_ERR_CUDA;
+    {
+        KTimer kt(p, st, RPCHOLQR_KERNEL_SPLIT_GRAM, static_cast<double>(m) * n * n);
+        if (launch_ozaki_gram(X, ldx, m, n, np, p->colexp, nranges, p->gpart, info, st,
+                              static_cast<long>(p->spin_limit)) != cudaSuccess)
+            return RPCHOLQR_ERR_CUDA;
+    }
     ++p->launches;
     launch_gram_reduce(p->gpart, nranges, np, n, G, ldg, info, st);
     ++p->launches;
@@ -817,7 +988,7 @@ static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m,
         pm.mark(RPCHOLQR_PHASE_PASS1);
         rc = solve_split_right(p, A, lda, p->Rs, np, m, n, A1, ld1, p->frag_s, p->diag_s, info, st, &pm);
     } else {
-        prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st);
+        prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st, kSplitSub);
         pm.mark(RPCHOLQR_PHASE_PASS1);
         rc = solve_blocked(p, A, lda, p->Rs, np, m, n, A1, ld1, p->frag_s, p->diag_s, true, true, info, st, &pm,
                            true);
@@ -826,17 +997,20 @@ static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m,
     pm.mark(RPCHOLQR_PHASE_GRAM_REDUCE);
     if ((rc = ozaki_gram_internal(p, A1, m, n, ld1, p->G, np, info, st, true)) != RPCHOLQR_OK) return rc;
     pm.mark(RPCHOLQR_PHASE_CHOLESKY);
-    if (launch_cholesky(p->G, np, n, np, p->R1, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    {
+        KTimer kt(p, st, RPCHOLQR_KERNEL_CHOLESKY, static_cast<double>(n) * n * n / 3.0);
+        if (launch_cholesky(p->G, np, n, np, p->R1, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    }
     ++p->launches;
     pm.mark(RPCHOLQR_PHASE_PREP_R1);
-    launch_triu_inv(p->R1, np, n, np, p->W, info, st);
+    if ((rc = inverse_r1(p, n, np, info, st)) != RPCHOLQR_OK) return rc;
     launch_pass2_gate(p->R1, p->W, n, np, kSplitPass2Tau, info, p->gates, st);
-    p->launches += 2;
+    ++p->launches;
     pm.mark(RPCHOLQR_PHASE_PASS2);
     // Q = A1 R1^{-1}: the split product with the explicit inverse when A1 is well conditioned, else the
     // FP64 row-wise substitution; both are launched, the gate words make the other one return at once
     if ((rc = ozaki_gemm_internal(p, false, A1, m, n, ld1, p->W, n, np, nullptr, 0, Q, ldq, p->gates, st,
-                                  true)) != RPCHOLQR_OK)
+                                  true, 0, false, true)) != RPCHOLQR_OK)
         return rc;
     if ((rc = solve_internal(p, A1, m, n, ld1, p->R1, np, Q, ldq, p->gates + 2, st, nullptr)) != RPCHOLQR_OK)
         return rc;
@@ -867,7 +1041,10 @@ rpcholqr_status rpcholqr_factor(rpcholqr_plan p, const double* A, int64_t m, int
         RPCHOLQR_OK)
         return rc;
     pm.mark(RPCHOLQR_PHASE_CHOLESKY);
-    if (launch_cholesky(p->G, np, n, np, p->R1, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    {
+        KTimer kt(p, st, RPCHOLQR_KERNEL_CHOLESKY, static_cast<double>(n) * n * n / 3.0);
+        if (launch_cholesky(p->G, np, n, np, p->R1, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    }
     ++p->launches;
     if ((rc = solve_internal(p, Q, m, n, ldq, p->R1, np, Q, ldq, info, st, &pm)) != RPCHOLQR_OK) return rc;
     pm.mark(RPCHOLQR_PHASE_RECOVER_R);
@@ -940,12 +1117,15 @@ rpcholqr_status rpcholqr_factor_f32(rpcholqr_plan p, const float* A, int64_t m, 
     pm.mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
     pm.mark(RPCHOLQR_PHASE_GRAM_REDUCE);
     const int np64 = (n + 63) / 64 * 64;
-    const int ranges = launch_syrk_f32(Q, ldq, m, n, p->grid, p->gpart, info, st);
+    const int ranges = launch_syrk_f32(Q, ldq, m, n, p->nparts, p->gpart, info, st);
     launch_gram_reduce(p->gpart, ranges, np64, n, p->G, np, info, st);
     p->launches += 2;
     // FP64 Cholesky, pass 2 in FP32 (in place), R = R1 R_s in FP64 rounded to FP32
     pm.mark(RPCHOLQR_PHASE_CHOLESKY);
-    if (launch_cholesky(p->G, np, n, np, p->R1, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    {
+        KTimer kt(p, st, RPCHOLQR_KERNEL_CHOLESKY, static_cast<double>(n) * n * n / 3.0);
+        if (launch_cholesky(p->G, np, n, np, p->R1, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    }
     ++p->launches;
     pm.mark(RPCHOLQR_PHASE_PREP_R1);
     launch_prep_f32(p->R1, np, n, p->T32, p->rinv32, RPCHOLQR_ERR_NOT_SPD, info, st);
@@ -968,19 +1148,56 @@ rpcholqr_status rpcholqr_plan_enable_timing(rpcholqr_plan p, int32_t max_calls) 
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
     free_events(p);
     if (max_calls == 0) return RPCHOLQR_OK;
+    if (max_calls > 4096) return RPCHOLQR_ERR_ARG;
     const int total = max_calls * (RPCHOLQR_NUM_PHASES + 1);
-    p->events = new (std::nothrow) cudaEvent_t[total];
-    if (!p->events) return RPCHOLQR_ERR_NOMEM;
-    for (int i = 0; i < total; ++i) {
+    const int ktotal = 2 * max_calls * kMaxTimedLaunches;
+    p->events = new (std::nothrow) cudaEvent_t[total]();
+    p->kevents = new (std::nothrow) cudaEvent_t[ktotal]();
+    p->kclass = new (std::nothrow) int8_t[max_calls * kMaxTimedLaunches]();
+    p->kflops = new (std::nothrow) double[max_calls * kMaxTimedLaunches]();
+    p->klaunches = new (std::nothrow) int32_t[max_calls]();
+    p->timing_slots = max_calls;   // free_events destroys what was created so far
+    if (!p->events || !p->kevents || !p->kclass || !p->kflops || !p->klaunches) {
+        free_events(p);
+        return RPCHOLQR_ERR_NOMEM;
+    }
+    for (int i = 0; i < total; ++i)
         if (cudaEventCreate(&p->events[i]) != cudaSuccess) {
-            for (int j = 0; j < i; ++j) cudaEventDestroy(p->events[j]);
-            delete[] p->events;
-            p->events = nullptr;
+            free_events(p);
             return RPCHOLQR_ERR_CUDA;
         }
-    }
-    p->timing_slots = max_calls;
+    for (int i = 0; i < ktotal; ++i)
+        if (cudaEventCreate(&p->kevents[i]) != cudaSuccess) {
+            free_events(p);
+            return RPCHOLQR_ERR_CUDA;
+        }
     p->timed_calls = 0;
+    return RPCHOLQR_OK;
+}
+
+rpcholqr_status rpcholqr_plan_collect_kernel_timing(rpcholqr_plan p, float* ms_per_class, int64_t* launches_per_class,
+                                                    double* flops_per_class) {
+    if (!p) return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    for (int c = 0; c < RPCHOLQR_NUM_KERNEL_CLASSES; ++c) {
+        if (ms_per_class) ms_per_class[c] = 0.f;
+        if (launches_per_class) launches_per_class[c] = 0;
+        if (flops_per_class) flops_per_class[c] = 0.0;
+    }
+    const int n = p->kevents ? p->timed_calls : 0;
+    for (int slot = 0; slot < n; ++slot)
+        for (int i = 0; i < p->klaunches[slot]; ++i) {
+            const int k = slot * kMaxTimedLaunches + i;
+            if (cudaEventSynchronize(p->kevents[2 * k + 1]) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p->kevents[2 * k], p->kevents[2 * k + 1]) != cudaSuccess)
+                return RPCHOLQR_ERR_CUDA;
+            const int c = p->kclass[k];
+            if (ms_per_class) ms_per_class[c] += ms;
+            if (launches_per_class) ++launches_per_class[c];
+            if (flops_per_class) flops_per_class[c] += p->kflops[k];
+        }
     return RPCHOLQR_OK;
 }
 
@@ -1086,16 +1303,19 @@ static rpcholqr_status factor_host_split(rpcholqr_plan p, const double* A, int64
             return rc;
     }
     if ((rc = ozaki_gram_internal(p, p->A1, m, n, ld1, p->G, np, info, st, true)) != RPCHOLQR_OK) return rc;
-    if (launch_cholesky(p->G, np, n, np, p->R1, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
-    launch_triu_inv(p->R1, np, n, np, p->W, info, st);
+    {
+        KTimer kt(p, st, RPCHOLQR_KERNEL_CHOLESKY, static_cast<double>(n) * n * n / 3.0);
+        if (launch_cholesky(p->G, np, n, np, p->R1, nullptr, info, st) != cudaSuccess) return RPCHOLQR_ERR_CUDA;
+    }
+    if ((rc = inverse_r1(p, n, np, info, st)) != RPCHOLQR_OK) return rc;
     launch_pass2_gate(p->R1, p->W, n, np, kSplitPass2Tau, info, p->gates, st);
-    p->launches += 3;
+    p->launches += 2;
     // pass 2 block by block; each block of Q goes back while the next is computed
     for (int c = 0; c < nchunks; ++c) {
         int64_t r0, rows;
         chunk(c, r0, rows);
         if ((rc = ozaki_gemm_internal(p, false, p->A1 + r0 * ld1, rows, n, ld1, p->W, n, np, nullptr, 0, dQ + r0 * n, n,
-                                      p->gates, st, true, r0, c > 0)) != RPCHOLQR_OK)
+                                      p->gates, st, true, r0, c > 0, true)) != RPCHOLQR_OK)
             return rc;
         if ((rc = solve_internal(p, p->A1 + r0 * ld1, rows, n, ld1, p->R1, np, dQ + r0 * n, n, p->gates + 2, st,
                                  nullptr)) != RPCHOLQR_OK)

@@ -5,8 +5,8 @@
 //   solve         Q   = A_1 R_1^{-1}            (k_ozaki_gemm_ws with the explicit R_1^{-1}; kappa(R_1) =
 //                                                kappa(A_1) is small, Lemma l_31)
 //   precondition  the off-diagonal block update A[:,J] - A_1[:,<J] R_s[<J,J] of the blocked row solve
-//                                               (k_ozaki_update for K <= 32, else k_ozaki_gemm, subtract
-//                                                form; the diagonal blocks stay FP64 substitution)
+//                                               (k_ozaki_update for K <= 32, else k_ozaki_gemm_ws,
+//                                                subtract form; the diagonal blocks stay FP64 substitution)
 //
 // Splitting (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix multiplication by using
 // fast routines of matrix multiplication and its applications", Numer. Algorithms 2012, restated): every
@@ -271,7 +271,8 @@ __device__ __forceinline__ double scale_pow2(long long I, int e) {
 // Add the eight TMEM group sums of this thread's row and its NC columns (col0.. of the 64-column tile,
 // read CW at a time) to int64 accumulators in units of 2^-53 (U53) or 2^-49 of the operand scale.
 // The sliced operands are below 0.51 of their power-of-two bounds, so a K-term sum stays below
-// 0.26 K scale: units of 2^-53 hold K <= 2^10 terms, units of 2^-49 hold 2^14 (a 64-window flush).
+// 0.26 K scale: units of 2^-53 hold K < 2^10 / 0.26 (about 3900) terms -- the products take K <= 2048,
+// a factor 2 below -- and units of 2^-49 hold 2^14 (a 64-window flush of the Gram).
 template <bool U53, int NC, int CW = 8>
 __device__ __forceinline__ void drain_acc(uint32_t tmem, int warp, int col0, long long (&acc)[NC]) {
 #pragma unroll
@@ -321,7 +322,7 @@ struct TmemState {
     uint32_t base;
 };
 
-// ---- column slices of a small K x N matrix Y (the B operand of k_ozaki_gemm) ----------------------
+// ---- column slices of a small K x N matrix Y (the B operand of k_ozaki_gemm_ws and k_ozaki_update) --
 // yexp[q] = exponent bound of column q over its K rows; blocks[(tn*nkw + kw)*8 + b] (4 KB each) hold
 // slice b of columns 64tn..64tn+63 and rows 32kw..32kw+31 in the core-matrix K-major layout.
 // Y rows >= K and columns >= N read as 0.  One CTA per (tn, kw), 256 threads: (column, 8-row chunk).
@@ -349,219 +350,6 @@ __global__ void __launch_bounds__(256) k_ozaki_slice_cols(const double* __restri
     slice_store8(x, E, blk + core_off(q, 16 * c), kBSlice);
 }
 
-// ---- C = X Y (SUB = false) or C = B - X Y (SUB = true) ------------------------------------------------
-// X: m x K FP64 (ldx) with row exponent bounds xexp[m] (max over the K columns used);
-// Y: pre-sliced by k_ozaki_slice_cols (K x N, column bounds yexp[N]);
-// B, C: m x N FP64 (ldb, ldc); C may equal B.  Persistent grid over 128-row x 64-column tiles.
-// WIN (128 < K <= 1024): the K range is cut into exactness windows of 128, each drained into int64
-// accumulators in units of 2^-53 of the scale (the same resolution as a single window).
-//
-// Pipeline: the CTA's (tile, K-stage) sequence is one stream of stages over two shared-memory buffers.
-// Stage g is sliced into buffer g & 1 while the MMAs of stage g - 1 run; when stage g opens a new
-// exactness window (or a new tile), the accumulators of the previous window are drained (into the
-// int64 accumulators, or out to C at a tile end) after stage g has been produced and before its MMAs
-// are issued, so the slicing of a tile's first stage overlaps the MMAs of the tile before.
-template <bool SUB, bool WIN, int NC>
-__device__ __forceinline__ void gemm_drain_tile(uint32_t tmem, int warp, int rq, int64_t row, int tn, int E,
-                                                int N, const int32_t* __restrict__ yexp, const double* B,
-                                                int64_t ldb, double* C, int64_t ldc, int64_t m,
-                                                long long (&acc)[NC]) {
-    if (WIN) {
-        drain_acc<true>(tmem, warp, NC * rq, acc);
-        if (row < m) {
-#pragma unroll
-            for (int j = 0; j < NC; ++j) {
-                const int col = tn * kTileN + NC * rq + j;
-                if (col < N) {
-                    const int ey = yexp[col];
-                    const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(acc[j], E + ey - 53) : 0.0;
-                    if (SUB) C[row * ldc + col] = B[row * ldb + col] - v;
-                    else C[row * ldc + col] = v;
-                }
-            }
-        }
-        return;
-    }
-#pragma unroll 1
-    for (int c0 = NC * rq; c0 < NC * rq + NC; c0 += 8) {
-        if (tn * kTileN + c0 >= N) break;   // (warp-uniform) no valid column left
-        double bv[8];
-        if (SUB) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int col = tn * kTileN + c0 + j;
-                bv[j] = (row < m && col < N) ? B[row * ldb + col] : 0.0;
-            }
-        }
-        float mg[kGroups][8];
-#pragma unroll
-        for (int g = 0; g < kGroups; ++g)
-            tmem_ld8(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + g * kTileN + c0, mg[g]);
-        tmem_wait_ld();
-        if (row < m) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int col = tn * kTileN + c0 + j;
-                if (col < N) {
-                    float grp[kGroups];
-#pragma unroll
-                    for (int g = 0; g < kGroups; ++g) grp[g] = mg[g][j];
-                    const long long I = combine_units53(grp);
-                    const int ey = yexp[col];
-                    const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(I, E + ey - 53) : 0.0;
-                    if (SUB) C[row * ldc + col] = bv[j] - v;
-                    else C[row * ldc + col] = v;
-                }
-            }
-        }
-    }
-}
-
-template <bool SUB, bool WIN>
-__global__ void __launch_bounds__(WIN ? kThreadsWin : kThreads, 1)
-k_ozaki_gemm(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int K,
-             const uint8_t* __restrict__ yblocks, const int32_t* __restrict__ yexp, int N,
-             const double* B, int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, long spin) {
-    extern __shared__ __align__(1024) uint8_t sm[];
-    __shared__ uint64_t mbar[2];
-    __shared__ uint32_t tslot;
-    if (load_status(info) != 0) return;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    uint8_t* stA[2] = {sm, sm + kAStage};
-    uint8_t* stB[2] = {sm + 2 * kAStage, sm + 2 * kAStage + kBStage};
-
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
-                         smem_u32(&tslot)), "r"(kTmemCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-    }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
-        asm volatile("fence.mbarrier_init.release.cluster;\n");
-    }
-    tc_before_sync();
-    __syncthreads();
-    tc_after_sync();
-    const uint32_t tmem = tslot;
-    constexpr int NT = WIN ? kThreadsWin : kThreads;
-    constexpr int NC = Share<NT>::kDrainCols, NCH = Share<NT>::kChunks;
-
-    const int nkw = (K + kKW - 1) / kKW;
-    const int ntn = (N + kTileN - 1) / kTileN;
-    const int64_t ntm = (m + kTileM - 1) / kTileM;
-    const int64_t ntiles = ntm * ntn;
-    const int64_t my_tiles =
-        static_cast<int64_t>(blockIdx.x) < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t nstages = my_tiles * nkw;
-    const int lr = tid & (kTileM - 1);  // tile row: producer row and drain row (TMEM lane)
-    const int rq = tid >> 7;            // producer K chunk(s) NCH*rq..; drain columns NC*rq..
-    uint32_t phase[2] = {0u, 0u};
-    bool pending[2] = {false, false};
-    bool timed_out = false;
-    long long acc[NC];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) acc[j] = 0;
-    int64_t cur_row = 0;                // the tile whose accumulators are in TMEM
-    int cur_tn = 0, cur_E = kNoExp;
-
-    for (int64_t g = 0; g < nstages; ++g) {
-        const int s = static_cast<int>(g & 1);
-        const int64_t t = blockIdx.x + (g / nkw) * gridDim.x;
-        const int kw = static_cast<int>(g % nkw);
-        const int64_t tm = t / ntn;
-        const int tn = static_cast<int>(t - tm * ntn);
-        const int64_t row = tm * kTileM + lr;
-        const int E = row < m ? xexp[row] : kNoExp;
-        // buffer s is free once the MMAs of stage g - 2 are done
-        if (pending[s]) {
-            const bool ok = mbar_wait(&mbar[s], phase[s], spin);
-            if (__syncthreads_or(!ok)) { timed_out = true; break; }
-            phase[s] ^= 1u;
-            pending[s] = false;
-        }
-        // produce stage g: B slices (one contiguous 32 KB block, 16-byte cp.async granules) and the A
-        // slices of this thread's row, two chunks of 8 K values
-        const uint8_t* src = yblocks + static_cast<size_t>((tn * nkw + kw) * kSlices) * kBSlice;
-        for (int e = tid; e < kBStage / 16; e += NT) {
-            const unsigned dst = smem_u32(stB[s] + 16 * e);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 16 * e));
-        }
-        asm volatile("cp.async.commit_group;\n");
-#pragma unroll
-        for (int cc = 0; cc < NCH; ++cc) {
-            const int c = NCH * rq + cc;
-            double x[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int k = kw * kKW + 8 * c + i;
-                x[i] = (row < m && k < K) ? X[row * ldx + k] : 0.0;
-            }
-            slice_store8(x, E, stA[s] + core_off(lr, 16 * c), kASlice);
-        }
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
-        fence_async_smem();
-        // stage g opens an exactness window: drain the previous window's accumulators first
-        const bool new_window = (kw & 3) == 0;
-        if (g > 0 && new_window) {
-            const int sp = s ^ 1;
-            if (pending[sp]) {
-                const bool ok = mbar_wait(&mbar[sp], phase[sp], spin);
-                if (__syncthreads_or(!ok)) { timed_out = true; break; }
-                phase[sp] ^= 1u;
-                pending[sp] = false;
-            }
-            tc_after_sync();
-            if (kw == 0) {
-                gemm_drain_tile<SUB, WIN, NC>(tmem, warp, rq, cur_row, cur_tn, cur_E, N, yexp, B, ldb, C, ldc, m,
-                                              acc);
-#pragma unroll
-                for (int j = 0; j < NC; ++j) acc[j] = 0;
-            } else if (WIN) {
-                drain_acc<true>(tmem, warp, NC * rq, acc);
-            }
-        }
-        tc_before_sync();
-        __syncthreads();
-        tc_after_sync();
-        if (kw == 0) {
-            cur_row = row;
-            cur_tn = tn;
-            cur_E = E;
-        }
-        if (tid == 0) {
-            issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), kBSlice, new_window);
-            mma_commit(&mbar[s]);
-        }
-        pending[s] = true;
-    }
-    // the last tile
-    if (!timed_out && nstages > 0) {
-        for (int s = 0; s < 2 && !timed_out; ++s)
-            if (pending[s]) {
-                const bool ok = mbar_wait(&mbar[s], phase[s], spin);
-                if (__syncthreads_or(!ok)) { timed_out = true; break; }
-                phase[s] ^= 1u;
-                pending[s] = false;
-            }
-        if (!timed_out) {
-            tc_after_sync();
-            gemm_drain_tile<SUB, WIN, NC>(tmem, warp, rq, cur_row, cur_tn, cur_E, N, yexp, B, ldb, C, ldc, m, acc);
-        }
-    }
-
-    if (timed_out) {
-        if (tid == 0) set_status(info, RPCHOLQR_ERR_TIMEOUT);
-        for (int s = 0; s < 2; ++s)
-            if (pending[s]) mbar_wait(&mbar[s], phase[s]);
-    }
-    tc_before_sync();
-    __syncthreads();
-    tc_after_sync();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
-}
-
 // ---- C = X Y, warp-specialised: helpers ------------------------------------------------------------
 // 128 rows x 32 K values of X (rows row0.., columns k0..) into R, one 8-byte cp.async per value, zero
 // outside the matrix; the 32 lanes of a warp copy one row.
@@ -581,10 +369,11 @@ __device__ __forceinline__ void prefetch_x(const double* X, int64_t ldx, int64_t
 // Write the finished tile (rows row0 + 0..127, columns 64 tn + 0..63) of C = X Y through the staging
 // buffer W (run by the NT producer threads): each thread puts its row's NC values into W, then the tile
 // is written in whole rows.  The values come from the TMEM accumulators (single window) or from acc (WIN).
-template <bool WIN, int NT, int NC>
+template <bool WIN, bool SUB, int NT, int NC>
 __device__ __forceinline__ void gemm_store_tile(uint32_t tmem, int warp, int tid, int64_t row0, int tn, int E,
-                                                int N, const int32_t* __restrict__ yexp, double* C, int64_t ldc,
-                                                int64_t m, double* W, long long (&acc)[NC]) {
+                                                int N, const int32_t* __restrict__ yexp, const double* B,
+                                                int64_t ldb, double* C, int64_t ldc, int64_t m, double* W,
+                                                long long (&acc)[NC]) {
     const int lr = tid & (kTileM - 1), rq = tid / kTileM;
     const int col0 = tn * kTileN;
     const int ncols = N - col0 < kTileN ? N - col0 : kTileN;
@@ -628,24 +417,66 @@ __device__ __forceinline__ void gemm_store_tile(uint32_t tmem, int warp, int tid
         const int e = tid + i * NT;
         const int r = e >> 6, c = e & 63;
         const int64_t row = row0 + r;
-        if (row < m && c < ncols) C[row * ldc + col0 + c] = W[r * kEpiLd + c];
+        if (row < m && c < ncols) {
+            // SUB: C = B - X Y, B read in whole rows like C is written (B may be C itself)
+            if (SUB) C[row * ldc + col0 + c] = B[row * ldb + col0 + c] - W[r * kEpiLd + c];
+            else C[row * ldc + col0 + c] = W[r * kEpiLd + c];
+        }
     }
     prod_sync(NT);   // W (a stage buffer) is free again
 }
 
-// ---- C = X Y, warp-specialised (the product of pass 2, Q = A_1 R_1^{-1}) -----------------------------
-// Same operands, tiles, exactness windows and results as k_ozaki_gemm<false, WIN>; the pipeline differs.
-// The raw X rows of stage g + 1 are copied (cp.async, whole rows per warp) while stage g is sliced, and
-// the finished tile is written in whole rows through a free stage buffer.  Warp roles: NT producer
+// ---- C = X Y (SUB = false: pass 2, Q = A_1 R_1^{-1}) or C = B - X Y (SUB = true: the off-diagonal block
+// updates of the wide first pass), warp-specialised ---------------------------------------------------
+// X: m x K FP64 (ldx) with row exponent bounds xexp[m] (max over the K columns used);
+// Y: pre-sliced by k_ozaki_slice_cols (K x N, column bounds yexp[N]);
+// B, C: m x N FP64 (ldb, ldc); C may equal B.  Persistent grid over 128-row x 64-column tiles.
+// WIN (128 < K <= 1024): the K range is cut into exactness windows of 128, each drained into int64
+// accumulators in units of 2^-53 of the scale (the same resolution as a single window).
+// The CTA's (tile, K-stage) sequence is one stream of stages over two shared-memory buffers: stage g is
+// sliced while the MMAs of stage g - 1 run; when stage g opens a new exactness window (or a new tile)
+// the previous window's accumulators are drained (into int64, or out to C at a tile end) before its
+// MMAs are issued.  The raw X rows of stage g + 1 are copied (cp.async, whole rows per warp) while
+// stage g is sliced, and the finished tile is written (B read) in whole rows through a free stage
+// buffer.  Warp roles: NT producer
 // threads (warps 0 .. NT/32 - 1) copy, slice and drain; the last warp issues the MMAs.  full[s]: the
 // producer warps filled stage buffer s (one arrival per warp); empty[s]: the MMAs of the stage in
 // buffer s are done (tcgen05.commit).  A drain waits for empty of the stage before and
 // arrives on full of the next stage only after it, so the next tile's MMAs start once TMEM is read out.
-template <bool WIN>
+// The K stages the output tile of column tile tn needs: all nkw, or, with an upper-triangular Y (tri),
+// those up to the last K row its columns reach (k < 64 (tn + 1)); the stages after it multiply zeros.
+__device__ __forceinline__ int tile_stages(int tn, int nkw, bool tri) {
+    if (!tri) return nkw;
+    const int last = ((tn + 1) * kTileN + kKW - 1) / kKW;
+    return last < nkw ? last : nkw;
+}
+
+// Walks the stages of the output tiles one CTA owns (tiles t = blockIdx.x, + gridDim.x, ...; stages
+// kw = 0 .. tile_stages - 1 of each).
+struct StageWalk {
+    int64_t t;
+    int tn, kw, nk, ntn, nkw;
+    bool tri;
+    __device__ __forceinline__ StageWalk(int ntn_, int nkw_, bool tri_)
+        : t(blockIdx.x), kw(0), ntn(ntn_), nkw(nkw_), tri(tri_) {
+        tn = static_cast<int>(t % ntn);
+        nk = tile_stages(tn, nkw, tri);
+    }
+    __device__ __forceinline__ void advance() {
+        if (++kw == nk) {
+            kw = 0;
+            t += gridDim.x;
+            tn = static_cast<int>(t % ntn);
+            nk = tile_stages(tn, nkw, tri);
+        }
+    }
+};
+
+template <bool WIN, bool SUB>
 __global__ void __launch_bounds__((WIN ? kThreadsWin : kThreads) + 32, 1)
 k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int K,
-                const uint8_t* __restrict__ yblocks, const int32_t* __restrict__ yexp, int N, double* C,
-                int64_t ldc, int64_t m, int32_t* info, long spin) {
+                const uint8_t* __restrict__ yblocks, const int32_t* __restrict__ yexp, int N, const double* B,
+                int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, long spin, int tri) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t empty_bar[2], full_bar[2], done_bar;
     __shared__ uint32_t tslot;
@@ -683,13 +514,20 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
     const int64_t ntiles = ntm * ntn;
     const int64_t my_tiles =
         static_cast<int64_t>(blockIdx.x) < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t nstages = my_tiles * nkw;
+    int64_t nstages = 0;
+    if (tri) {
+        for (int64_t u = 0; u < my_tiles; ++u)
+            nstages += tile_stages(static_cast<int>((blockIdx.x + u * gridDim.x) % ntn), nkw, true);
+    } else {
+        nstages = my_tiles * nkw;
+    }
 
     if (warp == NT / 32) {
         // MMA warp: one lane issues every stage once the producers have filled it
         if (lane == 0) {
             uint32_t fphase[2] = {0u, 0u};
-            for (int64_t g = 0; g < nstages; ++g) {
+            StageWalk wk(ntn, nkw, tri != 0);
+            for (int64_t g = 0; g < nstages; ++g, wk.advance()) {
                 const int s = static_cast<int>(g & 1);
                 if (!mbar_wait_ab(&full_bar[s], fphase[s], &abort_s, spin)) {
                     abort_s = 1;
@@ -697,7 +535,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
                 }
                 fphase[s] ^= 1u;
                 tc_after_sync();
-                issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), kBSlice, (g % nkw & 3) == 0);
+                issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), kBSlice, (wk.kw & 3) == 0);
                 mma_commit(&empty_bar[s]);
             }
             // every MMA issued here is complete before the tensor memory is released
@@ -716,26 +554,16 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
         for (int j = 0; j < NC; ++j) acc[j] = 0;
         int64_t cur_row0 = 0;               // the tile whose accumulators are in TMEM
         int cur_tn = 0, cur_E = kNoExp;
-        // first row and K offset of stage g
-        auto stage_origin = [&](int64_t g, int64_t& row0, int& k0) {
-            const int64_t t = blockIdx.x + (g / nkw) * gridDim.x;
-            row0 = (t / ntn) * kTileM;
-            k0 = static_cast<int>(g % nkw) * kKW;
-        };
-        if (nstages > 0) {
-            int64_t r0;
-            int k0;
-            stage_origin(0, r0, k0);
-            prefetch_x<NT>(X, ldx, m, K, r0, k0, R, tid);
-        }
+        StageWalk wk(ntn, nkw, tri != 0);   // stage g
+        if (nstages > 0) prefetch_x<NT>(X, ldx, m, K, (wk.t / ntn) * kTileM, wk.kw * kKW, R, tid);
         cp_async_commit();
 
-        for (int64_t g = 0; g < nstages; ++g) {
+        for (int64_t g = 0; g < nstages; ++g, wk.advance()) {
             const int s = static_cast<int>(g & 1);
-            const int64_t t = blockIdx.x + (g / nkw) * gridDim.x;
-            const int kw = static_cast<int>(g % nkw);
+            const int64_t t = wk.t;
+            const int kw = wk.kw;
             const int64_t tm = t / ntn;
-            const int tn = static_cast<int>(t - tm * ntn);
+            const int tn = wk.tn;
             const int64_t row = tm * kTileM + lr;
             const int E = row < m ? xexp[row] : kNoExp;
             // buffer s is free once the MMAs of stage g - 2 are done
@@ -771,10 +599,9 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
             // R is free: copy the raw X rows of stage g + 1
             prod_sync(NT);
             if (g + 1 < nstages) {
-                int64_t r0;
-                int k0;
-                stage_origin(g + 1, r0, k0);
-                prefetch_x<NT>(X, ldx, m, K, r0, k0, R, tid);
+                StageWalk nx = wk;
+                nx.advance();
+                prefetch_x<NT>(X, ldx, m, K, (nx.t / ntn) * kTileM, nx.kw * kKW, R, tid);
             }
             cp_async_commit();
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // the B slices of stage g
@@ -791,7 +618,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
                 tc_after_sync();
                 if (kw == 0) {
                     // every MMA so far is complete: stage sp's buffer stages the output tile
-                    gemm_store_tile<WIN, NT, NC>(tmem, warp, tid, cur_row0, cur_tn, cur_E, N, yexp, C, ldc, m,
+                    gemm_store_tile<WIN, SUB, NT, NC>(tmem, warp, tid, cur_row0, cur_tn, cur_E, N, yexp, B, ldb, C, ldc, m,
                                                  reinterpret_cast<double*>(stA[sp]), acc);
 #pragma unroll
                     for (int j = 0; j < NC; ++j) acc[j] = 0;
@@ -822,7 +649,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
                 }
             if (!timed_out) {
                 tc_after_sync();
-                gemm_store_tile<WIN, NT, NC>(tmem, warp, tid, cur_row0, cur_tn, cur_E, N, yexp, C, ldc, m,
+                gemm_store_tile<WIN, SUB, NT, NC>(tmem, warp, tid, cur_row0, cur_tn, cur_E, N, yexp, B, ldb, C, ldc, m,
                                              reinterpret_cast<double*>(stA[0]), acc);
             }
         }
@@ -846,7 +673,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
 // columns 8 ((w - 4) / 4)..: four warps per lane quarter keep enough independent FP64 conversions and
 // subtractions in flight), warp 20 issues the MMAs.  Barriers: stage_full/stage_empty per X stage
 // buffer, acc_full/acc_empty per TMEM buffer.  Same exactness window, combination and rounding as
-// k_ozaki_gemm<true, false>: the results are identical.
+// k_ozaki_gemm_ws<false, true>: the results are identical.
 constexpr int kUpdTileN = 32;
 constexpr int kUpdMaxN = 128;
 constexpr int kUpdProducers = 4, kUpdDrainers = 16;
@@ -1297,19 +1124,12 @@ void launch_ozaki_slice_cols(const double* Y, int64_t ldy, int K, int N, uint8_t
 cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int32_t* xexp, int K,
                               const uint8_t* yblocks, const int32_t* yexp, int N, const double* B,
                               int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, int grid,
-                              cudaStream_t st, long spin) {
-    if (K > 32 * oz::kKW) return cudaErrorInvalidValue;   // int64 accumulators hold K <= 1024
+                              cudaStream_t st, long spin, bool y_upper) {
+    if (K > 64 * oz::kKW) return cudaErrorInvalidValue;   // int64 accumulators hold K <= 2048 (see drain_acc)
     const bool win = K > 4 * oz::kKW;
     const int nt = win ? oz::kThreadsWin : oz::kThreads;
     cudaError_t err;
-    if (!sub) {
-        auto kern = win ? oz::k_ozaki_gemm_ws<true> : oz::k_ozaki_gemm_ws<false>;
-        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::kGemmSmem);
-        if (err != cudaSuccess) return err;
-        kern<<<grid, nt + 32, oz::kGemmSmem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, C, ldc, m, info, spin);
-        return cudaGetLastError();
-    }
-    if (K <= oz::kKW && N <= oz::kUpdMaxN) {
+    if (sub && K <= oz::kKW && N <= oz::kUpdMaxN) {
         const int64_t ntm = (m + oz::kTileM - 1) / oz::kTileM;
         const int g = static_cast<int>(grid < ntm ? grid : ntm);
         err = cudaFuncSetAttribute(oz::k_ozaki_update, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::kUpdSmem);
@@ -1318,11 +1138,12 @@ cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int3
                                                                     ldc, m, info, spin);
         return cudaGetLastError();
     }
-    const int smem = 2 * (oz::kAStage + oz::kBStage);
-    auto kern = win ? oz::k_ozaki_gemm<true, true> : oz::k_ozaki_gemm<true, false>;
-    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = win ? (sub ? oz::k_ozaki_gemm_ws<true, true> : oz::k_ozaki_gemm_ws<true, false>)
+                    : (sub ? oz::k_ozaki_gemm_ws<false, true> : oz::k_ozaki_gemm_ws<false, false>);
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::kGemmSmem);
     if (err != cudaSuccess) return err;
-    kern<<<grid, nt, smem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb, C, ldc, m, info, spin);
+    kern<<<grid, nt + 32, oz::kGemmSmem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb, C, ldc, m, info, spin,
+                                                y_upper ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -222,6 +222,18 @@ void launch_triu_mul(const double* R1, int64_t ld1, const double* Rs, int64_t ld
 }  // namespace rpq
 
 namespace rpq {
+__global__ void k_fill_identity(double* __restrict__ W, int np, const int32_t* info) {
+    if (info && load_status(info) != 0) return;
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e < static_cast<int64_t>(np) * np) W[e] = (e / np == e % np) ? 1.0 : 0.0;
+}
+
+// W (np x np) = I.
+void launch_fill_identity(double* W, int np, const int32_t* info, cudaStream_t st) {
+    const int64_t total = static_cast<int64_t>(np) * np;
+    k_fill_identity<<<static_cast<unsigned>((total + 255) / 256), 256, 0, st>>>(W, np, info);
+}
+
 void launch_triu_inv(const double* T, int64_t ldt, int n, int np, double* W, const int32_t* info,
                      cudaStream_t st) {
     if (n <= 128) k_triu_inv<4><<<(n + 7) / 8, 256, 0, st>>>(T, ldt, n, np, W, info);

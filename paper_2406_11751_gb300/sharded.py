@@ -54,6 +54,20 @@ class TorchDistComm:
         return [int(x) for x in t.tolist()]
 
 
+class SingleComm:
+    """The exchanges of a one-process run: nothing to exchange."""
+    world_size = 1
+
+    def allreduce_sum(self, t):
+        return t
+
+    def allgather(self, t):
+        return [t]
+
+    def allreduce_max_ints(self, v):
+        return [int(x) for x in v]
+
+
 class CudaSteps:
     """The steps through the C ABI, on device tensors (an FP64 plan sized for the local block)."""
 

@@ -38,7 +38,10 @@ def test_host_only_entry_points(lib):
     with pytest.raises(lib.RpcholqrError):
         lib.rpcholqr_workspace_size(100, 0, 10)         # n < 1
     with pytest.raises(lib.RpcholqrError):
-        lib.rpcholqr_workspace_size(1000, 513, 600)      # n above the built maximum
+        lib.rpcholqr_workspace_size(10000, 2049, 6200)   # n above the built maximum
+    # wide panels keep at most one Gram partial per 1024 rows and at most 1 GiB of them
+    wide = lib.rpcholqr_workspace_size(6000, 2048, 6000)
+    assert 8 * 6 * 2048 * 2048 <= wide <= 8 * (6000 * 2048 + 13 * 2048 * 2048)
     with pytest.raises(lib.RpcholqrError):
         lib.rpcholqr_workspace_size(100, 10, 5)         # s < n
     h = ctypes.c_void_p()

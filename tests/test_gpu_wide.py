@@ -1,4 +1,4 @@
-"""GPU parity for wide panels (128 < n <= 512): left-looking blocked solves over 64-column blocks, the
+"""GPU parity for wide panels (128 < n <= 2048): left-looking blocked solves over 64-column blocks, the
 blocked FP64 Gram, the windowed split products (K > 128) and the tiled split Gram, in both modes.
 
 Same gates as the narrow tests: R within 1e-12 of the oracle, Q within max(1e-10, 10x the oracle's
@@ -71,6 +71,37 @@ def test_wide_factor_matches_oracle(lib, oracle_mod, plans, mode, m, n, kappa):
         assert oracle_mod.residual(A, Qh, Rh) <= 10 * oracle_mod.residual(A, o["Q"], o["R"])
     if kappa <= 1e8:
         floor = nrm2(o["Q"] - oracle_mod.rpcholqr(A, s, 9, variant=1)["Q"])
+        assert nrm2(Qh - o["Q"]) <= max(1e-10, 10 * floor)
+
+
+@pytest.fixture(scope="module")
+def xplans(lib):
+    ps = {"fp64": lib.rpcholqr_plan_create(0, 12000, 2048, 6144),
+          "split": lib.rpcholqr_plan_create(0, 12000, 2048, 6144, mode=lib.SPLIT64)}
+    yield ps
+    for p in ps.values():
+        p.close()
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+@pytest.mark.parametrize("m,n,kappa", [(12000, 1000, 1e8), (10007, 2048, 1e6), (8000, 777, 1e14)])
+def test_extra_wide_factor_matches_oracle(lib, oracle_mod, xplans, mode, m, n, kappa):
+    # n > 512: R1^{-1} by the FP64 row solve of the identity, products with K up to 2048, Gram partials
+    # capped by rows; the same gates as above
+    A = inputs.usv(m, n, kappa, 1300 + n)
+    s = 3 * n if 3 * n <= 6144 else 6144
+    Q, R, info = lib.rpcholqr_factor(xplans[mode], cu(A), s, 4)
+    assert status(info) == (0, -1)
+    o = oracle_mod.rpcholqr(A, s, 4)
+    assert o["status"] == 0
+    Qh, Rh = host(Q), host(R)
+    assert nrm2(Rh - o["R"]) <= 1e-12 * nrm2(o["R"])
+    orth, orth_o = oracle_mod.orth_error_fast(Qh), oracle_mod.orth_error_fast(o["Q"])
+    assert orth <= 10 * orth_o
+    if mode == "split":
+        assert orth <= 1e-13
+    if kappa <= 1e8:
+        floor = nrm2(o["Q"] - oracle_mod.rpcholqr(A, s, 4, variant=1)["Q"])
         assert nrm2(Qh - o["Q"]) <= max(1e-10, 10 * floor)
 
 

@@ -143,3 +143,16 @@ def test_split_rows_covers_every_row():
                 assert o1 + l1 == o2
             assert sum(l for _, l in blocks) == m
             assert max(l for _, l in blocks) - min(l for _, l in blocks) <= 1
+
+
+def test_single_process_comm_matches_a_one_rank_group(oracle_mod):
+    # bench.py --sharded at N = 1 runs the driver without a process group: SingleComm must give what a
+    # one-rank group gives (the identity exchanges), so the result equals the whole-matrix oracle run
+    from paper_2406_11751_gb300.sharded import SingleComm, factor_row_sharded
+    A = inputs.usv(1500, 12, 1e6, 3)
+    comm = SingleComm()
+    t = torch.ones(3)
+    assert comm.allreduce_sum(t) is t and comm.allgather(t) == [t] and comm.allreduce_max_ints([0, 4]) == [0, 4]
+    Q, R, st = factor_row_sharded(OracleSteps(oracle_mod), comm, torch.from_numpy(A), 0, 1500, 36, 5)
+    o = oracle_mod.rpcholqr(A, 36, 5)
+    assert st == 0 and np.array_equal(R.numpy(), o["R"]) and np.array_equal(Q.numpy(), o["Q"])
