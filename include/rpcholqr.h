@@ -87,11 +87,38 @@ typedef struct rpcholqr_plan_s* rpcholqr_plan;
 
 /* Create a plan for matrices up to max_m x max_n sampled with up to max_s rows, on `device`.
  * The plan owns its device workspace (sample, R_s, fragment tables, per-CTA Gram partials),
- * allocated here with cudaMalloc; *plan receives the handle.
+ * allocated here with cudaMalloc; *plan receives the handle.  autotune_json (nullable): a tuning table
+ * written by rpcholqr_autotune -- its JSON text (starting with '{') or the path of its file; every call
+ * on the plan then takes the launch parameters of the table entry of its mode and padded n nearest in
+ * log2 m (no entry: the built-in rules).  A table that cannot be read or parsed is RPCHOLQR_ERR_ARG.
  * Requires 1 <= max_n <= RPCHOLQR_MAX_N (512 for RPCHOLQR_FP32), max_s >= max_n, max_m >= max_s.
  * Errors: RPCHOLQR_ERR_ARG, RPCHOLQR_ERR_UNSUPPORTED (mode), RPCHOLQR_ERR_NOMEM, RPCHOLQR_ERR_CUDA. */
 rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_mode mode,
-                                     int64_t max_m, int32_t max_n, int32_t max_s);
+                                     int64_t max_m, int32_t max_n, int32_t max_s, const char* autotune_json);
+
+/* Autotuner (no counterpart in the paper: launch parameters of this implementation).  For each shape
+ * class c (host arrays m[c], n[c], s[c] within the plan's limits) it fills a synthetic m x n matrix
+ * (uniform entries; any full-rank matrix serves), times rpcholqr_factor on it -- one warm-up and `reps`
+ * timed calls, CUDA events -- for every candidate set of launch parameters, and keeps the fastest in the
+ * plan's table under (mode, padded n, ceil(log2 m)):
+ *   SPLIT64: the width of the first pass's FP64 diagonal-block solves (16 or 32 columns; the rest of
+ *            the solve is split tensor-core updates) x the row ranges (split-K factor) of the Gram
+ *            matrix (the built-in rule, one per SM over the output tiles, twice that);
+ *   FP64, n > 128: the row ranges (split-K factor) of the wide Gram matrix (x1, x4 of one wave).
+ * Other shapes are timed with the built-in rules and recorded as such.  out_json (nullable): file the
+ * whole table is written to (the format rpcholqr_plan_create reads).  Synchronous; allocates and frees
+ * the test matrices (cudaMalloc); the results of the timed calls are discarded.  Parameters change
+ * rounding only (every candidate passes the same accuracy gates).  FP32 plans: ERR_UNSUPPORTED. */
+rpcholqr_status rpcholqr_autotune(rpcholqr_plan plan, int32_t nclasses, const int64_t* m, const int32_t* n,
+                                  const int32_t* s, int32_t reps, const char* out_json);
+
+/* The plan's tuning table as JSON text (host): *length = its length in bytes (without the terminating
+ * 0); with out != NULL, up to capacity - 1 bytes are copied to out and 0-terminated. */
+rpcholqr_status rpcholqr_autotune_table(rpcholqr_plan plan, char* out, size_t capacity, size_t* length);
+
+/* Host-only check of a tuning table (JSON text starting with '{', or a file path): *entries = the number
+ * of entries; RPCHOLQR_ERR_ARG when it cannot be read or parsed. */
+rpcholqr_status rpcholqr_autotune_parse(const char* json_or_path, int32_t* entries);
 
 /* Plan options (rpcholqr_plan_set_option / rpcholqr_plan_get_option); each holds until changed. */
 typedef enum {

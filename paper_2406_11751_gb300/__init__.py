@@ -52,6 +52,7 @@ EXPORTED_SYMBOLS = (
     "rpcholqr_plan_set_smoothing", "rpcholqr_smoothed_sample", "rpcholqr_plan_split_pass2_fp64",
     "rpcholqr_scholqr3", "rpcholqr_plan_set_option", "rpcholqr_plan_get_option",
     "rpcholqr_factor_batched", "rpcholqr_batch_factor", "rpcholqr_plan_collect_kernel_timing",
+    "rpcholqr_autotune", "rpcholqr_autotune_table", "rpcholqr_autotune_parse",
 )
 PHASES = ("sample", "sketch_qr", "prep_rs", "pass1", "pass1_update", "pass1_solve2", "gram_reduce",
           "cholesky", "prep_r1", "pass2", "recover_r")
@@ -83,7 +84,10 @@ def load_library():
                            ctypes.c_double)
     st = ctypes.c_int
     sig = {
-        "rpcholqr_plan_create": [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, I64, I32, I32],
+        "rpcholqr_plan_create": [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, I64, I32, I32, ctypes.c_char_p],
+        "rpcholqr_autotune": [P, I32, P, P, P, I32, ctypes.c_char_p],
+        "rpcholqr_autotune_table": [P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
+        "rpcholqr_autotune_parse": [ctypes.c_char_p, ctypes.POINTER(I32)],
         "rpcholqr_plan_destroy": [P],
         "rpcholqr_plan_set_option": [P, I32, I64],
         "rpcholqr_plan_get_option": [P, I32, ctypes.POINTER(I64)],
@@ -188,11 +192,44 @@ class Plan:
             pass
 
 
-def rpcholqr_plan_create(device: int, max_m: int, max_n: int, max_s: int, mode: int = FP64) -> Plan:
+def rpcholqr_plan_create(device: int, max_m: int, max_n: int, max_s: int, mode: int = FP64,
+                         autotune_json: str = None) -> Plan:
+    """A plan; autotune_json (optional): a tuning table from rpcholqr_autotune, as JSON text or a path."""
     h = ctypes.c_void_p()
+    tj = autotune_json.encode() if autotune_json is not None else None
     _check("rpcholqr_plan_create",
-           load_library().rpcholqr_plan_create(ctypes.byref(h), device, mode, max_m, max_n, max_s))
+           load_library().rpcholqr_plan_create(ctypes.byref(h), device, mode, max_m, max_n, max_s, tj))
     return Plan(h, device, max_m, max_n, max_s)
+
+
+def rpcholqr_autotune(plan: Plan, shapes, reps: int = 2, out_json: str = None) -> str:
+    """Time the candidate launch parameters for each (m, n, s) of `shapes` (synthetic matrices), keep the
+    fastest in the plan's table, write it to out_json if given; returns the table as JSON text."""
+    k = len(shapes)
+    ms = (ctypes.c_int64 * k)(*[int(x[0]) for x in shapes])
+    ns = (ctypes.c_int32 * k)(*[int(x[1]) for x in shapes])
+    ss = (ctypes.c_int32 * k)(*[int(x[2]) for x in shapes])
+    lib = load_library()
+    _check("rpcholqr_autotune", lib.rpcholqr_autotune(
+        plan.handle, k, ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(ns, ctypes.c_void_p),
+        ctypes.cast(ss, ctypes.c_void_p), reps, out_json.encode() if out_json else None))
+    return rpcholqr_autotune_table(plan)
+
+
+def rpcholqr_autotune_table(plan: Plan) -> str:
+    n = ctypes.c_size_t()
+    lib = load_library()
+    _check("rpcholqr_autotune_table", lib.rpcholqr_autotune_table(plan.handle, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check("rpcholqr_autotune_table", lib.rpcholqr_autotune_table(plan.handle, buf, n.value + 1, ctypes.byref(n)))
+    return buf.value.decode()
+
+
+def rpcholqr_autotune_parse(json_or_path: str) -> int:
+    """Number of entries of a tuning table (host-only check; raises on an unreadable table)."""
+    k = ctypes.c_int32()
+    _check("rpcholqr_autotune_parse", load_library().rpcholqr_autotune_parse(json_or_path.encode(), ctypes.byref(k)))
+    return int(k.value)
 
 
 def rpcholqr_plan_destroy(plan: Plan):

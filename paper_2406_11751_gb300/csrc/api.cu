@@ -1,9 +1,12 @@
 // C ABI of the library (declared in include/rpcholqr.h): plans, the full rpCholesky-QR call,
 // the individual steps, and the FP64 tensor-pipe probe.
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -100,6 +103,7 @@ void launch_pass2_gate(const double* R1, const double* W, int n, int np, double 
                        int32_t* gates, cudaStream_t st);
 void launch_gate_merge(int32_t* info, const int32_t* gates, cudaStream_t st);
 void launch_scholqr3_shift(double* G, int64_t ldg, int n, int64_t m, const int32_t* info, cudaStream_t st);
+void launch_fill_uniform(double* A, int64_t count, uint64_t seed, cudaStream_t st);
 // persist.cu
 struct BatchLayout {
     int64_t mat_stride, off_rs, off_r1, off_g, off_frag_s, off_frag_1, off_diag_s, off_diag_1;
@@ -120,6 +124,19 @@ cudaError_t prepare_batch_persistent(int32_t max_n, int32_t max_s, int sms, int*
 using namespace rpq;
 
 constexpr int64_t kDefaultSpinLimit = int64_t{1} << 24;
+
+// Launch parameters the autotuner chooses (rpcholqr_autotune); 0 = the built-in rule.
+struct Tuning {
+    int32_t split_sub = 0;      // SPLIT64 first pass: width of the FP64 diagonal-block solves (16 or 32)
+    int32_t gram_ranges = 0;    // SPLIT64 Gram: row ranges (split-K factor of G = A1^T A1)
+    int32_t syrk_ranges = 0;    // FP64 Gram of wide panels: row ranges
+};
+// One row of the autotuner's table: the parameters measured best for (mode, padded n, ceil(log2 m)).
+struct TuneEntry {
+    int32_t mode = 0, np = 0, m_log2 = 0;
+    Tuning t;
+    double ms = 0.0;
+};
 constexpr int64_t kMaxBatchCount = 1 << 16;   // matrices one rpcholqr_factor_batched call may take
 constexpr int32_t kMaxNF32 = 512;              // widest FP32 plan (the FP32 row solve stages T in shared memory)
 constexpr int kTriuInvMaxN = 512;              // widest R1^{-1} of the warp-per-column kernel
@@ -169,6 +186,11 @@ struct rpcholqr_plan_s {
     int32_t* klaunches = nullptr;
     int32_t cur_slot = -1;          // the slot of the call being issued (-1: not timed)
     int64_t launches = 0;
+    // autotuned launch parameters (rpcholqr_autotune, or loaded by rpcholqr_plan_create) and the
+    // parameters of the call being issued
+    std::vector<TuneEntry> tune_table;
+    Tuning cur_tune;
+    bool tune_forced = false;   // rpcholqr_autotune is timing a candidate: cur_tune is not looked up
     // options (rpcholqr_plan_set_option)
     int64_t spin_limit = kDefaultSpinLimit;   // polls of a pipeline wait before TIMEOUT
     int32_t scale_sample = 1;                 // sample scaled by sqrt(m/s) (Remark r_exp)
@@ -342,6 +364,37 @@ constexpr int kSplitSub = 32;
 // (kappa(A1) ~ 30) the explicit inverse already costs 10x in residual).
 constexpr double kSplitPass2Tau = 2.0;
 
+int ceil_log2(int64_t m) {
+    int l = 0;
+    while ((int64_t{1} << l) < m) ++l;
+    return l;
+}
+
+// The launch parameters of a call on an m x n matrix: the plan's table entry of the same mode and padded
+// width nearest in log2 m (none: the built-in rules).  Every public call that runs these kernels sets
+// them first.
+void select_tuning(rpcholqr_plan_s* p, int64_t m, int n) {
+    if (p->tune_forced) return;
+    Tuning t;
+    const int np = pad_np(n), lm = ceil_log2(m);
+    int best_d = 1 << 30;
+    for (const TuneEntry& e : p->tune_table) {
+        if (e.mode != p->mode || e.np != np) continue;
+        const int d = e.m_log2 > lm ? e.m_log2 - lm : lm - e.m_log2;
+        if (d < best_d) {
+            best_d = d;
+            t = e.t;
+        }
+    }
+    p->cur_tune = t;
+}
+
+// Width of the SPLIT64 first pass's FP64 diagonal-block solves for the current call.
+int split_sub(const rpcholqr_plan_s* p) {
+    const int v = p->cur_tune.split_sub;
+    return v == 16 || v == 32 ? v : kSplitSub;
+}
+
 // CTAs of a row pass over m rows: one per 128-row panel, at most one per SM.
 int row_grid(const rpcholqr_plan_s* p, int64_t m) {
     const int64_t panels = (m + 127) / 128;
@@ -393,6 +446,118 @@ void free_events(rpcholqr_plan_s* p) {
     p->cur_slot = -1;
 }
 
+const char* mode_name(int32_t mode) {
+    return mode == RPCHOLQR_SPLIT64 ? "split" : mode == RPCHOLQR_FP32 ? "fp32" : "fp64";
+}
+
+// The tuning table as JSON: {"gpu": ..., "sms": ..., "entries": [{"mode": ..., "np": ..., "m_log2": ...,
+// "split_sub": ..., "gram_ranges": ..., "syrk_ranges": ..., "ms": ...}, ...]}.
+std::string tune_json(const rpcholqr_plan_s* p) {
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) {
+        cudaGetLastError();
+        prop.name[0] = 0;
+    }
+    std::string out = "{\n  \"gpu\": \"" + std::string(prop.name) + "\",\n  \"sms\": " + std::to_string(p->grid) +
+                      ",\n  \"entries\": [";
+    for (size_t i = 0; i < p->tune_table.size(); ++i) {
+        const TuneEntry& e = p->tune_table[i];
+        char buf[320];
+        std::snprintf(buf, sizeof buf,
+                      "%s\n    {\"mode\": \"%s\", \"np\": %d, \"m_log2\": %d, \"split_sub\": %d, "
+                      "\"gram_ranges\": %d, \"syrk_ranges\": %d, \"ms\": %.4f}",
+                      i ? "," : "", mode_name(e.mode), e.np, e.m_log2, e.t.split_sub, e.t.gram_ranges,
+                      e.t.syrk_ranges, e.ms);
+        out += buf;
+    }
+    out += "\n  ]\n}\n";
+    return out;
+}
+
+// Reads the "entries" of a tuning table written by tune_json (whitespace and key order free; other keys
+// ignored).  False on malformed text.
+bool parse_tune_json(const char* text, std::vector<TuneEntry>& out) {
+    const char* q = std::strstr(text, "\"entries\"");
+    if (!q) return false;
+    q = std::strchr(q, '[');
+    if (!q) return false;
+    ++q;
+    for (;;) {
+        while (*q == ' ' || *q == '\n' || *q == '\r' || *q == '\t' || *q == ',') ++q;
+        if (*q == ']') return true;
+        if (*q != '{') return false;
+        const char* end = std::strchr(q, '}');
+        if (!end) return false;
+        const std::string obj(q + 1, end);
+        TuneEntry e;
+        bool have_mode = false, have_np = false, have_m = false;
+        size_t pos = 0;
+        while ((pos = obj.find('"', pos)) != std::string::npos) {
+            const size_t kend = obj.find('"', pos + 1);
+            if (kend == std::string::npos) return false;
+            const std::string key = obj.substr(pos + 1, kend - pos - 1);
+            size_t v = obj.find(':', kend);
+            if (v == std::string::npos) return false;
+            ++v;
+            while (v < obj.size() && (obj[v] == ' ' || obj[v] == '\n' || obj[v] == '\t')) ++v;
+            if (v < obj.size() && obj[v] == '"') {
+                const size_t vend = obj.find('"', v + 1);
+                if (vend == std::string::npos) return false;
+                const std::string val = obj.substr(v + 1, vend - v - 1);
+                if (key == "mode") {
+                    if (val == "fp64") e.mode = RPCHOLQR_FP64;
+                    else if (val == "split") e.mode = RPCHOLQR_SPLIT64;
+                    else if (val == "fp32") e.mode = RPCHOLQR_FP32;
+                    else return false;
+                    have_mode = true;
+                }
+                pos = vend + 1;
+            } else {
+                char* after = nullptr;
+                const double num = std::strtod(obj.c_str() + v, &after);
+                if (after == obj.c_str() + v) return false;
+                const int iv = static_cast<int>(num);
+                if (key == "np") { e.np = iv; have_np = true; }
+                else if (key == "m_log2") { e.m_log2 = iv; have_m = true; }
+                else if (key == "split_sub") e.t.split_sub = iv;
+                else if (key == "gram_ranges") e.t.gram_ranges = iv;
+                else if (key == "syrk_ranges") e.t.syrk_ranges = iv;
+                else if (key == "ms") e.ms = num;
+                pos = static_cast<size_t>(after - obj.c_str());
+            }
+        }
+        if (!have_mode || !have_np || !have_m || e.np < 1 || e.m_log2 < 0 || e.m_log2 > 62 ||
+            e.t.split_sub < 0 || e.t.gram_ranges < 0 || e.t.syrk_ranges < 0)
+            return false;
+        out.push_back(e);
+        q = end + 1;
+    }
+}
+
+// The table from JSON text (starting with '{') or from the file it names.
+bool load_tune_json(const char* json_or_path, std::vector<TuneEntry>& out) {
+    const char* t = json_or_path;
+    while (*t == ' ' || *t == '\n' || *t == '\t' || *t == '\r') ++t;
+    if (*t == '{') return parse_tune_json(t, out);
+    FILE* f = std::fopen(json_or_path, "rb");
+    if (!f) return false;
+    std::string text;
+    char buf[4096];
+    size_t k;
+    while ((k = std::fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, k);
+    std::fclose(f);
+    return parse_tune_json(text.c_str(), out);
+}
+
+void put_tune_entry(rpcholqr_plan_s* p, const TuneEntry& e) {
+    for (TuneEntry& x : p->tune_table)
+        if (x.mode == e.mode && x.np == e.np && x.m_log2 == e.m_log2) {
+            x = e;
+            return;
+        }
+    p->tune_table.push_back(e);
+}
+
 }  // namespace
 
 extern "C" {
@@ -435,9 +600,11 @@ rpcholqr_status rpcholqr_workspace_size(rpcholqr_plan p, int64_t max_m, int32_t 
 }
 
 rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_mode mode,
-                                     int64_t max_m, int32_t max_n, int32_t max_s) {
+                                     int64_t max_m, int32_t max_n, int32_t max_s, const char* autotune_json) {
     if (!plan) return RPCHOLQR_ERR_ARG;
     *plan = nullptr;
+    std::vector<TuneEntry> table;
+    if (autotune_json && !load_tune_json(autotune_json, table)) return RPCHOLQR_ERR_ARG;
     if (max_n < 1 || max_n > RPCHOLQR_MAX_N || max_s < max_n || max_m < max_s) return RPCHOLQR_ERR_ARG;
     if (mode != RPCHOLQR_FP64 && mode != RPCHOLQR_SPLIT64 && mode != RPCHOLQR_FP32) return RPCHOLQR_ERR_UNSUPPORTED;
     if (mode == RPCHOLQR_FP32 && max_n > kMaxNF32) return RPCHOLQR_ERR_UNSUPPORTED;
@@ -453,6 +620,7 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
     p->max_s = max_s;
     p->np = pad_np(max_n);
     p->grid = default_grid(device);
+    p->tune_table = table;
     // the FP32 Gram works on 64 x 64 tiles: size the shared FP64 buffers for max_n rounded up to 64
     const int32_t ws_n = mode == RPCHOLQR_FP32 ? (max_n + 63) / 64 * 64 : max_n;
     p->nparts = gram_parts(mode, max_m, max_n, p->grid);
@@ -671,7 +839,7 @@ static rpcholqr_status solve_split_right(rpcholqr_plan_s* p, const double* X, in
                                          const double* diag, int32_t* info, cudaStream_t st, const PhaseMarks* pm,
                                          int64_t row0 = 0) {
     const int grid = row_grid(p, m);
-    const int blk = kSplitBlk, sub = kSplitSub;
+    const int blk = kSplitBlk, sub = split_sub(p);
     bool first_update = true;
     auto update = [&](int c0, int K, int c1, int N, const double* B, int64_t ldb) -> rpcholqr_status {
         if (pm && first_update) pm->mark(RPCHOLQR_PHASE_PASS1_UPDATE);
@@ -757,27 +925,32 @@ static rpcholqr_status solve_blocked(rpcholqr_plan_s* p, const double* X, int64_
             if (pm && pass1_marks && J == 1) pm->mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
         }
         if (split) {
-            // two 32-column FP64 solves joined by one K = 32 split update of the block's second half
-            // (diagonal tables from prep_blocks with blk = kSplitSub)
-            for (int h = 0; h * kSplitSub < nj; ++h) {
-                const int c1 = c0 + h * kSplitSub;
-                const int nh = nj - h * kSplitSub < kSplitSub ? nj - h * kSplitSub : kSplitSub;
+            // sub-column FP64 solves (sub = the call's diagonal-block width, 16 or 32), each followed by
+            // one K = sub split update of the block's remaining columns (diagonal tables from prep_blocks
+            // with blk = sub)
+            const int sub = split_sub(p);
+            for (int h = 0; h * sub < nj; ++h) {
+                const int c1 = c0 + h * sub;
+                const int nh = nj - h * sub < sub ? nj - h * sub : sub;
                 const double* hsrc = h == 0 ? src : Y + c1;
                 const int64_t lh = h == 0 ? lsrc : ldy;
-                const int js = c1 / kSplitSub;
+                const int js = c1 / sub;
                 {
                     KTimer kt(p, st, RPCHOLQR_KERNEL_ROWPASS, static_cast<double>(m) * nh * nh);
-                    if (launch_rowpass_ex(false, pad16(nh), hsrc, lh, Y + c1, ldy, m, nh, frag + js * kSplitSub * kSplitSub,
-                                          diag + js * (kSplitSub / 8) * 64, nullptr, info, grid, st, check_finite, p->xexp,
+                    if (launch_rowpass_ex(false, pad16(nh), hsrc, lh, Y + c1, ldy, m, nh, frag + js * sub * sub,
+                                          diag + js * (sub / 8) * 64, nullptr, info, grid, st, check_finite, p->xexp,
                                           c1 == 0 ? 1 : 2, p->colexp + c1) != cudaSuccess)
                         return RPCHOLQR_ERR_CUDA;
                 }
                 ++p->launches;
-                if (h == 0 && nj > nh) {
-                    const double* B = (J == 0 ? X : Y) + c1 + nh;
-                    const int64_t ldb = J == 0 ? ldx : ldy;
+                const int rest = c0 + nj - (c1 + nh);
+                if (rest > 0) {
+                    // the first sub-block's update reads the block's input columns, later ones updated columns
+                    const bool from_input = J == 0 && h == 0;
+                    const double* B = (from_input ? X : Y) + c1 + nh;
+                    const int64_t ldb = from_input ? ldx : ldy;
                     rpcholqr_status rc = ozaki_gemm_internal(p, true, Y + c1, m, nh, ldy,
-                                                             T + static_cast<int64_t>(c1) * ldt + c1 + nh, nj - nh, ldt,
+                                                             T + static_cast<int64_t>(c1) * ldt + c1 + nh, rest, ldt,
                                                              B, ldb, Y + c1 + nh, ldy, info, st, true);
                     if (rc != RPCHOLQR_OK) return rc;
                 }
@@ -823,6 +996,7 @@ static rpcholqr_status gram_fp64_wide(rpcholqr_plan_s* p, const double* X, int64
     const int nb = np / kBlk;
     const int tiles = nb * (nb + 1) / 2;
     int ranges = 2 * p->grid / tiles;   // two CTAs per SM fit
+    if (p->cur_tune.syrk_ranges > 0) ranges = p->cur_tune.syrk_ranges;   // autotuned split-K factor
     if (ranges < 1) ranges = 1;
     if (ranges > p->nparts) ranges = p->nparts;
     const int64_t max_ranges = (m + 31) / 32;
@@ -953,6 +1127,8 @@ static rpcholqr_status ozaki_gram_internal(rpcholqr_plan p, const double* X, int
             nranges = r;
             break;
         }
+    if (p->cur_tune.gram_ranges > 0) nranges = p->cur_tune.gram_ranges;   // autotuned split-K factor
+    if (nranges > p->nparts) nranges = p->nparts;
     if (nranges < 1) nranges = 1;
     const int64_t max_ranges = (m + 31) / 32;
     if (nranges > max_ranges) nranges = static_cast<int>(max_ranges);
@@ -984,11 +1160,11 @@ static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m,
     // Up to 128 columns: 32-column blocks, right-looking (every update one K stage, wide N); above:
     // 64-column blocks, left-looking (long K windows; fewer passes over the trailing columns).
     if (np <= kMaxNP) {
-        prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st, kSplitSub);
+        prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st, split_sub(p));
         pm.mark(RPCHOLQR_PHASE_PASS1);
         rc = solve_split_right(p, A, lda, p->Rs, np, m, n, A1, ld1, p->frag_s, p->diag_s, info, st, &pm);
     } else {
-        prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st, kSplitSub);
+        prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st, split_sub(p));
         pm.mark(RPCHOLQR_PHASE_PASS1);
         rc = solve_blocked(p, A, lda, p->Rs, np, m, n, A1, ld1, p->frag_s, p->diag_s, true, true, info, st, &pm,
                            true);
@@ -1030,6 +1206,7 @@ rpcholqr_status rpcholqr_factor(rpcholqr_plan p, const double* A, int64_t m, int
     if (!shape_ok(p, m, n, s) || lda < n || ldq < n) return RPCHOLQR_ERR_ARG;
     DeviceGuard guard(p->device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    select_tuning(p, m, n);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int np = pad_np(n);
     const PhaseMarks pm(p, st);
@@ -1293,7 +1470,7 @@ static rpcholqr_status factor_host_split(rpcholqr_plan p, const double* A, int64
     p->launches += 3;
     // pass 1, block by block as A arrives
     launch_fill_noexp(p->colexp, n, st);
-    prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st, kSplitSub);
+    prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st, split_sub(p));
     for (int c = 0; c < nchunks; ++c) {
         int64_t r0, rows;
         chunk(c, r0, rows);
@@ -1346,6 +1523,7 @@ rpcholqr_status rpcholqr_factor_host(rpcholqr_plan p, const double* A, int64_t m
     if (!shape_ok(p, m, n, s) || lda < n || ldq < n) return RPCHOLQR_ERR_ARG;
     DeviceGuard guard(p->device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    select_tuning(p, m, n);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t elems = static_cast<size_t>(m) * static_cast<size_t>(n);
     if (elems > p->staged_elems || !p->hR) {
@@ -1405,6 +1583,7 @@ rpcholqr_status rpcholqr_precondition_gram(rpcholqr_plan p, const double* A, int
     if (n < 1 || n > p->max_n || m < 1 || m > p->max_m || lda < n || ld1 < n) return RPCHOLQR_ERR_ARG;
     DeviceGuard guard(p->device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    select_tuning(p, m, n);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rpcholqr_status rc = reset_info(info, st);
     if (rc != RPCHOLQR_OK) return rc;
@@ -1432,6 +1611,7 @@ rpcholqr_status rpcholqr_solve_rows(rpcholqr_plan p, const double* X, int64_t m,
     if (X == Y && ldx != ldy) return RPCHOLQR_ERR_ARG;
     DeviceGuard guard(p->device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    select_tuning(p, m, n);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rpcholqr_status rc = reset_info(info, st);
     if (rc != RPCHOLQR_OK) return rc;
@@ -1452,6 +1632,7 @@ rpcholqr_status rpcholqr_ozaki_gemm(rpcholqr_plan p, const double* X, int64_t m,
         return RPCHOLQR_ERR_ARG;
     DeviceGuard guard(p->device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    select_tuning(p, m, K);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rpcholqr_status rc = reset_info(info, st);
     if (rc != RPCHOLQR_OK) return rc;
@@ -1464,6 +1645,7 @@ rpcholqr_status rpcholqr_ozaki_gram(rpcholqr_plan p, const double* X, int64_t m,
     if (m < 1 || m > p->max_m || n < 1 || n > p->max_n || ldx < n) return RPCHOLQR_ERR_ARG;
     DeviceGuard guard(p->device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    select_tuning(p, m, n);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rpcholqr_status rc = reset_info(info, st);
     if (rc != RPCHOLQR_OK) return rc;
@@ -1515,6 +1697,7 @@ rpcholqr_status rpcholqr_cholqr(rpcholqr_plan p, const double* A, int64_t m, int
     if (rc != RPCHOLQR_OK) return rc;
     DeviceGuard guard(p->device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    select_tuning(p, m, n);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = reset_info(info, st)) != RPCHOLQR_OK) return rc;
     if ((rc = cholqr_step(p, A, m, n, lda, Q, ldq, p->R1, info, st)) != RPCHOLQR_OK) return rc;
@@ -1531,6 +1714,7 @@ rpcholqr_status rpcholqr_cholqr2(rpcholqr_plan p, const double* A, int64_t m, in
     if (rc != RPCHOLQR_OK) return rc;
     DeviceGuard guard(p->device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    select_tuning(p, m, n);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = reset_info(info, st)) != RPCHOLQR_OK) return rc;
     if ((rc = cholqr_step(p, A, m, n, lda, Q, ldq, p->Rs, info, st)) != RPCHOLQR_OK) return rc;   // R_a
@@ -1547,6 +1731,7 @@ rpcholqr_status rpcholqr_scholqr3(rpcholqr_plan p, const double* A, int64_t m, i
     if (rc != RPCHOLQR_OK) return rc;
     DeviceGuard guard(p->device);
     if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    select_tuning(p, m, n);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int np = pad_np(n);
     if ((rc = reset_info(info, st)) != RPCHOLQR_OK) return rc;
@@ -1596,6 +1781,132 @@ rpcholqr_status rpcholqr_sum_partials(const double* parts, int32_t nparts, int32
     if (!parts || !G || nparts < 1 || n < 1) return RPCHOLQR_ERR_ARG;
     launch_sum_parts(parts, nparts, n, G, static_cast<cudaStream_t>(stream));
     return check_launch();
+}
+
+rpcholqr_status rpcholqr_autotune(rpcholqr_plan p, int32_t nclasses, const int64_t* m, const int32_t* n,
+                                  const int32_t* s, int32_t reps, const char* out_json) {
+    if (!p || nclasses < 1 || !m || !n || !s || reps < 1) return RPCHOLQR_ERR_ARG;
+    if (p->mode == RPCHOLQR_FP32) return RPCHOLQR_ERR_UNSUPPORTED;
+    for (int c = 0; c < nclasses; ++c)
+        if (!shape_ok(p, m[c], n[c], s[c])) return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double *A = nullptr, *Q = nullptr, *R = nullptr;
+    int32_t* info = nullptr;
+    rpcholqr_status rc = RPCHOLQR_OK;
+    auto cleanup = [&] {
+        p->tune_forced = false;
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (st) cudaStreamDestroy(st);
+        cudaFree(A);
+        cudaFree(Q);
+        cudaFree(R);
+        cudaFree(info);
+    };
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        return RPCHOLQR_ERR_CUDA;
+    }
+    for (int c = 0; c < nclasses && rc == RPCHOLQR_OK; ++c) {
+        const int64_t mc = m[c];
+        const int nc = n[c], sc = s[c], np = pad_np(nc);
+        const size_t bytes = sizeof(double) * static_cast<size_t>(mc) * nc;
+        if (cudaMalloc(&A, bytes) != cudaSuccess || cudaMalloc(&Q, bytes) != cudaSuccess ||
+            cudaMalloc(&R, sizeof(double) * nc * nc) != cudaSuccess || cudaMalloc(&info, 2 * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            rc = RPCHOLQR_ERR_NOMEM;
+            break;
+        }
+        launch_fill_uniform(A, static_cast<int64_t>(mc) * nc, 20240617ull + c, st);
+        // candidates: the built-in rules first, then the alternatives of each parameter
+        std::vector<Tuning> cands(1);
+        if (p->mode == RPCHOLQR_SPLIT64) {
+            const int nh = ozaki_gram_halves(np);
+            const int plain = p->grid / nh > 0 ? p->grid / nh : 1;
+            for (int sub : {32, 16})
+                for (int gr : {0, plain, 2 * plain}) {
+                    if (sub == 32 && gr == 0) continue;
+                    Tuning t;
+                    t.split_sub = sub;
+                    t.gram_ranges = gr > p->nparts ? p->nparts : gr;
+                    cands.push_back(t);
+                }
+        } else if (np > kMaxNP) {
+            const int nb = np / kBlk, tiles = nb * (nb + 1) / 2;
+            for (int f : {1, 4}) {
+                Tuning t;
+                t.syrk_ranges = f * p->grid / tiles > 0 ? f * p->grid / tiles : 1;
+                cands.push_back(t);
+            }
+        }
+        TuneEntry best;
+        best.mode = p->mode;
+        best.np = np;
+        best.m_log2 = ceil_log2(mc);
+        best.ms = -1.0;
+        for (const Tuning& t : cands) {
+            p->tune_forced = true;
+            p->cur_tune = t;
+            float tot = 0.f;
+            for (int r = 0; r <= reps && rc == RPCHOLQR_OK; ++r) {   // r = 0: untimed warm-up
+                if (r == 1) cudaEventRecord(e0, st);
+                rc = rpcholqr_factor(p, A, mc, nc, nc, sc, 1 + r, Q, nc, R, info, st);
+            }
+            if (rc != RPCHOLQR_OK) break;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&tot, e0, e1) != cudaSuccess) {
+                rc = RPCHOLQR_ERR_CUDA;
+                break;
+            }
+            const double ms = tot / reps;
+            if (best.ms < 0.0 || ms < best.ms) {
+                best.ms = ms;
+                best.t = t;
+            }
+        }
+        p->tune_forced = false;
+        if (rc == RPCHOLQR_OK) put_tune_entry(p, best);
+        cudaFree(A);
+        cudaFree(Q);
+        cudaFree(R);
+        cudaFree(info);
+        A = Q = R = nullptr;
+        info = nullptr;
+    }
+    cleanup();
+    if (rc != RPCHOLQR_OK) return rc;
+    if (out_json) {
+        FILE* f = std::fopen(out_json, "wb");
+        if (!f) return RPCHOLQR_ERR_ARG;
+        const std::string text = tune_json(p);
+        const bool ok = std::fwrite(text.data(), 1, text.size(), f) == text.size();
+        if (std::fclose(f) != 0 || !ok) return RPCHOLQR_ERR_ARG;
+    }
+    return RPCHOLQR_OK;
+}
+
+rpcholqr_status rpcholqr_autotune_table(rpcholqr_plan p, char* out, size_t capacity, size_t* length) {
+    if (!p || !length) return RPCHOLQR_ERR_ARG;
+    const std::string text = tune_json(p);
+    *length = text.size();
+    if (out && capacity > 0) {
+        const size_t k = text.size() < capacity - 1 ? text.size() : capacity - 1;
+        std::memcpy(out, text.data(), k);
+        out[k] = 0;
+    }
+    return RPCHOLQR_OK;
+}
+
+rpcholqr_status rpcholqr_autotune_parse(const char* json_or_path, int32_t* entries) {
+    if (!json_or_path || !entries) return RPCHOLQR_ERR_ARG;
+    std::vector<TuneEntry> t;
+    if (!load_tune_json(json_or_path, t)) return RPCHOLQR_ERR_ARG;
+    *entries = static_cast<int32_t>(t.size());
+    return RPCHOLQR_OK;
 }
 
 rpcholqr_status rpcholqr_plan_set_smoothing(rpcholqr_plan p, int32_t kind) {

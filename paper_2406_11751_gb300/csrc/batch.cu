@@ -92,7 +92,7 @@ rpcholqr_status rpcholqr_batch_create(rpcholqr_batch* batch, int device, rpcholq
     b->streams.assign(slots, nullptr);
     b->joins.assign(slots, nullptr);
     for (int k = 0; k < slots; ++k) {
-        const rpcholqr_status rc = rpcholqr_plan_create(&b->plans[k], device, mode, max_m, max_n, max_s);
+        const rpcholqr_status rc = rpcholqr_plan_create(&b->plans[k], device, mode, max_m, max_n, max_s, nullptr);
         if (rc != RPCHOLQR_OK) { release(b); return rc; }
         if (cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&b->joins[k], cudaEventDisableTiming) != cudaSuccess) {

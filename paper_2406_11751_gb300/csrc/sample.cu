@@ -59,6 +59,22 @@ __global__ void k_sample_rows(const double* __restrict__ rows, int32_t n, double
     if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(info, RPCHOLQR_ERR_NONFINITE);
 }
 
+// A[i] = a uniform value in [-1, 1) from Philox word i mod 4 of block i / 4 under key (seed, 7): the
+// synthetic matrices the autotuner times (any full-rank A serves; it is never a result).
+__global__ void k_fill_uniform(double* __restrict__ A, int64_t count, uint64_t seed) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    uint64_t x[4] = {static_cast<uint64_t>(i >> 2), 0ull, 0ull, 0ull};
+    philox4x64_10_dev(x, seed, 7ull);
+    const int q = static_cast<int>(i & 3);
+    const uint64_t w = q == 0 ? x[0] : q == 1 ? x[1] : q == 2 ? x[2] : x[3];
+    A[i] = static_cast<double>(static_cast<int64_t>(w) >> 11) * 0x1.0p-52;
+}
+
+void launch_fill_uniform(double* A, int64_t count, uint64_t seed, cudaStream_t st) {
+    k_fill_uniform<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(A, count, seed);
+}
+
 void launch_sample_rows(const double* rows, int32_t n, int32_t s, double scale, double* As, int64_t lds,
                         int32_t np, int32_t* info, cudaStream_t st) {
     k_sample_rows<<<s, 128, 0, st>>>(rows, n, scale, As, lds, np, info);

@@ -45,8 +45,10 @@ def test_host_only_entry_points(lib):
     with pytest.raises(lib.RpcholqrError):
         lib.rpcholqr_workspace_size(100, 10, 5)         # s < n
     h = ctypes.c_void_p()
-    assert lib.load_library().rpcholqr_plan_create(ctypes.byref(h), 0, 0, 100, 0, 10) == 1
-    assert lib.load_library().rpcholqr_plan_create(ctypes.byref(h), 0, 7, 100, 10, 30) in (1, 8)
+    assert lib.load_library().rpcholqr_plan_create(ctypes.byref(h), 0, 0, 100, 0, 10, None) == 1
+    assert lib.load_library().rpcholqr_plan_create(ctypes.byref(h), 0, 7, 100, 10, 30, None) in (1, 8)
+    # an unreadable tuning table is refused before any device work
+    assert lib.load_library().rpcholqr_plan_create(ctypes.byref(h), 0, 0, 1000, 10, 30, b"{nope") == 1
     assert lib.load_library().rpcholqr_plan_destroy(None) == 0
 
 
@@ -56,3 +58,21 @@ def test_kernels_are_built_for_sm103a(lib):
     b = importlib.import_module("paper_2406_11751_gb300.build")
     assert b.ARCH_FLAGS == ["-gencode", "arch=compute_103a,code=sm_103a"]
     assert os.path.exists(b.LIB_PATH)
+
+
+def test_autotune_table_parser(lib, tmp_path):
+    table = """{"gpu": "x", "sms": 152, "entries": [
+        {"mode": "split", "np": 128, "m_log2": 20, "split_sub": 16, "gram_ranges": 38, "syrk_ranges": 0,
+         "ms": 12.5},
+        {"m_log2": 23, "np": 512, "mode": "fp64", "syrk_ranges": 8}]}"""
+    assert lib.rpcholqr_autotune_parse(table) == 2
+    path = tmp_path / "tune.json"
+    path.write_text(table)
+    assert lib.rpcholqr_autotune_parse(str(path)) == 2
+    assert lib.rpcholqr_autotune_parse('{"entries": []}') == 0
+    for bad in ('{"entries": [{"np": 128, "m_log2": 20}]}',              # no mode
+                '{"entries": [{"mode": "fp16", "np": 128, "m_log2": 20}]}',
+                '{"entries": [{"mode": "split", "np": 128, "m_log2": 20, "split_sub": -1}]}',
+                '{"no_entries": 1}', str(tmp_path / "missing.json")):
+        with pytest.raises(lib.RpcholqrError):
+            lib.rpcholqr_autotune_parse(bad)
