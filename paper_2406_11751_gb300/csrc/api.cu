@@ -60,7 +60,10 @@ void launch_slice_images(const double* X, int64_t ldx, int64_t m, int K, const i
                          const int32_t* info, cudaStream_t st);
 int ozaki_gram_halves(int np);
 cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
-                              int nranges, double* gpart, int32_t* info, cudaStream_t st, long spin);
+                              int nranges, double* gpart, int32_t* info, cudaStream_t st, long spin,
+                              const uint8_t* gimg, bool accum);
+void launch_slice_col_images(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
+                             uint8_t* img, const int32_t* info, cudaStream_t st);
 void launch_row_exp(const double* X, int64_t ldx, int64_t m, int K, int32_t* rowexp, cudaStream_t st);
 void launch_col_exp(const double* X, int64_t ldx, int64_t m, int n, int32_t* colexp, cudaStream_t st);
 cudaError_t launch_gemm_sub_fp64(const double* X, int64_t ldx, const double* Y, int64_t ldy, const double* B,
@@ -600,7 +603,7 @@ rpcholqr_status rpcholqr_workspace_size(rpcholqr_plan p, int64_t max_m, int32_t 
         int64_t rows = (int64_t{1} << 33) / static_cast<int64_t>(np * 16) / 128 * 128;
         if (rows > (max_m + 127) / 128 * 128) rows = (max_m + 127) / 128 * 128;
         if (rows < 128) rows = 128;
-        total += align256(ozaki_image_bytes(rows, static_cast<int>(np)));
+        total += align256(ozaki_image_bytes(rows, static_cast<int>((np + 127) / 128 * 128)));
     }
     if (mode == RPCHOLQR_FP32) {
         const size_t n32 = static_cast<size_t>(f32_pad(max_n));
@@ -671,7 +674,7 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
             img_rows = (int64_t{1} << 33) / static_cast<int64_t>(np * 16) / 128 * 128;
             if (img_rows > (max_m + 127) / 128 * 128) img_rows = (max_m + 127) / 128 * 128;
             if (img_rows < 128) img_rows = 128;
-            oI = take(ozaki_image_bytes(img_rows, static_cast<int>(np)));
+            oI = take(ozaki_image_bytes(img_rows, static_cast<int>((np + 127) / 128 * 128)));
         }
         if (cudaMalloc(&p->split_ws, off) != cudaSuccess) {
             cudaGetLastError();
@@ -931,7 +934,19 @@ static rpcholqr_status solve_blocked(rpcholqr_plan_s* p, const double* X, int64_
         int64_t lsrc = ldx;
         if (J > 0) {
             if (pm && pass1_marks && J == 1) pm->mark(RPCHOLQR_PHASE_PASS1_UPDATE);
-            if (split) {
+            if (split && p->aimg) {
+                // A1[:, <J] sliced once per row chunk into stage images (against the running row bounds),
+                // then the product copies them: the same slices as slicing inside it, so the same bits
+                for (int64_t r0 = 0; r0 < m; r0 += p->img_rows) {
+                    const int64_t rows = m - r0 < p->img_rows ? m - r0 : p->img_rows;
+                    launch_slice_images(Y + r0 * ldy, ldy, rows, c0, p->xexp + r0, p->aimg, info, st);
+                    ++p->launches;
+                    rpcholqr_status rc = ozaki_gemm_internal(p, true, Y + r0 * ldy, rows, c0, ldy, T + c0, nj, ldt,
+                                                             X + r0 * ldx + c0, ldx, Y + r0 * ldy + c0, ldy, info, st,
+                                                             true, r0, r0 > 0, false, p->aimg);
+                    if (rc != RPCHOLQR_OK) return rc;
+                }
+            } else if (split) {
                 rpcholqr_status rc = ozaki_gemm_internal(p, true, Y, m, c0, ldy, T + c0, nj, ldt, X + c0, ldx,
                                                          Y + c0, ldy, info, st, true);
                 if (rc != RPCHOLQR_OK) return rc;
@@ -1157,13 +1172,26 @@ static rpcholqr_status ozaki_gram_internal(rpcholqr_plan p, const double* X, int
     if (nranges < 1) nranges = 1;
     const int64_t max_ranges = (m + 31) / 32;
     if (nranges > max_ranges) nranges = static_cast<int>(max_ranges);
-    {
+    if (p->aimg) {
+        // above 128 columns: the column slices made once per row chunk into stage images; the chunks'
+        // partials are summed into the same nranges partials in chunk order
+        for (int64_t r0 = 0; r0 < m; r0 += p->img_rows) {
+            const int64_t rows = m - r0 < p->img_rows ? m - r0 : p->img_rows;
+            launch_slice_col_images(X + r0 * ldx, ldx, rows, n, np, p->colexp, p->aimg, info, st);
+            ++p->launches;
+            KTimer kt(p, st, RPCHOLQR_KERNEL_SPLIT_GRAM, static_cast<double>(rows) * n * n);
+            if (launch_ozaki_gram(X + r0 * ldx, ldx, rows, n, np, p->colexp, nranges, p->gpart, info, st,
+                                  static_cast<long>(p->spin_limit), p->aimg, r0 > 0) != cudaSuccess)
+                return RPCHOLQR_ERR_CUDA;
+            ++p->launches;
+        }
+    } else {
         KTimer kt(p, st, RPCHOLQR_KERNEL_SPLIT_GRAM, static_cast<double>(m) * n * n);
         if (launch_ozaki_gram(X, ldx, m, n, np, p->colexp, nranges, p->gpart, info, st,
-                              static_cast<long>(p->spin_limit)) != cudaSuccess)
+                              static_cast<long>(p->spin_limit), nullptr, false) != cudaSuccess)
             return RPCHOLQR_ERR_CUDA;
+        ++p->launches;
     }
-    ++p->launches;
     launch_gram_reduce(p->gpart, nranges, np, n, G, ldg, info, st);
     ++p->launches;
     return check_launch();

@@ -374,6 +374,29 @@ __global__ void __launch_bounds__(512) k_slice_images(const double* __restrict__
     slice_store8(x, E, img + static_cast<size_t>(tm * nkw + kw) * kAStage + core_off(lr, 16 * c), kASlice);
 }
 
+// ---- stage images of X's column slices (the split Gram's operands) -------------------------------------
+// img[(blk * nst + st) * kAStage ..] = the eight 8 KB slices of columns 128 blk .. 128 blk + 127 (the
+// tile's M dimension) over rows 32 st .. 32 st + 31 (K) of X, against the column bounds colexp, in the
+// layout k_ozaki_gram's producers would slice them (zeros outside X); nst = ceil(m / 32).
+__global__ void __launch_bounds__(512) k_slice_col_images(const double* __restrict__ X, int64_t ldx, int64_t m,
+                                                          int n, const int32_t* __restrict__ colexp,
+                                                          uint8_t* __restrict__ img, const int32_t* info) {
+    if (info && load_status(info) != 0) return;
+    const int64_t nst = (m + kKW - 1) / kKW;
+    const int blk = blockIdx.y;
+    const int64_t st = blockIdx.x;
+    const int lr = threadIdx.x & (kTileM - 1), c = threadIdx.x >> 7;
+    const int p = 128 * blk + lr;
+    const int E = p < n ? colexp[p] : kNoExp;
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t row = st * kKW + 8 * c + i;
+        x[i] = (row < m && p < n) ? X[row * ldx + p] : 0.0;
+    }
+    slice_store8(x, E, img + static_cast<size_t>(blk * nst + st) * kAStage + core_off(lr, 16 * c), kASlice);
+}
+
 // ---- C = X Y, warp-specialised: helpers ------------------------------------------------------------
 // 128 rows x 32 K values of X (rows row0.., columns k0..) into R, one 8-byte cp.async per value, zero
 // outside the matrix; the 32 lanes of a warp copy one row.
@@ -937,10 +960,15 @@ __device__ __forceinline__ void gram_tile_coords(int nqb, int tt, int& P, int& Q
 // sliced, one arrival per producer warp; empty[s]: its MMAs done).  A window's drain waits for the
 // MMAs of the stage before and arrives on full of the next stage only after reading TMEM.
 constexpr int kGramNT = kThreads;
+// PRE: the column slices of every (128-column block, 32-row stage) of this launch's rows were made
+// beforehand by k_slice_col_images (gimg): A is one 64 KB copy per stage, B (when it is not part of A)
+// the matching half of another block's image.  accum: add into the partials instead of starting them
+// (the launch is one of several row chunks summed in order).
+template <bool PRE>
 __global__ void __launch_bounds__(kGramNT + 32, 1)
 k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np,
              const int32_t* __restrict__ colexp, int64_t rows_per, int ntiles, double* __restrict__ gpart,
-             int32_t* info, long spin) {
+             int32_t* info, long spin, const uint8_t* __restrict__ gimg, int accum) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t empty_bar[2], full_bar[2], done_bar;
     __shared__ uint32_t tslot;
@@ -1017,7 +1045,7 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
 
         // Drain the window just finished (its MMAs complete) into acc; every 64 windows, and at the end,
         // add acc into the CTA's FP64 partial (the first flush initialises it) and clear it.
-        bool flushed = false;
+        bool flushed = accum != 0;
         auto drain_window = [&](bool flush) {
             tc_after_sync();
             drain_acc<false, kCols, 4>(tmem, warp, kCols * rq, acc);
@@ -1048,6 +1076,28 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
                 pending[s] = false;
             }
             const int64_t k0 = r0 + st * kKW;
+            if constexpr (PRE) {
+                const int64_t sg = k0 / kKW, nsg = (m + kKW - 1) / kKW;
+                const uint8_t* asrc = gimg + static_cast<size_t>(P * nsg + sg) * kAStage;
+                for (int e = tid; e < kAStage / 16; e += NT) {
+                    const unsigned dst = smem_u32(stA[s] + 16 * e);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(asrc + 16 * e));
+                }
+                if (!b_inside) {
+                    // columns 64 Qb .. 64 Qb + 63: half (Qb & 1) of every slice of block Qb / 2's image
+                    const uint8_t* bsrc = gimg + static_cast<size_t>((Qb >> 1) * nsg + sg) * kAStage +
+                                          (Qb & 1) * kBSlice;
+                    for (int e = tid; e < kBStage / 16; e += NT) {
+                        const int a = e / (kBSlice / 16), o = e - a * (kBSlice / 16);
+                        const unsigned dst = smem_u32(stB[s] + a * kBSlice + 16 * o);
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst),
+                                     "l"(bsrc + static_cast<size_t>(a) * kASlice + 16 * o));
+                    }
+                }
+                cp_async_commit();
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            }
+            if constexpr (!PRE) {
 #pragma unroll
             for (int cc = 0; cc < NCH; ++cc) {
                 const int c = NCH * rq + cc;
@@ -1059,7 +1109,8 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
                 }
                 slice_store8(x, Ep, stA[s] + core_off(lr, 16 * c), kASlice);
             }
-            if (!b_inside) {
+            }
+            if (!PRE && !b_inside) {
                 for (int e = tid; e < 4 * 64; e += NT) {
                     const int c = e >> 6, col = 64 * Qb + (e & 63);   // 64 columns x 4 chunks of 8 rows
                     const int Ec = col < n ? colexp[col] : kNoExp;
@@ -1100,7 +1151,7 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
         }
         if (timed_out) {
             abort_s = 1;
-        } else if (nstages == 0 && p < np) {
+        } else if (nstages == 0 && p < np && !accum) {
             double* out = gpart + static_cast<size_t>(rr) * np * np + static_cast<size_t>(p) * np;
             for (int j = 0; j < kCols; ++j) {
                 const int q = 64 * Qb + kCols * rq + j;
@@ -1177,8 +1228,8 @@ cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int3
                                                                     ldc, m, info, spin);
         return cudaGetLastError();
     }
-    if (aimg && sub) return cudaErrorInvalidValue;   // stage images serve C = X Y only
-    auto kern = aimg ? (win ? oz::k_ozaki_gemm_ws<true, false, true> : oz::k_ozaki_gemm_ws<false, false, true>)
+    auto kern = aimg ? (win ? (sub ? oz::k_ozaki_gemm_ws<true, true, true> : oz::k_ozaki_gemm_ws<true, false, true>)
+                            : (sub ? oz::k_ozaki_gemm_ws<false, true, true> : oz::k_ozaki_gemm_ws<false, false, true>))
               : win ? (sub ? oz::k_ozaki_gemm_ws<true, true, false> : oz::k_ozaki_gemm_ws<true, false, false>)
                     : (sub ? oz::k_ozaki_gemm_ws<false, true, false> : oz::k_ozaki_gemm_ws<false, false, false>);
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::kGemmSmem);
@@ -1223,17 +1274,26 @@ void launch_fill_noexp(int32_t* p, int n, cudaStream_t st) {
     oz::k_fill_i32<<<(n + 127) / 128, 128, 0, st>>>(p, n, kNoExp);
 }
 
+// gimg (nullable): column stage images of these m rows from launch_slice_col_images; accum: add into gpart.
 cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
-                              int nranges, double* gpart, int32_t* info, cudaStream_t st, long spin) {
+                              int nranges, double* gpart, int32_t* info, cudaStream_t st, long spin,
+                              const uint8_t* gimg, bool accum) {
     const int smem = 2 * (oz::kAStage + oz::kBStage);
-    cudaError_t err = cudaFuncSetAttribute(oz::k_ozaki_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = gimg ? oz::k_ozaki_gram<true> : oz::k_ozaki_gram<false>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (err != cudaSuccess) return err;
     const int nt = ozaki_gram_halves(np);
     int64_t rows_per = (m + nranges - 1) / nranges;
     rows_per = (rows_per + oz::kKW - 1) / oz::kKW * oz::kKW;
-    oz::k_ozaki_gram<<<nt * nranges, oz::kGramNT + 32, smem, st>>>(X, ldx, m, n, np, colexp, rows_per, nt, gpart,
-                                                               info, spin);
+    kern<<<nt * nranges, oz::kGramNT + 32, smem, st>>>(X, ldx, m, n, np, colexp, rows_per, nt, gpart, info, spin,
+                                                       gimg, accum ? 1 : 0);
     return cudaGetLastError();
+}
+
+void launch_slice_col_images(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
+                             uint8_t* img, const int32_t* info, cudaStream_t st) {
+    dim3 grid(static_cast<unsigned>((m + oz::kKW - 1) / oz::kKW), (np + 127) / 128);
+    oz::k_slice_col_images<<<grid, 512, 0, st>>>(X, ldx, m, n, colexp, img, info);
 }
 
 }  // namespace rpq
