@@ -7,7 +7,9 @@ Cholesky + second pass + R recovery) on an m x n FP64 matrix resident in HBM.
 Default workload (--config 5, the largest single-GPU workload): m = 2^23, n = 512, s = 3n = 1536,
 A = U diag(sigma) V^T with sigma log-spaced from 1 to 1e-18 (numerically singular), U, V Haar;
 SPLIT64 mode, with the plain FP64 mode timed beside it ("other_mode") and the m = 2^20, n = 128,
-kappa = 1e8 workload (--config 2) reported under "config2".  A (34.4 GB) is larger than L2, so
+kappa = 1e8 workload (--config 2) reported under "config2", with its kappa sweep (kappa 1 to 1e16,
+s = 3n and 10n, both modes, Cholesky-QR2 beside each kappa; --preset kappa-sweep runs config 2 with the
+sweep alone).  A (34.4 GB) is larger than L2, so
 consecutive steps do not reuse cached inputs.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config 1|2|3|5]
@@ -41,7 +43,7 @@ METRIC = "TS-QR matrices/s & effective TFLOP/s at ||Q^T Q - I||_2 <= 1e-13; % of
 # kappa 1e8; 3 = 2^22 x 256, kappa 1e12 (1e5 for the FP32 variant); 5 = 2^23 x 512, sigma to 1e-18.
 # (4 is the heterogeneous batch: --workload batch.)
 CONFIGS = {1: (10000, 50, 1e8), 2: (1 << 20, 128, 1e8), 3: (1 << 22, 256, 1e12), 5: (1 << 23, 512, 1e18)}
-PRESETS = {"small": 1, "headline": 2, "precision": 3, "large": 5}
+PRESETS = {"small": 1, "headline": 2, "precision": 3, "large": 5, "kappa-sweep": 2}
 
 
 def parse_args(argv=None):
@@ -53,7 +55,8 @@ def parse_args(argv=None):
     ap.add_argument("--config", type=int, choices=sorted(CONFIGS), default=5,
                     help="workload: 1 = 10,000 x 50; 2 = 2^20 x 128; 3 = 2^22 x 256; 5 = 2^23 x 512 (default)")
     ap.add_argument("--preset", choices=sorted(PRESETS), default=None,
-                    help="alias of --config: small 1, headline 2, precision 3, large 5")
+                    help="alias of --config: small 1, headline 2, precision 3, large 5; kappa-sweep: config 2 "
+                         "plus its kappa sweep (kappa 1..1e16, s 3n and 10n, both modes, Cholesky-QR2 beside)")
     ap.add_argument("--m", type=int, default=None)
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--s", type=int, default=None, help="sampled rows (default 3n)")
@@ -93,6 +96,7 @@ def parse_args(argv=None):
     ap.add_argument("--profile-window", action="store_true",
                     help="cudaProfilerStart/Stop around the timed steps of the main mode only")
     args = ap.parse_args(argv)
+    args.kappa_sweep = args.preset == "kappa-sweep"
     if args.preset:
         args.config = PRESETS[args.preset]
     m, n, kappa = CONFIGS[args.config]
@@ -251,23 +255,25 @@ def gpu_metrics(A, Q, R, rows=1 << 18):
     return orth, nd / na
 
 
-def traffic_from_profiles(kernel_tag, src_file, m=None):
-    """DRAM bytes per launch from profiles/traffic.txt when the kernel source is unchanged, scaled from
-    the captured row count to m (the row passes' traffic is proportional to the rows they process)."""
+def traffic_from_profiles(cls, n, src_file, m, launches_per_call):
+    """DRAM bytes per launch of a kernel class from profiles/traffic.txt, when the class's source file is
+    unchanged since the capture.  A line holds one call's total for the class at `measured_m` rows and width
+    n; the streaming kernels' traffic is proportional to the rows, so the total is scaled to m and divided
+    by the launches the class makes in one call at m."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     sha = hashlib.sha256(open(src_file, "rb").read()).hexdigest()[:16]
     for line in open(path):
+        if line.startswith("#"):
+            continue
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
-        if f.get("kernel") == kernel_tag and f.get("src_sha") == sha:
+        if f.get("class") == cls and f.get("n") == str(n) and f.get("src_sha") == sha:
             try:
-                t = float(f["dram_bytes_per_launch"])
-                if m is not None and "measured_m" in f:
-                    t *= m / float(f["measured_m"])
-                return t
+                per_call = float(f["dram_bytes_per_call"]) * m / float(f["measured_m"])
             except (KeyError, ValueError):
                 return None
+            return per_call / max(launches_per_call, 1)
     return None
 
 
@@ -509,29 +515,79 @@ def cpu_baseline_entry(m, n, s, kappa, seed, rows):
                       f"({t_half * 1e3:.1f} ms); full-m time extrapolated from the two: {full * 1e3:.1f} ms"}
 
 
-def run_config2(args, rq, torch, local, dev, dist, stream, ws):
-    """The 2^20 x 128, kappa = 1e8, s = 3n workload in SPLIT64 and FP64 (reported beside config 5)."""
+KAPPA_SWEEP = (1.0, 1e4, 1e8, 1e12, 1e16)
+
+
+def timed_cholqr2(rq, torch, local, dev, dist, A, Q, R, info, stream, K, W):
+    """Cholesky-QR2 (the paper's breakdown reference) on the FP64 plan: (ms over K calls or None, status
+    of the first call).  A call that breaks down (G not numerically SPD) is reported, not timed."""
+    m, n = A.shape
+    plan = rq.rpcholqr_plan_create(local, m, n, 3 * n, mode=rq.FP64)
+    try:
+        rq.rpcholqr_cholqr2(plan, A, Q=Q, R=R, info=info, stream=stream)
+        torch.cuda.synchronize(dev)
+        st = info.cpu().tolist()[0]
+        if st != 0:
+            return None, st
+        for _ in range(W):
+            rq.rpcholqr_cholqr2(plan, A, Q=Q, R=R, info=info, stream=stream)
+        barrier(dist)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            rq.rpcholqr_cholqr2(plan, A, Q=Q, R=R, info=info, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        barrier(dist)
+        return ms, info.cpu().tolist()[0]
+    finally:
+        plan.close()
+
+
+def run_config2(args, rq, torch, local, dev, dist, stream, ws, sweep=True):
+    """The 2^20 x 128 workload (sigma log-spaced, s = 3n) in SPLIT64 and FP64.  "split"/"fp64" are the
+    kappa = 1e8, s = 3n figures; with `sweep`, "kappa_sweep" repeats both modes for kappa in
+    {1, 1e4, 1e8, 1e12, 1e16} and s in {3n, 10n}, each entry with matrices/s, status, orthogonality and
+    residual, and Cholesky-QR2 on the same A beside each kappa (its breakdown is the reference point)."""
     import inputs
-    m, n, kappa = CONFIGS[2]
-    s = 3 * n
-    A = inputs.usv_torch(m, n, kappa, args.seed + 7, dev)
-    Q = torch.empty_like(A)
+    m, n, kappa0 = CONFIGS[2]
+    Q = torch.empty((m, n), dtype=torch.float64, device=dev)
     R = torch.empty((n, n), dtype=torch.float64, device=dev)
     info = torch.empty(2, dtype=torch.int32, device=dev)
-    out = {"workload": f"rpCholesky-QR m={m} n={n} s={s} kappa={kappa:g}", "m": m, "n": n, "s": s,
-           "kappa": kappa}
-    for mode in ("split", "fp64"):
-        ms, ph, calls, _, plan, _ = timed_factor(rq, torch, local, dev, dist, m, n, s, mode, A, Q, R, info, stream,
-                                                 args.steps, args.warmup)
-        plan.close()
-        st = info.cpu().tolist()
-        orth, res = (None, None) if args.no_metrics else gpu_metrics(A, Q, R)
-        out[mode] = {"value": ws * args.steps / (ms / 1e3), "unit": "matrices/s",
-                     "ms_per_step": ms / args.steps, "status": st[0], "orth": orth, "residual": res,
-                     "effective_tflops": alg_flops(m, n, s) * args.steps / (ms / 1e3) / 1e12,
-                     "phases_ms_per_step": phases_per_step(ph, calls)}
+    out = {"workload": f"rpCholesky-QR m={m} n={n} s={3 * n} kappa={kappa0:g}", "m": m, "n": n, "s": 3 * n,
+           "kappa": kappa0}
+    entries, cq2 = [], []
+    for kappa in (KAPPA_SWEEP if sweep else (kappa0,)):
+        A = inputs.usv_torch(m, n, kappa, args.seed + 7, dev)
+        for s in ((3 * n, 10 * n) if sweep else (3 * n,)):
+            for mode in ("split", "fp64"):
+                ms, ph, calls, _, plan, _ = timed_factor(rq, torch, local, dev, dist, m, n, s, mode, A, Q, R, info,
+                                                         stream, args.steps, args.warmup)
+                plan.close()
+                st = info.cpu().tolist()
+                orth, res = (None, None) if args.no_metrics else gpu_metrics(A, Q, R)
+                e = {"kappa": kappa, "s": s, "mode": mode, "value": ws * args.steps / (ms / 1e3),
+                     "unit": "matrices/s", "ms_per_step": ms / args.steps, "status": st[0], "orth": orth,
+                     "residual": res, "effective_tflops": alg_flops(m, n, s) * args.steps / (ms / 1e3) / 1e12}
+                entries.append(e)
+                if kappa == kappa0 and s == 3 * n:
+                    out[mode] = dict(e, phases_ms_per_step=phases_per_step(ph, calls))
+        if sweep:
+            ms, st = timed_cholqr2(rq, torch, local, dev, dist, A, Q, R, info, stream, args.steps, args.warmup)
+            orth, res = (None, None) if (args.no_metrics or st != 0) else gpu_metrics(A, Q, R)
+            cq2.append({"kappa": kappa, "status": rq.rpcholqr_status_string(st),
+                        "value": None if ms is None else ws * args.steps / (ms / 1e3), "unit": "matrices/s",
+                        "ms_per_step": None if ms is None else ms / args.steps, "orth": orth, "residual": res})
+        del A
+        torch.cuda.empty_cache()
     out["split_over_fp64"] = out["split"]["value"] / out["fp64"]["value"]
-    del A, Q
+    if sweep:
+        out["kappa_sweep"] = entries
+        out["cholqr2"] = cq2
+    del Q
     torch.cuda.empty_cache()
     return out
 
@@ -638,6 +694,12 @@ def run_ours(args, ws, rank, local):
         config2 = run_config2(args, rq, torch, local, dev, dist, stream, ws)
         if not args.no_config4:
             config4 = run_config4(args, rq, torch, local, dev, dist, ws)
+    elif args.kappa_sweep:
+        plan.close()
+        plan = None
+        del A, Q
+        torch.cuda.empty_cache()
+        config2 = run_config2(args, rq, torch, local, dev, dist, stream, ws)
 
     if rank != 0:
         if plan is not None:
@@ -675,8 +737,11 @@ def run_ours(args, ws, rank, local):
         roofline = dict(rooflines[dom])
         roofline["class"] = dom
         roofline["algorithmic_bytes_per_launch"] = class_bytes(dom, args.mode, m, n) / roofline["launches_per_step"]
-        roofline["traffic"] = traffic_from_profiles(f"{dom} n={n}", os.path.join(
-            ROOT, "paper_2406_11751_gb300", "csrc", CLASS_SOURCE[dom]), m)
+        roofline["traffic"] = traffic_from_profiles(dom, n, os.path.join(
+            ROOT, "paper_2406_11751_gb300", "csrc", CLASS_SOURCE[dom]), m, roofline["launches_per_step"])
+        for cls, r in rooflines.items():
+            r["traffic"] = traffic_from_profiles(cls, n, os.path.join(
+                ROOT, "paper_2406_11751_gb300", "csrc", CLASS_SOURCE[cls]), m, r["launches_per_step"])
 
     cpu = None
     if not args.no_cpu_baseline and N == 1:

@@ -1890,11 +1890,11 @@ rpcholqr_status rpcholqr_autotune(rpcholqr_plan p, int32_t nclasses, const int64
         // candidates: the built-in rules first, then the alternatives of each parameter
         std::vector<Tuning> cands(1);
         if (p->mode == RPCHOLQR_SPLIT64) {
+            cands.clear();
             const int nh = ozaki_gram_halves(np);
             const int plain = p->grid / nh > 0 ? p->grid / nh : 1;
-            for (int sub : {32, 16})
+            for (int sub : {kSplitSub, 16})   // the built-in width first; gram_ranges 0 = the wave rule
                 for (int gr : {0, plain, 2 * plain}) {
-                    if (sub == 32 && gr == 0) continue;
                     Tuning t;
                     t.split_sub = sub;
                     t.gram_ranges = gr > p->nparts ? p->nparts : gr;

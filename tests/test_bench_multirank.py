@@ -52,8 +52,8 @@ def test_bench_rank_logic_world2():
 
 
 def test_traffic_from_profiles_scales_and_checks_source(tmp_path, monkeypatch):
-    # the recorded DRAM bytes of a row pass are used only for an unchanged kernel source, and scaled
-    # from the captured row count to the run's
+    # a class's recorded DRAM bytes (one call's total at the captured rows) are used only for an unchanged
+    # kernel source, scaled from the captured row count to the run's and split over the call's launches
     sys.path.insert(0, ROOT)
     import bench
     src = tmp_path / "k.cu"
@@ -63,11 +63,13 @@ def test_traffic_from_profiles_scales_and_checks_source(tmp_path, monkeypatch):
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "traffic.txt").write_text(
-        "# comment\n"
-        f"kernel=k_rowpass<32,false> src_sha={sha} dram_bytes_per_launch=1000 measured_m=1024\n"
-        "kernel=k_rowpass<128,true> src_sha=0000000000000000 dram_bytes_per_launch=5 measured_m=1\n")
+        "# class=split_gemm n=512 src_sha=" + sha + " dram_bytes_per_call=1 measured_m=1 (a comment)\n"
+        f"class=split_gemm n=512 src_sha={sha} dram_bytes_per_call=1000 measured_m=1024\n"
+        f"class=split_gemm n=128 src_sha={sha} dram_bytes_per_call=64 measured_m=1024\n"
+        "class=rowpass n=512 src_sha=0000000000000000 dram_bytes_per_call=5 measured_m=1\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.traffic_from_profiles("k_rowpass<32,false>", str(src)) == 1000.0
-    assert bench.traffic_from_profiles("k_rowpass<32,false>", str(src), 256) == 250.0
-    assert bench.traffic_from_profiles("k_rowpass<128,true>", str(src), 1) is None      # source changed
-    assert bench.traffic_from_profiles("k_rowpass<64,false>", str(src), 1) is None     # never captured
+    assert bench.traffic_from_profiles("split_gemm", 512, str(src), 1024, 1) == 1000.0
+    assert bench.traffic_from_profiles("split_gemm", 512, str(src), 4096, 8) == 500.0
+    assert bench.traffic_from_profiles("split_gemm", 128, str(src), 2048, 2) == 64.0
+    assert bench.traffic_from_profiles("rowpass", 512, str(src), 1, 1) is None        # source changed
+    assert bench.traffic_from_profiles("split_gram", 512, str(src), 1, 1) is None     # never captured
