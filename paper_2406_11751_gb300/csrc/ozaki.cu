@@ -91,6 +91,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
         "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
 }
+// Instruction descriptor: BF16 x BF16 -> FP32, A and B K-major, M = 128, N = n (a multiple of 16, <= 256)
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+           (static_cast<uint32_t>(kTileM >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16_n(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
         smem_u32(bar)));
@@ -293,12 +304,13 @@ __device__ __forceinline__ void drain_acc(uint32_t tmem, int warp, int col0, lon
     }
 }
 
-// Issue the 72 MMAs of one stage: all pairs (a, b), a + b <= 9, for the two K=16 steps.
+// Issue the 72 MMAs of one stage: all pairs (a, b), a + b <= 9, for the two K=16 steps, one N = 64 MMA
+// per pair (any slice stride of B: used when B's slices are not stored back to back).
 // first_window: the stage starts an exactness window (the first MMA into each accumulator clears it).
 // The descriptors of the stage's two base addresses are formed once; every MMA adds its (constant)
 // offset to the 14-bit start field, which cannot carry (shared memory < 256 KB).
-__device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, uint32_t b_base,
-                                           uint32_t b_slice_bytes, bool first_window) {
+__device__ __forceinline__ void issue_stage_pairs(uint32_t tmem, uint32_t a_base, uint32_t b_base,
+                                                  uint32_t b_slice_bytes, bool first_window) {
     const uint64_t a0 = sdesc(a_base), b0 = sdesc(b_base);
     const uint32_t bstep = b_slice_bytes >> 4;
 #pragma unroll
@@ -314,6 +326,31 @@ __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, uint
                 const uint32_t acc = (first_window && kk == 0 && a == alo) ? 0u : 1u;
                 mma_bf16(tmem + (d - 2) * kTileN, ad, bd, acc);
             }
+        }
+    }
+}
+
+// The same 36 pairs per K = 16 step in 12 MMAs, for B slices stored back to back (kBSlice apart: the
+// eight 64-row slices form one 512-row operand in the same core-matrix layout).  For slice a of X the
+// pairs (a, b), b = 1 .. 9 - a, go to the groups d = a + b, whose accumulators are adjacent 64-column
+// ranges of tensor memory: one MMA with N = 64 nb multiplies slice a by nb consecutive B slices at once
+// (N <= 256, so slices 1-4 and 5-8 are two MMAs).  Same products, same exact integer sums.
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, uint32_t b_base, bool first_window) {
+    const uint64_t a0 = sdesc(a_base), b0 = sdesc(b_base);
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+        for (int a = 1; a <= 8; ++a) {
+            const int nb = 9 - a;
+            const int n1 = nb < 4 ? nb : 4;
+            const uint64_t ad = a0 + static_cast<uint32_t>(((a - 1) * kASlice + kk * 256) >> 4);
+            const uint32_t acc = (first_window && kk == 0 && a == 1) ? 0u : 1u;
+            mma_bf16_n(tmem + (a - 1) * kTileN, ad, b0 + static_cast<uint32_t>(kk * 16), idesc_bf16(kTileN * n1),
+                       acc);
+            if (nb > 4)
+                mma_bf16_n(tmem + (a + 3) * kTileN, ad,
+                           b0 + static_cast<uint32_t>((4 * kBSlice) >> 4) + static_cast<uint32_t>(kk * 16),
+                           idesc_bf16(kTileN * (nb - 4)), acc);
         }
     }
 }
@@ -498,6 +535,15 @@ __device__ __forceinline__ int tile_stages(int tn, int nkw, bool tri) {
     return last < nkw ? last : nkw;
 }
 
+// Column tile of tile t (row tile t / ntn).  With a triangular Y the tiles' costs differ (2 (tn + 1)
+// stages), and a grid that is a multiple of ntn would give every CTA one fixed tn: the column tile is
+// rotated by the row tile, so a CTA's tiles t, t + gridDim.x, ... cycle through all tn, while the ntn
+// tiles of one row tile still run side by side (their A stages shared in L2).
+__device__ __forceinline__ int tile_col(int64_t t, int ntn, bool tri) {
+    const int j = static_cast<int>(t % ntn);
+    return tri ? static_cast<int>((j + t / ntn) % ntn) : j;
+}
+
 // Walks the stages of the output tiles one CTA owns (tiles t = blockIdx.x, + gridDim.x, ...; stages
 // kw = 0 .. tile_stages - 1 of each).
 struct StageWalk {
@@ -506,14 +552,14 @@ struct StageWalk {
     bool tri;
     __device__ __forceinline__ StageWalk(int ntn_, int nkw_, bool tri_)
         : t(blockIdx.x), kw(0), ntn(ntn_), nkw(nkw_), tri(tri_) {
-        tn = static_cast<int>(t % ntn);
+        tn = tile_col(t, ntn, tri);
         nk = tile_stages(tn, nkw, tri);
     }
     __device__ __forceinline__ void advance() {
         if (++kw == nk) {
             kw = 0;
             t += gridDim.x;
-            tn = static_cast<int>(t % ntn);
+            tn = tile_col(t, ntn, tri);
             nk = tile_stages(tn, nkw, tri);
         }
     }
@@ -568,7 +614,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
     int64_t nstages = 0;
     if (tri) {
         for (int64_t u = 0; u < my_tiles; ++u)
-            nstages += tile_stages(static_cast<int>((blockIdx.x + u * gridDim.x) % ntn), nkw, true);
+            nstages += tile_stages(tile_col(blockIdx.x + u * gridDim.x, ntn, true), nkw, true);
     } else {
         nstages = my_tiles * nkw;
     }
@@ -586,7 +632,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
                 }
                 fphase[s] ^= 1u;
                 tc_after_sync();
-                issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), kBSlice, (wk.kw & 3) == 0);
+                issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), (wk.kw & 3) == 0);
                 mma_commit(&empty_bar[s]);
             }
             // every MMA issued here is complete before the tensor memory is released
@@ -741,33 +787,22 @@ constexpr int kUpdMaxN = 128;
 constexpr int kUpdProducers = 4, kUpdDrainers = 16;
 constexpr int kUpdThreads = 32 * (kUpdProducers + kUpdDrainers + 1);
 constexpr int kUpdSmem = 2 * kAStage + (kUpdMaxN / kTileN) * kBStage;   // 192 KB
-constexpr uint32_t kIdescN32 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kUpdTileN >> 3) << 17) |
-                               ((uint32_t)(kTileM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16_n32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-        "l"(ad), "l"(bd), "r"(kIdescN32), "r"(acc));
-}
-
+constexpr int kUpdBSlice = kUpdTileN * kKW * 2;                          // 2 KB: one slice of a 32-column tile
+constexpr int kUpdBTile = kSlices * kUpdBSlice;                          // 16 KB: its eight slices
 // The 36 slice pairs of one 32-column tile for nkk K steps of 16 (group d into columns (d - 2) * 32 of
-// the tile's TMEM buffer); the first MMA into each group clears it.
+// the tile's TMEM buffer), 8 MMAs per step: the tile's eight B slices lie back to back (2 KB apart, one
+// 256-row operand), so slice a of X meets slices b = 1 .. 9 - a in one MMA with N = 32 (9 - a) whose
+// accumulators d = a + 1 .. 9 are adjacent.  The first MMA (a = 1, all eight groups) clears them.
 __device__ __forceinline__ void issue_tile_n32(uint32_t tmem, uint32_t a_base, uint32_t b_base, int nkk) {
     const uint64_t a0 = sdesc(a_base), b0 = sdesc(b_base);
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
         if (kk >= nkk) break;
 #pragma unroll
-        for (int d = 2; d <= 9; ++d) {
-            const int alo = d - 8 > 1 ? d - 8 : 1, ahi = d - 1 < 8 ? d - 1 : 8;
-#pragma unroll
-            for (int a = alo; a <= ahi; ++a) {
-                const int b = d - a;
-                const uint64_t ad = a0 + static_cast<uint32_t>(((a - 1) * kASlice + kk * 256) >> 4);
-                const uint64_t bd = b0 + static_cast<uint32_t>(((b - 1) * kBSlice + kk * 256) >> 4);
-                mma_bf16_n32(tmem + (d - 2) * kUpdTileN, ad, bd, (kk == 0 && a == alo) ? 0u : 1u);
-            }
+        for (int a = 1; a <= 8; ++a) {
+            const uint64_t ad = a0 + static_cast<uint32_t>(((a - 1) * kASlice + kk * 256) >> 4);
+            mma_bf16_n(tmem + (a - 1) * kUpdTileN, ad, b0 + static_cast<uint32_t>(kk * 16),
+                       idesc_bf16(kUpdTileN * (9 - a)), (kk == 0 && a == 1) ? 0u : 1u);
         }
     }
 }
@@ -783,7 +818,7 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
     if (load_status(info) != 0) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint8_t* stA[2] = {sm, sm + kAStage};
-    uint8_t* yres = sm + 2 * kAStage;                 // Y slices: 64-column block j at j * kBStage
+    uint8_t* yres = sm + 2 * kAStage;                 // Y slices: 32-column tile j at j * kUpdBTile
     const int nsub = (N + kUpdTileN - 1) / kUpdTileN;
     const int nkk = (K + 15) / 16;
     const int64_t ntm = (m + kTileM - 1) / kTileM;
@@ -808,12 +843,17 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
         asm volatile("fence.mbarrier_init.release.cluster;\n");
         abort_s = 0;
     }
-    // the Y slices of every column block (K <= 32: one K stage each), resident for the launch
+    // the Y slices of every column block (K <= 32: one K stage each), resident for the launch, regrouped
+    // per 32-column tile u: its slice b (rows 32 (u & 1).. of slice b of 64-column block u / 2, 2 KB) at
+    // u * kUpdBTile + b * 2 KB
     {
         const int bytes = ((N + kTileN - 1) / kTileN) * kBStage;
         for (int e = tid; e < bytes / 16; e += kUpdThreads) {
+            const int u = e / (kUpdBTile / 16), r = e - u * (kUpdBTile / 16);
+            const int b = r / (kUpdBSlice / 16), o = r - b * (kUpdBSlice / 16);
             const unsigned dst = smem_u32(yres + 16 * e);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(yblocks + 16 * e));
+            const uint8_t* src = yblocks + static_cast<size_t>(u >> 1) * kBStage + b * kBSlice + (u & 1) * kUpdBSlice + 16 * o;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
         }
         cp_async_commit();
         cp_async_wait_all();
@@ -920,7 +960,7 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
                         break;
                     }
                     tc_after_sync();
-                    const uint32_t bbase = smem_u32(yres) + (j >> 1) * kBStage + (j & 1) * (kUpdTileN / 8) * kSBO;
+                    const uint32_t bbase = smem_u32(yres) + j * kUpdBTile;
                     issue_tile_n32(tmem + 256u * b, smem_u32(stA[s]), bbase, nkk);
                     mma_commit(&acc_full[b]);
                 }
@@ -1019,10 +1059,10 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
                 }
                 fphase[s] ^= 1u;
                 tc_after_sync();
-                if (b_inside)
-                    issue_stage(tmem, smem_u32(stA[s]), smem_u32(stA[s]) + boff, kASlice, (st & 3) == 0);
+                if (!PRE && b_inside)
+                    issue_stage_pairs(tmem, smem_u32(stA[s]), smem_u32(stA[s]) + boff, kASlice, (st & 3) == 0);
                 else
-                    issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), kBSlice, (st & 3) == 0);
+                    issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), (st & 3) == 0);
                 mma_commit(&empty_bar[s]);
             }
             mma_commit(&done_bar);
@@ -1083,8 +1123,9 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
                     const unsigned dst = smem_u32(stA[s] + 16 * e);
                     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(asrc + 16 * e));
                 }
-                if (!b_inside) {
-                    // columns 64 Qb .. 64 Qb + 63: half (Qb & 1) of every slice of block Qb / 2's image
+                {
+                    // columns 64 Qb .. 64 Qb + 63: half (Qb & 1) of every slice of block Qb / 2's image (P's own
+                    // image when they lie inside the P block), copied back to back for the stacked MMAs
                     const uint8_t* bsrc = gimg + static_cast<size_t>((Qb >> 1) * nsg + sg) * kAStage +
                                           (Qb & 1) * kBSlice;
                     for (int e = tid; e < kBStage / 16; e += NT) {
