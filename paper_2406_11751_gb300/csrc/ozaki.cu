@@ -47,9 +47,9 @@ template <int NT> struct Share {
 };
 constexpr int kDrainCols = Share<kThreads>::kDrainCols;
 constexpr int kChunks = Share<kThreads>::kChunks;
-// The windowed GEMM (K > 128) keeps int64 accumulators live across stages: 256 threads leave it the
-// registers (512 threads cap a thread at 128).
-constexpr int kThreadsWin = 256;
+// The windowed GEMM (K > 128) keeps int64 accumulators live across stages (16 columns per thread with 512
+// threads, drained 4 columns at a time to fit the 120 registers a 544-thread CTA allows).
+constexpr int kThreadsWin = 512;
 constexpr int kSBO = (kKW * 2 / 16) * 128; // 512 B between 8-row core-matrix groups
 constexpr int kLBO = 128;                  // 128 B between K-adjacent core matrices
 constexpr int kASlice = kTileM * kKW * 2;  // 8 KB
@@ -145,6 +145,34 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, con
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
+// Pre-sliced stages arrive by bulk copies (the TMA engine, no tensor map): the issuing thread arms the
+// stage's load barrier with the byte count, and each copy completes its share of the transaction on it.
+// Sizes are multiples of 16 bytes and both addresses 16-byte aligned (64 KB / 4 KB / 32 KB images at
+// 1 KB-aligned stage buffers).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Before a kernel that issued bulk copies returns (also after a timeout): the last copy issued into each
+// stage buffer has landed (parity of its phase), bounded like every wait.
+__device__ __forceinline__ bool bulk_drain(uint64_t* load_bar, const int64_t (&issued)[2]) {
+    bool ok = true;
+    for (int b = 0; b < 2; ++b)
+        if (issued[b] > 0) {
+            const uint32_t par = static_cast<uint32_t>((issued[b] - 1) & 1);
+            uint32_t done = 0;
+            for (long it = 0; it < kSpinLimit && !done; ++it) done = mbar_try(&load_bar[b], par);
+            ok = ok && done;
+        }
+    return ok;
+}
+
 // Barrier 1 over the n producer threads only (the MMA warp does not take part).
 __device__ __forceinline__ void prod_sync(int n) { asm volatile("bar.sync 1, %0;\n" ::"r"(n) : "memory"); }
 __device__ __forceinline__ bool prod_sync_or(bool v, int n) {
@@ -463,7 +491,7 @@ __device__ __forceinline__ void gemm_store_tile(uint32_t tmem, int warp, int tid
     const int ncols = N - col0 < kTileN ? N - col0 : kTileN;
     double* wr = W + lr * kEpiLd + NC * rq;
     if (WIN) {
-        drain_acc<true>(tmem, warp, NC * rq, acc);
+        drain_acc<true, NC, 4>(tmem, warp, NC * rq, acc);
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
             const int col = col0 + NC * rq + j;
@@ -507,7 +535,8 @@ __device__ __forceinline__ void gemm_store_tile(uint32_t tmem, int warp, int tid
             else C[row * ldc + col0 + c] = W[r * kEpiLd + c];
         }
     }
-    prod_sync(NT);   // W (a stage buffer) is free again
+    fence_async_smem();   // the next bulk copy into this buffer (async proxy) follows these accesses
+    prod_sync(NT);        // W (a stage buffer) is free again
 }
 
 // ---- C = X Y (SUB = false: pass 2, Q = A_1 R_1^{-1}) or C = B - X Y (SUB = true: the off-diagonal block
@@ -575,7 +604,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
                 int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, long spin, int tri,
                 const uint8_t* __restrict__ aimg) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    __shared__ uint64_t empty_bar[2], full_bar[2], done_bar;
+    __shared__ uint64_t empty_bar[2], full_bar[2], load_bar[2], done_bar;
     __shared__ uint32_t tslot;
     __shared__ int abort_s;
     if (load_status(info) != 0) return;
@@ -595,6 +624,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
         for (int i = 0; i < 2; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty_bar[i])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full_bar[i])), "r"(NT / 32));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&load_bar[i])));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&done_bar)));
         asm volatile("fence.mbarrier_init.release.cluster;\n");
@@ -622,15 +652,17 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
     if (warp == NT / 32) {
         // MMA warp: one lane issues every stage once the producers have filled it
         if (lane == 0) {
-            uint32_t fphase[2] = {0u, 0u};
+            uint32_t fphase[2] = {0u, 0u}, lphase[2] = {0u, 0u};
             StageWalk wk(ntn, nkw, tri != 0);
             for (int64_t g = 0; g < nstages; ++g, wk.advance()) {
                 const int s = static_cast<int>(g & 1);
-                if (!mbar_wait_ab(&full_bar[s], fphase[s], &abort_s, spin)) {
+                if (!mbar_wait_ab(&full_bar[s], fphase[s], &abort_s, spin) ||
+                    (PRE && !mbar_wait_ab(&load_bar[s], lphase[s], &abort_s, spin))) {
                     abort_s = 1;
                     break;
                 }
                 fphase[s] ^= 1u;
+                lphase[s] ^= 1u;
                 tc_after_sync();
                 issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), (wk.kw & 3) == 0);
                 mma_commit(&empty_bar[s]);
@@ -646,6 +678,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
         uint32_t phase[2] = {0u, 0u};
         bool pending[2] = {false, false};
         bool timed_out = false;
+        int64_t issued[2] = {0, 0};         // bulk copies issued into each stage buffer (PRE, thread 0)
         long long acc[NC];
 #pragma unroll
         for (int j = 0; j < NC; ++j) acc[j] = 0;
@@ -670,22 +703,23 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
                 phase[s] ^= 1u;
                 pending[s] = false;
             }
-            // B slices of stage g: one contiguous 32 KB block, 16-byte cp.async granules
+            // B slices of stage g: one contiguous 32 KB block
             const uint8_t* src = yblocks + static_cast<size_t>((tn * nkw + kw) * kSlices) * kBSlice;
-            for (int e = tid; e < kBStage / 16; e += NT) {
-                const unsigned dst = smem_u32(stB[s] + 16 * e);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 16 * e));
-            }
             if constexpr (PRE) {
-                // the stage's A slices, made beforehand in this layout: one contiguous 64 KB block
-                const uint8_t* asrc = aimg + static_cast<size_t>(tm * nkw + kw) * kAStage;
-                for (int e = tid; e < kAStage / 16; e += NT) {
-                    const unsigned dst = smem_u32(stA[s] + 16 * e);
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(asrc + 16 * e));
+                // the stage's A slices, made beforehand in this layout (one contiguous 64 KB block), and B:
+                // two bulk copies on the stage's load barrier; the producers do not wait for them
+                if (tid == 0) {
+                    const uint8_t* asrc = aimg + static_cast<size_t>(tm * nkw + kw) * kAStage;
+                    mbar_expect_tx(&load_bar[s], kStageBytes);
+                    bulk_g2s(stB[s], src, kBStage, &load_bar[s]);
+                    bulk_g2s(stA[s], asrc, kAStage, &load_bar[s]);
+                    ++issued[s];
                 }
-                cp_async_commit();
-                asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // A and B of stage g
             } else {
+                for (int e = tid; e < kBStage / 16; e += NT) {
+                    const unsigned dst = smem_u32(stB[s] + 16 * e);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 16 * e));
+                }
                 cp_async_commit();
                 // the raw X rows of stage g (copied during stage g - 1) are complete: slice this thread's row
                 asm volatile("cp.async.wait_group 1;\n" ::: "memory");
@@ -731,7 +765,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
 #pragma unroll
                     for (int j = 0; j < NC; ++j) acc[j] = 0;
                 } else if (WIN) {
-                    drain_acc<true>(tmem, warp, NC * rq, acc);
+                    drain_acc<true, NC, 4>(tmem, warp, NC * rq, acc);
                 }
             }
             if (kw == 0) {
@@ -761,6 +795,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
                                              reinterpret_cast<double*>(stA[0]), acc);
             }
         }
+        if (PRE && tid == 0 && !bulk_drain(load_bar, issued)) timed_out = true;
         if (timed_out) abort_s = 1;
     }
 
@@ -1010,7 +1045,7 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
              const int32_t* __restrict__ colexp, int64_t rows_per, int ntiles, double* __restrict__ gpart,
              int32_t* info, long spin, const uint8_t* __restrict__ gimg, int accum) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    __shared__ uint64_t empty_bar[2], full_bar[2], done_bar;
+    __shared__ uint64_t empty_bar[2], full_bar[2], load_bar[2], done_bar;
     __shared__ uint32_t tslot;
     __shared__ int abort_s;
     if (load_status(info) != 0) return;
@@ -1036,6 +1071,7 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
         for (int i = 0; i < 2; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty_bar[i])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full_bar[i])), "r"(NT / 32));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&load_bar[i])));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&done_bar)));
         asm volatile("fence.mbarrier_init.release.cluster;\n");
@@ -1049,15 +1085,17 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
 
     if (warp == NT / 32) {
         if (lane == 0) {
-            uint32_t fphase[2] = {0u, 0u};
+            uint32_t fphase[2] = {0u, 0u}, lphase[2] = {0u, 0u};
             const uint32_t boff = b_inside ? static_cast<uint32_t>(((64 * Qb - 128 * P) / 8) * kSBO) : 0u;
             for (int64_t st = 0; st < nstages; ++st) {
                 const int s = static_cast<int>(st & 1);
-                if (!mbar_wait_ab(&full_bar[s], fphase[s], &abort_s, spin)) {
+                if (!mbar_wait_ab(&full_bar[s], fphase[s], &abort_s, spin) ||
+                    (PRE && !mbar_wait_ab(&load_bar[s], lphase[s], &abort_s, spin))) {
                     abort_s = 1;
                     break;
                 }
                 fphase[s] ^= 1u;
+                lphase[s] ^= 1u;
                 tc_after_sync();
                 if (!PRE && b_inside)
                     issue_stage_pairs(tmem, smem_u32(stA[s]), smem_u32(stA[s]) + boff, kASlice, (st & 3) == 0);
@@ -1082,6 +1120,7 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
         uint32_t phase[2] = {0u, 0u};
         bool pending[2] = {false, false};
         bool timed_out = false;
+        int64_t issued[2] = {0, 0};         // bulk copies issued into each stage buffer (PRE, thread 0)
 
         // Drain the window just finished (its MMAs complete) into acc; every 64 windows, and at the end,
         // add acc into the CTA's FP64 partial (the first flush initialises it) and clear it.
@@ -1117,26 +1156,21 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
             }
             const int64_t k0 = r0 + st * kKW;
             if constexpr (PRE) {
-                const int64_t sg = k0 / kKW, nsg = (m + kKW - 1) / kKW;
-                const uint8_t* asrc = gimg + static_cast<size_t>(P * nsg + sg) * kAStage;
-                for (int e = tid; e < kAStage / 16; e += NT) {
-                    const unsigned dst = smem_u32(stA[s] + 16 * e);
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(asrc + 16 * e));
-                }
-                {
-                    // columns 64 Qb .. 64 Qb + 63: half (Qb & 1) of every slice of block Qb / 2's image (P's own
-                    // image when they lie inside the P block), copied back to back for the stacked MMAs
+                // A: the P block's 64 KB stage image; B (columns 64 Qb .. 64 Qb + 63): half (Qb & 1) of every
+                // slice of block Qb / 2's image (P's own when they lie inside the P block), eight 4 KB pieces
+                // placed back to back for the stacked MMAs.  Bulk copies on the stage's load barrier.
+                if (tid == 0) {
+                    const int64_t sg = k0 / kKW, nsg = (m + kKW - 1) / kKW;
+                    const uint8_t* asrc = gimg + static_cast<size_t>(P * nsg + sg) * kAStage;
                     const uint8_t* bsrc = gimg + static_cast<size_t>((Qb >> 1) * nsg + sg) * kAStage +
                                           (Qb & 1) * kBSlice;
-                    for (int e = tid; e < kBStage / 16; e += NT) {
-                        const int a = e / (kBSlice / 16), o = e - a * (kBSlice / 16);
-                        const unsigned dst = smem_u32(stB[s] + a * kBSlice + 16 * o);
-                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst),
-                                     "l"(bsrc + static_cast<size_t>(a) * kASlice + 16 * o));
-                    }
+                    mbar_expect_tx(&load_bar[s], kAStage + kBStage);
+                    bulk_g2s(stA[s], asrc, kAStage, &load_bar[s]);
+#pragma unroll
+                    for (int a = 0; a < kSlices; ++a)
+                        bulk_g2s(stB[s] + a * kBSlice, bsrc + static_cast<size_t>(a) * kASlice, kBSlice, &load_bar[s]);
+                    ++issued[s];
                 }
-                cp_async_commit();
-                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
             }
             if constexpr (!PRE) {
 #pragma unroll
@@ -1190,6 +1224,7 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
                 }
             if (!timed_out) drain_window(true);
         }
+        if (PRE && tid == 0 && !bulk_drain(load_bar, issued)) timed_out = true;
         if (timed_out) {
             abort_s = 1;
         } else if (nstages == 0 && p < np && !accum) {
