@@ -431,8 +431,9 @@ SPLIT_CLASSES = ("split_update", "split_gemm_sub", "split_gemm", "split_gram")
 KERNEL_NAMES = {
     "rowpass": "k_rowpass (FP64 row solves: mma.sync m16n8k16 + DFMA)",
     "split_update": "oz::k_ozaki_update (split C = B - X Y, K <= 32)",
-    "split_gemm_sub": "oz::k_ozaki_gemm_ws<.,SUB> (split C = B - X Y, wide pass-1 block updates)",
-    "split_gemm": "oz::k_ozaki_gemm_ws (split Q = A1 R1^-1)",
+    "split_gemm_sub": "oz::k_ozaki_gemm_db<SUB> (n > 128; k_ozaki_gemm_ws<.,SUB> up to 128) (split C = B - X Y, "
+                      "wide pass-1 block updates)",
+    "split_gemm": "oz::k_ozaki_gemm_db (n > 128; k_ozaki_gemm_ws up to 128) (split Q = A1 R1^-1)",
     "split_gram": "oz::k_ozaki_gram (split G1 = A1^T A1)",
     "fp64_gemm": "k_gemm_sub_fp64 (FP64 block updates)",
     "fp64_syrk": "k_syrk_fp64 (FP64 Gram)",

@@ -54,11 +54,15 @@ void launch_ozaki_slice_cols(const double* Y, int64_t ldy, int K, int N, uint8_t
 cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int32_t* xexp, int K,
                               const uint8_t* yblocks, const int32_t* yexp, int N, const double* B,
                               int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, int grid,
-                              cudaStream_t st, long spin, bool y_upper, const uint8_t* aimg);
+                              cudaStream_t st, long spin, bool y_upper, const uint8_t* aimg, int img_nkw,
+                              const int32_t* bexp, int64_t ld_bexp);
 size_t ozaki_image_bytes(int64_t m, int K);
 void launch_slice_images(const double* X, int64_t ldx, int64_t m, int K, const int32_t* xexp, uint8_t* img,
                          const int32_t* info, cudaStream_t st);
+void launch_slice_block_images(const double* X, int64_t ldx, int64_t m, int nc, uint8_t* img, int img_nkw, int kw0,
+                               int32_t* bexp, const int32_t* info, cudaStream_t st);
 int ozaki_gram_halves(int np);
+int ozaki_gram_tiles(int np, bool images);
 cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
                               int nranges, double* gpart, int32_t* info, cudaStream_t st, long spin,
                               const uint8_t* gimg, bool accum);
@@ -213,6 +217,7 @@ struct rpcholqr_plan_s {
     int32_t* yexp = nullptr;    // np
     uint8_t* yblocks = nullptr; // Ozaki column slices (K, N <= np)
     uint8_t* aimg = nullptr;    // stage images of A1's row slices for pass 2 (np > 128), img_rows rows
+    int32_t* bexp = nullptr;    // per 64-column block of the image, the row bounds of that block (img_rows each)
     int64_t img_rows = 0;
     double* W = nullptr;        // np x np
     int32_t* gates = nullptr;   // split pass-2 gate words: {split status, pivot, fp64 status, pivot, used fp64}
@@ -310,7 +315,7 @@ bool shape_ok(const rpcholqr_plan_s* p, int64_t m, int32_t n, int32_t s) {
 
 // Records the start of `phase` (or the end of the call for phase == RPCHOLQR_NUM_PHASES) when
 // the plan times this call.
-constexpr int kMaxTimedLaunches = 256;   // per timed call
+constexpr int kMaxTimedLaunches = 1024;   // per timed call
 
 struct PhaseMarks {
     rpcholqr_plan_s* p;
@@ -670,12 +675,13 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
         const size_t oG = take(sizeof(int32_t) * 8);
         // pass 2 above 128 columns slices A1 once per row chunk into stage images (at most 8 GiB)
         int64_t img_rows = 0;
-        size_t oI = 0;
+        size_t oI = 0, oE = 0;
         if (np > static_cast<size_t>(kMaxNP)) {
             img_rows = (int64_t{1} << 33) / static_cast<int64_t>(np * 16) / 128 * 128;
             if (img_rows > (max_m + 127) / 128 * 128) img_rows = (max_m + 127) / 128 * 128;
             if (img_rows < 128) img_rows = 128;
             oI = take(ozaki_image_bytes(img_rows, static_cast<int>((np + 127) / 128 * 128)));
+            oE = take(sizeof(int32_t) * static_cast<size_t>(img_rows) * ((np + kBlk - 1) / kBlk));
         }
         if (cudaMalloc(&p->split_ws, off) != cudaSuccess) {
             cudaGetLastError();
@@ -693,6 +699,7 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
         p->gates = reinterpret_cast<int32_t*>(c + oG);
         if (img_rows > 0) {
             p->aimg = reinterpret_cast<uint8_t*>(c + oI);
+            p->bexp = reinterpret_cast<int32_t*>(c + oE);
             p->img_rows = img_rows;
         }
         if (cudaMemset(p->gates, 0, sizeof(int32_t) * 8) != cudaSuccess) cudaGetLastError();
@@ -837,7 +844,8 @@ static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const doub
                                            int64_t ldx, const double* Y, int N, int64_t ldy, const double* B,
                                            int64_t ldb, double* C, int64_t ldc, int32_t* info, cudaStream_t st,
                                            bool xexp_ready = false, int64_t row0 = 0, bool y_ready = false,
-                                           bool y_upper = false, const uint8_t* aimg = nullptr);
+                                           bool y_upper = false, const uint8_t* aimg = nullptr, int img_nkw = 0,
+                                           const int32_t* bexp = nullptr, int64_t ld_bexp = 0);
 
 // Diagonal-block setups for the blocked solve with T (n x n, ld ldt): block J (64 columns, the last
 // one ragged) gets frag + 4096 J and diag + 512 J.
@@ -914,6 +922,77 @@ static rpcholqr_status solve_split_right(rpcholqr_plan_s* p, const double* X, in
     return check_launch();
 }
 
+// The SPLIT64 first pass above 128 columns, Y = X T^{-1} (T = R_s upper triangular), left-looking over
+// 64-column blocks, one row chunk (p->img_rows rows) at a time so that the chunk's stage image holds the
+// slices of every finished block: block J of a chunk is first Y[:, J] = X[:, J] - Y[:, <J] T[<J, J], one
+// split product over the image of blocks < J (each block its own exactness window, sliced against the
+// row's bound over that block alone), then its sub-block FP64 row passes joined by a K = sub split update
+// (as in solve_blocked), and the finished block is sliced into the image once.  The row passes max-merge
+// the bounds of the whole row into p->xexp (pass 2 slices against them) and of each column into
+// p->colexp.  Marks PASS1_UPDATE / PASS1_SOLVE2 around the first chunk's first product.
+static rpcholqr_status solve_split_wide(rpcholqr_plan_s* p, const double* X, int64_t ldx, const double* T,
+                                        int64_t ldt, int64_t m, int n, double* Y, int64_t ldy, const double* frag,
+                                        const double* diag, int32_t* info, cudaStream_t st, const PhaseMarks* pm) {
+    const int img_nkw = (n + 31) / 32;
+    const int sub = split_sub(p);
+    bool marked = false;
+    for (int64_t r0 = 0; r0 < m; r0 += p->img_rows) {
+        const int64_t rows = m - r0 < p->img_rows ? m - r0 : p->img_rows;
+        const int grid = row_grid(p, rows);
+        const double* Xc = X + r0 * ldx;
+        double* Yc = Y + r0 * ldy;
+        for (int J = 0; J * kBlk < n; ++J) {
+            const int c0 = J * kBlk;
+            const int nj = n - c0 < kBlk ? n - c0 : kBlk;
+            if (J > 0) {
+                const bool mark = pm && !marked;
+                if (mark) pm->mark(RPCHOLQR_PHASE_PASS1_UPDATE);
+                rpcholqr_status rc = ozaki_gemm_internal(p, true, Yc, rows, c0, ldy, T + c0, nj, ldt, Xc + c0, ldx,
+                                                         Yc + c0, ldy, info, st, true, r0, false, false, p->aimg,
+                                                         img_nkw, p->bexp, p->img_rows);
+                if (rc != RPCHOLQR_OK) return rc;
+                if (mark) {
+                    pm->mark(RPCHOLQR_PHASE_PASS1_SOLVE2);
+                    marked = true;
+                }
+            }
+            for (int h = 0; h * sub < nj; ++h) {
+                const int c1 = c0 + h * sub;
+                const int nh = nj - h * sub < sub ? nj - h * sub : sub;
+                const bool from_input = J == 0 && h == 0;
+                const double* hsrc = (from_input ? Xc : Yc) + c1;
+                const int64_t lh = from_input ? ldx : ldy;
+                const int js = c1 / sub;
+                {
+                    KTimer kt(p, st, RPCHOLQR_KERNEL_ROWPASS, static_cast<double>(rows) * nh * nh);
+                    if (launch_rowpass_ex(false, pad16(nh), hsrc, lh, Yc + c1, ldy, rows, nh, frag + js * sub * sub,
+                                          diag + js * (sub / 8) * 64, nullptr, info, grid, st, true, p->xexp + r0,
+                                          c1 == 0 ? 1 : 2, p->colexp + c1) != cudaSuccess)
+                        return RPCHOLQR_ERR_CUDA;
+                }
+                ++p->launches;
+                const int rest = c0 + nj - (c1 + nh);
+                if (rest > 0) {
+                    // the block's first sub-block update reads its input columns (X for block 0, else the
+                    // product's output in Y), later ones the updated columns
+                    const double* B = (from_input ? Xc : Yc) + c1 + nh;
+                    const int64_t ldb = from_input ? ldx : ldy;
+                    rpcholqr_status rc = ozaki_gemm_internal(p, true, Yc + c1, rows, nh, ldy,
+                                                             T + static_cast<int64_t>(c1) * ldt + c1 + nh, rest, ldt,
+                                                             B, ldb, Yc + c1 + nh, ldy, info, st, true, r0);
+                    if (rc != RPCHOLQR_OK) return rc;
+                }
+            }
+            if (c0 + nj < n) {
+                launch_slice_block_images(Yc + c0, ldy, rows, nj, p->aimg, img_nkw, 2 * J,
+                                          p->bexp + static_cast<int64_t>(J) * p->img_rows, info, st);
+                ++p->launches;
+            }
+        }
+    }
+    return check_launch();
+}
+
 // Left-looking blocked row solve Y = X T^{-1} (T upper triangular, n x n, ld ldt) over 64-column
 // blocks J:  Y[:, J] = X[:, J] - Y[:, <J] T[<J, J]  (FP64 mma, or the split tensor-core product when
 // split), then Y[:, J] <- Y[:, J] T[J, J]^{-1} by the row pass (NP = 64; split: two 32-column row
@@ -935,19 +1014,7 @@ static rpcholqr_status solve_blocked(rpcholqr_plan_s* p, const double* X, int64_
         int64_t lsrc = ldx;
         if (J > 0) {
             if (pm && pass1_marks && J == 1) pm->mark(RPCHOLQR_PHASE_PASS1_UPDATE);
-            if (split && p->aimg) {
-                // A1[:, <J] sliced once per row chunk into stage images (against the running row bounds),
-                // then the product copies them: the same slices as slicing inside it, so the same bits
-                for (int64_t r0 = 0; r0 < m; r0 += p->img_rows) {
-                    const int64_t rows = m - r0 < p->img_rows ? m - r0 : p->img_rows;
-                    launch_slice_images(Y + r0 * ldy, ldy, rows, c0, p->xexp + r0, p->aimg, info, st);
-                    ++p->launches;
-                    rpcholqr_status rc = ozaki_gemm_internal(p, true, Y + r0 * ldy, rows, c0, ldy, T + c0, nj, ldt,
-                                                             X + r0 * ldx + c0, ldx, Y + r0 * ldy + c0, ldy, info, st,
-                                                             true, r0, r0 > 0, false, p->aimg);
-                    if (rc != RPCHOLQR_OK) return rc;
-                }
-            } else if (split) {
+            if (split) {
                 rpcholqr_status rc = ozaki_gemm_internal(p, true, Y, m, c0, ldy, T + c0, nj, ldt, X + c0, ldx,
                                                          Y + c0, ldy, info, st, true);
                 if (rc != RPCHOLQR_OK) return rc;
@@ -1124,7 +1191,7 @@ static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const doub
                                            int64_t ldx, const double* Y, int N, int64_t ldy, const double* B,
                                            int64_t ldb, double* C, int64_t ldc, int32_t* info, cudaStream_t st,
                                            bool xexp_ready, int64_t row0, bool y_ready, bool y_upper,
-                                           const uint8_t* aimg) {
+                                           const uint8_t* aimg, int img_nkw, const int32_t* bexp, int64_t ld_bexp) {
     int32_t* xexp = p->xexp + row0;
     if (!xexp_ready) {
         launch_row_exp(X, ldx, m, K, xexp, st);
@@ -1140,7 +1207,8 @@ static rpcholqr_status ozaki_gemm_internal(rpcholqr_plan p, bool sub, const doub
     {
         KTimer kt(p, st, ozaki_class(sub, K, N), ozaki_flops(sub, y_upper, m, K, N));
         if (launch_ozaki_gemm(sub, X, ldx, xexp, K, p->yblocks, p->yexp, N, B, ldb, C, ldc, m, info, grid, st,
-                              static_cast<long>(p->spin_limit), y_upper, aimg) !=
+                              static_cast<long>(p->spin_limit), y_upper, aimg,
+                              img_nkw > 0 ? img_nkw : (K + 31) / 32, bexp, ld_bexp) !=
             cudaSuccess)
             return RPCHOLQR_ERR_CUDA;
     }
@@ -1160,7 +1228,7 @@ static rpcholqr_status ozaki_gram_internal(rpcholqr_plan p, const double* X, int
     }
     // row ranges: the fewest that make (tiles x ranges) a whole number of waves over the SMs, so no SM
     // idles in the last wave (p->gpart holds p->nparts partials)
-    const int nh = ozaki_gram_halves(np);
+    const int nh = ozaki_gram_tiles(np, p->aimg != nullptr);
     int nranges = p->grid / nh;
     if (nranges > p->nparts) nranges = p->nparts;
     for (int r = nranges > 1 ? nranges : 1; r <= p->nparts; ++r)
@@ -1220,8 +1288,9 @@ static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m,
     } else {
         prep_blocks(p, p->Rs, np, n, p->frag_s, p->diag_s, info, st, split_sub(p));
         pm.mark(RPCHOLQR_PHASE_PASS1);
-        rc = solve_blocked(p, A, lda, p->Rs, np, m, n, A1, ld1, p->frag_s, p->diag_s, true, true, info, st, &pm,
-                           true);
+        rc = p->aimg ? solve_split_wide(p, A, lda, p->Rs, np, m, n, A1, ld1, p->frag_s, p->diag_s, info, st, &pm)
+                     : solve_blocked(p, A, lda, p->Rs, np, m, n, A1, ld1, p->frag_s, p->diag_s, true, true, info, st,
+                                     &pm, true);
     }
     if (rc != RPCHOLQR_OK) return rc;
     pm.mark(RPCHOLQR_PHASE_GRAM_REDUCE);
@@ -1897,7 +1966,7 @@ rpcholqr_status rpcholqr_autotune(rpcholqr_plan p, int32_t nclasses, const int64
         std::vector<Tuning> cands(1);
         if (p->mode == RPCHOLQR_SPLIT64) {
             cands.clear();
-            const int nh = ozaki_gram_halves(np);
+            const int nh = ozaki_gram_tiles(np, p->aimg != nullptr);
             const int plain = p->grid / nh > 0 ? p->grid / nh : 1;
             for (int sub : {kSplitSub, 16})   // the built-in width first; gram_ranges 0 = the wave rule
                 for (int gr : {0, plain, 2 * plain}) {

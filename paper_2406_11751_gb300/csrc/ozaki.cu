@@ -1,12 +1,16 @@
 // Split-precision (Ozaki-style) FP64 products on the GB300 BF16 tensor cores (tcgen05).
 //
 // Used by the SPLIT64 mode for the well-conditioned products of Algorithm alg_2 (Section 4):
-//   Gram          G_1 = A_1^T A_1               (k_ozaki_gram)
-//   solve         Q   = A_1 R_1^{-1}            (k_ozaki_gemm_ws with the explicit R_1^{-1}; kappa(R_1) =
-//                                                kappa(A_1) is small, Lemma l_31)
+//   Gram          G_1 = A_1^T A_1               (k_ozaki_gram; above 128 columns k_ozaki_gram_db)
+//   solve         Q   = A_1 R_1^{-1}            (k_ozaki_gemm_ws with the explicit R_1^{-1}; above 128
+//                                                columns k_ozaki_gemm_db; kappa(R_1) = kappa(A_1) is
+//                                                small, Lemma l_31)
 //   precondition  the off-diagonal block update A[:,J] - A_1[:,<J] R_s[<J,J] of the blocked row solve
-//                                               (k_ozaki_update for K <= 32, else k_ozaki_gemm_ws,
-//                                                subtract form; the diagonal blocks stay FP64 substitution)
+//                                               (k_ozaki_update for K <= 32, else k_ozaki_gemm_ws /
+//                                                k_ozaki_gemm_db, subtract form; the diagonal blocks stay
+//                                                FP64 substitution)
+// Above 128 columns the left operand is sliced beforehand into stage images (k_slice_images,
+// k_slice_block_images, k_slice_col_images) that the *_db kernels stream in by TMA bulk copies.
 //
 // Splitting (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix multiplication by using
 // fast routines of matrix multiplication and its applications", Numer. Algorithms 2012, restated): every
@@ -45,8 +49,6 @@ template <int NT> struct Share {
     static constexpr int kChunks = (32 / 8) / kRowThreads;   // 8-value K chunks sliced per stage
     static constexpr int kDrainCols = 64 / kRowThreads;      // output columns drained
 };
-constexpr int kDrainCols = Share<kThreads>::kDrainCols;
-constexpr int kChunks = Share<kThreads>::kChunks;
 // The windowed GEMM (K > 128) keeps int64 accumulators live across stages (16 columns per thread with 512
 // threads, drained 4 columns at a time to fit the 120 registers a 544-thread CTA allows).
 constexpr int kThreadsWin = 512;
@@ -462,6 +464,46 @@ __global__ void __launch_bounds__(512) k_slice_col_images(const double* __restri
     slice_store8(x, E, img + static_cast<size_t>(blk * nst + st) * kAStage + core_off(lr, 16 * c), kASlice);
 }
 
+// ---- stage images of one 64-column block, against the block's own row bounds ---------------------------
+// The left-looking wide first pass slices each finished block of A_1 once: columns c0 .. c0 + nc - 1 of X
+// (nc <= 64) become stages kw0 and kw0 + 1 of row tile tm's image (img_nkw stages per row tile), sliced
+// against the row's bound over the block alone, which is written to bexp[row].  The products that read
+// the image treat each block as its own exactness window with its own row bound.  One CTA per 128-row
+// tile; thread (row, q) holds values 16 q .. 16 q + 15 of its row (the row bound is the maximum over
+// the four).
+__global__ void __launch_bounds__(512) k_slice_block_images(const double* __restrict__ X, int64_t ldx, int64_t m,
+                                                            int nc, uint8_t* __restrict__ img, int img_nkw, int kw0,
+                                                            int32_t* __restrict__ bexp, const int32_t* info) {
+    __shared__ int red[4][kTileM];
+    if (info && load_status(info) != 0) return;
+    const int64_t tm = blockIdx.x;
+    const int lr = threadIdx.x & (kTileM - 1), q = threadIdx.x >> 7;
+    const int64_t row = tm * kTileM + lr;
+    double x[16];
+    int e = kNoExp;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int k = 16 * q + i;
+        x[i] = (row < m && k < nc) ? X[row * ldx + k] : 0.0;
+        const int ek = exp_bound(x[i]);
+        e = ek > e ? ek : e;
+    }
+    red[q][lr] = e;
+    __syncthreads();
+    int E = red[0][lr];
+#pragma unroll
+    for (int j = 1; j < 4; ++j) E = red[j][lr] > E ? red[j][lr] : E;
+    if (q == 0 && row < m) bexp[row] = E;
+    uint8_t* dst = img + static_cast<size_t>(tm * img_nkw + kw0 + (q >> 1)) * kAStage;
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+        double x8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x8[i] = x[8 * cc + i];
+        slice_store8(x8, E, dst + core_off(lr, 16 * ((2 * q + cc) & 3)), kASlice);
+    }
+}
+
 // ---- C = X Y, warp-specialised: helpers ------------------------------------------------------------
 // 128 rows x 32 K values of X (rows row0.., columns k0..) into R, one 8-byte cp.async per value, zero
 // outside the matrix; the 32 lanes of a warp copy one row.
@@ -594,17 +636,13 @@ struct StageWalk {
     }
 };
 
-// PRE: the A slices of every stage were made beforehand by k_slice_images (aimg, the stage images of
-// X's row tiles in the shared-memory stage layout): the producers copy them instead of slicing, so a
-// stage costs one 64 KB copy; X itself is not read.
-template <bool WIN, bool SUB, bool PRE>
+template <bool WIN, bool SUB>
 __global__ void __launch_bounds__((WIN ? kThreadsWin : kThreads) + 32, 1)
 k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, int K,
                 const uint8_t* __restrict__ yblocks, const int32_t* __restrict__ yexp, int N, const double* B,
-                int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, long spin, int tri,
-                const uint8_t* __restrict__ aimg) {
+                int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, long spin, int tri) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    __shared__ uint64_t empty_bar[2], full_bar[2], load_bar[2], done_bar;
+    __shared__ uint64_t empty_bar[2], full_bar[2], done_bar;
     __shared__ uint32_t tslot;
     __shared__ int abort_s;
     if (load_status(info) != 0) return;
@@ -624,7 +662,6 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
         for (int i = 0; i < 2; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty_bar[i])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full_bar[i])), "r"(NT / 32));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&load_bar[i])));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&done_bar)));
         asm volatile("fence.mbarrier_init.release.cluster;\n");
@@ -652,17 +689,15 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
     if (warp == NT / 32) {
         // MMA warp: one lane issues every stage once the producers have filled it
         if (lane == 0) {
-            uint32_t fphase[2] = {0u, 0u}, lphase[2] = {0u, 0u};
+            uint32_t fphase[2] = {0u, 0u};
             StageWalk wk(ntn, nkw, tri != 0);
             for (int64_t g = 0; g < nstages; ++g, wk.advance()) {
                 const int s = static_cast<int>(g & 1);
-                if (!mbar_wait_ab(&full_bar[s], fphase[s], &abort_s, spin) ||
-                    (PRE && !mbar_wait_ab(&load_bar[s], lphase[s], &abort_s, spin))) {
+                if (!mbar_wait_ab(&full_bar[s], fphase[s], &abort_s, spin)) {
                     abort_s = 1;
                     break;
                 }
                 fphase[s] ^= 1u;
-                lphase[s] ^= 1u;
                 tc_after_sync();
                 issue_stage(tmem, smem_u32(stA[s]), smem_u32(stB[s]), (wk.kw & 3) == 0);
                 mma_commit(&empty_bar[s]);
@@ -678,14 +713,13 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
         uint32_t phase[2] = {0u, 0u};
         bool pending[2] = {false, false};
         bool timed_out = false;
-        int64_t issued[2] = {0, 0};         // bulk copies issued into each stage buffer (PRE, thread 0)
         long long acc[NC];
 #pragma unroll
         for (int j = 0; j < NC; ++j) acc[j] = 0;
         int64_t cur_row0 = 0;               // the tile whose accumulators are in TMEM
         int cur_tn = 0, cur_E = kNoExp;
         StageWalk wk(ntn, nkw, tri != 0);   // stage g
-        if (!PRE && nstages > 0) prefetch_x<NT>(X, ldx, m, K, (wk.t / ntn) * kTileM, wk.kw * kKW, R, tid);
+        if (nstages > 0) prefetch_x<NT>(X, ldx, m, K, (wk.t / ntn) * kTileM, wk.kw * kKW, R, tid);
         cp_async_commit();
 
         for (int64_t g = 0; g < nstages; ++g, wk.advance()) {
@@ -705,17 +739,7 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
             }
             // B slices of stage g: one contiguous 32 KB block
             const uint8_t* src = yblocks + static_cast<size_t>((tn * nkw + kw) * kSlices) * kBSlice;
-            if constexpr (PRE) {
-                // the stage's A slices, made beforehand in this layout (one contiguous 64 KB block), and B:
-                // two bulk copies on the stage's load barrier; the producers do not wait for them
-                if (tid == 0) {
-                    const uint8_t* asrc = aimg + static_cast<size_t>(tm * nkw + kw) * kAStage;
-                    mbar_expect_tx(&load_bar[s], kStageBytes);
-                    bulk_g2s(stB[s], src, kBStage, &load_bar[s]);
-                    bulk_g2s(stA[s], asrc, kAStage, &load_bar[s]);
-                    ++issued[s];
-                }
-            } else {
+            {
                 for (int e = tid; e < kBStage / 16; e += NT) {
                     const unsigned dst = smem_u32(stB[s] + 16 * e);
                     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 16 * e));
@@ -795,8 +819,285 @@ k_ozaki_gemm_ws(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, 
                                              reinterpret_cast<double*>(stA[0]), acc);
             }
         }
-        if (PRE && tid == 0 && !bulk_drain(load_bar, issued)) timed_out = true;
         if (timed_out) abort_s = 1;
+    }
+
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid == 0 && abort_s) set_status(info, RPCHOLQR_ERR_TIMEOUT);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// ---- C = X Y / C = B - X Y from stage images, with the accumulators double-buffered ------------------------
+// The product over pre-sliced X (k_slice_images) for the wide passes: pass 2 (Q = A_1 R_1^{-1}, Y upper
+// triangular) and the left-looking block updates of the first pass (C = B - X Y, K up to 2048).  Output
+// tiles of 128 rows x 32 columns, so that one exactness window's eight group accumulators take 256 TMEM
+// columns and two sets fit: consecutive windows of a CTA (within a tile and across its tiles) alternate
+// between the sets, so a window's drain (the eight FP32 group sums into int64, or the tile's result out
+// to C) runs while the tensor core fills the other set.  Warp roles: warps 0-7 drain (two threads per
+// tile row, 16 columns each: warp w reads TMEM lanes 32 (w % 4)..), warp 8 lane 0 streams the stages
+// (one 64 KB bulk copy of X's stage image, eight 2 KB copies of Y's slices, on the stage's load barrier),
+// warp 9 lane 0 issues the MMAs (8 per K = 16 step: Y's eight 32-column slices are stacked, N = 32 (9 - a)
+// for slice a of X).  Barriers: load[s] (bytes landed) and empty[s] (MMAs of the stage done) per stage
+// buffer; acc_full[b] (the window's MMAs done) and acc_empty[b] (the set read out) per accumulator set.
+// The arithmetic is that of k_ozaki_gemm_ws: the same slices, exact group sums per window of 128, the
+// same int64 combination in units of 2^-53, so the results are the same bits.
+constexpr int kDbN = 32;
+constexpr int kDbBSlice = kDbN * kKW * 2;            // 2 KB: one slice of a 32-column tile's stage
+constexpr int kDbBStage = kSlices * kDbBSlice;       // 16 KB
+constexpr int kDbStage = kAStage + kDbBStage;        // 80 KB
+constexpr int kDbEpiWarps = 8;
+constexpr int kDbEpi = 32 * kDbEpiWarps;             // 256 drain threads
+constexpr int kDbThreads = kDbEpi + 64;              // + the copy warp and the MMA warp
+constexpr int kDbCols = kDbN / (kDbEpi / kTileM);    // 16 columns per drain thread
+constexpr int kDbEpiLd = kDbN + 1;
+constexpr int kDbSmem = 2 * kDbStage + kTileM * kDbEpiLd * 8;
+static_assert(kDbSmem + 1024 <= 232448, "k_ozaki_gemm_db exceeds the 227 KB shared-memory limit");
+
+// K stages an output tile of 32-column tile tn needs (tri: those up to the last K row its columns reach).
+__device__ __forceinline__ int db_tile_stages(int tn, int nkw, bool tri) {
+    if (!tri) return nkw;
+    const int last = ((tn + 1) * kDbN + kKW - 1) / kKW;
+    return last < nkw ? last : nkw;
+}
+
+// The 36 slice pairs of one 32-wide K stage into accumulator set `tset` (group d at columns (d - 2) 32):
+// 8 MMAs per K = 16 step; `first`: the stage opens a window (the a = 1 MMA clears all eight groups).
+__device__ __forceinline__ void issue_stage_n32(uint32_t tset, uint32_t a_base, uint32_t b_base, bool first) {
+    const uint64_t a0 = sdesc(a_base), b0 = sdesc(b_base);
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+        for (int a = 1; a <= 8; ++a) {
+            const uint64_t ad = a0 + static_cast<uint32_t>(((a - 1) * kASlice + kk * 256) >> 4);
+            mma_bf16_n(tset + (a - 1) * kDbN, ad, b0 + static_cast<uint32_t>(kk * 16), idesc_bf16(kDbN * (9 - a)),
+                       (first && kk == 0 && a == 1) ? 0u : 1u);
+        }
+    }
+}
+
+// I 2^-sh rounded to nearest (ties up), sh >= 0; |I| < 2^62.
+__device__ __forceinline__ long long shift_round(long long I, int sh) {
+    if (sh == 0) return I;
+    if (sh > 62) return 0;
+    return (I + (1ll << (sh - 1))) >> sh;
+}
+
+// Add one window's eight group sums of this thread's row (TMEM address taddr: set + lane quarter) and
+// columns col0 .. col0 + NC - 1 of the 32-column tile to int64 accumulators in units of 2^-53 (U49: 2^-49)
+// of the window's scale, shifted down by sh bits (a window sliced against a row bound 2^sh below the
+// tile's).
+template <int NC, bool U49 = false>
+__device__ __forceinline__ void drain_set32(uint32_t taddr, int col0, int sh, long long (&acc)[NC]) {
+#pragma unroll
+    for (int c0 = 0; c0 < NC; c0 += 8) {
+        float mg[kGroups][8];
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g) tmem_ld8(taddr + g * kDbN + col0 + c0, mg[g]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float grp[kGroups];
+#pragma unroll
+            for (int g = 0; g < kGroups; ++g) grp[g] = mg[g][j];
+            acc[c0 + j] += shift_round(U49 ? combine_units49(grp) : combine_units53(grp), sh);
+        }
+    }
+}
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 2, %0;\n" ::"r"(kDbEpi) : "memory"); }
+// Barrier 2 over the drain warps with an OR of v: a wait that gave up in any drain warp ends all of them
+// at the same point (none is left at a barrier the others no longer reach).
+__device__ __forceinline__ bool epi_sync_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 2, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"(static_cast<uint32_t>(v)), "r"(kDbEpi)
+        : "memory");
+    return r != 0;
+}
+
+template <bool SUB>
+__global__ void __launch_bounds__(kDbThreads, 1)
+k_ozaki_gemm_db(const uint8_t* __restrict__ aimg, const int32_t* __restrict__ xexp, int K,
+                const uint8_t* __restrict__ yblocks, const int32_t* __restrict__ yexp, int N, const double* B,
+                int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, long spin, int tri, int img_nkw,
+                const int32_t* __restrict__ bexp, int64_t ld_bexp) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint64_t load_bar[2], empty_bar[2], acc_full[2], acc_empty[2], done_bar;
+    __shared__ uint32_t tslot;
+    __shared__ int abort_s;
+    if (load_status(info) != 0) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t* stA[2] = {sm, sm + kDbStage};
+    uint8_t* stB[2] = {sm + kAStage, sm + kDbStage + kAStage};
+    double* W = reinterpret_cast<double*>(sm + 2 * kDbStage);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tslot)), "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&load_bar[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty_bar[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&acc_full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&acc_empty[i])), "r"(kDbEpiWarps));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&done_bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+        abort_s = 0;
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tslot;
+
+    const int nkw = (K + kKW - 1) / kKW;
+    const int ntn = (N + kDbN - 1) / kDbN;
+    const int64_t ntm = (m + kTileM - 1) / kTileM;
+    const int64_t ntiles = ntm * ntn;
+    const bool tr = tri != 0;
+    // exactness windows: 4 stages (K = 128) against one row bound xexp, or (bexp) one 64-column block of
+    // 2 stages each, against its own row bound bexp[w * ld_bexp + row]
+    const int wlen = bexp ? 2 : 4;
+
+    if (warp == kDbEpiWarps) {
+        // stage copies, running ahead of the MMAs by the two stage buffers
+        if (lane == 0) {
+            int64_t g = 0, issued[2] = {0, 0};
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int64_t tm = t / ntn;
+                const int tn = tile_col(t, ntn, tr);
+                const int nk = db_tile_stages(tn, nkw, tr);
+                for (int kw = 0; kw < nk; ++kw, ++g) {
+                    const int s = static_cast<int>(g & 1);
+                    if (g >= 2 && !mbar_wait_ab(&empty_bar[s], static_cast<uint32_t>(((g >> 1) - 1) & 1), &abort_s, spin)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&load_bar[s], kDbStage);
+                    bulk_g2s(stA[s], aimg + static_cast<size_t>(tm * img_nkw + kw) * kAStage, kAStage, &load_bar[s]);
+                    // slices of Y's 64-column block tn / 2, rows 32 (tn & 1).. of each: the 32-column tile
+                    const uint8_t* bsrc = yblocks + static_cast<size_t>(((tn >> 1) * nkw + kw) * kSlices) * kBSlice +
+                                          (tn & 1) * kDbBSlice;
+#pragma unroll
+                    for (int b = 0; b < kSlices; ++b)
+                        bulk_g2s(stB[s] + b * kDbBSlice, bsrc + static_cast<size_t>(b) * kBSlice, kDbBSlice, &load_bar[s]);
+                    ++issued[s];
+                }
+            }
+            if (!bulk_drain(load_bar, issued)) ok = false;
+            if (!ok) abort_s = 1;
+        }
+        __syncwarp();
+    } else if (warp == kDbEpiWarps + 1) {
+        // MMAs: window by window into alternating accumulator sets
+        if (lane == 0) {
+            int64_t g = 0, wc = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int nk = db_tile_stages(tile_col(t, ntn, tr), nkw, tr);
+                for (int kw = 0; kw < nk; ++kw, ++g) {
+                    const bool first = kw % wlen == 0;
+                    const int set = static_cast<int>(wc & 1);
+                    if (first && wc >= 2 &&
+                        !mbar_wait_ab(&acc_empty[set], static_cast<uint32_t>(((wc >> 1) - 1) & 1), &abort_s, spin)) {
+                        ok = false;
+                        break;
+                    }
+                    const int s = static_cast<int>(g & 1);
+                    if (!mbar_wait_ab(&load_bar[s], static_cast<uint32_t>((g >> 1) & 1), &abort_s, spin)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_after_sync();
+                    issue_stage_n32(tmem + static_cast<uint32_t>(set) * (kGroups * kDbN), smem_u32(stA[s]),
+                                    smem_u32(stB[s]), first);
+                    mma_commit(&empty_bar[s]);
+                    if (kw % wlen == wlen - 1 || kw == nk - 1) {
+                        mma_commit(&acc_full[set]);
+                        ++wc;
+                    }
+                }
+            }
+            // every MMA issued here is complete before the tensor memory is released
+            mma_commit(&done_bar);
+            if (!mbar_wait(&done_bar, 0u)) ok = false;
+            if (!ok) abort_s = 1;
+        }
+        __syncwarp();
+    } else {
+        // drain: thread (row lr, column half h); the tile's result is staged in W and written in whole rows
+        const int lr = tid & (kTileM - 1), h = tid >> 7;
+        const uint32_t lane_off = static_cast<uint32_t>((warp & 3) * 32) << 16;
+        int64_t wc = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int64_t tm = t / ntn;
+            const int tn = tile_col(t, ntn, tr);
+            const int nk = db_tile_stages(tn, nkw, tr);
+            const int64_t row = tm * kTileM + lr;
+            const int nwin = (nk + wlen - 1) / wlen;
+            int E = kNoExp;
+            if (row < m) {
+                if (bexp) {
+                    for (int w = 0; w < nwin; ++w) E = bexp[w * ld_bexp + row] > E ? bexp[w * ld_bexp + row] : E;
+                } else {
+                    E = xexp[row];
+                }
+            }
+            long long acc[kDbCols];
+#pragma unroll
+            for (int j = 0; j < kDbCols; ++j) acc[j] = 0;
+            for (int w = 0; w < nwin; ++w, ++wc) {
+                const int set = static_cast<int>(wc & 1);
+                const bool got = mbar_wait_ab(&acc_full[set], static_cast<uint32_t>((wc >> 1) & 1), &abort_s, spin);
+                if (epi_sync_or(!got)) {
+                    ok = false;
+                    break;
+                }
+                tc_after_sync();
+                int sh = 0;
+                if (bexp && row < m) {
+                    const int ew = bexp[w * ld_bexp + row];
+                    sh = ew > kNoExp ? E - ew : 63;
+                }
+                drain_set32<kDbCols>(tmem + lane_off + static_cast<uint32_t>(set) * (kGroups * kDbN), kDbCols * h, sh,
+                                     acc);
+                tc_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[set]);
+            }
+            if (!ok) break;   // (uniform over the drain warps)
+            const int col0 = tn * kDbN;
+#pragma unroll
+            for (int j = 0; j < kDbCols; ++j) {
+                const int col = col0 + kDbCols * h + j;
+                const int ey = col < N ? yexp[col] : kNoExp;
+                W[lr * kDbEpiLd + kDbCols * h + j] =
+                    (E > kNoExp && ey > kNoExp) ? scale_pow2(acc[j], E + ey - 53) : 0.0;
+            }
+            epi_sync();
+            const int ncols = N - col0 < kDbN ? N - col0 : kDbN;
+#pragma unroll 4
+            for (int i = 0; i < kTileM * kDbN / kDbEpi; ++i) {
+                const int e = tid + i * kDbEpi;
+                const int r = e >> 5, c = e & 31;
+                const int64_t grow = tm * kTileM + r;
+                if (grow < m && c < ncols) {
+                    if (SUB) C[grow * ldc + col0 + c] = B[grow * ldb + col0 + c] - W[r * kDbEpiLd + c];
+                    else C[grow * ldc + col0 + c] = W[r * kDbEpiLd + c];
+                }
+            }
+            epi_sync();
+        }
+        if (!ok) abort_s = 1;
     }
 
     tc_before_sync();
@@ -1016,6 +1317,178 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
 }
 
+// ---- Gram partials from column stage images, with the accumulators double-buffered ------------------------
+// Output tiles (P, Qb) of rows p in [128P, 128P+128) (TMEM lanes) x columns q in [32Qb, 32Qb+32), all
+// tiles with Qb >= 4P (every q >= p is covered); grid = ntiles x nranges, CTA (tile, rr) sums the rows
+// [rr*rows_per, ...) of the launch.  A = P's 128-column stage image (64 KB), B = rows 32 (Qb % 4).. of
+// each slice of block Qb / 4's image (eight 2 KB copies); windows of 128 rows alternate between the two
+// TMEM sets as in k_ozaki_gemm_db, each drained into int64 in units of 2^-49 and, every 64 windows and
+// at the end, added into the CTA's FP64 partial (accum: the launch adds into partials of earlier row
+// chunks).  The same slices, sums and flush points as k_ozaki_gram's 64-column tiles: the same bits.
+__device__ __forceinline__ void gram_tile_coords32(int nqb, int tt, int& P, int& Qb) {
+    P = 0;
+    while (tt >= nqb - 4 * P) { tt -= nqb - 4 * P; ++P; }
+    Qb = 4 * P + tt;
+}
+
+__global__ void __launch_bounds__(kDbThreads, 1)
+k_ozaki_gram_db(int64_t m, int n, int np, const int32_t* __restrict__ colexp, int64_t rows_per, int ntiles,
+                double* __restrict__ gpart, int32_t* info, long spin, const uint8_t* __restrict__ gimg, int accum) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint64_t load_bar[2], empty_bar[2], acc_full[2], acc_empty[2], done_bar;
+    __shared__ uint32_t tslot;
+    __shared__ int abort_s;
+    if (load_status(info) != 0) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t* stA[2] = {sm, sm + kDbStage};
+    uint8_t* stB[2] = {sm + kAStage, sm + kDbStage + kAStage};
+    const int nqb = (np + kDbN - 1) / kDbN;
+    int P, Qb;
+    gram_tile_coords32(nqb, blockIdx.x % ntiles, P, Qb);
+    const int64_t rr = blockIdx.x / ntiles;
+    const int64_t r0 = rr * rows_per;
+    const int64_t r1 = (r0 + rows_per < m) ? r0 + rows_per : m;
+    const int64_t nstages = r1 > r0 ? (r1 - r0 + kKW - 1) / kKW : 0;
+    const int64_t nsg = (m + kKW - 1) / kKW;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tslot)), "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&load_bar[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty_bar[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&acc_full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&acc_empty[i])), "r"(kDbEpiWarps));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&done_bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+        abort_s = 0;
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tslot;
+
+    if (warp == kDbEpiWarps) {
+        if (lane == 0) {
+            int64_t issued[2] = {0, 0};
+            bool ok = true;
+            const uint8_t* abase = gimg + static_cast<size_t>(P) * nsg * kAStage;
+            const uint8_t* bbase = gimg + static_cast<size_t>(Qb >> 2) * nsg * kAStage + (Qb & 3) * kDbBSlice;
+            for (int64_t st = 0; st < nstages; ++st) {
+                const int s = static_cast<int>(st & 1);
+                if (st >= 2 && !mbar_wait_ab(&empty_bar[s], static_cast<uint32_t>(((st >> 1) - 1) & 1), &abort_s, spin)) {
+                    ok = false;
+                    break;
+                }
+                const size_t sg = static_cast<size_t>(r0 / kKW + st);
+                mbar_expect_tx(&load_bar[s], kDbStage);
+                bulk_g2s(stA[s], abase + sg * kAStage, kAStage, &load_bar[s]);
+#pragma unroll
+                for (int b = 0; b < kSlices; ++b)
+                    bulk_g2s(stB[s] + b * kDbBSlice, bbase + sg * kAStage + static_cast<size_t>(b) * kASlice, kDbBSlice,
+                             &load_bar[s]);
+                ++issued[s];
+            }
+            if (!bulk_drain(load_bar, issued)) ok = false;
+            if (!ok) abort_s = 1;
+        }
+        __syncwarp();
+    } else if (warp == kDbEpiWarps + 1) {
+        if (lane == 0) {
+            int64_t wc = 0;
+            bool ok = true;
+            for (int64_t st = 0; st < nstages; ++st) {
+                const bool first = (st & 3) == 0;
+                const int set = static_cast<int>(wc & 1);
+                if (first && wc >= 2 &&
+                    !mbar_wait_ab(&acc_empty[set], static_cast<uint32_t>(((wc >> 1) - 1) & 1), &abort_s, spin)) {
+                    ok = false;
+                    break;
+                }
+                const int s = static_cast<int>(st & 1);
+                if (!mbar_wait_ab(&load_bar[s], static_cast<uint32_t>((st >> 1) & 1), &abort_s, spin)) {
+                    ok = false;
+                    break;
+                }
+                tc_after_sync();
+                issue_stage_n32(tmem + static_cast<uint32_t>(set) * (kGroups * kDbN), smem_u32(stA[s]), smem_u32(stB[s]),
+                                first);
+                mma_commit(&empty_bar[s]);
+                if ((st & 3) == 3 || st == nstages - 1) {
+                    mma_commit(&acc_full[set]);
+                    ++wc;
+                }
+            }
+            mma_commit(&done_bar);
+            if (!mbar_wait(&done_bar, 0u)) ok = false;
+            if (!ok) abort_s = 1;
+        }
+        __syncwarp();
+    } else {
+        const int lr = tid & (kTileM - 1), h = tid >> 7;
+        const uint32_t lane_off = static_cast<uint32_t>((warp & 3) * 32) << 16;
+        const int p = 128 * P + lr;
+        const int Ep = p < n ? colexp[p] : kNoExp;
+        double* out = gpart + static_cast<size_t>(rr) * np * np + static_cast<size_t>(p) * np;
+        long long acc[kDbCols];
+#pragma unroll
+        for (int j = 0; j < kDbCols; ++j) acc[j] = 0;
+        bool flushed = accum != 0, ok = true;
+        // acc into the FP64 partial (the first flush of a launch that does not accumulate initialises it)
+        auto flush = [&]() {
+            if (p < np) {
+#pragma unroll
+                for (int j = 0; j < kDbCols; ++j) {
+                    const int q = kDbN * Qb + kDbCols * h + j;
+                    if (q < np) {
+                        const int Eq = q < n ? colexp[q] : kNoExp;
+                        const double v = (Ep > kNoExp && Eq > kNoExp) ? scale_pow2(acc[j], Ep + Eq - 49) : 0.0;
+                        out[q] = (flushed ? out[q] : 0.0) + v;
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kDbCols; ++j) acc[j] = 0;
+            flushed = true;
+        };
+        const int64_t nwin = (nstages + 3) / 4;
+        for (int64_t w = 0; w < nwin; ++w) {
+            const int set = static_cast<int>(w & 1);
+            const bool got = mbar_wait_ab(&acc_full[set], static_cast<uint32_t>((w >> 1) & 1), &abort_s, spin);
+            if (epi_sync_or(!got)) {
+                ok = false;
+                break;
+            }
+            tc_after_sync();
+            drain_set32<kDbCols, true>(tmem + lane_off + static_cast<uint32_t>(set) * (kGroups * kDbN), kDbCols * h, 0,
+                                       acc);
+            tc_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[set]);
+            if ((w & 63) == 63 || w == nwin - 1) flush();   // every 64 windows and at the end
+        }
+        if (!ok) {
+            abort_s = 1;
+        } else if (nstages == 0 && !accum && p < np) {
+            for (int j = 0; j < kDbCols; ++j) {
+                const int q = kDbN * Qb + kDbCols * h + j;
+                if (q < np) out[q] = 0.0;
+            }
+        }
+    }
+
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid == 0 && abort_s) set_status(info, RPCHOLQR_ERR_TIMEOUT);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+}
+
 // ---- Gram partials G_rr = X_rr^T X_rr -------------------------------------------------------------------
 // X: m x n FP64 (ldx), column exponent bounds colexp[n] over all m rows.  Output tiles (P, Qb): rows
 // p in [128P, 128P+128) (TMEM lanes) x columns q in [64Qb, 64Qb+64), all tiles with Qb >= 2P (every
@@ -1112,8 +1585,6 @@ k_ozaki_gram(const double* __restrict__ X, int64_t ldx, int64_t m, int n, int np
         const int rq = tid >> 7;                // producer row chunk(s) NCH*rq..; drain columns kCols*rq..
         const int p = 128 * P + lr;
         const int Ep = p < n ? colexp[p] : kNoExp;
-        const int qb_col = 64 * Qb + (tid & 63);          // B producer column (when B is separate)
-        const int Eqb = qb_col < n ? colexp[qb_col] : kNoExp;
         long long acc[kCols];
 #pragma unroll
         for (int j = 0; j < kCols; ++j) acc[j] = 0;
@@ -1290,7 +1761,8 @@ void launch_ozaki_slice_cols(const double* Y, int64_t ldy, int K, int N, uint8_t
 cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int32_t* xexp, int K,
                               const uint8_t* yblocks, const int32_t* yexp, int N, const double* B,
                               int64_t ldb, double* C, int64_t ldc, int64_t m, int32_t* info, int grid,
-                              cudaStream_t st, long spin, bool y_upper, const uint8_t* aimg) {
+                              cudaStream_t st, long spin, bool y_upper, const uint8_t* aimg, int img_nkw,
+                              const int32_t* bexp, int64_t ld_bexp) {
     if (K > 64 * oz::kKW) return cudaErrorInvalidValue;   // int64 accumulators hold K <= 2048 (see drain_acc)
     const bool win = K > 4 * oz::kKW;
     const int nt = win ? oz::kThreadsWin : oz::kThreads;
@@ -1304,14 +1776,25 @@ cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int3
                                                                     ldc, m, info, spin);
         return cudaGetLastError();
     }
-    auto kern = aimg ? (win ? (sub ? oz::k_ozaki_gemm_ws<true, true, true> : oz::k_ozaki_gemm_ws<true, false, true>)
-                            : (sub ? oz::k_ozaki_gemm_ws<false, true, true> : oz::k_ozaki_gemm_ws<false, false, true>))
-              : win ? (sub ? oz::k_ozaki_gemm_ws<true, true, false> : oz::k_ozaki_gemm_ws<true, false, false>)
-                    : (sub ? oz::k_ozaki_gemm_ws<false, true, false> : oz::k_ozaki_gemm_ws<false, false, false>);
+    if (aimg) {
+        // pre-sliced X: the double-buffered kernel over 128 x 32 tiles
+        auto kdb = sub ? oz::k_ozaki_gemm_db<true> : oz::k_ozaki_gemm_db<false>;
+        err = cudaFuncSetAttribute(kdb, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::kDbSmem);
+        if (err != cudaSuccess) return err;
+        const int64_t tiles = ((m + oz::kTileM - 1) / oz::kTileM) * ((N + oz::kDbN - 1) / oz::kDbN);
+        const int g = static_cast<int>(grid < tiles ? grid : tiles);
+        const int nkw = (K + oz::kKW - 1) / oz::kKW;
+        if (img_nkw < nkw || (bexp && (K % 64 != 0))) return cudaErrorInvalidValue;
+        kdb<<<g, oz::kDbThreads, oz::kDbSmem, st>>>(aimg, xexp, K, yblocks, yexp, N, B, ldb, C, ldc, m, info, spin,
+                                                    y_upper ? 1 : 0, img_nkw, bexp, ld_bexp);
+        return cudaGetLastError();
+    }
+    auto kern = win ? (sub ? oz::k_ozaki_gemm_ws<true, true> : oz::k_ozaki_gemm_ws<true, false>)
+                    : (sub ? oz::k_ozaki_gemm_ws<false, true> : oz::k_ozaki_gemm_ws<false, false>);
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::kGemmSmem);
     if (err != cudaSuccess) return err;
     kern<<<grid, nt + 32, oz::kGemmSmem, st>>>(X, ldx, xexp, K, yblocks, yexp, N, B, ldb, C, ldc, m, info, spin,
-                                                y_upper ? 1 : 0, aimg);
+                                                y_upper ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1345,6 +1828,14 @@ int ozaki_gram_halves(int np) {
     for (int P = 0; 2 * P < nqb; ++P) c += nqb - 2 * P;
     return c;
 }
+// Output tiles of the split Gram: 128 x 64 (k_ozaki_gram), or 128 x 32 from stage images (k_ozaki_gram_db).
+int ozaki_gram_tiles(int np, bool images) {
+    if (!images) return ozaki_gram_halves(np);
+    const int nqb = (np + oz::kDbN - 1) / oz::kDbN;
+    int c = 0;
+    for (int P = 0; 4 * P < nqb; ++P) c += nqb - 4 * P;
+    return c;
+}
 
 void launch_fill_noexp(int32_t* p, int n, cudaStream_t st) {
     oz::k_fill_i32<<<(n + 127) / 128, 128, 0, st>>>(p, n, kNoExp);
@@ -1354,8 +1845,19 @@ void launch_fill_noexp(int32_t* p, int n, cudaStream_t st) {
 cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
                               int nranges, double* gpart, int32_t* info, cudaStream_t st, long spin,
                               const uint8_t* gimg, bool accum) {
+    if (gimg) {
+        cudaError_t err = cudaFuncSetAttribute(oz::k_ozaki_gram_db, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               oz::kDbSmem);
+        if (err != cudaSuccess) return err;
+        const int nt = ozaki_gram_tiles(np, true);
+        int64_t rows_per = (m + nranges - 1) / nranges;
+        rows_per = (rows_per + oz::kKW - 1) / oz::kKW * oz::kKW;
+        oz::k_ozaki_gram_db<<<nt * nranges, oz::kDbThreads, oz::kDbSmem, st>>>(m, n, np, colexp, rows_per, nt, gpart,
+                                                                              info, spin, gimg, accum ? 1 : 0);
+        return cudaGetLastError();
+    }
     const int smem = 2 * (oz::kAStage + oz::kBStage);
-    auto kern = gimg ? oz::k_ozaki_gram<true> : oz::k_ozaki_gram<false>;
+    auto kern = oz::k_ozaki_gram<false>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (err != cudaSuccess) return err;
     const int nt = ozaki_gram_halves(np);
@@ -1366,6 +1868,11 @@ cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, in
     return cudaGetLastError();
 }
 
+void launch_slice_block_images(const double* X, int64_t ldx, int64_t m, int nc, uint8_t* img, int img_nkw, int kw0,
+                               int32_t* bexp, const int32_t* info, cudaStream_t st) {
+    oz::k_slice_block_images<<<static_cast<unsigned>((m + oz::kTileM - 1) / oz::kTileM), 512, 0, st>>>(
+        X, ldx, m, nc, img, img_nkw, kw0, bexp, info);
+}
 void launch_slice_col_images(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
                              uint8_t* img, const int32_t* info, cudaStream_t st) {
     dim3 grid(static_cast<unsigned>((m + oz::kKW - 1) / oz::kKW), (np + 127) / 128);
