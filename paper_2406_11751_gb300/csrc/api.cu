@@ -201,6 +201,7 @@ struct rpcholqr_plan_s {
     // parameters of the call being issued
     std::vector<TuneEntry> tune_table;
     Tuning cur_tune;
+    int cur_np = 0;             // padded width of the current call (select_tuning)
     bool tune_forced = false;   // rpcholqr_autotune is timing a candidate: cur_tune is not looked up
     // options (rpcholqr_plan_set_option)
     int64_t spin_limit = kDefaultSpinLimit;   // polls of a pipeline wait before TIMEOUT
@@ -366,13 +367,16 @@ double ozaki_flops(bool sub, bool y_upper, int64_t m, int K, int N) {
 }
 
 constexpr int kBlk = 64;   // column block of the FP64 blocked solves (n > 128)
-// Blocks of the split mode's first pass (n <= 128): the FP64 row passes solve kSplitSub-column diagonal
-// blocks (FP64 work per row n * kSplitSub); the rest of the solve runs as split tensor-core updates,
-// K = kSplitBlk across blocks and K = kSplitSub inside one.  At m = 2^20, n = 128, sub-blocks of 16
-// measured the same step time as 32 (13.75 vs 13.79 ms: the FP64 work halves, the four extra K = 16
-// updates cost as much), so the blocks are not split.
+// Blocks of the split mode's first pass: the FP64 row passes solve split_sub-column diagonal blocks
+// (FP64 work per row n * split_sub); the rest of the solve runs as split tensor-core updates, K =
+// kSplitBlk across blocks and K = split_sub inside one (n <= 128; wider, 64-column blocks).  At
+// m = 2^20, n = 128, sub-blocks of 16 measured the same step time as 32 (13.75 vs 13.79 ms: the FP64
+// work halves, the extra K = 16 updates cost as much), so up to 128 columns the blocks are not split; at
+// m = 2^23, n = 512, 16 took the step from 558 to 540 ms (row passes 159 -> 96 ms, updates 32 -> 76 ms),
+// so wider matrices take 16.
 constexpr int kSplitBlk = 32;
 constexpr int kSplitSub = 32;
+constexpr int kSplitSubWide = 16;
 // Split mode: the explicit-inverse second pass is used while ||R1||_F ||R1^{-1}||_F / n <= this
 // (1.1-1.25 for well-sampled incoherent A; the estimate lies in [kappa(A1)/n, kappa(A1)]; at 3.3
 // (kappa(A1) ~ 30) the explicit inverse already costs 10x in residual).
@@ -388,6 +392,7 @@ int ceil_log2(int64_t m) {
 // width nearest in log2 m (none: the built-in rules).  Every public call that runs these kernels sets
 // them first.
 void select_tuning(rpcholqr_plan_s* p, int64_t m, int n) {
+    p->cur_np = pad_np(n);
     if (p->tune_forced) return;
     Tuning t;
     const int np = pad_np(n), lm = ceil_log2(m);
@@ -406,7 +411,7 @@ void select_tuning(rpcholqr_plan_s* p, int64_t m, int n) {
 // Width of the SPLIT64 first pass's FP64 diagonal-block solves for the current call.
 int split_sub(const rpcholqr_plan_s* p) {
     const int v = p->cur_tune.split_sub;
-    return v == 16 || v == 32 ? v : kSplitSub;
+    return v == 16 || v == 32 ? v : (p->cur_np > kMaxNP ? kSplitSubWide : kSplitSub);
 }
 
 // CTAs of a row pass over m rows: one per 128-row panel, at most one per SM.

@@ -39,61 +39,131 @@ k_cholesky(const double* __restrict__ G, int64_t ldg, int n, int np, double* __r
     cholesky_small<kCholThreads>(G, ldg, n, np, R, R_user, info, csm);
 }
 
-// The same factorisation for np > 128, working in global memory: R (np x np) is the work array, held
-// column-major while factoring (column l of R contiguous, so the lanes of a warp read both operands of
-// a dot product coalesced) and transposed to row-major at the end.  Left-looking: step j forms row j,
-// R[j][l] = G[j][l] - sum_{k<j} R[k][j] R[k][l], one warp per column l splitting the sum over its lanes.
-__global__ void __launch_bounds__(1024)
-k_cholesky_wide(const double* __restrict__ G, int64_t ldg, int n, int np, double* __restrict__ R,
-                double* __restrict__ R_user, int32_t* info) {
-    __shared__ double diag_s;
-    __shared__ int fail_s;
+// ---- blocked Cholesky for np > 128 (right-looking over 32 x 32 blocks, on many SMs) ---------------------
+// The n x n Cholesky G = R^T R takes n^3/3 FP64 flops, 45 MFLOP at n = 512: about 5.5 ms on the FP64
+// units of one SM, so the wide factorisation spreads every step over the SMs.  R (np x np row-major) is
+// the work array: k_chol_init copies G's upper triangle (zero below, identity padding); step k of
+// nb = ceil(n / 32) is
+//   k_chol_panel (nb - k CTAs): every CTA factors the updated diagonal block W_kk = R_kk^T R_kk itself
+//     (32 column steps in shared memory); CTA 0 stores R_kk and reports a non-positive pivot; CTA c > 0
+//     solves R_{k,k+c} = R_kk^{-T} W_{k,k+c} (forward substitution, one thread per column);
+//   k_chol_trail (one CTA per block pair k < i <= j): W_ij -= R_ki^T R_kj.
+// Every sum runs in a fixed order, so the factor does not depend on the launch shape.
+constexpr int kCb = 32;
+
+__global__ void k_chol_init(const double* __restrict__ G, int64_t ldg, int n, int np, double* __restrict__ R,
+                            const int32_t* info) {
     if (load_status(info) != 0) return;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
-    for (int e = tid; e < np * np; e += blockDim.x) R[e] = 0.0;
-    if (tid == 0) fail_s = -1;
-    __syncthreads();
-    for (int j = 0; j < n; ++j) {
-        const double* cj = R + static_cast<size_t>(j) * np;   // column j (rows < j are final)
-        for (int l = j + warp; l < n; l += nwarps) {
-            const double* cl = R + static_cast<size_t>(l) * np;
-            double part = 0.0;
-            for (int k = lane; k < j; k += 32) part = fma(cj[k], cl[k], part);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (lane == 0) R[static_cast<size_t>(l) * np + j] = G[static_cast<int64_t>(j) * ldg + l] - part;
-        }
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= static_cast<int64_t>(np) * np) return;
+    const int r = static_cast<int>(e / np), c = static_cast<int>(e % np);
+    double v;
+    if (r >= n || c >= n) v = r == c ? 1.0 : 0.0;
+    else v = r <= c ? G[static_cast<int64_t>(r) * ldg + c] : 0.0;
+    R[e] = v;
+}
+
+// The updated diagonal block (rows/columns k0 .. k0 + nk - 1) factored in shared memory: d[i][j] (i <= j)
+// becomes R_kk; returns (in *bad) the first non-positive pivot's local index, or -1.  256 threads.
+__device__ __forceinline__ void chol_block32(double (*d)[kCb + 1], int nk, int* bad) {
+    const int tid = threadIdx.x;
+    for (int i = 0; i < nk; ++i) {
         __syncthreads();
         if (tid == 0) {
-            const double d = R[static_cast<size_t>(j) * np + j];
-            if (!(d > 0.0)) fail_s = j;
-            else { diag_s = sqrt(d); R[static_cast<size_t>(j) * np + j] = diag_s; }
+            const double piv = d[i][i];
+            if (!(piv > 0.0) && *bad < 0) *bad = i;
+            d[i][i] = piv > 0.0 ? sqrt(piv) : 1.0;
         }
         __syncthreads();
-        if (fail_s >= 0) break;
-        const double inv = 1.0 / diag_s;
-        for (int l = j + 1 + tid; l < n; l += blockDim.x) R[static_cast<size_t>(l) * np + j] *= inv;
+        const double inv = 1.0 / d[i][i];
+        for (int j = i + 1 + tid; j < nk; j += blockDim.x) d[i][j] *= inv;
         __syncthreads();
-    }
-    if (fail_s >= 0) {
-        if (tid == 0) set_status(info, RPCHOLQR_ERR_NOT_SPD, fail_s);
-        return;
-    }
-    // column-major -> row-major
-    for (int e = tid; e < np * np; e += blockDim.x) {
-        const int r = e / np, c = e - r * np;
-        if (r < c) {
-            const double t = R[e];
-            R[e] = R[static_cast<size_t>(c) * np + r];
-            R[static_cast<size_t>(c) * np + r] = t;
+        // trailing part of the block: d[j][l] -= d[i][j] d[i][l], i < j <= l
+        for (int e = tid; e < (nk - i - 1) * (nk - i - 1); e += blockDim.x) {
+            const int j = i + 1 + e / (nk - i - 1), l = i + 1 + e % (nk - i - 1);
+            if (j <= l) d[j][l] -= d[i][j] * d[i][l];
         }
     }
     __syncthreads();
-    for (int e = tid; e < np * np; e += blockDim.x) {
-        const int r = e / np, c = e - r * np;
-        if (r >= n || c >= n) R[e] = (r == c) ? 1.0 : 0.0;
-        else if (R_user) R_user[r * n + c] = R[e];
+}
+
+__global__ void __launch_bounds__(256) k_chol_panel(double* __restrict__ R, int n, int np, int k, int32_t* info) {
+    __shared__ double d[kCb][kCb + 1];
+    __shared__ int bad;
+    if (load_status(info) != 0) return;
+    const int tid = threadIdx.x;
+    const int k0 = k * kCb, nk = n - k0 < kCb ? n - k0 : kCb;
+    for (int e = tid; e < kCb * kCb; e += blockDim.x) {
+        const int i = e / kCb, j = e % kCb;
+        d[i][j] = (i < nk && j < nk && i <= j) ? R[static_cast<int64_t>(k0 + i) * np + k0 + j] : 0.0;
     }
+    if (tid == 0) bad = -1;
+    chol_block32(d, nk, &bad);
+    const int c = blockIdx.x;
+    if (c == 0) {
+        for (int e = tid; e < nk * nk; e += blockDim.x) {
+            const int i = e / nk, j = e % nk;
+            if (i <= j) R[static_cast<int64_t>(k0 + i) * np + k0 + j] = d[i][j];
+        }
+        if (tid == 0 && bad >= 0) set_status(info, RPCHOLQR_ERR_NOT_SPD, k0 + bad);
+        return;
+    }
+    if (bad >= 0) return;
+    // R_{k,j} = R_kk^{-T} W_{k,j} for column block j = k + c: thread = column, rows i in order
+    const int j0 = (k + c) * kCb, nj = n - j0 < kCb ? n - j0 : kCb;
+    if (tid < nj) {
+        double x[kCb];
+        const int64_t col = j0 + tid;
+#pragma unroll
+        for (int i = 0; i < kCb; ++i) {
+            if (i < nk) {
+                double v = R[static_cast<int64_t>(k0 + i) * np + col];
+                for (int p = 0; p < i; ++p) v -= d[p][i] * x[p];
+                x[i] = v / d[i][i];
+                R[static_cast<int64_t>(k0 + i) * np + col] = x[i];
+            }
+        }
+    }
+}
+
+// W_ij -= R_ki^T R_kj for the block pair of this CTA (i <= j, both > k); 256 threads, 4 outputs each.
+__global__ void __launch_bounds__(256) k_chol_trail(double* __restrict__ R, int n, int np, int k, const int32_t* info) {
+    __shared__ double a[kCb][kCb + 1], b[kCb][kCb + 1];
+    if (load_status(info) != 0) return;
+    const int nb = (n + kCb - 1) / kCb, m = nb - k - 1;
+    // pair index -> (i, j), k < i <= j < nb: row-major over the upper triangle of the m x m trailing blocks
+    int t = blockIdx.x, ii = 0;
+    while (t >= m - ii) { t -= m - ii; ++ii; }
+    const int bi = k + 1 + ii, bj = bi + t;
+    const int k0 = k * kCb, nk = n - k0 < kCb ? n - k0 : kCb;
+    const int i0 = bi * kCb, j0 = bj * kCb;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < kCb * kCb; e += blockDim.x) {
+        const int p = e / kCb, q = e % kCb;
+        a[p][q] = (p < nk && i0 + q < n) ? R[static_cast<int64_t>(k0 + p) * np + i0 + q] : 0.0;
+        b[p][q] = (p < nk && j0 + q < n) ? R[static_cast<int64_t>(k0 + p) * np + j0 + q] : 0.0;
+    }
+    __syncthreads();
+    const int q = tid & 31, r0 = tid >> 5;   // column q of the tile, rows r0, r0 + 8, r0 + 16, r0 + 24
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+        const int r = r0 + 8 * rr;
+        const int gi = i0 + r, gj = j0 + q;
+        if (gi < n && gj < n && gi <= gj) {
+            double sum = 0.0;
+            for (int p = 0; p < nk; ++p) sum = fma(a[p][r], b[p][q], sum);
+            R[static_cast<int64_t>(gi) * np + gj] -= sum;
+        }
+    }
+}
+
+__global__ void k_chol_out(const double* __restrict__ R, int n, int np, double* __restrict__ R_user,
+                           const int32_t* info) {
+    if (load_status(info) != 0) return;
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= static_cast<int64_t>(n) * n) return;
+    const int r = static_cast<int>(e / n), c = static_cast<int>(e % n);
+    R_user[e] = R[static_cast<int64_t>(r) * np + c];
 }
 
 // R[i][j] = sum_{k=i..j} R1[i][k] Rs[k][j] for j >= i, 0 below; block i = row i.
@@ -202,7 +272,17 @@ cudaError_t launch_householder(double* W, int64_t lds, int s, int n, int np, dou
 cudaError_t launch_cholesky(const double* G, int64_t ldg, int n, int np, double* R, double* R_user,
                             int32_t* info, cudaStream_t st) {
     if (np > kMaxNP) {
-        k_cholesky_wide<<<1, 1024, 0, st>>>(G, ldg, n, np, R, R_user, info);
+        const int64_t tot = static_cast<int64_t>(np) * np;
+        k_chol_init<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(G, ldg, n, np, R, info);
+        const int nb = (n + kCb - 1) / kCb;
+        for (int k = 0; k < nb; ++k) {
+            k_chol_panel<<<nb - k, 256, 0, st>>>(R, n, np, k, info);
+            const int m = nb - k - 1;
+            if (m > 0) k_chol_trail<<<m * (m + 1) / 2, 256, 0, st>>>(R, n, np, k, info);
+        }
+        if (R_user)
+            k_chol_out<<<static_cast<unsigned>((static_cast<int64_t>(n) * n + 255) / 256), 256, 0, st>>>(R, n, np,
+                                                                                                     R_user, info);
         return cudaGetLastError();
     }
     const size_t smem = static_cast<size_t>(np + kCholParts) * np * sizeof(double);
