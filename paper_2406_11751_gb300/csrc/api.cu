@@ -930,9 +930,10 @@ static rpcholqr_status solve_split_right(rpcholqr_plan_s* p, const double* X, in
 // The SPLIT64 first pass above 128 columns, Y = X T^{-1} (T = R_s upper triangular), left-looking over
 // 64-column blocks, one row chunk (p->img_rows rows) at a time so that the chunk's stage image holds the
 // slices of every finished block: block J of a chunk is first Y[:, J] = X[:, J] - Y[:, <J] T[<J, J], one
-// split product over the image of blocks < J (each block its own exactness window, sliced against the
-// row's bound over that block alone), then its sub-block FP64 row passes joined by a K = sub split update
-// (as in solve_blocked), and the finished block is sliced into the image once.  The row passes max-merge
+// split product over the image of blocks < J (each pair of blocks one exactness window, sliced against
+// the row's bound over that pair alone), then its sub-block FP64 row passes joined by K = sub split
+// updates (as in solve_blocked), and the finished block is sliced into the image (an odd block together
+// with its even partner, which was sliced alone before).  The row passes max-merge
 // the bounds of the whole row into p->xexp (pass 2 slices against them) and of each column into
 // p->colexp.  Marks PASS1_UPDATE / PASS1_SOLVE2 around the first chunk's first product.
 static rpcholqr_status solve_split_wide(rpcholqr_plan_s* p, const double* X, int64_t ldx, const double* T,
@@ -989,8 +990,12 @@ static rpcholqr_status solve_split_wide(rpcholqr_plan_s* p, const double* X, int
                 }
             }
             if (c0 + nj < n) {
-                launch_slice_block_images(Yc + c0, ldy, rows, nj, p->aimg, img_nkw, 2 * J,
-                                          p->bexp + static_cast<int64_t>(J) * p->img_rows, info, st);
+                // the products' exactness windows are pairs of blocks (K = 128) with their own row bound: an
+                // even block is sliced alone (the last window of block J + 1's update), an odd one re-slices
+                // its pair
+                const int g0 = (J & 1) ? c0 - kBlk : c0;
+                launch_slice_block_images(Yc + g0, ldy, rows, c0 + nj - g0, p->aimg, img_nkw, g0 / 32,
+                                          p->bexp + static_cast<int64_t>(J >> 1) * p->img_rows, info, st);
                 ++p->launches;
             }
         }

@@ -464,13 +464,13 @@ __global__ void __launch_bounds__(512) k_slice_col_images(const double* __restri
     slice_store8(x, E, img + static_cast<size_t>(blk * nst + st) * kAStage + core_off(lr, 16 * c), kASlice);
 }
 
-// ---- stage images of one 64-column block, against the block's own row bounds ---------------------------
-// The left-looking wide first pass slices each finished block of A_1 once: columns c0 .. c0 + nc - 1 of X
-// (nc <= 64) become stages kw0 and kw0 + 1 of row tile tm's image (img_nkw stages per row tile), sliced
-// against the row's bound over the block alone, which is written to bexp[row].  The products that read
-// the image treat each block as its own exactness window with its own row bound.  One CTA per 128-row
-// tile; thread (row, q) holds values 16 q .. 16 q + 15 of its row (the row bound is the maximum over
-// the four).
+// ---- stage images of up to 128 finished columns, against their own row bounds --------------------------
+// The left-looking wide first pass slices its finished 64-column blocks in pairs: columns c0 .. c0 + nc - 1
+// of X (nc <= 128: one block, or a pair) become stages kw0 .. kw0 + ceil(nc / 32) - 1 of row tile tm's
+// image (img_nkw stages per row tile), sliced against the row's bound over those columns alone, written
+// to bexp[row].  The products that read the image take each such group of up to 128 columns as one
+// exactness window with its own row bound.  One CTA per 128-row tile; thread (row, q) slices stage
+// kw0 + q (values 32 q .. 32 q + 31 of its row); the row bound is the maximum over the four.
 __global__ void __launch_bounds__(512) k_slice_block_images(const double* __restrict__ X, int64_t ldx, int64_t m,
                                                             int nc, uint8_t* __restrict__ img, int img_nkw, int kw0,
                                                             int32_t* __restrict__ bexp, const int32_t* info) {
@@ -479,13 +479,11 @@ __global__ void __launch_bounds__(512) k_slice_block_images(const double* __rest
     const int64_t tm = blockIdx.x;
     const int lr = threadIdx.x & (kTileM - 1), q = threadIdx.x >> 7;
     const int64_t row = tm * kTileM + lr;
-    double x[16];
     int e = kNoExp;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const int k = 16 * q + i;
-        x[i] = (row < m && k < nc) ? X[row * ldx + k] : 0.0;
-        const int ek = exp_bound(x[i]);
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) {
+        const int k = 32 * q + i;
+        const int ek = exp_bound((row < m && k < nc) ? X[row * ldx + k] : 0.0);
         e = ek > e ? ek : e;
     }
     red[q][lr] = e;
@@ -494,13 +492,17 @@ __global__ void __launch_bounds__(512) k_slice_block_images(const double* __rest
 #pragma unroll
     for (int j = 1; j < 4; ++j) E = red[j][lr] > E ? red[j][lr] : E;
     if (q == 0 && row < m) bexp[row] = E;
-    uint8_t* dst = img + static_cast<size_t>(tm * img_nkw + kw0 + (q >> 1)) * kAStage;
-#pragma unroll
-    for (int cc = 0; cc < 2; ++cc) {
+    if (32 * q >= nc) return;   // no stage of this group
+    uint8_t* dst = img + static_cast<size_t>(tm * img_nkw + kw0 + q) * kAStage;
+    // the row's values again (now from cache), 8 at a time
+    for (int c = 0; c < 4; ++c) {
         double x8[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) x8[i] = x[8 * cc + i];
-        slice_store8(x8, E, dst + core_off(lr, 16 * ((2 * q + cc) & 3)), kASlice);
+        for (int i = 0; i < 8; ++i) {
+            const int k = 32 * q + 8 * c + i;
+            x8[i] = (row < m && k < nc) ? X[row * ldx + k] : 0.0;
+        }
+        slice_store8(x8, E, dst + core_off(lr, 16 * c), kASlice);
     }
 }
 
@@ -962,9 +964,9 @@ k_ozaki_gemm_db(const uint8_t* __restrict__ aimg, const int32_t* __restrict__ xe
     const int64_t ntm = (m + kTileM - 1) / kTileM;
     const int64_t ntiles = ntm * ntn;
     const bool tr = tri != 0;
-    // exactness windows: 4 stages (K = 128) against one row bound xexp, or (bexp) one 64-column block of
-    // 2 stages each, against its own row bound bexp[w * ld_bexp + row]
-    const int wlen = bexp ? 2 : 4;
+    // exactness windows of 4 stages (K = 128), against one row bound xexp, or (bexp) each against its own
+    // row bound bexp[w * ld_bexp + row] (the image's column groups: window w = columns 128 w .. 128 w + 127)
+    const int wlen = 4;
 
     if (warp == kDbEpiWarps) {
         // stage copies, running ahead of the MMAs by the two stage buffers
@@ -1784,7 +1786,7 @@ cudaError_t launch_ozaki_gemm(bool sub, const double* X, int64_t ldx, const int3
         const int64_t tiles = ((m + oz::kTileM - 1) / oz::kTileM) * ((N + oz::kDbN - 1) / oz::kDbN);
         const int g = static_cast<int>(grid < tiles ? grid : tiles);
         const int nkw = (K + oz::kKW - 1) / oz::kKW;
-        if (img_nkw < nkw || (bexp && (K % 64 != 0))) return cudaErrorInvalidValue;
+        if (img_nkw < nkw) return cudaErrorInvalidValue;
         kdb<<<g, oz::kDbThreads, oz::kDbSmem, st>>>(aimg, xexp, K, yblocks, yexp, N, B, ldb, C, ldc, m, info, spin,
                                                     y_upper ? 1 : 0, img_nkw, bexp, ld_bexp);
         return cudaGetLastError();
