@@ -161,6 +161,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+// A hint to bring `bytes` (a multiple of 16, 16-byte aligned source) into L2 ahead of a bulk copy: with two
+// stage buffers a stage's copy is issued only when the MMAs two stages back are done, so a stage coming
+// cold from HBM would leave the tensor core waiting for the whole DRAM latency.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
+}
+// Stages prefetched into L2 ahead of the stage being copied (64 KB each: 152 SMs x 4 x 64 KB = 39 MB of L2).
+constexpr int kPrefetchAhead = 4;
+
 // Before a kernel that issued bulk copies returns (also after a timeout): the last copy issued into each
 // stage buffer has landed (parity of its phase), bounded like every wait.
 __device__ __forceinline__ bool bulk_drain(uint64_t* load_bar, const int64_t (&issued)[2]) {
@@ -469,22 +478,39 @@ __global__ void __launch_bounds__(512) k_slice_col_images(const double* __restri
 // of X (nc <= 128: one block, or a pair) become stages kw0 .. kw0 + ceil(nc / 32) - 1 of row tile tm's
 // image (img_nkw stages per row tile), sliced against the row's bound over those columns alone, written
 // to bexp[row].  The products that read the image take each such group of up to 128 columns as one
-// exactness window with its own row bound.  One CTA per 128-row tile; thread (row, q) slices stage
-// kw0 + q (values 32 q .. 32 q + 31 of its row); the row bound is the maximum over the four.
-__global__ void __launch_bounds__(512) k_slice_block_images(const double* __restrict__ X, int64_t ldx, int64_t m,
+// exactness window with its own row bound.  One CTA per 64 rows (half a 128-row tile): the rows are
+// copied into shared memory in whole rows (consecutive lanes, consecutive columns), then thread (row, q)
+// takes stage kw0 + q (values 32 q .. 32 q + 31 of its row); the row bound is the maximum over the four.
+constexpr int kSbRows = 64;
+constexpr int kSbLd = 129;   // odd row stride (doubles): 8-byte reads of 32 consecutive rows hit distinct banks
+constexpr int kSbSmem = kSbRows * kSbLd * 8;
+__global__ void __launch_bounds__(256) k_slice_block_images(const double* __restrict__ X, int64_t ldx, int64_t m,
                                                             int nc, uint8_t* __restrict__ img, int img_nkw, int kw0,
                                                             int32_t* __restrict__ bexp, const int32_t* info) {
-    __shared__ int red[4][kTileM];
+    extern __shared__ double sb_tile[];
+    __shared__ int red[4][kSbRows];
     if (info && load_status(info) != 0) return;
-    const int64_t tm = blockIdx.x;
-    const int lr = threadIdx.x & (kTileM - 1), q = threadIdx.x >> 7;
-    const int64_t row = tm * kTileM + lr;
+    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * kSbRows;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < kSbRows * nc; e += 256) {
+        const int r = e / nc, c = e - r * nc;
+        const bool ok = r0 + r < m;
+        cp_async8(&sb_tile[r * kSbLd + c], ok ? X + (r0 + r) * ldx + c : X, ok);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    const int lr = tid & (kSbRows - 1), q = tid >> 6;
+    const int64_t row = r0 + lr;
+    const double* xr = sb_tile + lr * kSbLd;
     int e = kNoExp;
+    if (row < m) {
 #pragma unroll 8
-    for (int i = 0; i < 32; ++i) {
-        const int k = 32 * q + i;
-        const int ek = exp_bound((row < m && k < nc) ? X[row * ldx + k] : 0.0);
-        e = ek > e ? ek : e;
+        for (int i = 0; i < 32; ++i) {
+            const int k = 32 * q + i;
+            const int ek = exp_bound(k < nc ? xr[k] : 0.0);
+            e = ek > e ? ek : e;
+        }
     }
     red[q][lr] = e;
     __syncthreads();
@@ -493,16 +519,17 @@ __global__ void __launch_bounds__(512) k_slice_block_images(const double* __rest
     for (int j = 1; j < 4; ++j) E = red[j][lr] > E ? red[j][lr] : E;
     if (q == 0 && row < m) bexp[row] = E;
     if (32 * q >= nc) return;   // no stage of this group
+    const int64_t tm = r0 / kTileM;
+    const int tr = static_cast<int>(r0 - tm * kTileM) + lr;   // row inside the 128-row stage tile
     uint8_t* dst = img + static_cast<size_t>(tm * img_nkw + kw0 + q) * kAStage;
-    // the row's values again (now from cache), 8 at a time
     for (int c = 0; c < 4; ++c) {
         double x8[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int k = 32 * q + 8 * c + i;
-            x8[i] = (row < m && k < nc) ? X[row * ldx + k] : 0.0;
+            x8[i] = (row < m && k < nc) ? xr[k] : 0.0;
         }
-        slice_store8(x8, E, dst + core_off(lr, 16 * c), kASlice);
+        slice_store8(x8, E, dst + core_off(tr, 16 * c), kASlice);
     }
 }
 
@@ -973,10 +1000,33 @@ k_ozaki_gemm_db(const uint8_t* __restrict__ aimg, const int32_t* __restrict__ xe
         if (lane == 0) {
             int64_t g = 0, issued[2] = {0, 0};
             bool ok = true;
+            // L2 prefetch cursor, kPrefetchAhead stages ahead of the copies (the same walk over tiles/stages)
+            int64_t pt = blockIdx.x;
+            int pkw = 0, pnk = pt < ntiles ? db_tile_stages(tile_col(pt, ntn, tr), nkw, tr) : 0;
+            auto prefetch_next = [&]() {
+                if (pt >= ntiles) return;
+                bulk_prefetch_l2(aimg + static_cast<size_t>((pt / ntn) * img_nkw + pkw) * kAStage, kAStage);
+                if (++pkw == pnk) {
+                    pkw = 0;
+                    pt += gridDim.x;
+                    if (pt < ntiles) pnk = db_tile_stages(tile_col(pt, ntn, tr), nkw, tr);
+                }
+            };
+            for (int i = 0; i < kPrefetchAhead; ++i) prefetch_next();
+            // B rows of a tile are read at its end, after all its stages: bring them into L2 when its first
+            // stage is issued (whole 16-byte granules of each row inside the row; only for 16-byte aligned rows)
+            const bool b_pf = SUB && (reinterpret_cast<uintptr_t>(B) & 15) == 0 && (ldb & 1) == 0;
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 const int64_t tm = t / ntn;
                 const int tn = tile_col(t, ntn, tr);
                 const int nk = db_tile_stages(tn, nkw, tr);
+                if (b_pf) {
+                    const int nb = ((N - tn * kDbN < kDbN ? N - tn * kDbN : kDbN) * 8) & ~15;
+                    const int64_t rend = (tm + 1) * kTileM < m ? (tm + 1) * kTileM : m;
+                    if (nb > 0)
+                        for (int64_t r = tm * kTileM; r < rend; ++r)
+                            bulk_prefetch_l2(B + r * ldb + tn * kDbN, static_cast<uint32_t>(nb));
+                }
                 for (int kw = 0; kw < nk; ++kw, ++g) {
                     const int s = static_cast<int>(g & 1);
                     if (g >= 2 && !mbar_wait_ab(&empty_bar[s], static_cast<uint32_t>(((g >> 1) - 1) & 1), &abort_s, spin)) {
@@ -992,6 +1042,7 @@ k_ozaki_gemm_db(const uint8_t* __restrict__ aimg, const int32_t* __restrict__ xe
                     for (int b = 0; b < kSlices; ++b)
                         bulk_g2s(stB[s] + b * kDbBSlice, bsrc + static_cast<size_t>(b) * kBSlice, kDbBSlice, &load_bar[s]);
                     ++issued[s];
+                    prefetch_next();
                 }
             }
             if (!bulk_drain(load_bar, issued)) ok = false;
@@ -1078,6 +1129,19 @@ k_ozaki_gemm_db(const uint8_t* __restrict__ aimg, const int32_t* __restrict__ xe
             }
             if (!ok) break;   // (uniform over the drain warps)
             const int col0 = tn * kDbN;
+            const int ncols = N - col0 < kDbN ? N - col0 : kDbN;
+            // this thread's B values of the store loop below, all in flight while the tile is scaled
+            constexpr int kStoreIt = kTileM * kDbN / kDbEpi;
+            double bv[SUB ? kStoreIt : 1];
+            if constexpr (SUB) {
+#pragma unroll
+                for (int i = 0; i < kStoreIt; ++i) {
+                    const int e = tid + i * kDbEpi;
+                    const int r = e >> 5, c = e & 31;
+                    const int64_t grow = tm * kTileM + r;
+                    bv[i] = (grow < m && c < ncols) ? B[grow * ldb + col0 + c] : 0.0;
+                }
+            }
 #pragma unroll
             for (int j = 0; j < kDbCols; ++j) {
                 const int col = col0 + kDbCols * h + j;
@@ -1086,14 +1150,13 @@ k_ozaki_gemm_db(const uint8_t* __restrict__ aimg, const int32_t* __restrict__ xe
                     (E > kNoExp && ey > kNoExp) ? scale_pow2(acc[j], E + ey - 53) : 0.0;
             }
             epi_sync();
-            const int ncols = N - col0 < kDbN ? N - col0 : kDbN;
-#pragma unroll 4
-            for (int i = 0; i < kTileM * kDbN / kDbEpi; ++i) {
+#pragma unroll
+            for (int i = 0; i < kStoreIt; ++i) {
                 const int e = tid + i * kDbEpi;
                 const int r = e >> 5, c = e & 31;
                 const int64_t grow = tm * kTileM + r;
                 if (grow < m && c < ncols) {
-                    if (SUB) C[grow * ldc + col0 + c] = B[grow * ldb + col0 + c] - W[r * kDbEpiLd + c];
+                    if constexpr (SUB) C[grow * ldc + col0 + c] = bv[i] - W[r * kDbEpiLd + c];
                     else C[grow * ldc + col0 + c] = W[r * kDbEpiLd + c];
                 }
             }
@@ -1380,6 +1443,17 @@ k_ozaki_gram_db(int64_t m, int n, int np, const int32_t* __restrict__ colexp, in
             bool ok = true;
             const uint8_t* abase = gimg + static_cast<size_t>(P) * nsg * kAStage;
             const uint8_t* bbase = gimg + static_cast<size_t>(Qb >> 2) * nsg * kAStage + (Qb & 3) * kDbBSlice;
+            // L2 prefetch of the stage kPrefetchAhead ahead (A stage and B's eight slices)
+            auto prefetch = [&](int64_t pst) {
+                if (pst >= nstages) return;
+                const size_t sg = static_cast<size_t>(r0 / kKW + pst);
+                bulk_prefetch_l2(abase + sg * kAStage, kAStage);
+                if ((Qb >> 2) != P)
+#pragma unroll
+                    for (int b = 0; b < kSlices; ++b)
+                        bulk_prefetch_l2(bbase + sg * kAStage + static_cast<size_t>(b) * kASlice, kDbBSlice);
+            };
+            for (int i = 0; i < kPrefetchAhead; ++i) prefetch(i);
             for (int64_t st = 0; st < nstages; ++st) {
                 const int s = static_cast<int>(st & 1);
                 if (st >= 2 && !mbar_wait_ab(&empty_bar[s], static_cast<uint32_t>(((st >> 1) - 1) & 1), &abort_s, spin)) {
@@ -1394,6 +1468,7 @@ k_ozaki_gram_db(int64_t m, int n, int np, const int32_t* __restrict__ colexp, in
                     bulk_g2s(stB[s] + b * kDbBSlice, bbase + sg * kAStage + static_cast<size_t>(b) * kASlice, kDbBSlice,
                              &load_bar[s]);
                 ++issued[s];
+                prefetch(st + kPrefetchAhead);
             }
             if (!bulk_drain(load_bar, issued)) ok = false;
             if (!ok) abort_s = 1;
@@ -1872,7 +1947,11 @@ cudaError_t launch_ozaki_gram(const double* X, int64_t ldx, int64_t m, int n, in
 
 void launch_slice_block_images(const double* X, int64_t ldx, int64_t m, int nc, uint8_t* img, int img_nkw, int kw0,
                                int32_t* bexp, const int32_t* info, cudaStream_t st) {
-    oz::k_slice_block_images<<<static_cast<unsigned>((m + oz::kTileM - 1) / oz::kTileM), 512, 0, st>>>(
+    if (cudaFuncSetAttribute(oz::k_slice_block_images, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::kSbSmem) !=
+        cudaSuccess)
+        return;   // the launch error surfaces at the caller's check
+    // both halves of every 128-row tile (rows past m are written as zero slices, as the products read them)
+    oz::k_slice_block_images<<<static_cast<unsigned>((m + oz::kTileM - 1) / oz::kTileM * 2), 256, oz::kSbSmem, st>>>(
         X, ldx, m, nc, img, img_nkw, kw0, bexp, info);
 }
 void launch_slice_col_images(const double* X, int64_t ldx, int64_t m, int n, int np, const int32_t* colexp,
