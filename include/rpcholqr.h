@@ -260,6 +260,15 @@ rpcholqr_status rpcholqr_ozaki_gemm(rpcholqr_plan plan, const double* X, int64_t
                                     const double* Y, int32_t N, int64_t ldy, double* C, int64_t ldc,
                                     int32_t* info, void* stream);
 
+/* Split-precision update C = B - X Y (the off-diagonal block update of the blocked row solve,
+ * Section 4's A1 = A Rs^{-1} by column blocks): the product as rpcholqr_ozaki_gemm, subtracted from B
+ * in FP64 (B device m x N, ldb; C device m x N, ldc; C may equal B, must not overlap X).  K <= 32 runs
+ * the update kernel of SPLIT64's first pass, larger K the windowed product in subtract form.  Same
+ * error bound per entry as rpcholqr_ozaki_gemm plus the rounding of the subtraction.  SPLIT64 plan. */
+rpcholqr_status rpcholqr_ozaki_update(rpcholqr_plan plan, const double* X, int64_t m, int32_t K, int64_t ldx,
+                                      const double* Y, int32_t N, int64_t ldy, const double* B, int64_t ldb,
+                                      double* C, int64_t ldc, int32_t* info, void* stream);
+
 /* Split-precision Gram matrix G = X^T X (device n x n, full) of X (device m x n, ldx), the kernel
  * SPLIT64 uses for G1; error per entry below ~2^-53 * 2^(Ep+Eq) * rows (Ep: power-of-two bound of
  * column p).  SPLIT64 plan, m <= plan max_m. */

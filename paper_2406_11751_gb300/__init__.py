@@ -25,7 +25,7 @@ __all__ = [
     "rpcholqr_batch_replay", "rpcholqr_batch_autotune", "FP32", "rpcholqr_factor_f32",
     "rpcholqr_gather_owned_rows", "rpcholqr_sketch_r_from_sample", "rpcholqr_sum_partials",
     "rpcholqr_plan_set_smoothing", "rpcholqr_smoothed_sample", "SMOOTH_NONE", "SMOOTH_WHT", "SMOOTH_DCT",
-    "rpcholqr_plan_split_pass2_fp64", "rpcholqr_scholqr3",
+    "rpcholqr_plan_split_pass2_fp64", "rpcholqr_scholqr3", "rpcholqr_ozaki_update",
 ]
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NONFINITE", 3: "ERR_SINGULAR_SKETCH", 4: "ERR_NOT_SPD",
@@ -52,7 +52,7 @@ EXPORTED_SYMBOLS = (
     "rpcholqr_plan_set_smoothing", "rpcholqr_smoothed_sample", "rpcholqr_plan_split_pass2_fp64",
     "rpcholqr_scholqr3", "rpcholqr_plan_set_option", "rpcholqr_plan_get_option",
     "rpcholqr_factor_batched", "rpcholqr_batch_factor", "rpcholqr_plan_collect_kernel_timing",
-    "rpcholqr_autotune", "rpcholqr_autotune_table", "rpcholqr_autotune_parse",
+    "rpcholqr_autotune", "rpcholqr_autotune_table", "rpcholqr_autotune_parse", "rpcholqr_ozaki_update",
 )
 PHASES = ("sample", "sketch_qr", "prep_rs", "pass1", "pass1_update", "pass1_solve2", "gram_reduce",
           "cholesky", "prep_r1", "pass2", "recover_r")
@@ -112,6 +112,7 @@ def load_library():
         "rpcholqr_plan_collect_timing": [P, P, ctypes.POINTER(I32), ctypes.POINTER(I64)],
         "rpcholqr_plan_collect_kernel_timing": [P, P, P, P],
         "rpcholqr_ozaki_gemm": [P, P, I64, I32, I64, P, I32, I64, P, I64, P, P],
+        "rpcholqr_ozaki_update": [P, P, I64, I32, I64, P, I32, I64, P, I64, P, I64, P, P],
         "rpcholqr_ozaki_gram": [P, P, I64, I32, I64, P, P, P],
         "rpcholqr_cholqr": [P, P, I64, I32, I64, P, I64, P, P, P],
         "rpcholqr_cholqr2": [P, P, I64, I32, I64, P, I64, P, P, P],
@@ -513,6 +514,28 @@ def rpcholqr_ozaki_gemm(plan: Plan, X, Y, C=None, info=None, stream=None):
     _check("rpcholqr_ozaki_gemm", load_library().rpcholqr_ozaki_gemm(
         plan.handle, _ptr(X), m, K, X.stride(0), _ptr(Y), N, Y.stride(0), _ptr(C), C.stride(0),
         _ptr(info), _stream(stream, X.device)))
+    return C, info
+
+
+def rpcholqr_ozaki_update(plan: Plan, X, Y, B, C=None, info=None, stream=None):
+    """C = B - X Y with the split-precision (FP64-accurate) product (SPLIT64 plan); C may be B."""
+    torch = _torch()
+    _mat(X, "X")
+    _mat(Y, "Y")
+    _mat(B, "B")
+    m, K = X.shape
+    N = Y.shape[1]
+    if tuple(B.shape) != (m, N):
+        raise ValueError(f"B must be {m} x {N}, got {tuple(B.shape)}")
+    if C is None:
+        C = torch.empty((m, N), dtype=torch.float64, device=X.device)
+    _mat(C, "C")
+    if tuple(C.shape) != (m, N):
+        raise ValueError(f"C must be {m} x {N}, got {tuple(C.shape)}")
+    info = _info(info, X.device)
+    _check("rpcholqr_ozaki_update", load_library().rpcholqr_ozaki_update(
+        plan.handle, _ptr(X), m, K, X.stride(0), _ptr(Y), N, Y.stride(0), _ptr(B), B.stride(0), _ptr(C),
+        C.stride(0), _ptr(info), _stream(stream, X.device)))
     return C, info
 
 

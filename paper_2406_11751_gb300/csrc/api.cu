@@ -1789,6 +1789,22 @@ rpcholqr_status rpcholqr_ozaki_gemm(rpcholqr_plan p, const double* X, int64_t m,
     return ozaki_gemm_internal(p, false, X, m, K, ldx, Y, N, ldy, nullptr, 0, C, ldc, info, st);
 }
 
+rpcholqr_status rpcholqr_ozaki_update(rpcholqr_plan p, const double* X, int64_t m, int32_t K, int64_t ldx,
+                                      const double* Y, int32_t N, int64_t ldy, const double* B, int64_t ldb,
+                                      double* C, int64_t ldc, int32_t* info, void* stream) {
+    if (!p || !X || !Y || !B || !C || !info || p->mode != RPCHOLQR_SPLIT64) return RPCHOLQR_ERR_ARG;
+    if (m < 1 || m > p->max_m || K < 1 || K > p->np || N < 1 || N > p->np || ldx < K || ldy < N || ldb < N ||
+        ldc < N)
+        return RPCHOLQR_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+    select_tuning(p, m, K);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rpcholqr_status rc = reset_info(info, st);
+    if (rc != RPCHOLQR_OK) return rc;
+    return ozaki_gemm_internal(p, true, X, m, K, ldx, Y, N, ldy, B, ldb, C, ldc, info, st);
+}
+
 rpcholqr_status rpcholqr_ozaki_gram(rpcholqr_plan p, const double* X, int64_t m, int32_t n, int64_t ldx,
                                     double* G, int32_t* info, void* stream) {
     if (!p || !X || !G || !info || p->mode != RPCHOLQR_SPLIT64) return RPCHOLQR_ERR_ARG;

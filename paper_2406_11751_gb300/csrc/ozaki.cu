@@ -1177,7 +1177,9 @@ k_ozaki_gemm_db(const uint8_t* __restrict__ aimg, const int32_t* __restrict__ xe
 // Tiles of 128 rows x 32 output columns, so that one tile's eight group accumulators take 256 TMEM
 // columns and two tiles are in flight: the tensor core fills one buffer while the other is drained.
 // The X slices of a 128-row block (one K stage) are produced once and used by all N/32 column tiles of
-// the block; the Y slices (at most 128 columns) stay in shared memory for the whole launch.  Warp roles:
+// the block; the Y slices (at most 128 columns) stay in shared memory for the whole launch.  The X rows
+// of the producers' next block arrive by cp.async in a raw buffer (whole rows across consecutive lanes)
+// while the current block is sliced, so the slicing reads shared memory.  Warp roles:
 // warps 0-3 produce (thread = row of the block), warps 4-19 drain (warp w reads TMEM lanes 32 (w % 4)..,
 // columns 8 ((w - 4) / 4)..: four warps per lane quarter keep enough independent FP64 conversions and
 // subtractions in flight), warp 20 issues the MMAs.  Barriers: stage_full/stage_empty per X stage
@@ -1187,7 +1189,10 @@ constexpr int kUpdTileN = 32;
 constexpr int kUpdMaxN = 128;
 constexpr int kUpdProducers = 4, kUpdDrainers = 16;
 constexpr int kUpdThreads = 32 * (kUpdProducers + kUpdDrainers + 1);
-constexpr int kUpdSmem = 2 * kAStage + (kUpdMaxN / kTileN) * kBStage;   // 192 KB
+constexpr int kUpdRawLd = kKW + 1;                                       // raw X row stride (doubles)
+constexpr int kUpdRawOff = 2 * kAStage + (kUpdMaxN / kTileN) * kBStage;  // after the stages and Y slices
+constexpr int kUpdSmem = kUpdRawOff + kTileM * kUpdRawLd * 8;            // 225 KB
+static_assert(kUpdSmem + 1024 <= 232448, "k_ozaki_update exceeds the 227 KB shared-memory limit");
 constexpr int kUpdBSlice = kUpdTileN * kKW * 2;                          // 2 KB: one slice of a 32-column tile
 constexpr int kUpdBTile = kSlices * kUpdBSlice;                          // 16 KB: its eight slices
 // The 36 slice pairs of one 32-column tile for nkk K steps of 16 (group d into columns (d - 2) * 32 of
@@ -1220,6 +1225,7 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint8_t* stA[2] = {sm, sm + kAStage};
     uint8_t* yres = sm + 2 * kAStage;                 // Y slices: 32-column tile j at j * kUpdBTile
+    double* raw = reinterpret_cast<double*>(sm + kUpdRawOff);   // X rows of the producers' next block
     const int nsub = (N + kUpdTileN - 1) / kUpdTileN;
     const int nkk = (K + 15) / 16;
     const int64_t ntm = (m + kTileM - 1) / kTileM;
@@ -1266,14 +1272,31 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
     const uint32_t tmem = tslot;
 
     if (warp < kUpdProducers) {
-        // producers: thread = row of the 128-row block; slice its K values into the block's stage
+        // producers: the 128 threads copy a block's X rows into raw (whole rows, one value per lane) one
+        // block ahead; thread lr slices row lr of the current block from raw into its stage
         const int lr = tid;
+        auto copy_raw = [&](int64_t tt) {
+            const int64_t rbase = (blockIdx.x + tt * gridDim.x) * kTileM;
+            for (int e = tid; e < kTileM * K; e += 32 * kUpdProducers) {
+                const int r = e / K, c = e - r * K;
+                const bool in = rbase + r < m;
+                cp_async8(raw + r * kUpdRawLd + c, in ? X + (rbase + r) * ldx + c : X, in);
+            }
+            cp_async_commit();
+        };
+        if (my_tiles > 0) copy_raw(0);
         uint32_t ph[2] = {0u, 0u};
         for (int64_t t = 0; t < my_tiles; ++t) {
             const int s = static_cast<int>(t & 1);
+            bool ok = true;
             if (t >= 2) {
-                if (!mbar_wait_ab(&stage_empty[s], ph[s], &abort_s, spin)) { abort_s = 1; break; }
+                ok = mbar_wait_ab(&stage_empty[s], ph[s], &abort_s, spin);
                 ph[s] ^= 1u;
+            }
+            cp_async_wait_all();
+            if (prod_sync_or(!ok, 32 * kUpdProducers)) {   // raw rows landed; a wait that gave up ends all
+                abort_s = 1;
+                break;
             }
             const int64_t row = (blockIdx.x + t * gridDim.x) * kTileM + lr;
             const int E = row < m ? xexp[row] : kNoExp;
@@ -1284,18 +1307,23 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int k = 8 * c + i;
-                    x[i] = (row < m && k < K) ? X[row * ldx + k] : 0.0;
+                    x[i] = k < K ? raw[lr * kUpdRawLd + k] : 0.0;
                 }
                 slice_store8(x, E, stA[s] + core_off(lr, 16 * c), kASlice);
             }
             fence_async_smem();
-            __syncwarp();
+            prod_sync(32 * kUpdProducers);        // every row sliced, raw free
             if (lane == 0) mbar_arrive(&stage_full[s]);
+            if (t + 1 < my_tiles) copy_raw(t + 1);
         }
+        cp_async_wait_all();
     } else if (warp < kUpdProducers + kUpdDrainers) {
         // drainers: warp w reads TMEM lanes 32 (w % 4).. and columns 8 h.. of every tile
         const int q = warp & 3, h = (warp - kUpdProducers) >> 2;
         const int lr = 32 * q + lane;
+        // B and C rows 16-byte aligned (column tiles start at multiples of 8 values): pairs as one access
+        const bool vec = ((reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15) == 0 &&
+                         ((ldb | ldc) & 1) == 0;
         int64_t u = 0;   // tiles drained so far (TMEM buffer u & 1)
         for (int64_t t = 0; t < my_tiles && !*reinterpret_cast<volatile int*>(&abort_s); ++t) {
             const int64_t row = (blockIdx.x + t * gridDim.x) * kTileM + lr;
@@ -1303,12 +1331,19 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
             for (int j = 0; j < nsub; ++j, ++u) {
                 const int b = static_cast<int>(u & 1);
                 const int cbase = j * kUpdTileN + 8 * h;
-                // this thread's 8 values of B, read while the tile's MMAs run
+                // this thread's 8 values of B, read while the tile's MMAs run (16-byte pairs where aligned)
                 double bv[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < 8; i += 2) {
                     const int col = cbase + i;
-                    bv[i] = (row < m && col < N) ? B[row * ldb + col] : 0.0;
+                    if (vec && row < m && col + 1 < N) {
+                        const double2 v2 = *reinterpret_cast<const double2*>(B + row * ldb + col);
+                        bv[i] = v2.x;
+                        bv[i + 1] = v2.y;
+                    } else {
+                        bv[i] = (row < m && col < N) ? B[row * ldb + col] : 0.0;
+                        bv[i + 1] = (row < m && col + 1 < N) ? B[row * ldb + col + 1] : 0.0;
+                    }
                 }
                 if (!mbar_wait_ab(&acc_full[b], static_cast<uint32_t>((u >> 1) & 1), &abort_s, spin)) {
                     abort_s = 1;
@@ -1323,17 +1358,26 @@ k_ozaki_update(const double* X, int64_t ldx, const int32_t* __restrict__ xexp, i
                     for (int g = 0; g < kGroups; ++g) tmem_ld4(tb + g * kUpdTileN + c0, mg[g]);
                     tmem_wait_ld();
                     if (row < m) {
+                        double cv[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const int col = cbase + c0 + i;
-                            if (col < N) {
-                                float grp[kGroups];
+                            float grp[kGroups];
 #pragma unroll
-                                for (int g = 0; g < kGroups; ++g) grp[g] = mg[g][i];
-                                const long long I = combine_units53_k32(grp);
-                                const int ey = yexp[col];
-                                const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(I, E + ey - 53) : 0.0;
-                                C[row * ldc + col] = bv[c0 + i] - v;
+                            for (int g = 0; g < kGroups; ++g) grp[g] = mg[g][i];
+                            const long long I = combine_units53_k32(grp);
+                            const int ey = col < N ? yexp[col] : kNoExp;
+                            const double v = (E > kNoExp && ey > kNoExp) ? scale_pow2(I, E + ey - 53) : 0.0;
+                            cv[i] = bv[c0 + i] - v;
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; i += 2) {
+                            const int col = cbase + c0 + i;
+                            if (vec && col + 1 < N) {
+                                *reinterpret_cast<double2*>(C + row * ldc + col) = make_double2(cv[i], cv[i + 1]);
+                            } else {
+                                if (col < N) C[row * ldc + col] = cv[i];
+                                if (col + 1 < N) C[row * ldc + col + 1] = cv[i + 1];
                             }
                         }
                     }

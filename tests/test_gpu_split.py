@@ -51,6 +51,35 @@ def test_ozaki_gemm_matches_fp64(lib, splan, m, K, N):
     assert np.max(err / np.maximum(scale, 1e-300)) <= 8 * K * EPS
 
 
+# C = B - X Y: K <= 32 runs the first pass's update kernel (staged rows, B/C tiles in shared memory),
+# larger K the windowed product in subtract form.  Views with row strides wider than the matrix (odd
+# ones: rows not 16-byte aligned), ragged m, K and N, many row blocks per CTA, and C == B in place.
+@pytest.mark.parametrize("m,K,N,layout", [(128, 16, 48, "plain"), (1000, 16, 32, "plain"), (4099, 32, 96, "plain"),
+                                          (70001, 16, 48, "view"), (300, 9, 37, "odd"), (257, 32, 128, "inplace"),
+                                          (262147, 16, 16, "inplace"), (5000, 64, 64, "view"), (129, 1, 1, "plain")])
+def test_ozaki_update_matches_fp64(lib, splan, m, K, N, layout):
+    rng = np.random.default_rng(7 * m + K + N)
+    X = rng.standard_normal((m, K)) * (10.0 ** rng.uniform(-6, 6, size=(m, 1)))
+    Y = np.triu(rng.standard_normal((K, N)) * (10.0 ** rng.uniform(-3, 3, size=(1, N))), 1 - K)
+    B = rng.standard_normal((m, N)) * (10.0 ** rng.uniform(-4, 4, size=(m, 1)))
+    if layout == "plain" or layout == "inplace":
+        Xd, Bd = cu(X), cu(B)
+    else:
+        # columns of wider matrices: row strides K + 16 / N + 8, or odd ones (unaligned rows)
+        wx, wb = (K + 16, N + 8) if layout == "view" else (K + 5, N + 3)
+        Xw = torch.zeros((m, wx), dtype=torch.float64, device=DEV)
+        Bw = torch.zeros((m, wb), dtype=torch.float64, device=DEV)
+        Xd, Bd = Xw[:, 3:3 + K], Bw[:, 1:1 + N]
+        Xd.copy_(cu(X))
+        Bd.copy_(cu(B))
+    C, info = lib.rpcholqr_ozaki_update(splan, Xd, cu(Y), Bd, C=Bd if layout == "inplace" else None)
+    assert int(info[0]) == 0
+    ref = B - X @ Y
+    scale = pow2_bound(X, 1)[:, None] * pow2_bound(Y, 0)[None, :]
+    err = np.abs(host(C) - ref)
+    assert np.all(err <= 8 * K * EPS * scale + 2 * EPS * np.abs(ref))
+
+
 def test_ozaki_gemm_exact_on_small_integers(lib, splan):
     # integer inputs with few bits: every slice product and sum is exact, so is the result
     rng = np.random.default_rng(3)
