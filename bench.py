@@ -93,6 +93,9 @@ def parse_args(argv=None):
     ap.add_argument("--sharded", action="store_true",
                     help="one m x n matrix split by rows over the N processes (row-sharded factorisation: "
                          "FP64 steps, the sample and the Gram partials exchanged over NCCL; strong scaling)")
+    ap.add_argument("--image-rows", type=int, default=0,
+                    help="SPLIT64 above 128 columns: stage-image rows kept at a time (plan option "
+                         "RPCHOLQR_OPT_IMAGE_ROWS; 0 = automatic: every row when they fit a quarter of the device)")
     ap.add_argument("--profile-window", action="store_true",
                     help="cudaProfilerStart/Stop around the timed steps of the main mode only")
     args = ap.parse_args(argv)
@@ -369,7 +372,7 @@ def preload_torch_linalg():
 
 
 def timed_factor(rq, torch, local, dev, dist, m, n, s, mode, A, Q, R, info, stream, K, W, smoothing="none",
-                 clocks=False, profile=False, A32=None, Q32=None, R32=None):
+                 clocks=False, profile=False, A32=None, Q32=None, R32=None, image_rows=0):
     """W warm-up + K timed factor calls on a fresh plan of `mode` (CUDA events on the launching stream,
     barrier + synchronize on both sides): (ms over the K steps, phases, calls, launches, plan, clocks)."""
     modes = {"fp64": rq.FP64, "split": rq.SPLIT64, "fp32": rq.FP32}
@@ -381,6 +384,8 @@ def timed_factor(rq, torch, local, dev, dist, m, n, s, mode, A, Q, R, info, stre
             rq.rpcholqr_factor(plan, A, s, seed, Q=Q, R=R, info=info, stream=stream)
 
     plan = rq.rpcholqr_plan_create(local, m, n, s, mode=modes[mode])
+    if image_rows and mode == "split" and n > 128:
+        rq.rpcholqr_plan_set_option(plan, rq.OPT_IMAGE_ROWS, image_rows)
     if smoothing != "none":
         rq.rpcholqr_plan_set_smoothing(plan, rq.SMOOTH_WHT if smoothing == "wht" else rq.SMOOTH_DCT)
     for w in range(W):
@@ -616,6 +621,7 @@ def run_ours(args, ws, rank, local):
     R = torch.empty((n, n), dtype=torch.float64, device=dev)
     info = torch.empty(2, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    torch.cuda.empty_cache()    # the generator's temporaries back to the device before the plans allocate
     fp64_peak = rq.rpcholqr_probe_fp64_mma(local, 4096)
     A32 = Q32 = R32 = None
     if args.mode == "fp32":
@@ -625,7 +631,8 @@ def run_ours(args, ws, rank, local):
 
     def run(mode, steps, warm, clocks=False, profile=False):
         return timed_factor(rq, torch, local, dev, dist, m, n, s, mode, A, Q, R, info, stream, steps, warm,
-                            smoothing=args.smoothing, clocks=clocks, profile=profile, A32=A32, Q32=Q32, R32=R32)
+                            smoothing=args.smoothing, clocks=clocks, profile=profile, A32=A32, Q32=Q32, R32=R32,
+                            image_rows=args.image_rows)
 
     other = None
     if not args.no_compare:
@@ -638,6 +645,9 @@ def run_ours(args, ws, rank, local):
                  "warmup": ow, "phases_ms_per_step": phases_per_step(o_ph, o_calls)}
     t_ms_max, phases, calls, launches, plan, clk = run(args.mode, K, W, clocks=True, profile=args.profile_window)
     st = info.cpu().tolist()
+    image_rows = None
+    if args.mode == "split" and n > 128:
+        image_rows = rq.rpcholqr_plan_get_option(plan, rq.OPT_IMAGE_ROWS)
     if args.no_metrics:
         orth, res = None, None
     elif args.mode == "fp32":
@@ -771,6 +781,7 @@ def run_ours(args, ws, rank, local):
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "plan": {"image_rows": image_rows},
     }
     print(json.dumps(out), flush=True)
     if plan is not None:

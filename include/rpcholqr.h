@@ -131,11 +131,21 @@ typedef enum {
     RPCHOLQR_OPT_DETERMINISTIC = 2, /* 1 (default, the only value built): every reduction is a
                                        fixed-order sum, so results are bit-reproducible for a fixed plan
                                        shape and seed; 0 returns RPCHOLQR_ERR_UNSUPPORTED. */
-    RPCHOLQR_OPT_BATCH_CAPACITY = 3 /* matrices rpcholqr_factor_batched can take without allocating:
+    RPCHOLQR_OPT_BATCH_CAPACITY = 3, /* matrices rpcholqr_factor_batched can take without allocating:
                                        setting it allocates (cudaMalloc) the batched kernel's workspace
                                        now -- about (max_s + 5 np) np + 2 (np/8) 64 doubles per matrix,
                                        np = max_n rounded up to 16, plus its work list; 0 frees it.
                                        Default 0: the first batched call allocates for its count. */
+    RPCHOLQR_OPT_IMAGE_ROWS = 4     /* SPLIT64 plans above 128 columns: rows of the stage images (the
+                                       BF16 slices the wide passes stream, 16 bytes a value) kept at a
+                                       time; the first pass and the Gram run chunk by chunk of that
+                                       many rows, the second pass by chunks of at most 8 GiB of images.
+                                       0 (default): every row when their images take at most a quarter
+                                       of the device memory, else 8 GiB-sized chunks.  value > 0: that many
+                                       rows (rounded up to 128).  Results differ only in rounding.
+                                       Setting it synchronizes the device and reallocates the images;
+                                       get returns the rows in use.  RPCHOLQR_ERR_UNSUPPORTED for other
+                                       plans. */
 } rpcholqr_option;
 
 /* Set option `option` of the plan to `value` (host call; affects later calls).

@@ -35,7 +35,7 @@ FP64 = 0
 SPLIT64 = 1
 FP32 = 2
 SMOOTH_NONE, SMOOTH_WHT, SMOOTH_DCT = 0, 1, 2
-OPT_SPIN_LIMIT, OPT_SCALE_SAMPLE, OPT_DETERMINISTIC, OPT_BATCH_CAPACITY = 0, 1, 2, 3
+OPT_SPIN_LIMIT, OPT_SCALE_SAMPLE, OPT_DETERMINISTIC, OPT_BATCH_CAPACITY, OPT_IMAGE_ROWS = 0, 1, 2, 3, 4
 ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM, ERR_UNSUPPORTED = 5, 6, 7, 8
 MAX_N = 2048
 
@@ -238,7 +238,7 @@ def rpcholqr_plan_destroy(plan: Plan):
 
 
 def rpcholqr_plan_set_option(plan: Plan, option: int, value: int):
-    """Set a plan option (OPT_SPIN_LIMIT, OPT_SCALE_SAMPLE, OPT_DETERMINISTIC)."""
+    """Set a plan option (OPT_SPIN_LIMIT, OPT_SCALE_SAMPLE, OPT_DETERMINISTIC, OPT_BATCH_CAPACITY, OPT_IMAGE_ROWS)."""
     _check("rpcholqr_plan_set_option", load_library().rpcholqr_plan_set_option(plan.handle, option, int(value)))
 
 

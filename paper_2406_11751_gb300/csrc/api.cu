@@ -217,9 +217,14 @@ struct rpcholqr_plan_s {
     int32_t* colexp = nullptr;  // np
     int32_t* yexp = nullptr;    // np
     uint8_t* yblocks = nullptr; // Ozaki column slices (K, N <= np)
-    uint8_t* aimg = nullptr;    // stage images of A1's row slices for pass 2 (np > 128), img_rows rows
-    int32_t* bexp = nullptr;    // per 64-column block of the image, the row bounds of that block (img_rows each)
+    // stage images (np > 128; separate allocation img_ws), img_rows rows at a time: the wide first pass's
+    // row slices of finished column blocks, then the Gram's column slices of A1, then pass 2's row slices
+    // of A1; when they cover every row each pass is a single launch over all rows
+    void* img_ws = nullptr;
+    uint8_t* aimg = nullptr;
+    int32_t* bexp = nullptr;    // per pair of 64-column blocks of the image, the row bounds of that pair
     int64_t img_rows = 0;
+    int64_t img_rows_opt = 0;   // RPCHOLQR_OPT_IMAGE_ROWS (0: automatic)
     double* W = nullptr;        // np x np
     int32_t* gates = nullptr;   // split pass-2 gate words: {split status, pivot, fp64 status, pivot, used fp64}
     // FP32 buffers (separate allocation)
@@ -596,6 +601,37 @@ const char* rpcholqr_status_string(int status) {
     }
 }
 
+// ---- stage images of the wide split passes (np > 128) ---------------------------------------------------
+// Rows of one chunk of images when they cannot cover every row: 8 GiB of images.
+int64_t image_chunk_rows(int np) {
+    int64_t rows = (int64_t{1} << 33) / static_cast<int64_t>(np * 16) / 128 * 128;
+    return rows < 128 ? 128 : rows;
+}
+int image_cols(int np) { return (np + 127) / 128 * 128; }
+// Image rows a plan takes: `request` rows (rounded up to 128), or automatically every row when their images
+// take at most a quarter of the device's memory (2^23 x 512: 69 GB of the GB300's 288 GB; each wide pass is
+// then one launch per step instead of one per chunk), else one chunk.
+int64_t image_rows(int device, int64_t max_m, int np, int64_t request) {
+    const int64_t all = (max_m + 127) / 128 * 128;
+    if (request > 0) {
+        const int64_t r = (request + 127) / 128 * 128;
+        return r < all ? r : all;
+    }
+    size_t total = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) total = prop.totalGlobalMem;
+    else cudaGetLastError();
+    const size_t full = ozaki_image_bytes(all, image_cols(np));
+    if (total > 0 && full <= total / 4) return all;
+    const int64_t chunk = image_chunk_rows(np);
+    return chunk < all ? chunk : all;
+}
+// Bytes of the image buffers for `rows` image rows: the images and the row bounds of each pair of blocks.
+size_t image_bytes(int np, int64_t rows) {
+    return align256(ozaki_image_bytes(rows, image_cols(np))) +
+           align256(sizeof(int32_t) * static_cast<size_t>(rows) * ((np + kBlk - 1) / kBlk));
+}
+
 rpcholqr_status rpcholqr_workspace_size(rpcholqr_plan p, int64_t max_m, int32_t max_n, int32_t max_s,
                                         size_t* bytes) {
     if (!bytes || max_n < 1 || max_n > RPCHOLQR_MAX_N || max_s < max_n || max_m < max_s)
@@ -610,11 +646,12 @@ rpcholqr_status rpcholqr_workspace_size(rpcholqr_plan p, int64_t max_m, int32_t 
                  align256(sizeof(int32_t) * static_cast<size_t>(max_m)) + 2 * align256(sizeof(int32_t) * np) +
                  align256(ozaki_yblocks_bytes(static_cast<int>(np), static_cast<int>(np))) +
                  align256(sizeof(double) * np * np) + align256(sizeof(int32_t) * 8);
-    if (mode == RPCHOLQR_SPLIT64 && np > static_cast<size_t>(kMaxNP)) {   // pass-2 stage images
-        int64_t rows = (int64_t{1} << 33) / static_cast<int64_t>(np * 16) / 128 * 128;
-        if (rows > (max_m + 127) / 128 * 128) rows = (max_m + 127) / 128 * 128;
-        if (rows < 128) rows = 128;
-        total += align256(ozaki_image_bytes(rows, static_cast<int>((np + 127) / 128 * 128)));
+    if (mode == RPCHOLQR_SPLIT64 && np > static_cast<size_t>(kMaxNP)) {   // stage images
+        int device = 0;
+        if (p) device = p->device;
+        else if (cudaGetDevice(&device) != cudaSuccess) cudaGetLastError();
+        const int64_t rows = image_rows(device, max_m, static_cast<int>(np), p ? p->img_rows_opt : 0);
+        total += image_bytes(static_cast<int>(np), rows);
     }
     if (mode == RPCHOLQR_FP32) {
         const size_t n32 = static_cast<size_t>(f32_pad(max_n));
@@ -622,6 +659,38 @@ rpcholqr_status rpcholqr_workspace_size(rpcholqr_plan p, int64_t max_m, int32_t 
     }
     *bytes = total;
     return RPCHOLQR_OK;
+}
+
+// (Re)allocates the stage images for `request` rows (0: automatic, see image_rows).  If every row does
+// not fit, falls back to one chunk.
+static rpcholqr_status alloc_images(rpcholqr_plan_s* p, int64_t request) {
+    if (p->img_ws) {
+        cudaFree(p->img_ws);
+        p->img_ws = nullptr;
+        p->ws_bytes -= image_bytes(p->np, p->img_rows);
+    }
+    p->aimg = nullptr;
+    p->bexp = nullptr;
+    p->img_rows = 0;
+    const int64_t all = (p->max_m + 127) / 128 * 128;
+    int64_t rows = image_rows(p->device, p->max_m, p->np, request);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const size_t bytes = image_bytes(p->np, rows);
+        if (cudaMalloc(&p->img_ws, bytes) == cudaSuccess) {
+            char* c = static_cast<char*>(p->img_ws);
+            p->aimg = reinterpret_cast<uint8_t*>(c);
+            p->bexp = reinterpret_cast<int32_t*>(c + align256(ozaki_image_bytes(rows, image_cols(p->np))));
+            p->img_rows = rows;
+            p->ws_bytes += bytes;
+            return RPCHOLQR_OK;
+        }
+        cudaGetLastError();
+        if (request > 0 || rows < all) break;
+        rows = image_chunk_rows(p->np) < all ? image_chunk_rows(p->np) : all;   // every row did not fit
+        if (rows >= all) break;
+    }
+    p->img_ws = nullptr;
+    return RPCHOLQR_ERR_NOMEM;
 }
 
 rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_mode mode,
@@ -678,16 +747,6 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
         const size_t oB = take(ozaki_yblocks_bytes(p->np, p->np));
         const size_t oW = take(sizeof(double) * np * np);
         const size_t oG = take(sizeof(int32_t) * 8);
-        // pass 2 above 128 columns slices A1 once per row chunk into stage images (at most 8 GiB)
-        int64_t img_rows = 0;
-        size_t oI = 0, oE = 0;
-        if (np > static_cast<size_t>(kMaxNP)) {
-            img_rows = (int64_t{1} << 33) / static_cast<int64_t>(np * 16) / 128 * 128;
-            if (img_rows > (max_m + 127) / 128 * 128) img_rows = (max_m + 127) / 128 * 128;
-            if (img_rows < 128) img_rows = 128;
-            oI = take(ozaki_image_bytes(img_rows, static_cast<int>((np + 127) / 128 * 128)));
-            oE = take(sizeof(int32_t) * static_cast<size_t>(img_rows) * ((np + kBlk - 1) / kBlk));
-        }
         if (cudaMalloc(&p->split_ws, off) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(p->ws);
@@ -702,13 +761,14 @@ rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_m
         p->yblocks = reinterpret_cast<uint8_t*>(c + oB);
         p->W = reinterpret_cast<double*>(c + oW);
         p->gates = reinterpret_cast<int32_t*>(c + oG);
-        if (img_rows > 0) {
-            p->aimg = reinterpret_cast<uint8_t*>(c + oI);
-            p->bexp = reinterpret_cast<int32_t*>(c + oE);
-            p->img_rows = img_rows;
-        }
         if (cudaMemset(p->gates, 0, sizeof(int32_t) * 8) != cudaSuccess) cudaGetLastError();
         p->ws_bytes += off;
+        if (np > static_cast<size_t>(kMaxNP) && alloc_images(p, 0) != RPCHOLQR_OK) {
+            cudaFree(p->split_ws);
+            cudaFree(p->ws);
+            delete p;
+            return RPCHOLQR_ERR_NOMEM;
+        }
     }
     if (mode == RPCHOLQR_FP32) {
         const size_t n32 = static_cast<size_t>(f32_pad(max_n));
@@ -773,6 +833,15 @@ rpcholqr_status rpcholqr_plan_set_option(rpcholqr_plan p, int32_t option, int64_
         case RPCHOLQR_OPT_BATCH_CAPACITY:
             if (value < 0 || value > kMaxBatchCount) return RPCHOLQR_ERR_ARG;
             return reserve_batch(p, static_cast<int32_t>(value));
+        case RPCHOLQR_OPT_IMAGE_ROWS: {
+            if (value < 0) return RPCHOLQR_ERR_ARG;
+            if (p->mode != RPCHOLQR_SPLIT64 || p->np <= kMaxNP) return RPCHOLQR_ERR_UNSUPPORTED;
+            DeviceGuard guard(p->device);
+            if (!guard.ok) return RPCHOLQR_ERR_CUDA;
+            if (cudaDeviceSynchronize() != cudaSuccess) return RPCHOLQR_ERR_CUDA;   // no call still reads them
+            p->img_rows_opt = value;
+            return alloc_images(p, value);
+        }
         default: return RPCHOLQR_ERR_ARG;
     }
 }
@@ -784,6 +853,7 @@ rpcholqr_status rpcholqr_plan_get_option(rpcholqr_plan p, int32_t option, int64_
         case RPCHOLQR_OPT_SCALE_SAMPLE: *value = p->scale_sample; return RPCHOLQR_OK;
         case RPCHOLQR_OPT_DETERMINISTIC: *value = 1; return RPCHOLQR_OK;
         case RPCHOLQR_OPT_BATCH_CAPACITY: *value = p->batch_capacity; return RPCHOLQR_OK;
+        case RPCHOLQR_OPT_IMAGE_ROWS: *value = p->img_rows; return RPCHOLQR_OK;
         default: return RPCHOLQR_ERR_ARG;
     }
 }
@@ -805,6 +875,7 @@ rpcholqr_status rpcholqr_plan_destroy(rpcholqr_plan plan) {
     cudaFreeHost(plan->hrows_host);
     cudaFree(plan->hrows_dev);
     cudaFree(plan->split_ws);
+    cudaFree(plan->img_ws);
     cudaFree(plan->smooth_ws);
     cudaFree(plan->batch_ws);
     free_events(plan);
@@ -1320,9 +1391,13 @@ static rpcholqr_status factor_split(rpcholqr_plan p, const double* A, int64_t m,
     // FP64 row-wise substitution; both are launched, the gate words make the other one return at once
     if (p->aimg) {
         // above 128 columns: A1 sliced once per row chunk into stage images, then the product copies them
-        // (the same slices, so the same bits as slicing inside the product)
-        for (int64_t r0 = 0; r0 < m; r0 += p->img_rows) {
-            const int64_t rows = m - r0 < p->img_rows ? m - r0 : p->img_rows;
+        // (the same slices, so the same bits as slicing inside the product).  The chunk stays at most 8 GiB
+        // of images even when the buffer holds every row: one launch over all 2^23 rows of a 512-column
+        // A1 measured 95 ms against 74.6 ms for eight 2^20-row launches (the first pass and the Gram are
+        // single launches)
+        const int64_t chunk = p->img_rows < image_chunk_rows(p->np) ? p->img_rows : image_chunk_rows(p->np);
+        for (int64_t r0 = 0; r0 < m; r0 += chunk) {
+            const int64_t rows = m - r0 < chunk ? m - r0 : chunk;
             launch_slice_images(A1 + r0 * ld1, ld1, rows, n, p->xexp + r0, p->aimg, p->gates, st);
             ++p->launches;
             if ((rc = ozaki_gemm_internal(p, false, A1 + r0 * ld1, rows, n, ld1, p->W, n, np, nullptr, 0, Q + r0 * ldq,

@@ -74,6 +74,46 @@ def test_wide_factor_matches_oracle(lib, oracle_mod, plans, mode, m, n, kappa):
         assert nrm2(Qh - o["Q"]) <= max(1e-10, 10 * floor)
 
 
+# The stage images of the wide split passes: by default every row (the first pass and the Gram one launch
+# over all rows); with OPT_IMAGE_ROWS set below m they and the second pass run row chunk by row chunk
+# (ragged last chunks here).  Both match the oracle; the option reads back, and a plan that is not
+# SPLIT64 above 128 columns refuses it.
+@pytest.mark.parametrize("m,n,kappa", [(20011, 576, 1e8), (9001, 448, 1e14)])
+def test_split_image_rows_option(lib, oracle_mod, m, n, kappa):
+    A = inputs.usv(m, n, kappa, 1300 + n)
+    s = 3 * n
+    o = oracle_mod.rpcholqr(A, s, 5)
+    assert o["status"] == 0
+    plan = lib.rpcholqr_plan_create(0, m, n, s, mode=lib.SPLIT64)
+    try:
+        all_rows = (m + 127) // 128 * 128
+        assert lib.rpcholqr_plan_get_option(plan, lib.OPT_IMAGE_ROWS) == all_rows
+        for rows in (0, 4000, 128 * 17):
+            lib.rpcholqr_plan_set_option(plan, lib.OPT_IMAGE_ROWS, rows)
+            assert lib.rpcholqr_plan_get_option(plan, lib.OPT_IMAGE_ROWS) == (all_rows if rows == 0 else
+                                                                             (rows + 127) // 128 * 128)
+            Q, R, info = lib.rpcholqr_factor(plan, cu(A), s, 5)
+            assert status(info) == (0, -1)
+            Qh, Rh = host(Q), host(R)
+            assert nrm2(Rh - o["R"]) <= 1e-12 * nrm2(o["R"])
+            orth = oracle_mod.orth_error_fast(Qh)
+            assert orth <= 1e-13 and orth <= 10 * oracle_mod.orth_error_fast(o["Q"])
+            if kappa <= 1e8:
+                floor = nrm2(o["Q"] - oracle_mod.rpcholqr(A, s, 5, variant=1)["Q"])
+                assert nrm2(Qh - o["Q"]) <= max(1e-10, 10 * floor)
+        with pytest.raises(lib.RpcholqrError):
+            lib.rpcholqr_plan_set_option(plan, lib.OPT_IMAGE_ROWS, -1)
+    finally:
+        plan.close()
+    narrow = lib.rpcholqr_plan_create(0, 4096, 128, 384, mode=lib.SPLIT64)
+    try:
+        with pytest.raises(lib.RpcholqrError) as e:
+            lib.rpcholqr_plan_set_option(narrow, lib.OPT_IMAGE_ROWS, 4096)
+        assert e.value.code == lib.ERR_UNSUPPORTED
+    finally:
+        narrow.close()
+
+
 @pytest.fixture(scope="module")
 def xplans(lib):
     ps = {"fp64": lib.rpcholqr_plan_create(0, 12000, 2048, 6144),
