@@ -143,9 +143,10 @@ typedef enum {
                                        0 (default): every row when their images take at most a quarter
                                        of the device memory, else 8 GiB-sized chunks.  value > 0: that many
                                        rows (rounded up to 128).  Results differ only in rounding.
-                                       Setting it synchronizes the device and reallocates the images;
-                                       get returns the rows in use.  RPCHOLQR_ERR_UNSUPPORTED for other
-                                       plans. */
+                                       Setting it synchronizes the device and reallocates the images
+                                       (the new buffer before the old one is freed: RPCHOLQR_ERR_NOMEM
+                                       leaves the plan as it was); get returns the rows in use.
+                                       RPCHOLQR_ERR_UNSUPPORTED for other plans. */
 } rpcholqr_option;
 
 /* Set option `option` of the plan to `value` (host call; affects later calls).

@@ -661,36 +661,33 @@ rpcholqr_status rpcholqr_workspace_size(rpcholqr_plan p, int64_t max_m, int32_t 
     return RPCHOLQR_OK;
 }
 
-// (Re)allocates the stage images for `request` rows (0: automatic, see image_rows).  If every row does
-// not fit, falls back to one chunk.
+// (Re)allocates the stage images for `request` rows (0: automatic, see image_rows; if every row does not
+// fit, one chunk).  The new buffer is allocated before the old one is freed: when it cannot be had the
+// plan keeps its images as they were and RPCHOLQR_ERR_NOMEM is returned.
 static rpcholqr_status alloc_images(rpcholqr_plan_s* p, int64_t request) {
-    if (p->img_ws) {
-        cudaFree(p->img_ws);
-        p->img_ws = nullptr;
-        p->ws_bytes -= image_bytes(p->np, p->img_rows);
-    }
-    p->aimg = nullptr;
-    p->bexp = nullptr;
-    p->img_rows = 0;
     const int64_t all = (p->max_m + 127) / 128 * 128;
     int64_t rows = image_rows(p->device, p->max_m, p->np, request);
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        const size_t bytes = image_bytes(p->np, rows);
-        if (cudaMalloc(&p->img_ws, bytes) == cudaSuccess) {
-            char* c = static_cast<char*>(p->img_ws);
-            p->aimg = reinterpret_cast<uint8_t*>(c);
-            p->bexp = reinterpret_cast<int32_t*>(c + align256(ozaki_image_bytes(rows, image_cols(p->np))));
-            p->img_rows = rows;
-            p->ws_bytes += bytes;
-            return RPCHOLQR_OK;
-        }
+    void* buf = nullptr;
+    for (int attempt = 0; attempt < 2 && !buf; ++attempt) {
+        if (cudaMalloc(&buf, image_bytes(p->np, rows)) == cudaSuccess) break;
         cudaGetLastError();
+        buf = nullptr;
         if (request > 0 || rows < all) break;
         rows = image_chunk_rows(p->np) < all ? image_chunk_rows(p->np) : all;   // every row did not fit
         if (rows >= all) break;
     }
-    p->img_ws = nullptr;
-    return RPCHOLQR_ERR_NOMEM;
+    if (!buf) return RPCHOLQR_ERR_NOMEM;
+    if (p->img_ws) {
+        cudaFree(p->img_ws);
+        p->ws_bytes -= image_bytes(p->np, p->img_rows);
+    }
+    p->img_ws = buf;
+    char* c = static_cast<char*>(buf);
+    p->aimg = reinterpret_cast<uint8_t*>(c);
+    p->bexp = reinterpret_cast<int32_t*>(c + align256(ozaki_image_bytes(rows, image_cols(p->np))));
+    p->img_rows = rows;
+    p->ws_bytes += image_bytes(p->np, rows);
+    return RPCHOLQR_OK;
 }
 
 rpcholqr_status rpcholqr_plan_create(rpcholqr_plan* plan, int device, rpcholqr_mode mode,
@@ -839,8 +836,9 @@ rpcholqr_status rpcholqr_plan_set_option(rpcholqr_plan p, int32_t option, int64_
             DeviceGuard guard(p->device);
             if (!guard.ok) return RPCHOLQR_ERR_CUDA;
             if (cudaDeviceSynchronize() != cudaSuccess) return RPCHOLQR_ERR_CUDA;   // no call still reads them
-            p->img_rows_opt = value;
-            return alloc_images(p, value);
+            const rpcholqr_status rc = alloc_images(p, value);
+            if (rc == RPCHOLQR_OK) p->img_rows_opt = value;
+            return rc;
         }
         default: return RPCHOLQR_ERR_ARG;
     }
